@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark: Sylvester-tensor-equation unknowns solved per second, to a true relative residual
+of 1e-10, on GB300.
+
+One step = one complete solve of A*X - X*B = C from X0 = 0 through the C ABI (operator setup
+ts_op_create_dense included), with the inputs resident in HBM.  The default workload is the
+dense 1024 x 1024 x 16 family (A^(1) = tridiag(-1,4,-1) + 0.1 G/sqrt(n), ...; X* ~ U(-1,1),
+C = M(X*)) solved by FP64 tGMRES(30).  Every rank solves its own instance (weak scaling, no
+collective on the data path).
+
+The JSON line also carries: `e2e` (the same metric with host buffers, copies inside the timed
+region), `roofline` for the dominant kernel (the per-slice GEMM, timed by CUDA events inside
+the library over the timed region), `cpu_baseline` (the CPU oracle on this host's cores, on a
+bounded sample), `clocks` sampled during the timed region, `gpu_launches`, and `variants`
+(mixed precision on the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "STE unknowns/s at rel. residual 1e-10: mixed/batched vs FP64 tGMRES, 1 GB300"
+UNIT = "unknowns/s"
+FP64_NOMINAL_TFLOPS = 4 * 152 * 2.070e9 / 1e12   # 4 FP64 FLOP/clk/SM x 152 SMs x 2070 MHz
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="dense_n1024_s1024_p16")
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--variants", default="mixed_fp32", help="comma list of extra precisions to time ('' = none)")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+# ------------------------------------------------------------------------------------------------
+# the CPU oracle on a bounded sample (rank 0, N = 1)
+# ------------------------------------------------------------------------------------------------
+def oracle_apply_sample(wl_cfg, seed, n_applies=2):
+    """Time n_applies oracle applications of M (Definition 2.1 route) at the full workload size."""
+    import numpy as np
+    from paper_2405_09233_gb300 import inputs
+    from oracle import krylov
+    pr = inputs.dense_problem(wl_cfg["n"], wl_cfg["s"], wl_cfg["p"], seed=seed, scale=wl_cfg["scale"])
+    X = pr.Xstar
+    times = []
+    for _ in range(n_applies):
+        t0 = time.perf_counter()
+        Y = krylov.sylv_apply(pr.A, pr.B, X)
+        times.append(time.perf_counter() - t0)
+        X = Y / np.linalg.norm(Y)
+    return min(times)
+
+
+def oracle_applies_needed(wl_cfg, seed):
+    """Operator applications the oracle's own tGMRES needs on the same family at n = s = 128
+    (the spectrum of this family, hence the iteration count, does not depend on n)."""
+    from paper_2405_09233_gb300 import inputs
+    from oracle import krylov
+    pr = inputs.dense_problem(128, 128, wl_cfg["p"], seed=seed, scale=wl_cfg["scale"])
+    C = krylov.sylv_apply(pr.A, pr.B, pr.Xstar)
+    r = krylov.tgmres(pr.A, pr.B, C, m=wl_cfg["restart"], tol=1e-10)
+    return r.iters + r.cycles + 1, r
+
+
+def cpu_baseline(wl_cfg, seed):
+    import numpy as np
+    n, s, p = wl_cfg["n"], wl_cfg["s"], wl_cfg["p"]
+    t_apply = oracle_apply_sample(wl_cfg, seed)
+    applies, r = oracle_applies_needed(wl_cfg, seed)
+    t_solve = t_apply * applies
+    cores = os.cpu_count()
+    return {"value": n * s * p / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle M(X) (bcirc block-row definition, numpy FP64, {cores} host threads) timed at "
+                       f"n={n}, s={s}, p={p}: {t_apply:.2f} s/apply; x {applies} applies (the oracle tGMRES("
+                       f"{wl_cfg['restart']}) iteration count + residuals at n=s=128, same family); "
+                       f"MGS cost (<1%) not included")}
+
+
+# ------------------------------------------------------------------------------------------------
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2405_09233_gb300 import inputs
+    cfg = inputs.WORKLOADS[a.workload]
+    n, s, p = cfg["n"], cfg["s"], cfg["p"]
+    applies, _ = oracle_applies_needed(cfg, 1)
+    for _ in range(a.warmup):
+        oracle_apply_sample(cfg, 1, n_applies=1)
+    ts = []
+    for _ in range(a.steps):
+        ts.append(oracle_apply_sample(cfg, 1, n_applies=1))
+    t_step = statistics.mean(ts)
+    value = n * s * p / (t_step * applies)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_step * applies * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": a.workload, "n": n, "s": s, "p": p,
+                                            "restart": cfg["restart"], "tol": 1e-10},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step = one oracle M(X) at full size ({t_step:.2f} s); "
+                                       f"solve time = step x {applies} applies (oracle tGMRES count at n=s=128)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+    from paper_2405_09233_gb300 import Context, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = inputs.WORKLOADS[a.workload]
+    n, s, p, m = cfg["n"], cfg["s"], cfg["p"], cfg["restart"]
+    seed = 1 + rank
+    pr = inputs.dense_problem(n, s, p, seed=seed, scale=cfg["scale"])
+    A_h = torch.from_numpy(inputs.to_device_layout(pr.A)).pin_memory()
+    B_h = torch.from_numpy(inputs.to_device_layout(pr.B)).pin_memory()
+    Xs_h = torch.from_numpy(inputs.to_device_layout(pr.Xstar)).pin_memory()
+    Ad, Bd, Xs = A_h.to(dev), B_h.to(dev), Xs_h.to(dev)
+    ctx = Context(local)
+    op0 = ctx.op_create_dense(Ad, Bd)
+    Cd = ctx.sylv_apply(op0, Xs)              # manufactured right-hand side C = M(X*)
+    op0.close()
+    X = torch.zeros_like(Cd)
+    torch.cuda.synchronize()
+
+    def step(precision):
+        op = ctx.op_create_dense(Ad, Bd)
+        X.zero_()
+        r = ctx.tgmres_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision,
+                             inner_tol=1e-6 if precision != "fp64" else 0.0)
+        op.close()
+        return r
+
+    for _ in range(a.warmup):
+        r = step(a.precision)
+    assert r.status == 0, r
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    ctx.stats_reset()
+    ctx.stats_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record()
+    results = [step(a.precision) for _ in range(a.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ctx.stats_enable(False)
+    st = ctx.stats_get()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    last = results[-1]
+    assert all(r.status == 0 for r in results), results
+    relres = last.info.relres_true
+    err_xstar = float(torch.max(torch.abs(X - Xs)) / torch.max(torch.abs(Xs)))
+    unknowns = n * s * p
+    value = unknowns * world / (ms / 1e3)
+
+    # dominant kernel: the per-slice GEMM (FP64 pipe bound for the FP64 path)
+    gemm_avg_ms = st.gemm_ms / max(st.gemm_launches, 1)
+    flops_per_launch = st.gemm_flops / max(st.gemm_launches, 1)
+    achieved_tflops = flops_per_launch / (gemm_avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tflops / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "k_gemm_slices<double> (FP64 DFMA, 3-multiply complex)",
+                "note": ("FP64 on CUDA cores; peak = 4 FLOP/clk/SM x 152 SMs x 2070 MHz (nominal). Algorithmic "
+                         "FLOPs count 8 per complex multiply-add; the kernel performs 6 (Gauss), so frac can "
+                         "exceed 0.75 of the FP64 pipe's own rate. GEMM share of the step: "
+                         f"{st.gemm_ms / (ms * a.steps):.3f}")}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    C_h = Cd.cpu().pin_memory()
+    X_h = torch.zeros_like(C_h).pin_memory()
+    e2e_times = []
+    for _ in range(a.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op = ctx.op_create_dense(A_h, B_h)
+        X_h.zero_()
+        r = ctx.tgmres_solve(op, C_h, X_h, restart=m, tol=1e-10, precision=a.precision)
+        op.close()
+        e2e_times.append(time.perf_counter() - t0)
+        assert r.status == 0, r
+    e2e = {"value": unknowns * world / statistics.median(e2e_times), "unit": UNIT,
+           "h2d_bytes_per_step": 8 * (n * n * p + s * s * p + 2 * n * s * p),
+           "d2h_bytes_per_step": 8 * n * s * p}
+
+    variants = {}
+    for prec in [v for v in a.variants.split(",") if v and v != a.precision]:
+        try:
+            step(prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rv = step(prec)
+            e1.record()
+            torch.cuda.synchronize()
+            tv = e0.elapsed_time(e1)
+            variants[prec] = {"value": unknowns * world / (tv / 1e3), "ms_per_step": tv,
+                              "status": rv.status_name, "relres_true": rv.info.relres_true,
+                              "outer": rv.info.outer, "inner_iters": rv.info.iters,
+                              "applies_fp64": rv.info.applies_fp64, "applies_low": rv.info.applies_low,
+                              "err_vs_xstar": float(torch.max(torch.abs(X - Xs)) / torch.max(torch.abs(Xs)))}
+        except Exception as e:  # report, do not hide
+            variants[prec] = {"error": str(e)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(cfg, seed)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": a.workload, "n": n, "s": s, "p": p, "restart": m, "tol": 1e-10,
+                           "precision": a.precision, "method": "tGMRES", "l2": "inputs larger than L2 "
+                           "(A-hat 151 MB, Krylov basis 4.2 GB at n=s=1024, p=16)",
+                           "iters": last.info.iters, "cycles": last.info.cycles,
+                           "applies_fp64": last.info.applies_fp64, "relres_true": relres,
+                           "err_vs_xstar": err_xstar},
+                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": int(st.launches), "variants": variants}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * tstar.h -- C ABI of libtstar: tensor Krylov solvers for the Sylvester tensor
+ * equation  M(X) = A*X - X*B = C  under the Kilmer-Martin T-product
+ * (Bouyghf, El Guide, El Ichi, "Tensor Krylov subspace methods via the
+ * T-product for large Sylvester tensor equations", arXiv:2405.09233).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout.  A third-order tensor X in R^{n1 x n2 x p} is stored column-major,
+ *   X(i, j, k) at X[i + n1*(j + n2*k)]: frontal slice k is a contiguous
+ *   column-major n1 x n2 matrix (the MATLAB layout the paper uses, §2).
+ *   In PyTorch this is a contiguous tensor of shape (p, n2, n1).
+ * Memory.  Unless stated otherwise a tensor pointer may be device memory or
+ *   host memory (pageable or pinned); the library detects which with
+ *   cudaPointerGetAttributes and stages host data through its own device
+ *   workspace.  The caller owns every pointer it passes; the library never
+ *   frees caller memory.  Pointers must stay valid until the call returns.
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   ts_tstar and ts_sylv_apply with device pointers are asynchronous on that
+ *   stream; every other call returns after its work on the stream completed.
+ * Errors.  Every call returns a ts_status; nothing throws, exits or aborts.
+ *   ts_last_error(ctx) describes the last failure on that context.
+ * Threads.  A ts_ctx (and the ts_op objects made from it) must be used by one
+ *   host thread at a time.
+ */
+#ifndef TSTAR_H
+#define TSTAR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ts_stream; /* identical to cudaStream_t */
+
+typedef enum {
+  TS_OK = 0,
+  TS_BREAKDOWN = 1,      /* Krylov breakdown and the true residual still misses tol; X = best iterate */
+  TS_NOT_CONVERGED = 2,  /* iteration budget exhausted; X = last iterate */
+  TS_SINGULAR = 3,       /* a small projected system was singular */
+  TS_ERR_ARG = -1,       /* invalid argument (sizes, null pointers, tolerances) */
+  TS_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+  TS_ERR_NOMEM = -3,     /* device or host allocation failed */
+  TS_ERR_NONFINITE = -4, /* NaN/Inf met in a residual or norm */
+  TS_ERR_TIMEOUT = -5,   /* a bounded device-side wait expired */
+  TS_ERR_UNSUPPORTED = -6
+} ts_status;
+
+typedef enum {
+  TS_FP64 = 0,        /* every step in FP64 */
+  TS_MIXED_FP32 = 1,  /* FP64 refinement around an FP32 inner tGMRES (FP32 CUDA-core GEMMs) */
+  TS_MIXED_TF32 = 2,  /* inner GEMMs on tcgen05 tensor cores, TF32 inputs, FP32 accumulation */
+  TS_MIXED_BF16 = 3   /* inner GEMMs on tcgen05 tensor cores, BF16 inputs, FP32 accumulation */
+} ts_precision;
+
+typedef struct ts_ctx ts_ctx; /* device, workspace, scratch, error text */
+typedef struct ts_op ts_op;   /* a prepared operator M: Fourier slices of A and B */
+
+/* Create a context on CUDA device `device`.  Allocates nothing on the device
+ * until first use.  Returns TS_ERR_CUDA if the device cannot be selected. */
+ts_status ts_create(ts_ctx** ctx, int device);
+/* Free the context and all of its workspace.  NULL is ignored. */
+void ts_destroy(ts_ctx* ctx);
+/* Text of the last error on ctx ("" if none).  Valid until the next call on ctx. */
+const char* ts_last_error(const ts_ctx* ctx);
+/* Static name of a status code. */
+const char* ts_status_string(ts_status s);
+
+/* T-product C = A*B (Definition 2.1), evaluated through the block
+ * diagonalisation of Eq. (5) as Algorithm 1 does: a real DFT along mode 3
+ * that keeps the floor(p/2)+1 non-redundant Fourier slices (the Nyquist slice
+ * is computed, not mirrored), one complex matrix product per slice, and the
+ * inverse DFT.  A is n1 x n2 x p, B is n2 x m x p, C is n1 x m x p (FP64).
+ * n1, n2, m, p >= 1.  C must not alias A or B. */
+ts_status ts_tstar(ts_ctx* ctx, const double* A, int n1, int n2, const double* B, int m, int p,
+                   double* C, ts_stream stream);
+
+/* Prepare the operator M(X) = A*X - X*B of Eq. (2) from dense A (n x n x p)
+ * and B (s x s x p): computes and keeps the Fourier slices A_k, B_k for
+ * k = 0..floor(p/2) (FP64; lower-precision copies are made on first use by a
+ * mixed-precision solve).  `flags` is reserved (pass 0).  *op is owned by the
+ * caller and freed with ts_op_destroy before ts_destroy(ctx). */
+ts_status ts_op_create_dense(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p,
+                             unsigned flags, ts_op** op, ts_stream stream);
+/* Free an operator.  NULL is ignored. */
+void ts_op_destroy(ts_op* op);
+/* Sizes of a prepared operator (any output pointer may be NULL). */
+ts_status ts_op_shape(const ts_op* op, int* n, int* s, int* p);
+
+/* Y = M(X) = A*X - X*B (Eq. (2)) for X, Y of size n x s x p (FP64).  Y must
+ * not alias X.  Asynchronous when X and Y are device pointers. */
+ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, ts_stream stream);
+
+typedef struct {
+  int restart;           /* m, the Krylov dimension per cycle (Algorithm 3), 1..256 */
+  int max_restarts;      /* Iter_max (Algorithm 3): cycles allowed (per inner solve when mixed) */
+  double tol;            /* stop when ||C - M(X)||_F <= tol * ||C||_F (true residual) */
+  int precision;         /* ts_precision */
+  double inner_tol;      /* mixed precision: relative tolerance of each inner solve (0 = 1e-4) */
+  int max_outer;         /* mixed precision: refinement steps allowed (0 = 50) */
+  double* history;       /* optional host array: residual estimate after every inner step */
+  int history_cap;       /* capacity of history (entries); extra entries are dropped */
+  double* true_history;  /* optional host array: true residual norm at every restart / outer step */
+  int true_history_cap;
+} ts_solve_opts;
+
+typedef struct {
+  int iters;             /* inner Krylov steps taken (all cycles, all outer steps) */
+  int cycles;            /* restart cycles run */
+  int outer;             /* refinement steps (mixed precision), else 0 */
+  int history_len;       /* entries the solver produced for history (may exceed history_cap) */
+  int true_history_len;
+  int applies_fp64;      /* FP64 operator applications */
+  int applies_low;       /* low-precision operator applications */
+  double normC;          /* ||C||_F */
+  double relres_true;    /* final ||C - M(X)||_F / ||C||_F, computed in FP64 */
+  double relres_est;     /* last residual estimate / ||C||_F */
+  double ms_total;       /* wall time of the call on the stream (CUDA events), ms */
+} ts_solve_info;
+
+/* Fill opts with defaults: restart 20, max_restarts 200, tol 1e-10, FP64. */
+void ts_solve_opts_default(ts_solve_opts* opts);
+
+/* Restarted tGMRES(m) (§3.3, Algorithm 3 with the minimum-residual small
+ * problem of Proposition 3.4, solved by Givens rotations).  C: right-hand
+ * side, X: initial guess on entry, solution on return (both n x s x p, FP64).
+ * info may be NULL.  Returns TS_OK when the true relative residual is
+ * <= opts->tol, TS_NOT_CONVERGED / TS_BREAKDOWN otherwise (X holds the last
+ * iterate).  With opts->precision != TS_FP64 the FP64 tGMRES becomes the outer
+ * iterative refinement X += d, d from an inner low-precision tGMRES on
+ * M(d) = C - M(X). */
+ts_status ts_tgmres_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X,
+                          const ts_solve_opts* opts, ts_solve_info* info, ts_stream stream);
+
+/* Restarted tFOM(m) (§3.2, Algorithm 3 with the Galerkin small problem
+ * H_m y = ||R0|| e1 and the estimate of Proposition 3.3).  Arguments and
+ * results as ts_tgmres_solve; FP64 only (TS_ERR_UNSUPPORTED otherwise). */
+ts_status ts_tfom_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X,
+                        const ts_solve_opts* opts, ts_solve_info* info, ts_stream stream);
+
+/* Kernel statistics, for measurement.  Launch counts are process-wide (every libtstar kernel
+ * launch on any context); kernel timings are per context and only collected while enabled,
+ * by CUDA events recorded on the launching stream around each timed launch. */
+typedef struct {
+  long long launches;      /* libtstar kernels launched since the last ts_stats_reset */
+  long long gemm_launches; /* per-Fourier-slice GEMM launches timed while enabled */
+  double gemm_ms;          /* their summed event durations */
+  double gemm_flops;       /* their algorithmic FLOPs: 8 per complex and 2 per real multiply-add */
+  long long fft_launches;  /* forward and inverse DFT launches timed while enabled */
+  double fft_ms;
+  double fft_bytes;        /* their algorithmic HBM bytes (input read + output written once) */
+} ts_stats;
+
+/* Enable (1) or disable (0) per-kernel event timing on ctx. */
+ts_status ts_stats_enable(ts_ctx* ctx, int enable);
+/* Read the statistics (synchronises the recorded events). */
+ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out);
+/* Zero the statistics and the process-wide launch counter. */
+ts_status ts_stats_reset(ts_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSTAR_H */

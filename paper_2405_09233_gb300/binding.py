@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libtstar (include/tstar.h): argument marshalling only.
+
+Tensors are passed as torch tensors in the library's layout: a tensor
+X in R^{n1 x n2 x p} is a contiguous float64 torch tensor of shape (p, n2, n1)
+(column-major X(i, j, k) at i + n1*(j + n2*k)).  CUDA tensors are passed by
+device pointer on the current torch stream; CPU tensors by host pointer (the
+library stages them).  Every computation runs inside libtstar; there is no
+Python or CPU fallback, and a missing library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtstar.so")
+
+TS_OK, TS_BREAKDOWN, TS_NOT_CONVERGED, TS_SINGULAR = 0, 1, 2, 3
+TS_ERR_ARG, TS_ERR_CUDA, TS_ERR_NOMEM, TS_ERR_NONFINITE, TS_ERR_TIMEOUT, TS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+PRECISIONS = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
+STATUS_NAMES = {0: "ok", 1: "breakdown", 2: "not_converged", 3: "singular", -1: "err_arg", -2: "err_cuda",
+                -3: "err_nomem", -4: "err_nonfinite", -5: "err_timeout", -6: "err_unsupported"}
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_restarts", ctypes.c_int), ("tol", ctypes.c_double),
+                ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int),
+                ("true_history", ctypes.POINTER(ctypes.c_double)), ("true_history_cap", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("outer", ctypes.c_int),
+                ("history_len", ctypes.c_int), ("true_history_len", ctypes.c_int),
+                ("applies_fp64", ctypes.c_int), ("applies_low", ctypes.c_int),
+                ("normC", ctypes.c_double), ("relres_true", ctypes.c_double), ("relres_est", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("gemm_launches", ctypes.c_longlong), ("gemm_ms", ctypes.c_double),
+                ("gemm_flops", ctypes.c_double), ("fft_launches", ctypes.c_longlong), ("fft_ms", ctypes.c_double),
+                ("fft_bytes", ctypes.c_double)]
+
+
+class TstarError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_vp, _i, _u, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double
+_SIGNATURES = {
+    "ts_create": (_i, [ctypes.POINTER(_vp), _i]),
+    "ts_destroy": (None, [_vp]),
+    "ts_last_error": (ctypes.c_char_p, [_vp]),
+    "ts_status_string": (ctypes.c_char_p, [_i]),
+    "ts_tstar": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _vp, _vp]),
+    "ts_op_create_dense": (_i, [_vp, _vp, _i, _vp, _i, _i, _u, ctypes.POINTER(_vp), _vp]),
+    "ts_op_destroy": (None, [_vp]),
+    "ts_op_shape": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "ts_sylv_apply": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "ts_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+    "ts_tgmres_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
+    "ts_tfom_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
+    "ts_stats_enable": (_i, [_vp, _i]),
+    "ts_stats_get": (_i, [_vp, ctypes.POINTER(Stats)]),
+    "ts_stats_reset": (_i, [_vp]),
+}
+
+
+def lib():
+    """Load libtstar.so (built in-tree by paper_2405_09233_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> int:
+    import torch
+    assert isinstance(t, torch.Tensor), "expected a torch tensor"
+    assert t.dtype == torch.float64, "expected float64"
+    assert t.is_contiguous(), "expected a contiguous tensor in (p, n2, n1) layout"
+    return t.data_ptr()
+
+
+def _stream(*tensors):
+    import torch
+    if any(t.is_cuda for t in tensors):
+        return ctypes.c_void_p(torch.cuda.current_stream(tensors[0].device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+class Context:
+    """A libtstar context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = _vp()
+        st = lib().ts_create(ctypes.byref(self._h), device)
+        if st != TS_OK:
+            raise TstarError(st, "ts_create failed")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().ts_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st < 0:
+            raise TstarError(st, f"{what}: {lib().ts_last_error(self._h).decode()}")
+        return st
+
+    # --- statistics ---------------------------------------------------------------------------
+    def stats_enable(self, enable: bool = True):
+        self._check(lib().ts_stats_enable(self._h, int(enable)), "ts_stats_enable")
+
+    def stats_get(self) -> Stats:
+        s = Stats()
+        self._check(lib().ts_stats_get(self._h, ctypes.byref(s)), "ts_stats_get")
+        return s
+
+    def stats_reset(self):
+        self._check(lib().ts_stats_reset(self._h), "ts_stats_reset")
+
+    # --- entry points -------------------------------------------------------------------------
+    def tstar(self, A, B, C=None):
+        """C = A * B (T-product).  A: (p, n2, n1), B: (p, m, n2) float64 torch tensors."""
+        import torch
+        p, n2, n1 = A.shape
+        pB, m, n2b = B.shape
+        assert p == pB and n2 == n2b
+        if C is None:
+            C = torch.empty((p, m, n1), dtype=torch.float64, device=A.device)
+        self._check(lib().ts_tstar(self._h, _ptr(A), n1, n2, _ptr(B), m, p, _ptr(C), _stream(A, B, C)), "ts_tstar")
+        return C
+
+    def op_create_dense(self, A, B) -> "Operator":
+        p, n, n_ = A.shape
+        pB, s, s_ = B.shape
+        assert n == n_ and s == s_ and p == pB
+        h = _vp()
+        self._check(lib().ts_op_create_dense(self._h, _ptr(A), n, _ptr(B), s, p, 0, ctypes.byref(h),
+                                             _stream(A, B)), "ts_op_create_dense")
+        return Operator(self, h, n, s, p)
+
+    def sylv_apply(self, op: "Operator", X, Y=None):
+        import torch
+        if Y is None:
+            Y = torch.empty_like(X)
+        self._check(lib().ts_sylv_apply(self._h, op._h, _ptr(X), _ptr(Y), _stream(X, Y)), "ts_sylv_apply")
+        return Y
+
+    def _solve(self, fn, name, op, C, X, restart, tol, max_restarts, precision, inner_tol, max_outer,
+               history_cap):
+        opts = SolveOpts()
+        lib().ts_solve_opts_default(ctypes.byref(opts))
+        opts.restart, opts.tol, opts.max_restarts = restart, tol, max_restarts
+        opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        opts.inner_tol, opts.max_outer = inner_tol, max_outer
+        hist = np.zeros(history_cap)
+        thist = np.zeros(history_cap)
+        opts.history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        opts.history_cap = history_cap
+        opts.true_history = thist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        opts.true_history_cap = history_cap
+        info = SolveInfo()
+        st = self._check(fn(self._h, op._h, _ptr(C), _ptr(X), ctypes.byref(opts), ctypes.byref(info),
+                            _stream(C, X)), name)
+        return SolveResult(st, info, hist[:min(info.history_len, history_cap)].copy(),
+                           thist[:min(info.true_history_len, history_cap)].copy())
+
+    def tgmres_solve(self, op, C, X, restart=20, tol=1e-10, max_restarts=200, precision="fp64",
+                     inner_tol=0.0, max_outer=0, history_cap=4096):
+        """Restarted tGMRES(m); X holds X0 on entry and the solution on return."""
+        return self._solve(lib().ts_tgmres_solve, "ts_tgmres_solve", op, C, X, restart, tol, max_restarts,
+                           precision, inner_tol, max_outer, history_cap)
+
+    def tfom_solve(self, op, C, X, restart=20, tol=1e-10, max_restarts=200, history_cap=4096):
+        """Restarted tFOM(m) (FP64)."""
+        return self._solve(lib().ts_tfom_solve, "ts_tfom_solve", op, C, X, restart, tol, max_restarts,
+                           "fp64", 0.0, 0, history_cap)
+
+
+class Operator:
+    """A prepared operator M(X) = A*X - X*B (owns the Fourier slices of A and B on the device)."""
+
+    def __init__(self, ctx: Context, h, n: int, s: int, p: int):
+        self.ctx, self._h, self.n, self.s, self.p = ctx, h, n, s, p
+
+    def close(self):
+        if self._h:
+            lib().ts_op_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SolveResult:
+    def __init__(self, status: int, info: SolveInfo, history: np.ndarray, true_history: np.ndarray):
+        self.status = status
+        self.status_name = STATUS_NAMES.get(status, str(status))
+        self.info = info
+        self.history = history
+        self.true_history = true_history
+
+    @property
+    def relres(self) -> float:
+        return self.info.relres_true
+
+    def __repr__(self):
+        i = self.info
+        return (f"SolveResult({self.status_name}, iters={i.iters}, cycles={i.cycles}, outer={i.outer}, "
+                f"relres={i.relres_true:.3e}, fp64_applies={i.applies_fp64}, low_applies={i.applies_low}, "
+                f"ms={i.ms_total:.2f})")
+
+
+def declared_symbols(header: Optional[str] = None):
+    """Names of the functions include/tstar.h declares (for the ABI completeness test)."""
+    import re
+    header = header or os.path.join(_PKG, "..", "include", "tstar.h")
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ts_[a-z0-9_]+)\s*\(", text)))

@@ -1,0 +1,384 @@
+// Context, workspace, operator setup and the operator-level entry points of libtstar:
+// ts_tstar (Definition 2.1 via Algorithm 1) and ts_sylv_apply (Eq. (2)).
+#include <cstring>
+#include <cstdio>
+#include "internal.cuh"
+#include "apply.cuh"
+
+namespace ts {
+
+void* Workspace::get(const std::string& name, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  Buf& b = bufs[name];
+  if (b.bytes < bytes) {
+    if (b.ptr) TS_CUDA(cudaFree(b.ptr));
+    b.ptr = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.ptr, bytes);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      throw Error{TS_ERR_NOMEM, "workspace '" + name + "': cudaMalloc(" + std::to_string(bytes) +
+                                    ") failed: " + cudaGetErrorString(e)};
+    }
+    b.bytes = bytes;
+  }
+  return b.ptr;
+}
+
+void Workspace::release_all() {
+  for (auto& kv : bufs)
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+  bufs.clear();
+}
+
+std::atomic<long long> g_launches{0};
+
+void KernelTimer::begin(cudaStream_t st, int kind, double work) {
+  if (!enabled) return;
+  if (pool.empty()) {
+    cudaEvent_t a, b;
+    TS_CUDA(cudaEventCreate(&a));
+    TS_CUDA(cudaEventCreate(&b));
+    pool.push_back({a, b});
+  }
+  auto ev = pool.back();
+  pool.pop_back();
+  TS_CUDA(cudaEventRecord(ev.first, st));
+  done.push_back(TimedRegion{ev.first, ev.second, kind, work});
+}
+
+void KernelTimer::end(cudaStream_t st) {
+  if (!enabled || done.empty()) return;
+  TS_CUDA(cudaEventRecord(done.back().b, st));
+  if (done.size() >= 256) collect();
+}
+
+void KernelTimer::collect() {
+  for (auto& r : done) {
+    TS_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    TS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    if (r.kind == 0) {
+      ++gemm_launches;
+      gemm_ms += ms;
+      gemm_flops += r.work;
+    } else {
+      ++fft_launches;
+      fft_ms += ms;
+      fft_bytes += r.work;
+    }
+    pool.push_back({r.a, r.b});
+  }
+  done.clear();
+}
+
+void KernelTimer::reset() {
+  collect();
+  gemm_launches = fft_launches = 0;
+  gemm_ms = gemm_flops = fft_ms = fft_bytes = 0;
+}
+
+void KernelTimer::destroy() {
+  for (auto& r : done) pool.push_back({r.a, r.b});
+  done.clear();
+  for (auto& e : pool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  pool.clear();
+}
+
+double gemm_flops(int M, int N, int L1, int L2, int K, int nyq) {
+  const int nreal = 1 + (nyq >= 0 ? 1 : 0);
+  const double per = (double)M * N * ((double)L1 + L2);
+  return per * (8.0 * (K - nreal) + 2.0 * nreal);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+StagedIn::StagedIn(ts_ctx* ctx, const std::string& name, const double* p, size_t count, cudaStream_t st) {
+  if (is_device_ptr(p)) {
+    dev = p;
+  } else {
+    double* d = static_cast<double*>(ctx->ws.get(name, count * sizeof(double)));
+    TS_CUDA(cudaMemcpyAsync(d, p, count * sizeof(double), cudaMemcpyHostToDevice, st));
+    dev = d;
+    staged = true;
+  }
+}
+
+StagedOut::StagedOut(ts_ctx* ctx, const std::string& name, double* p, size_t count, bool copy_in,
+                     cudaStream_t st)
+    : host(p), count(count), stream(st) {
+  if (is_device_ptr(p)) {
+    dev = p;
+  } else {
+    dev = static_cast<double*>(ctx->ws.get(name, count * sizeof(double)));
+    if (copy_in) TS_CUDA(cudaMemcpyAsync(dev, p, count * sizeof(double), cudaMemcpyHostToDevice, st));
+    staged = true;
+  }
+}
+
+void StagedOut::finish() {
+  if (staged) {
+    TS_CUDA(cudaMemcpyAsync(host, dev, count * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    TS_CUDA(cudaStreamSynchronize(stream));
+  }
+}
+
+// Forward DFT of the operator tensors once (§8 setup: A_k, B_k for k <= p/2).
+static void op_prepare(ts_op* op, const double* A, const double* B, cudaStream_t st) {
+  const int n = op->n, s = op->s, p = op->p, K = op->K;
+  TS_CUDA(cudaMalloc(&op->Ah, sizeof(double2) * (size_t)K * n * n));
+  TS_CUDA(cudaMalloc(&op->Bh, sizeof(double2) * (size_t)K * s * s));
+  StagedIn a(op->ctx, "stage_A", A, (size_t)n * n * p, st);
+  StagedIn b(op->ctx, "stage_B", B, (size_t)s * s * p, st);
+  rfft_tube<double, double2>(a.dev, op->Ah, (long long)n * n, p, st);
+  rfft_tube<double, double2>(b.dev, op->Bh, (long long)s * s, p, st);
+  TS_CUDA(cudaStreamSynchronize(st));  // the staging buffers may be reused right after
+}
+
+void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
+               double* partials, cudaStream_t st) {
+  const int n = op->n, s = op->s, p = op->p, K = op->K;
+  const long long T = (long long)n * s;
+  double2* Xh = static_cast<double2*>(ctx->ws.get("apply_Xh", sizeof(double2) * (size_t)K * T));
+  double2* Yh = static_cast<double2*>(ctx->ws.get("apply_Yh", sizeof(double2) * (size_t)K * T));
+  KernelTimer& tm = ctx->timer;
+  tm.begin(st, 1, 8.0 * T * p + 16.0 * K * T);
+  rfft_tube<double, double2>(X, Xh, T, p, st);
+  tm.end(st);
+  ZGemmArgs g{};
+  g.A1 = op->Ah; g.sA1 = (long long)n * n; g.lda1 = n;
+  g.B1 = Xh;     g.sB1 = T;                g.ldb1 = n; g.L1 = n;
+  g.A2 = Xh;     g.sA2 = T;                g.lda2 = n;
+  g.B2 = op->Bh; g.sB2 = (long long)s * s; g.ldb2 = s; g.L2 = s;
+  g.Y = Yh; g.sY = T; g.ldy = n;
+  g.M = n; g.N = s; g.K = K; g.nyq = nyquist_index(p); g.sgn2 = -1.0;
+  tm.begin(st, 0, gemm_flops(n, s, n, s, K, g.nyq));
+  zgemm_slices_f64(g, st);
+  tm.end(st);
+  tm.begin(st, 1, 16.0 * K * T + 8.0 * T * p * (mode == IRFFT_RESIDUAL ? 2 : 1));
+  irfft_tube<double, double2>(Yh, Y, T, p, mode, C, partials, st);
+  tm.end(st);
+}
+
+}  // namespace ts
+
+using namespace ts;
+
+#define TS_API_BEGIN try {
+#define TS_API_END(ctxp)                              \
+  }                                                   \
+  catch (const ts::Error& e) {                        \
+    if (ctxp) (ctxp)->err = e.msg;                    \
+    return e.status;                                  \
+  }                                                   \
+  catch (const std::bad_alloc&) {                     \
+    if (ctxp) (ctxp)->err = "host allocation failed"; \
+    return TS_ERR_NOMEM;                              \
+  }                                                   \
+  catch (...) {                                       \
+    if (ctxp) (ctxp)->err = "unknown error";          \
+    return TS_ERR_CUDA;                               \
+  }
+
+extern "C" {
+
+const char* ts_status_string(ts_status s) {
+  switch (s) {
+    case TS_OK: return "TS_OK";
+    case TS_BREAKDOWN: return "TS_BREAKDOWN";
+    case TS_NOT_CONVERGED: return "TS_NOT_CONVERGED";
+    case TS_SINGULAR: return "TS_SINGULAR";
+    case TS_ERR_ARG: return "TS_ERR_ARG";
+    case TS_ERR_CUDA: return "TS_ERR_CUDA";
+    case TS_ERR_NOMEM: return "TS_ERR_NOMEM";
+    case TS_ERR_NONFINITE: return "TS_ERR_NONFINITE";
+    case TS_ERR_TIMEOUT: return "TS_ERR_TIMEOUT";
+    case TS_ERR_UNSUPPORTED: return "TS_ERR_UNSUPPORTED";
+  }
+  return "TS_UNKNOWN";
+}
+
+ts_status ts_create(ts_ctx** out, int device) {
+  if (!out) return TS_ERR_ARG;
+  *out = nullptr;
+  ts_ctx* ctx = nullptr;
+  try {
+    ctx = new ts_ctx();
+    ctx->device = device;
+    TS_CUDA(cudaSetDevice(device));
+    TS_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+    TS_CUDA(cudaMallocHost(&ctx->host_scalars, 256 * sizeof(double)));
+    TS_CUDA(cudaEventCreate(&ctx->ev0));
+    TS_CUDA(cudaEventCreate(&ctx->ev1));
+    *out = ctx;
+    return TS_OK;
+  } catch (const ts::Error& e) {
+    if (ctx) {
+      if (ctx->host_scalars) cudaFreeHost(ctx->host_scalars);
+      delete ctx;
+    }
+    return e.status;
+  } catch (...) {
+    delete ctx;
+    return TS_ERR_NOMEM;
+  }
+}
+
+void ts_destroy(ts_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  ctx->ws.release_all();
+  ctx->timer.destroy();
+  if (ctx->host_scalars) cudaFreeHost(ctx->host_scalars);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+}
+
+const char* ts_last_error(const ts_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+ts_status ts_tstar(ts_ctx* ctx, const double* A, int n1, int n2, const double* B, int m, int p, double* C,
+                   ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  TS_REQUIRE(A && B && C, "ts_tstar: null pointer");
+  TS_REQUIRE(n1 >= 1 && n2 >= 1 && m >= 1 && p >= 1, "ts_tstar: sizes must be >= 1");
+  TS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int K = num_slices(p);
+  StagedIn a(ctx, "tstar_inA", A, (size_t)n1 * n2 * p, st);
+  StagedIn b(ctx, "tstar_inB", B, (size_t)n2 * m * p, st);
+  StagedOut c(ctx, "tstar_outC", C, (size_t)n1 * m * p, false, st);
+  double2* Ah = static_cast<double2*>(ctx->ws.get("tstar_Ah", sizeof(double2) * (size_t)K * n1 * n2));
+  double2* Bh = static_cast<double2*>(ctx->ws.get("tstar_Bh", sizeof(double2) * (size_t)K * n2 * m));
+  double2* Ch = static_cast<double2*>(ctx->ws.get("tstar_Ch", sizeof(double2) * (size_t)K * n1 * m));
+  rfft_tube<double, double2>(a.dev, Ah, (long long)n1 * n2, p, st);
+  rfft_tube<double, double2>(b.dev, Bh, (long long)n2 * m, p, st);
+  ZGemmArgs g{};
+  g.A1 = Ah; g.sA1 = (long long)n1 * n2; g.lda1 = n1;
+  g.B1 = Bh; g.sB1 = (long long)n2 * m;  g.ldb1 = n2; g.L1 = n2;
+  g.L2 = 0;
+  g.Y = Ch; g.sY = (long long)n1 * m; g.ldy = n1;
+  g.M = n1; g.N = m; g.K = K; g.nyq = nyquist_index(p); g.sgn2 = 0.0;
+  zgemm_slices_f64(g, st);
+  irfft_tube<double, double2>(Ch, c.dev, (long long)n1 * m, p, IRFFT_STORE, nullptr, nullptr, st);
+  c.finish();
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
+ts_status ts_op_create_dense(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p, unsigned flags,
+                             ts_op** out, ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  ts_op* op = nullptr;
+  TS_API_BEGIN
+  TS_REQUIRE(out, "ts_op_create_dense: null output");
+  *out = nullptr;
+  TS_REQUIRE(A && B, "ts_op_create_dense: null pointer");
+  TS_REQUIRE(n >= 1 && s >= 1 && p >= 1, "ts_op_create_dense: sizes must be >= 1");
+  TS_REQUIRE(flags == 0, "ts_op_create_dense: flags must be 0");
+  TS_CUDA(cudaSetDevice(ctx->device));
+  op = new ts_op();
+  op->ctx = ctx;
+  op->n = n;
+  op->s = s;
+  op->p = p;
+  op->K = num_slices(p);
+  op_prepare(op, A, B, reinterpret_cast<cudaStream_t>(stream));
+  *out = op;
+  return TS_OK;
+  }
+  catch (const ts::Error& e) {
+    ctx->err = e.msg;
+    ts_op_destroy(op);
+    return e.status;
+  }
+  catch (...) {
+    ctx->err = "unknown error";
+    ts_op_destroy(op);
+    return TS_ERR_NOMEM;
+  }
+}
+
+void ts_op_destroy(ts_op* op) {
+  if (!op) return;
+  if (op->ctx) cudaSetDevice(op->ctx->device);
+  cudaFree(op->Ah);
+  cudaFree(op->Bh);
+  cudaFree(op->Ah32);
+  cudaFree(op->Bh32);
+  cudaFree(op->tc_A);
+  cudaFree(op->tc_B);
+  delete op;
+}
+
+ts_status ts_op_shape(const ts_op* op, int* n, int* s, int* p) {
+  if (!op) return TS_ERR_ARG;
+  if (n) *n = op->n;
+  if (s) *s = op->s;
+  if (p) *p = op->p;
+  return TS_OK;
+}
+
+ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  TS_REQUIRE(op && X && Y, "ts_sylv_apply: null pointer");
+  TS_REQUIRE(X != Y, "ts_sylv_apply: Y must not alias X");
+  TS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t N = (size_t)op->n * op->s * op->p;
+  StagedIn x(ctx, "apply_inX", X, N, st);
+  StagedOut y(ctx, "apply_outY", Y, N, false, st);
+  apply_f64(ctx, op, x.dev, y.dev, IRFFT_STORE, nullptr, nullptr, st);
+  y.finish();
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
+ts_status ts_stats_enable(ts_ctx* ctx, int enable) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  if (!enable) ctx->timer.collect();
+  ctx->timer.enabled = enable != 0;
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
+ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out) {
+  if (!ctx || !out) return TS_ERR_ARG;
+  TS_API_BEGIN
+  ctx->timer.collect();
+  const KernelTimer& t = ctx->timer;
+  out->launches = g_launches.load();
+  out->gemm_launches = t.gemm_launches;
+  out->gemm_ms = t.gemm_ms;
+  out->gemm_flops = t.gemm_flops;
+  out->fft_launches = t.fft_launches;
+  out->fft_ms = t.fft_ms;
+  out->fft_bytes = t.fft_bytes;
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
+ts_status ts_stats_reset(ts_ctx* ctx) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  ctx->timer.reset();
+  g_launches.store(0);
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
+}  // extern "C"

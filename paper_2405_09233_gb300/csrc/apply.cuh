@@ -1,0 +1,38 @@
+// Host-side helpers shared by the entry points: host/device staging and the operator pipeline.
+#pragma once
+#include "internal.cuh"
+
+namespace ts {
+
+// A read-only tensor argument: used in place when it is device memory, else copied into a
+// named workspace buffer on `st`.
+struct StagedIn {
+  const double* dev = nullptr;
+  bool staged = false;
+  StagedIn(ts_ctx* ctx, const std::string& name, const double* p, size_t count, cudaStream_t st);
+};
+
+// An output (or in/out) tensor argument: written in place when it is device memory, else through
+// a workspace buffer that finish() copies back (and synchronises).
+struct StagedOut {
+  double* dev = nullptr;
+  double* host = nullptr;
+  size_t count = 0;
+  bool staged = false;
+  cudaStream_t stream = nullptr;
+  StagedOut(ts_ctx* ctx, const std::string& name, double* p, size_t count, bool copy_in, cudaStream_t st);
+  void finish();
+};
+
+// Y = M(X) in FP64 (rfft -> fused per-slice GEMMs -> irfft).  mode IRFFT_RESIDUAL writes
+// Y = C - M(X) and the kRedBlocks partial sums of Y^2 to `partials`.
+void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
+               double* partials, cudaStream_t st);
+
+// Algorithmic FLOPs of one fused slice-GEMM launch (8 per complex, 2 per real multiply-add).
+double gemm_flops(int M, int N, int L1, int L2, int K, int nyq);
+
+// Low-precision apply used by the inner solve of mixed precision: X, Y FP32.
+void apply_low(ts_ctx* ctx, ts_op* op, int precision, const float* X, float* Y, cudaStream_t st);
+
+}  // namespace ts

@@ -1,0 +1,169 @@
+// Internal declarations of libtstar (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <atomic>
+#include <map>
+#include <vector>
+#include "../../include/tstar.h"
+
+namespace ts {
+
+// ----------------------------------------------------------------------------------------------
+// Errors
+// ----------------------------------------------------------------------------------------------
+struct Error {
+  ts_status status;
+  std::string msg;
+};
+
+#define TS_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw ::ts::Error{TS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define TS_REQUIRE(cond, msg)                                   \
+  do {                                                          \
+    if (!(cond)) throw ::ts::Error{TS_ERR_ARG, std::string(msg)}; \
+  } while (0)
+
+// ----------------------------------------------------------------------------------------------
+// Device workspace: named buffers that grow on demand and live as long as the context.
+// ----------------------------------------------------------------------------------------------
+struct Workspace {
+  struct Buf { void* ptr = nullptr; size_t bytes = 0; };
+  std::map<std::string, Buf> bufs;
+  void* get(const std::string& name, size_t bytes);
+  void release_all();
+};
+
+// ----------------------------------------------------------------------------------------------
+// Reductions: a fixed grid so that the summation order (hence the result) is reproducible.
+// ----------------------------------------------------------------------------------------------
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs
+constexpr int kRedThreads = 256;
+
+// Process-wide count of kernel launches (reported by ts_stats_get).
+extern std::atomic<long long> g_launches;
+inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Event timing of selected kernels while a context has statistics enabled.
+struct TimedRegion {
+  cudaEvent_t a, b;
+  int kind;        // 0 = GEMM, 1 = FFT
+  double work;     // algorithmic FLOPs (GEMM) or bytes (FFT)
+};
+struct KernelTimer {
+  bool enabled = false;
+  std::vector<TimedRegion> done;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+  long long gemm_launches = 0, fft_launches = 0;
+  double gemm_ms = 0, gemm_flops = 0, fft_ms = 0, fft_bytes = 0;
+  void begin(cudaStream_t st, int kind, double work);
+  void end(cudaStream_t st);
+  void collect();  // synchronise the recorded events and accumulate
+  void reset();
+  void destroy();
+};
+
+}  // namespace ts
+
+struct ts_ctx {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  ts::Workspace ws;
+  double* host_scalars = nullptr;  // pinned, 256 doubles, for small device->host reads
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ts::KernelTimer timer;
+};
+
+struct ts_op {
+  ts_ctx* ctx = nullptr;
+  int n = 0, s = 0, p = 0, K = 0;
+  double2* Ah = nullptr;   // K slices, column-major n x n complex (FP64)
+  double2* Bh = nullptr;   // K slices, column-major s x s complex (FP64)
+  float2* Ah32 = nullptr;  // FP32 copies, made on first mixed-precision use
+  float2* Bh32 = nullptr;
+  void* tc_A = nullptr;    // tensor-core operand copies (precision-specific), made on first use
+  void* tc_B = nullptr;
+  int tc_prec = -1;
+};
+
+namespace ts {
+
+inline int nyquist_index(int p) { return (p % 2 == 0 && p > 1) ? p / 2 : -1; }
+inline int num_slices(int p) { return p / 2 + 1; }
+
+// Memory-kind helpers (host or device pointer).
+bool is_device_ptr(const void* p);
+
+// ---------------- FFT along mode 3 (fft_tube.cu) ----------------
+// Forward: out[k*T + e] = sum_{t<p} in[t*T + e] exp(-2 pi i k t / p), k < K = p/2+1.
+template <typename Real, typename Cplx>
+void rfft_tube(const Real* in, Cplx* out, long long T, int p, cudaStream_t st);
+// Inverse: out[t*T + e] = (1/p) sum over the full Hermitian spectrum; mode selects the epilogue.
+enum IrfftMode { IRFFT_STORE = 0, IRFFT_RESIDUAL = 1 };
+// IRFFT_STORE: out = y.  IRFFT_RESIDUAL: out = C - y and partials[b] = block sums of out^2.
+template <typename Real, typename Cplx>
+void irfft_tube(const Cplx* in, Real* out, long long T, int p, int mode, const Real* C,
+                double* partials, cudaStream_t st);
+
+// ---------------- per-slice complex GEMM on CUDA cores, FP64 / FP32 (gemm_simt.cu) ----------------
+// Y_k = A1_k B1_k + sgn2 * A2_k B2_k for k < K (phase 2 skipped when L2 == 0);
+// slices k == 0 and k == nyq are treated as real (imaginary parts ignored, result imag = 0).
+template <typename Cplx>
+struct GemmArgs {
+  const Cplx* A1; long long sA1; int lda1;
+  const Cplx* B1; long long sB1; int ldb1; int L1;
+  const Cplx* A2; long long sA2; int lda2;
+  const Cplx* B2; long long sB2; int ldb2; int L2;
+  Cplx* Y; long long sY; int ldy;
+  int M, N, K, nyq;
+  double sgn2;
+};
+using ZGemmArgs = GemmArgs<double2>;
+using CGemmArgs = GemmArgs<float2>;
+void zgemm_slices_f64(const ZGemmArgs& a, cudaStream_t st);
+void cgemm_slices_f32(const CGemmArgs& a, cudaStream_t st);
+
+// ---------------- vector kernels (vec.cu) ----------------
+// All reductions write kRedBlocks partial sums; consumers finalise them in a fixed order.
+template <typename T> void dot_partials(const T* x, const T* y, long long N, double* partials, cudaStream_t st);
+// W -= h * Vi with h = finalize(Pin) (stored to *h_out by block 0); Pout = partials of <Vnext, W>
+// (or of <W, W> when Vnext == nullptr).
+template <typename T> void mgs_pass(T* W, const T* Vi, const T* Vnext, long long N, const double* Pin,
+                                    double* h_out, double* Pout, cudaStream_t st);
+// y = x * (*scale)
+template <typename T, typename U> void scale_dev(const T* x, U* y, long long N, const double* scale, cudaStream_t st);
+// X += sum_{i<k} y[i] * V[i*ldv ...]
+template <typename T, typename U> void multi_axpy(U* X, const T* V, long long ldv, long long N, const double* y, int k,
+                                                  double alpha_scale, const double* alpha_dev, cudaStream_t st);
+// out = sqrt(finalize(P)) to a device scalar; also writes 1/out to out[1].
+void finalize_norm(const double* P, double* out, cudaStream_t st);
+// a = b - c (elementwise)
+template <typename T> void sub3(const T* b, const T* c, T* a, long long N, cudaStream_t st);
+// convert
+template <typename T, typename U> void convert(const T* x, U* y, long long N, cudaStream_t st);
+void fill_zero(void* p, size_t bytes, cudaStream_t st);
+
+// ---------------- small FP64 Hessenberg kernels (small.cu) ----------------
+struct KrylovState;  // device-resident, see small.cu
+size_t krylov_state_bytes(int m);
+void ks_init(void* state, int m, const double* beta_and_inv, cudaStream_t st);
+// GMRES (method 0) / FOM (method 1) step j: consumes column j of H (rows 0..j written by MGS) and
+// ||W|| from Pnorm partials; writes the estimate and 1/h_{j+1,j} into the state.
+void ks_step(void* state, int m, int j, int method, const double* Pnorm, cudaStream_t st);
+// Solve for y over the first k columns; result in the state's y array.
+void ks_solve(void* state, int m, int k, int method, cudaStream_t st);
+// Device addresses inside the state block.
+double* ks_H(void* state, int m);          // column-major (m+1) x m, H[i + (m+1)*j]
+double* ks_y(void* state, int m);
+double* ks_est(void* state, int m);        // [0] = estimate, [1] = 1/h_{j+1,j}, [2] = h_{j+1,j}, [3] = flags
+double* ks_beta(void* state, int m);       // [0] = beta, [1] = 1/beta
+
+}  // namespace ts

@@ -1,0 +1,246 @@
+// Restarted tGMRES(m) and tFOM(m) (Algorithm 3), and their mixed-precision form.
+//
+// One cycle:  R = C - M(X) (FP64, fused into the inverse FFT with the norm partials),
+//             V_1 = R / ||R||, then for j = 1..m: W = M(V_j); MGS against V_1..V_j
+//             (Algorithm 2); h_{j+1,j} = ||W||; Givens (tGMRES) or Hessenberg LU (tFOM) on the
+//             device gives the residual estimate; stop early when it reaches the tolerance;
+//             V_{j+1} = W / h_{j+1,j}.  Then y, X += V_k (*) y, and the true residual.
+// The host reads 4 doubles per inner step (estimate, 1/h, h, flags) to decide whether to stop.
+//
+// Mixed precision: the Arnoldi cycle (basis, W, operator) runs in FP32 storage with a FP32 or
+// tensor-core operator, while R = C - M(X), the small problem, and X += ||R|| (V (*) y) stay in
+// FP64.  Every cycle is thus one step of iterative refinement with an inner tGMRES whose own
+// stopping tolerance is inner_tol relative to ||R||; only the residual needs an FP64 apply.
+#include <cmath>
+#include <vector>
+#include "internal.cuh"
+#include "apply.cuh"
+
+namespace ts {
+
+namespace {
+
+struct Result {
+  ts_status status = TS_NOT_CONVERGED;
+};
+
+template <typename T>
+T* basis_ptr(T* V, long long N, int i) {
+  return V + (long long)i * N;
+}
+
+void apply_basis(ts_ctx* ctx, ts_op* op, int prec, const double* x, double* y, cudaStream_t st) {
+  (void)prec;
+  apply_f64(ctx, op, x, y, IRFFT_STORE, nullptr, nullptr, st);
+}
+void apply_basis(ts_ctx* ctx, ts_op* op, int prec, const float* x, float* y, cudaStream_t st) {
+  apply_low(ctx, op, prec, x, y, st);
+}
+
+template <typename T>
+ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const ts_solve_opts& o,
+                       ts_solve_info& info, cudaStream_t st, int method, int prec) {
+  const long long N = (long long)op->n * op->s * op->p;
+  const int m = o.restart;
+  const bool mixed = prec != TS_FP64;
+  const int max_cycles = mixed ? (o.max_outer > 0 ? o.max_outer : 50) : o.max_restarts;
+  const double inner_tol = mixed ? (o.inner_tol > 0 ? o.inner_tol : 1e-4) : 0.0;
+
+  T* V = static_cast<T*>(ctx->ws.get("krylov_V", sizeof(T) * (size_t)(m + 1) * N));
+  T* W = static_cast<T*>(ctx->ws.get("krylov_W", sizeof(T) * (size_t)N));
+  double* R = static_cast<double*>(ctx->ws.get("krylov_R", sizeof(double) * (size_t)N));
+  double* P = static_cast<double*>(ctx->ws.get("krylov_P", sizeof(double) * 3 * kRedBlocks));
+  double* Pp[2] = {P, P + kRedBlocks};
+  double* P2 = P + 2 * kRedBlocks;
+  double* sc = static_cast<double*>(ctx->ws.get("krylov_scalars", sizeof(double) * 64));
+  void* state = ctx->ws.get("krylov_state", krylov_state_bytes(m));
+  double* hs = ctx->host_scalars;
+
+  int hist_len = 0, true_len = 0;
+  auto push_hist = [&](double v) {
+    if (o.history && hist_len < o.history_cap) o.history[hist_len] = v;
+    ++hist_len;
+  };
+  auto push_true = [&](double v) {
+    if (o.true_history && true_len < o.true_history_cap) o.true_history[true_len] = v;
+    ++true_len;
+  };
+
+  // ||C|| and the initial residual R = C - M(X0) (Algorithm 3, step 3).
+  dot_partials<double>(C, C, N, P2, st);
+  finalize_norm(P2, sc + 0, st);
+  apply_f64(ctx, op, X, R, IRFFT_RESIDUAL, C, P2, st);
+  finalize_norm(P2, sc + 2, st);
+  TS_CUDA(cudaMemcpyAsync(hs, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  const double normC = hs[0];
+  double res = hs[2];
+  info.normC = normC;
+  info.applies_fp64 = 1;
+  push_true(res);
+  ts_status status = TS_NOT_CONVERGED;
+  double last_est = res;
+
+  auto finish = [&](ts_status s) {
+    info.history_len = hist_len;
+    info.true_history_len = true_len;
+    info.relres_true = normC > 0 ? res / normC : res;
+    info.relres_est = normC > 0 ? last_est / normC : last_est;
+    return s;
+  };
+
+  if (!std::isfinite(res) || !std::isfinite(normC)) return finish(TS_ERR_NONFINITE);
+  if (normC == 0.0) {
+    // C = 0: the solution is X = 0 (M is invertible under Theorem 2.1's condition).
+    fill_zero(X, sizeof(double) * (size_t)N, st);
+    res = 0.0;
+    return finish(TS_OK);
+  }
+  if (res <= o.tol * normC) return finish(TS_OK);
+
+  for (int cycle = 0; cycle < max_cycles; ++cycle) {
+    ks_init(state, m, sc + 2, st);
+    scale_dev<double, T>(R, basis_ptr(V, N, 0), N, sc + 3, st);  // V_1 = R / ||R||
+    int k = 0;
+    double flags = 0.0;
+    for (int j = 0; j < m; ++j) {
+      apply_basis(ctx, op, prec, basis_ptr(V, N, j), W, st);        // W = M(V_j)
+      if (mixed) ++info.applies_low; else ++info.applies_fp64;
+      dot_partials<T>(basis_ptr(V, N, 0), W, N, Pp[0], st);
+      for (int i = 0; i <= j; ++i) {                                  // MGS sweep, fused with the next dot
+        const T* Vn = i < j ? basis_ptr(V, N, i + 1) : nullptr;
+        mgs_pass<T>(W, basis_ptr(V, N, i), Vn, N, Pp[i & 1], ks_H(state, m) + i + (size_t)(m + 1) * j,
+                    Pp[(i + 1) & 1], st);
+      }
+      ks_step(state, m, j, method, Pp[(j + 1) & 1], st);
+      TS_CUDA(cudaMemcpyAsync(hs + 8, ks_est(state, m), 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      TS_CUDA(cudaStreamSynchronize(st));
+      const double est = hs[8];
+      flags = hs[11];
+      k = j + 1;
+      ++info.iters;
+      last_est = est;
+      push_hist(est);
+      const bool broke = ((int)flags & 1) != 0;
+      const bool bad = ((int)flags & 6) != 0;
+      if (bad || broke || est <= o.tol * normC || (mixed && est <= inner_tol * res)) break;
+      scale_dev<T, T>(W, basis_ptr(V, N, j + 1), N, ks_est(state, m) + 1, st);  // V_{j+1} = W / h
+    }
+    ++info.cycles;
+    if ((int)flags & 2) {
+      status = TS_SINGULAR;
+      break;
+    }
+    if ((int)flags & 4) {
+      status = TS_ERR_NONFINITE;
+      break;
+    }
+    ks_solve(state, m, k, method, st);
+    multi_axpy<T, double>(X, V, N, N, ks_y(state, m), k, 1.0, nullptr, st);   // X = X0 + V_k (*) y
+    apply_f64(ctx, op, X, R, IRFFT_RESIDUAL, C, P2, st);                     // true residual
+    ++info.applies_fp64;
+    finalize_norm(P2, sc + 2, st);
+    TS_CUDA(cudaMemcpyAsync(hs, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TS_CUDA(cudaStreamSynchronize(st));
+    res = hs[2];
+    push_true(res);
+    if (!std::isfinite(res)) {
+      status = TS_ERR_NONFINITE;
+      break;
+    }
+    if (res <= o.tol * normC) {
+      status = TS_OK;
+      break;
+    }
+    if (((int)flags & 1) && !mixed) {
+      status = TS_BREAKDOWN;
+      break;
+    }
+  }
+  if (mixed) info.outer = info.cycles;
+  return finish(status);
+}
+
+ts_status solve_entry(ts_ctx* ctx, const ts_op* cop, const double* C, double* X, const ts_solve_opts* opts,
+                      ts_solve_info* info_out, ts_stream stream, int method) {
+  ts_op* op = const_cast<ts_op*>(cop);  // lower-precision operator copies are cached on first use
+  TS_REQUIRE(op && C && X && opts, "solve: null pointer");
+  const ts_solve_opts& o = *opts;
+  TS_REQUIRE(o.restart >= 1 && o.restart <= 256, "solve: restart must be in 1..256");
+  TS_REQUIRE(o.max_restarts >= 1, "solve: max_restarts must be >= 1");
+  TS_REQUIRE(o.tol > 0.0 && std::isfinite(o.tol), "solve: tol must be positive");
+  TS_REQUIRE(o.precision >= TS_FP64 && o.precision <= TS_MIXED_BF16, "solve: unknown precision");
+  TS_REQUIRE(!(o.history && o.history_cap < 0) && !(o.true_history && o.true_history_cap < 0),
+             "solve: negative history capacity");
+  if (method == 1 && o.precision != TS_FP64)
+    throw Error{TS_ERR_UNSUPPORTED, "tFOM runs in FP64 only"};
+  TS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ts_solve_info info{};
+  TS_CUDA(cudaEventRecord(ctx->ev0, st));
+  const size_t N = (size_t)op->n * op->s * op->p;
+  StagedIn c(ctx, "solve_inC", C, N, st);
+  StagedOut x(ctx, "solve_ioX", X, N, true, st);
+  ts_status s;
+  if (o.precision == TS_FP64)
+    s = krylov_solve<double>(ctx, op, c.dev, x.dev, o, info, st, method, o.precision);
+  else
+    s = krylov_solve<float>(ctx, op, c.dev, x.dev, o, info, st, method, o.precision);
+  x.finish();
+  TS_CUDA(cudaEventRecord(ctx->ev1, st));
+  TS_CUDA(cudaEventSynchronize(ctx->ev1));
+  float ms = 0.f;
+  TS_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  info.ms_total = ms;
+  if (info_out) *info_out = info;
+  return s;
+}
+
+}  // namespace
+
+}  // namespace ts
+
+using namespace ts;
+
+extern "C" {
+
+void ts_solve_opts_default(ts_solve_opts* o) {
+  if (!o) return;
+  *o = ts_solve_opts{};
+  o->restart = 20;
+  o->max_restarts = 200;
+  o->tol = 1e-10;
+  o->precision = TS_FP64;
+  o->inner_tol = 0.0;
+  o->max_outer = 0;
+}
+
+ts_status ts_tgmres_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X, const ts_solve_opts* opts,
+                          ts_solve_info* info, ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  try {
+    return solve_entry(ctx, op, C, X, opts, info, stream, 0);
+  } catch (const ts::Error& e) {
+    ctx->err = e.msg;
+    return e.status;
+  } catch (...) {
+    ctx->err = "unknown error";
+    return TS_ERR_CUDA;
+  }
+}
+
+ts_status ts_tfom_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X, const ts_solve_opts* opts,
+                        ts_solve_info* info, ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  try {
+    return solve_entry(ctx, op, C, X, opts, info, stream, 1);
+  } catch (const ts::Error& e) {
+    ctx->err = e.msg;
+    return e.status;
+  } catch (...) {
+    ctx->err = "unknown error";
+    return TS_ERR_CUDA;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Streaming kernels of the Arnoldi process (Algorithm 2) and of the solution update: inner
+// products and norms (Definition 2.3), the modified Gram-Schmidt sweep, scaling and the
+// (*) product of §3.1.  All are HBM-bound: grid-stride loops over 16-byte vectors, a fixed grid
+// of kRedBlocks blocks wherever a sum is formed, FP64 accumulation whatever the storage type.
+//
+// Reductions never use atomics: each block writes one partial sum, and whoever needs the total
+// (the next MGS pass, the Givens kernel) adds the kRedBlocks partials in a fixed order.  The
+// results are therefore bitwise reproducible from run to run.
+#include "internal.cuh"
+#include "reduce.cuh"
+
+namespace ts {
+namespace {
+
+template <typename T> struct V2;
+template <> struct V2<double> { using T = double2; };
+template <> struct V2<float> { using T = float2; };
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_dot(const T* __restrict__ x, const T* __restrict__ y,
+                                                     long long N, double* __restrict__ partials) {
+  double acc = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride)
+    acc += (double)x[e] * (double)y[e];
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// One modified Gram-Schmidt step fused with the inner product the next step needs:
+//   h = <V_i, W> (finalised from Pin);  W -= h V_i;  Pout = partials of <V_next, W> or <W, W>.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_mgs(T* __restrict__ W, const T* __restrict__ Vi,
+                                                     const T* __restrict__ Vn, long long N,
+                                                     const double* __restrict__ Pin, double* __restrict__ h_out,
+                                                     double* __restrict__ Pout) {
+  const double h = finalize_partials(Pin);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *h_out = h;
+  const T hT = (T)h;
+  double acc = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const T* __restrict__ other = Vn ? Vn : W;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride) {
+    const T w = W[e] - hT * Vi[e];
+    W[e] = w;
+    acc += (double)(Vn ? other[e] : w) * (double)w;
+  }
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) Pout[blockIdx.x] = tot;
+}
+
+template <typename T, typename U>
+__global__ void k_scale(const T* __restrict__ x, U* __restrict__ y, long long N, const double* __restrict__ s) {
+  const double sc = *s;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride)
+    y[e] = (U)((double)x[e] * sc);
+}
+
+// X += alpha * sum_{i<k} y_i V_i ; alpha = alpha_scale * (*alpha_dev if given).
+template <typename T, typename U>
+__global__ void k_multi_axpy(U* __restrict__ X, const T* __restrict__ V, long long ldv, long long N,
+                             const double* __restrict__ y, int k, double alpha_scale,
+                             const double* __restrict__ alpha_dev) {
+  __shared__ double ys[256];
+  const double alpha = alpha_scale * (alpha_dev ? *alpha_dev : 1.0);
+  for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) ys[i] = y[i] * alpha;
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc = fma(ys[i], (double)V[(long long)i * ldv + e], acc);
+    X[e] = (U)((double)X[e] + acc);
+  }
+}
+
+__global__ void k_finalize_norm(const double* __restrict__ P, double* __restrict__ out) {
+  const double s = finalize_partials(P);
+  if (threadIdx.x == 0) {
+    const double nv = sqrt(s);
+    out[0] = nv;
+    out[1] = nv > 0.0 ? 1.0 / nv : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void k_sub3(const T* __restrict__ b, const T* __restrict__ c, T* __restrict__ a, long long N) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride) a[e] = b[e] - c[e];
+}
+
+template <typename T, typename U>
+__global__ void k_convert(const T* __restrict__ x, U* __restrict__ y, long long N) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride) y[e] = (U)x[e];
+}
+
+int grid_for(long long N) {
+  long long b = (N + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+template <typename T>
+void dot_partials(const T* x, const T* y, long long N, double* partials, cudaStream_t st) {
+  k_dot<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, y, N, partials);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void mgs_pass(T* W, const T* Vi, const T* Vnext, long long N, const double* Pin, double* h_out, double* Pout,
+              cudaStream_t st) {
+  k_mgs<T><<<kRedBlocks, kRedThreads, 0, st>>>(W, Vi, Vnext, N, Pin, h_out, Pout);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+template <typename T, typename U>
+void scale_dev(const T* x, U* y, long long N, const double* scale, cudaStream_t st) {
+  k_scale<T, U><<<grid_for(N), 256, 0, st>>>(x, y, N, scale);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+template <typename T, typename U>
+void multi_axpy(U* X, const T* V, long long ldv, long long N, const double* y, int k, double alpha_scale,
+                const double* alpha_dev, cudaStream_t st) {
+  TS_REQUIRE(k <= 256, "multi_axpy: at most 256 basis vectors");
+  if (k <= 0) return;
+  k_multi_axpy<T, U><<<grid_for(N), 256, 0, st>>>(X, V, ldv, N, y, k, alpha_scale, alpha_dev);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void finalize_norm(const double* P, double* out, cudaStream_t st) {
+  k_finalize_norm<<<1, 256, 0, st>>>(P, out);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void sub3(const T* b, const T* c, T* a, long long N, cudaStream_t st) {
+  k_sub3<T><<<grid_for(N), 256, 0, st>>>(b, c, a, N);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+template <typename T, typename U>
+void convert(const T* x, U* y, long long N, cudaStream_t st) {
+  k_convert<T, U><<<grid_for(N), 256, 0, st>>>(x, y, N);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void fill_zero(void* p, size_t bytes, cudaStream_t st) { TS_CUDA(cudaMemsetAsync(p, 0, bytes, st)); }
+
+template void dot_partials<double>(const double*, const double*, long long, double*, cudaStream_t);
+template void dot_partials<float>(const float*, const float*, long long, double*, cudaStream_t);
+template void mgs_pass<double>(double*, const double*, const double*, long long, const double*, double*, double*,
+                               cudaStream_t);
+template void mgs_pass<float>(float*, const float*, const float*, long long, const double*, double*, double*,
+                              cudaStream_t);
+template void scale_dev<double, double>(const double*, double*, long long, const double*, cudaStream_t);
+template void scale_dev<double, float>(const double*, float*, long long, const double*, cudaStream_t);
+template void scale_dev<float, float>(const float*, float*, long long, const double*, cudaStream_t);
+template void multi_axpy<double, double>(double*, const double*, long long, long long, const double*, int, double,
+                                         const double*, cudaStream_t);
+template void multi_axpy<float, double>(double*, const float*, long long, long long, const double*, int, double,
+                                        const double*, cudaStream_t);
+template void multi_axpy<float, float>(float*, const float*, long long, long long, const double*, int, double,
+                                       const double*, cudaStream_t);
+template void sub3<double>(const double*, const double*, double*, long long, cudaStream_t);
+template void convert<double, float>(const double*, float*, long long, cudaStream_t);
+template void convert<float, double>(const float*, double*, long long, cudaStream_t);
+
+}  // namespace ts
