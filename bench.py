@@ -41,7 +41,8 @@ def args_parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dense_n1024_s1024_p16")
     ap.add_argument("--precision", default="fp64")
-    ap.add_argument("--variants", default="mixed_fp32", help="comma list of extra precisions to time ('' = none)")
+    ap.add_argument("--variants", default="mixed_fp32,mixed_tf32,mixed_bf16",
+                    help="comma list of extra precisions to time ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -216,8 +217,7 @@ def main():
     def step(precision):
         op = ctx.op_create_dense(Ad, Bd)
         X.zero_()
-        r = ctx.tgmres_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision,
-                             inner_tol=1e-6 if precision != "fp64" else 0.0)
+        r = ctx.tgmres_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision)
         op.close()
         return r
 

@@ -90,12 +90,20 @@ ts_status ts_op_shape(const ts_op* op, int* n, int* s, int* p);
  * not alias X.  Asynchronous when X and Y are device pointers. */
 ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, ts_stream stream);
 
+/* Y = M(X) in a lower precision, the operator of the mixed-precision inner solve: X, Y are
+ * FP32 device tensors (n x s x p).  precision TS_MIXED_FP32: FP32 DFT and FP32 CUDA-core slice
+ * GEMMs; TS_MIXED_TF32 / TS_MIXED_BF16: the slice GEMMs run on the tcgen05 tensor cores with
+ * TF32 / BF16 inputs and FP32 accumulation (p <= 32).  The first call with a precision builds
+ * that precision's copy of the operator's Fourier slices.  Asynchronous on `stream`. */
+ts_status ts_sylv_apply_lowp(ts_ctx* ctx, const ts_op* op, int precision, const float* X, float* Y,
+                             ts_stream stream);
+
 typedef struct {
   int restart;           /* m, the Krylov dimension per cycle (Algorithm 3), 1..256 */
   int max_restarts;      /* Iter_max (Algorithm 3): cycles allowed (per inner solve when mixed) */
   double tol;            /* stop when ||C - M(X)||_F <= tol * ||C||_F (true residual) */
   int precision;         /* ts_precision */
-  double inner_tol;      /* mixed precision: relative tolerance of each inner solve (0 = 1e-4) */
+  double inner_tol;      /* mixed precision: relative tolerance of each inner solve (0 = 1e-6 FP32, 1e-3 TF32, 1e-2 BF16) */
   int max_outer;         /* mixed precision: refinement steps allowed (0 = 50) */
   double* history;       /* optional host array: residual estimate after every inner step */
   int history_cap;       /* capacity of history (entries); extra entries are dropped */

@@ -65,6 +65,7 @@ _SIGNATURES = {
     "ts_op_destroy": (None, [_vp]),
     "ts_op_shape": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "ts_sylv_apply": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "ts_sylv_apply_lowp": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "ts_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "ts_tgmres_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
     "ts_tfom_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
@@ -168,6 +169,17 @@ class Context:
         if Y is None:
             Y = torch.empty_like(X)
         self._check(lib().ts_sylv_apply(self._h, op._h, _ptr(X), _ptr(Y), _stream(X, Y)), "ts_sylv_apply")
+        return Y
+
+    def sylv_apply_lowp(self, op: "Operator", X, precision="mixed_bf16", Y=None):
+        """Y = M(X) in low precision; X, Y float32 CUDA tensors of shape (p, s, n)."""
+        import torch
+        assert X.dtype == torch.float32 and X.is_cuda and X.is_contiguous()
+        if Y is None:
+            Y = torch.empty_like(X)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._check(lib().ts_sylv_apply_lowp(self._h, op._h, prec, X.data_ptr(), Y.data_ptr(), _stream(X, Y)),
+                    "ts_sylv_apply_lowp")
         return Y
 
     def _solve(self, fn, name, op, C, X, restart, tol, max_restarts, precision, inner_tol, max_outer,

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include "internal.cuh"
 #include "apply.cuh"
+#include "tc.cuh"
 
 namespace ts {
 
@@ -318,8 +319,10 @@ void ts_op_destroy(ts_op* op) {
   cudaFree(op->Bh);
   cudaFree(op->Ah32);
   cudaFree(op->Bh32);
-  cudaFree(op->tc_A);
-  cudaFree(op->tc_B);
+  if (op->tc) {
+    op->tc->release();
+    delete op->tc;
+  }
   delete op;
 }
 
@@ -343,6 +346,21 @@ ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y
   StagedOut y(ctx, "apply_outY", Y, N, false, st);
   apply_f64(ctx, op, x.dev, y.dev, IRFFT_STORE, nullptr, nullptr, st);
   y.finish();
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
+ts_status ts_sylv_apply_lowp(ts_ctx* ctx, const ts_op* op, int precision, const float* X, float* Y,
+                             ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  TS_REQUIRE(op && X && Y, "ts_sylv_apply_lowp: null pointer");
+  TS_REQUIRE(X != Y, "ts_sylv_apply_lowp: Y must not alias X");
+  TS_REQUIRE(precision == TS_MIXED_FP32 || precision == TS_MIXED_TF32 || precision == TS_MIXED_BF16,
+             "ts_sylv_apply_lowp: precision must be a mixed precision");
+  TS_REQUIRE(is_device_ptr(X) && is_device_ptr(Y), "ts_sylv_apply_lowp: X and Y must be device memory");
+  TS_CUDA(cudaSetDevice(ctx->device));
+  apply_low(ctx, const_cast<ts_op*>(op), precision, X, Y, reinterpret_cast<cudaStream_t>(stream));
   return TS_OK;
   TS_API_END(ctx)
 }

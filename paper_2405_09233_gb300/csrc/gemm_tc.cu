@@ -1,0 +1,576 @@
+// Per-Fourier-slice complex products on the 5th-generation tensor cores (tcgen05), the
+// low-precision operator of the mixed-precision inner solve:
+//     Y_k = A_k X_k - X_k B_k      (Eq. (2) in the Fourier domain, Algorithm 1 step 2)
+// with BF16 or TF32 inputs and FP32 accumulation in tensor memory.
+//
+// Planar complex, four real products per K step into two TMEM accumulators:
+//     Re Y += Ar Xr - Ai Xi,   Im Y += Ai Xr + Ar Xi              (l over n)
+//     Re Y += -Xr Br + Xi Bi,  Im Y += -Xr Bi - Xi Br             (l over s)
+// The minus signs are the instruction descriptor's negate-A bit, so no negated copies exist.
+// Keeping the operands planar (rather than a realified 2n x 2n matrix) halves the bytes of A_k
+// that stream from HBM, which matters because for s ~ 256 the product sits at the HBM/tensor
+// ridge point.
+//
+// Operand layouts (all K-major, i.e. the reduction index l contiguous; rows padded to ld):
+//   A_k planes  [k][i][l]  (row-major A_k, prepared once per operator)
+//   X_k planes  [k][j][l]  (column-major X_k, written by the planar DFT)        -> B operand
+//   X_k planes  [k][i][l]  (row-major X_k, a transposed copy)                    -> A operand
+//   B_k planes  [k][j][l]  (column-major B_k, prepared once per operator)        -> B operand
+//
+// One CTA computes a 128 x BN output tile of one slice.  Warp roles (192 threads):
+//   warps 0-3  epilogue: TMEM -> registers -> Y (float2, column-major), TMEM lanes 32w..32w+31
+//   warp 4     TMA producer: 4 tiles per stage (A re/im, B re/im), 128-byte swizzle
+//   warp 5     TMEM allocator and MMA issuer (one elected lane)
+// Stages are recycled through full/empty mbarriers; tcgen05.commit arrives on "empty" when the
+// MMAs reading a stage have completed.  Every wait is bounded: on expiry the kernel records an
+// error code, skips the rest of its work, still frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include "internal.cuh"
+#include "tc.cuh"
+
+namespace ts {
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kStageBytesMax = 200 * 1024;
+constexpr long long kWaitLimit = 1ll << 26;  // polls (with nanosleep backoff) before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false (and records `code`) when the limit expires.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (i > 64) __nanosleep(128);
+  }
+  atomicCAS(err, 0, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile with 128-byte rows and the 128-byte
+// swizzle TMA applied (8-row atoms of 1024 bytes; stride between atoms 1024 bytes).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);   // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc,
+                                          int kind_tf32) {
+  if (kind_tf32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Instruction descriptor (kind::f16 / kind::tf32): FP32 accumulator, both operands K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int fmt, int M, int N, bool negA) {
+  return (1u << 4)                        // accumulator format: F32
+         | ((uint32_t)fmt << 7)           // A format (1 = BF16, 2 = TF32)
+         | ((uint32_t)fmt << 10)          // B format
+         | ((negA ? 1u : 0u) << 13)       // negate A
+         | ((uint32_t)(N >> 3) << 17)     // N / 8
+         | ((uint32_t)(M >> 4) << 24);    // M / 16
+}
+
+struct TcMaps {
+  CUtensorMap a_re, a_im;      // A_k planes          [K][n][ldn]
+  CUtensorMap xc_re, xc_im;    // X_k column-major    [K][s][ldn]
+  CUtensorMap xr_re, xr_im;    // X_k row-major       [K][n][lds]
+  CUtensorMap b_re, b_im;      // B_k column-major    [K][s][lds]
+};
+
+template <int BN, int ESZ>
+struct TcCfg {
+  static constexpr int kElemsK = 128 / ESZ;                  // K elements per 128-byte row
+  static constexpr int kTileA = kTileM * 128;                // bytes of one A plane tile
+  static constexpr int kTileB = BN * 128;                    // bytes of one B plane tile
+  static constexpr int kStage = 2 * kTileA + 2 * kTileB;
+  static constexpr int kStages = (kStageBytesMax / kStage) > 4 ? 4 : (kStageBytesMax / kStage);
+  static constexpr int kSmem = kStages * kStage + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int kTmemCols = 2 * BN;                   // Re and Im accumulators
+  static constexpr int kSubK = 128 / 32;                     // MMA K steps per stage (32 bytes each)
+};
+
+template <int BN, int ESZ>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_sylv(const __grid_constant__ TcMaps maps, float2* __restrict__ Y, int n, int s, int nyq, int* err) {
+  using Cfg = TcCfg<BN, ESZ>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStage);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * Cfg::kStages + 1);
+  const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + Cfg::kStages);
+  const uint32_t bar_acc = smem_u32(bars + 2 * Cfg::kStages);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = blockIdx.x * BN, i0 = blockIdx.y * kTileM, k = blockIdx.z;
+  const bool real = (k == 0) || (k == nyq);
+  const int it1 = (n + Cfg::kElemsK - 1) / Cfg::kElemsK;      // stages of the A_k X_k product
+  const int it2 = (s + Cfg::kElemsK - 1) / Cfg::kElemsK;      // stages of the X_k B_k product
+  const int iters = it1 + it2;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < Cfg::kStages; ++q) {
+      mbar_init(bar_full + 8 * q, 1);
+      mbar_init(bar_empty + 8 * q, 1);
+    }
+    mbar_init(bar_acc, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      for (int it = 0; it < iters; ++it) {
+        const int slot = it % Cfg::kStages;
+        const uint32_t phase = (uint32_t)(it / Cfg::kStages) & 1u;
+        if (!mbar_wait(bar_empty + 8 * slot, phase ^ 1u, err, 1)) break;
+        const uint32_t full = bar_full + 8 * slot;
+        mbar_expect_tx(full, Cfg::kStage);
+        const uint32_t sA = base + slot * Cfg::kStage;
+        const uint32_t sAi = sA + Cfg::kTileA, sB = sA + 2 * Cfg::kTileA, sBi = sB + Cfg::kTileB;
+        if (it < it1) {
+          const int l0 = it * Cfg::kElemsK;
+          tma_load_3d(sA, &maps.a_re, l0, i0, k, full);
+          tma_load_3d(sAi, &maps.a_im, l0, i0, k, full);
+          tma_load_3d(sB, &maps.xc_re, l0, j0, k, full);
+          tma_load_3d(sBi, &maps.xc_im, l0, j0, k, full);
+        } else {
+          const int l0 = (it - it1) * Cfg::kElemsK;
+          tma_load_3d(sA, &maps.xr_re, l0, i0, k, full);
+          tma_load_3d(sAi, &maps.xr_im, l0, i0, k, full);
+          tma_load_3d(sB, &maps.b_re, l0, j0, k, full);
+          tma_load_3d(sBi, &maps.b_im, l0, j0, k, full);
+        }
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      constexpr int fmt = ESZ == 2 ? 1 : 2;
+      constexpr uint32_t idp = make_idesc(fmt, kTileM, BN, false);
+      constexpr uint32_t idn = make_idesc(fmt, kTileM, BN, true);
+      const uint32_t d_re = tmem, d_im = tmem + BN;
+      bool ok = true;
+      for (int it = 0; it < iters && ok; ++it) {
+        const int slot = it % Cfg::kStages;
+        const uint32_t phase = (uint32_t)(it / Cfg::kStages) & 1u;
+        if (!mbar_wait(bar_full + 8 * slot, phase, err, 2)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sA = base + slot * Cfg::kStage;
+        const uint64_t dAr = smem_desc_sw128(sA), dAi = smem_desc_sw128(sA + Cfg::kTileA);
+        const uint64_t dBr = smem_desc_sw128(sA + 2 * Cfg::kTileA);
+        const uint64_t dBi = smem_desc_sw128(sA + 2 * Cfg::kTileA + Cfg::kTileB);
+#pragma unroll
+        for (int kk = 0; kk < Cfg::kSubK; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 2);   // 32 bytes >> 4
+          const uint32_t first = (it == 0 && kk == 0) ? 0u : 1u;
+          if (it < it1) {
+            mma_issue(d_re, dAr + o, dBr + o, idp, first, ESZ == 4);
+            if (!real) {
+              mma_issue(d_re, dAi + o, dBi + o, idn, 1u, ESZ == 4);
+              mma_issue(d_im, dAi + o, dBr + o, idp, first, ESZ == 4);
+              mma_issue(d_im, dAr + o, dBi + o, idp, 1u, ESZ == 4);
+            }
+          } else {
+            mma_issue(d_re, dAr + o, dBr + o, idn, 1u, ESZ == 4);
+            if (!real) {
+              mma_issue(d_re, dAi + o, dBi + o, idp, 1u, ESZ == 4);
+              mma_issue(d_im, dAr + o, dBi + o, idn, 1u, ESZ == 4);
+              mma_issue(d_im, dAi + o, dBr + o, idn, 1u, ESZ == 4);
+            }
+          }
+        }
+        mma_commit(bar_empty + 8 * slot);
+      }
+      mma_commit(bar_acc);
+    }
+  } else {
+    // Epilogue: warp w reads TMEM lanes 32w..32w+31 (= output rows i0 + 32w + lane).
+    const bool ok = mbar_wait(bar_acc, 0u, err, 3);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int row = i0 + warp * 32 + lane;
+      float2* Yk = Y + (long long)k * n * s;
+      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float re[32], im[32];
+        tmem_ld32(lane_base + c0, re);
+        if (!real) {
+          tmem_ld32(lane_base + BN + c0, im);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) im[c] = 0.f;
+        }
+        if (row < n) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            const int j = j0 + c0 + c;
+            if (j < s) Yk[(long long)j * n + row] = make_float2(re[c], im[c]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 5) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::kTmemCols));
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Operand preparation
+// ------------------------------------------------------------------------------------------------
+template <typename OpT> __device__ __forceinline__ OpT to_op(float v);
+template <> __device__ __forceinline__ __nv_bfloat16 to_op<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ float to_op<float>(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
+// A_k (double2, column-major n x n) -> planes [k][i][ld] (row-major), via a 32 x 32 tile transpose.
+template <typename OpT>
+__global__ void k_prep_A(const double2* __restrict__ Ah, OpT* __restrict__ re, OpT* __restrict__ im, int n, int ld) {
+  __shared__ float tr[32][33], ti[32][33];
+  const int k = blockIdx.z;
+  const int i0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
+  const double2* A = Ah + (long long)k * n * n;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {   // read column l0+q, rows i0 + tx
+    const int i = i0 + threadIdx.x, l = l0 + q;
+    double2 v = make_double2(0.0, 0.0);
+    if (i < n && l < n) v = A[(long long)l * n + i];
+    tr[q][threadIdx.x] = (float)v.x;
+    ti[q][threadIdx.x] = (float)v.y;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {   // write row i0+q, columns l0 + tx
+    const int i = i0 + q, l = l0 + threadIdx.x;
+    if (i < n && l < ld) {
+      const long long o = (long long)k * n * ld + (long long)i * ld + l;
+      re[o] = to_op<OpT>(l < n ? tr[threadIdx.x][q] : 0.f);
+      im[o] = to_op<OpT>(l < n ? ti[threadIdx.x][q] : 0.f);
+    }
+  }
+}
+
+// B_k (double2, column-major s x s) -> planes [k][j][ld] (no transpose), negative-free.
+template <typename OpT>
+__global__ void k_prep_B(const double2* __restrict__ Bh, OpT* __restrict__ re, OpT* __restrict__ im, int s, int ld,
+                         int K) {
+  const long long total = (long long)K * s * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(e % ld);
+    const long long r = e / ld;
+    const int j = (int)(r % s), k = (int)(r / s);
+    double2 v = make_double2(0.0, 0.0);
+    if (l < s) v = Bh[(long long)k * s * s + (long long)j * s + l];
+    re[e] = to_op<OpT>((float)v.x);
+    im[e] = to_op<OpT>((float)v.y);
+  }
+}
+
+// Planar DFT along mode 3 of an FP32 tensor: X (n x s x p) -> planes [k][j][ldn] (column-major X_k).
+template <typename OpT, int PMAX>
+__global__ void __launch_bounds__(256) k_rfft_planar(const float* __restrict__ X, OpT* __restrict__ re,
+                                                     OpT* __restrict__ im, int n, int s, int p, int ldn) {
+  __shared__ float tc[PMAX], tsn[PMAX];
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    double sv, cv;
+    sincospi(2.0 * r / p, &sv, &cv);
+    tc[r] = (float)cv;
+    tsn[r] = (float)sv;
+  }
+  __syncthreads();
+  const int K = p / 2 + 1;
+  const long long T = (long long)n * s;
+  const long long Tp = (long long)ldn * s;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < Tp; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ldn);
+    const long long j = e / ldn;
+    float x[PMAX];
+#pragma unroll
+    for (int t = 0; t < PMAX; ++t) x[t] = (t < p && i < n) ? X[t * T + j * n + i] : 0.f;
+#pragma unroll 1
+    for (int kk = 0; kk < K; ++kk) {
+      float a = 0.f, b = 0.f;
+      int r = 0;
+#pragma unroll
+      for (int t = 0; t < PMAX; ++t) {
+        if (t < p) {
+          a = fmaf(x[t], tc[r], a);
+          b = fmaf(-x[t], tsn[r], b);
+          r += kk;
+          if (r >= p) r -= p;
+        }
+      }
+      re[kk * Tp + e] = to_op<OpT>(a);
+      im[kk * Tp + e] = to_op<OpT>(b);
+    }
+  }
+}
+
+// planes [k][j][ldn] (column-major X_k) -> planes [k][i][lds] (row-major X_k).
+template <typename OpT>
+__global__ void k_transpose_planes(const OpT* __restrict__ cre, const OpT* __restrict__ cim, OpT* __restrict__ rre,
+                                   OpT* __restrict__ rim, int n, int s, int ldn, int lds) {
+  __shared__ OpT tr[32][33], ti[32][33];
+  const int k = blockIdx.z, i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const OpT* cr = cre + (long long)k * s * ldn;
+  const OpT* ci = cim + (long long)k * s * ldn;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int j = j0 + q, i = i0 + threadIdx.x;
+    OpT a = to_op<OpT>(0.f), b = to_op<OpT>(0.f);
+    if (j < s && i < n) {
+      a = cr[(long long)j * ldn + i];
+      b = ci[(long long)j * ldn + i];
+    }
+    tr[q][threadIdx.x] = a;
+    ti[q][threadIdx.x] = b;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int i = i0 + q, j = j0 + threadIdx.x;
+    if (i < n && j < lds) {
+      const long long o = (long long)k * n * lds + (long long)i * lds + j;
+      rre[o] = j < s ? tr[threadIdx.x][q] : to_op<OpT>(0.f);
+      rim[o] = j < s ? ti[threadIdx.x][q] : to_op<OpT>(0.f);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    TS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) throw Error{TS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"};
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3-D map over planes [K][rows][ld] of ESZ-byte elements, box = (128 bytes of l) x box_rows x 1.
+void make_map(CUtensorMap* m, const void* base, int esz, int ld, int cols, int rows, int K, int box_rows) {
+  TS_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, "TMA base must be 16-byte aligned");
+  TS_REQUIRE(((long long)ld * esz) % 16 == 0, "TMA row pitch must be a multiple of 16 bytes");
+  const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)K};
+  const cuuint64_t strides[2] = {(cuuint64_t)ld * esz, (cuuint64_t)ld * esz * rows};
+  const cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(m, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                           const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error{TS_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r)};
+}
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+template <int BN, int ESZ>
+void launch_tc(const TcMaps& maps, float2* Y, int n, int s, int K, int nyq, int* err, cudaStream_t st) {
+  using Cfg = TcCfg<BN, ESZ>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    TS_CUDA(cudaFuncSetAttribute(k_tc_sylv<BN, ESZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+    attr_set = true;
+  }
+  dim3 grid((s + BN - 1) / BN, (n + kTileM - 1) / kTileM, K);
+  k_tc_sylv<BN, ESZ><<<grid, 192, Cfg::kSmem, st>>>(maps, Y, n, s, nyq, err);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+template <typename OpT>
+void prepare_operator(ts_op* op, TcOperands& t, cudaStream_t st) {
+  const int n = op->n, s = op->s, K = op->K;
+  dim3 blk(32, 8);
+  k_prep_A<OpT><<<dim3((n + 31) / 32, (t.ldn + 31) / 32, K), blk, 0, st>>>(op->Ah, (OpT*)t.a_re, (OpT*)t.a_im, n, t.ldn);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+  const long long tot = (long long)K * s * t.lds;
+  int g = (int)((tot + 255) / 256);
+  if (g > 152 * 16) g = 152 * 16;
+  k_prep_B<OpT><<<g, 256, 0, st>>>(op->Bh, (OpT*)t.b_re, (OpT*)t.b_im, s, t.lds, K);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+template <typename OpT>
+void planar_dft(const float* X, TcWork& w, int n, int s, int p, int ldn, int lds, cudaStream_t st) {
+  const long long Tp = (long long)ldn * s;
+  int g = (int)((Tp + 255) / 256);
+  if (g > 152 * 16) g = 152 * 16;
+  OpT* cre = (OpT*)w.xc_re; OpT* cim = (OpT*)w.xc_im;
+  if (p <= 4) k_rfft_planar<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
+  else if (p <= 8) k_rfft_planar<OpT, 8><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
+  else if (p <= 16) k_rfft_planar<OpT, 16><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
+  else if (p <= 32) k_rfft_planar<OpT, 32><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
+  else throw Error{TS_ERR_UNSUPPORTED, "tensor-core path supports p <= 32"};
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+  const int K = p / 2 + 1;
+  k_transpose_planes<OpT><<<dim3((n + 31) / 32, (lds + 31) / 32, K), dim3(32, 8), 0, st>>>(
+      cre, cim, (OpT*)w.xr_re, (OpT*)w.xr_im, n, s, ldn, lds);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+// Build (once per operator and precision) the tensor-core operand planes of A_k and B_k.
+void tc_prepare(ts_op* op, int precision, cudaStream_t st) {
+  if (op->tc_prec == precision && op->tc) return;
+  const int esz = precision == TS_MIXED_BF16 ? 2 : 4;
+  TcOperands* t = op->tc ? op->tc : new TcOperands();
+  op->tc = t;
+  t->release();
+  t->esz = esz;
+  t->ldn = round_up(op->n, 64);
+  t->lds = round_up(op->s, 64);
+  const size_t na = (size_t)op->K * op->n * t->ldn * esz, nb = (size_t)op->K * op->s * t->lds * esz;
+  TS_CUDA(cudaMalloc(&t->a_re, na));
+  TS_CUDA(cudaMalloc(&t->a_im, na));
+  TS_CUDA(cudaMalloc(&t->b_re, nb));
+  TS_CUDA(cudaMalloc(&t->b_im, nb));
+  if (esz == 2) prepare_operator<__nv_bfloat16>(op, *t, st);
+  else prepare_operator<float>(op, *t, st);
+  op->tc_prec = precision;
+}
+
+void tc_apply(ts_ctx* ctx, ts_op* op, int precision, const float* X, float2* Yh, cudaStream_t st) {
+  tc_prepare(op, precision, st);
+  TcOperands& t = *op->tc;
+  const int n = op->n, s = op->s, p = op->p, K = op->K, esz = t.esz;
+  TcWork w;
+  const size_t nx = (size_t)K * s * t.ldn * esz, nr = (size_t)K * n * t.lds * esz;
+  w.xc_re = ctx->ws.get("tc_xc_re", nx);
+  w.xc_im = ctx->ws.get("tc_xc_im", nx);
+  w.xr_re = ctx->ws.get("tc_xr_re", nr);
+  w.xr_im = ctx->ws.get("tc_xr_im", nr);
+  int* err = static_cast<int*>(ctx->ws.get("tc_err", sizeof(int) * 4));
+  KernelTimer& tm = ctx->timer;
+  tm.begin(st, 1, 4.0 * n * s * p + 2.0 * K * n * s * esz * 2);
+  if (esz == 2) planar_dft<__nv_bfloat16>(X, w, n, s, p, t.ldn, t.lds, st);
+  else planar_dft<float>(X, w, n, s, p, t.ldn, t.lds, st);
+  tm.end(st);
+  TcMaps maps;
+  const int bn = s <= 64 ? 64 : (s <= 128 ? 128 : 256);
+  make_map(&maps.a_re, t.a_re, esz, t.ldn, n, n, K, kTileM);
+  make_map(&maps.a_im, t.a_im, esz, t.ldn, n, n, K, kTileM);
+  make_map(&maps.xc_re, w.xc_re, esz, t.ldn, n, s, K, bn);
+  make_map(&maps.xc_im, w.xc_im, esz, t.ldn, n, s, K, bn);
+  make_map(&maps.xr_re, w.xr_re, esz, t.lds, s, n, K, kTileM);
+  make_map(&maps.xr_im, w.xr_im, esz, t.lds, s, n, K, kTileM);
+  make_map(&maps.b_re, t.b_re, esz, t.lds, s, s, K, bn);
+  make_map(&maps.b_im, t.b_im, esz, t.lds, s, s, K, bn);
+  const int nyq = nyquist_index(p);
+  tm.begin(st, 0, gemm_flops_tc(n, s, K, nyq));
+  if (esz == 2) {
+    if (bn == 64) launch_tc<64, 2>(maps, Yh, n, s, K, nyq, err, st);
+    else if (bn == 128) launch_tc<128, 2>(maps, Yh, n, s, K, nyq, err, st);
+    else launch_tc<256, 2>(maps, Yh, n, s, K, nyq, err, st);
+  } else {
+    if (bn == 64) launch_tc<64, 4>(maps, Yh, n, s, K, nyq, err, st);
+    else if (bn == 128) launch_tc<128, 4>(maps, Yh, n, s, K, nyq, err, st);
+    else launch_tc<256, 4>(maps, Yh, n, s, K, nyq, err, st);
+  }
+  tm.end(st);
+}
+
+double gemm_flops_tc(int n, int s, int K, int nyq) {
+  const int nreal = 1 + (nyq >= 0 ? 1 : 0);
+  const double per = (double)n * s * ((double)n + s);
+  return per * (8.0 * (K - nreal) + 2.0 * nreal);
+}
+
+void TcOperands::release() {
+  cudaFree(a_re);
+  cudaFree(a_im);
+  cudaFree(b_re);
+  cudaFree(b_im);
+  a_re = a_im = b_re = b_im = nullptr;
+}
+
+}  // namespace ts

@@ -72,6 +72,8 @@ struct KernelTimer {
 
 }  // namespace ts
 
+namespace ts { struct TcOperands; }
+
 struct ts_ctx {
   int device = 0;
   int num_sms = 0;
@@ -89,8 +91,7 @@ struct ts_op {
   double2* Bh = nullptr;   // K slices, column-major s x s complex (FP64)
   float2* Ah32 = nullptr;  // FP32 copies, made on first mixed-precision use
   float2* Bh32 = nullptr;
-  void* tc_A = nullptr;    // tensor-core operand copies (precision-specific), made on first use
-  void* tc_B = nullptr;
+  ts::TcOperands* tc = nullptr;  // tensor-core operand planes (BF16 or TF32), made on first use
   int tc_prec = -1;
 };
 

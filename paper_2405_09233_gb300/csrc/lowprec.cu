@@ -2,6 +2,7 @@
 // W = M(V) with V, W in FP32 storage.  TS_MIXED_FP32 uses FP32 CUDA-core slice GEMMs.
 #include "internal.cuh"
 #include "apply.cuh"
+#include "tc.cuh"
 
 namespace ts {
 
@@ -19,12 +20,17 @@ static void ensure_f32_operator(ts_op* op, cudaStream_t st) {
 void apply_low(ts_ctx* ctx, ts_op* op, int precision, const float* X, float* Y, cudaStream_t st) {
   const int n = op->n, s = op->s, p = op->p, K = op->K;
   const long long T = (long long)n * s;
-  if (precision != TS_MIXED_FP32)
-    throw Error{TS_ERR_UNSUPPORTED, "tensor-core precisions are not available in this build"};
-  ensure_f32_operator(op, st);
-  float2* Xh = static_cast<float2*>(ctx->ws.get("low_Xh", sizeof(float2) * (size_t)K * T));
   float2* Yh = static_cast<float2*>(ctx->ws.get("low_Yh", sizeof(float2) * (size_t)K * T));
   KernelTimer& tm = ctx->timer;
+  if (precision == TS_MIXED_BF16 || precision == TS_MIXED_TF32) {
+    tc_apply(ctx, op, precision, X, Yh, st);
+    tm.begin(st, 1, 8.0 * K * T + 4.0 * T * p);
+    irfft_tube<float, float2>(Yh, Y, T, p, IRFFT_STORE, nullptr, nullptr, st);
+    tm.end(st);
+    return;
+  }
+  ensure_f32_operator(op, st);
+  float2* Xh = static_cast<float2*>(ctx->ws.get("low_Xh", sizeof(float2) * (size_t)K * T));
   tm.begin(st, 1, 4.0 * T * p + 8.0 * K * T);
   rfft_tube<float, float2>(X, Xh, T, p, st);
   tm.end(st);

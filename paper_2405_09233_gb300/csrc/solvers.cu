@@ -44,7 +44,10 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
   const int m = o.restart;
   const bool mixed = prec != TS_FP64;
   const int max_cycles = mixed ? (o.max_outer > 0 ? o.max_outer : 50) : o.max_restarts;
-  const double inner_tol = mixed ? (o.inner_tol > 0 ? o.inner_tol : 1e-4) : 0.0;
+  // Default inner tolerance: a little above what the inner operator's rounding lets the inner
+  // tGMRES resolve (FP32 ~1e-7, TF32 ~5e-4, BF16 ~4e-3 relative).
+  const double inner_default = prec == TS_MIXED_FP32 ? 1e-6 : (prec == TS_MIXED_TF32 ? 1e-3 : 1e-2);
+  const double inner_tol = mixed ? (o.inner_tol > 0 ? o.inner_tol : inner_default) : 0.0;
 
   T* V = static_cast<T*>(ctx->ws.get("krylov_V", sizeof(T) * (size_t)(m + 1) * N));
   T* W = static_cast<T*>(ctx->ws.get("krylov_W", sizeof(T) * (size_t)N));
@@ -55,6 +58,8 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
   double* sc = static_cast<double*>(ctx->ws.get("krylov_scalars", sizeof(double) * 64));
   void* state = ctx->ws.get("krylov_state", krylov_state_bytes(m));
   double* hs = ctx->host_scalars;
+  int* tc_err = static_cast<int*>(ctx->ws.get("tc_err", sizeof(int) * 4));
+  if (mixed) TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
 
   int hist_len = 0, true_len = 0;
   auto push_hist = [&](double v) {
@@ -134,6 +139,11 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
     if ((int)flags & 4) {
       status = TS_ERR_NONFINITE;
       break;
+    }
+    if (mixed && (prec == TS_MIXED_BF16 || prec == TS_MIXED_TF32)) {
+      int e = 0;
+      TS_CUDA(cudaMemcpy(&e, tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (e != 0) throw Error{TS_ERR_TIMEOUT, "tensor-core kernel wait expired (code " + std::to_string(e) + ")"};
     }
     ks_solve(state, m, k, method, st);
     multi_axpy<T, double>(X, V, N, N, ks_y(state, m), k, 1.0, nullptr, st);   // X = X0 + V_k (*) y
