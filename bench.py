@@ -45,7 +45,61 @@ def args_parse():
                     help="comma list of extra precisions to time ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
+                    help="solve: full solves (the benchmark); apply: operator applications only (kernel runs)")
+    ap.add_argument("--n", type=int)
+    ap.add_argument("--s", type=int)
+    ap.add_argument("--p", type=int)
     return ap.parse_args()
+
+
+def workload_cfg(a):
+    from paper_2405_09233_gb300 import inputs
+    cfg = dict(inputs.WORKLOADS[a.workload])
+    for key in ("n", "s", "p"):
+        if getattr(a, key) is not None:
+            cfg[key] = getattr(a, key)
+    return cfg
+
+
+def peaks():
+    """Roofline denominators: MEASURED_PEAKS.json when present, else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_burst": d["bf16_tflops"], "bf16_sustained": d["bf16_tflops_sustained"],
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_burst": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
+
+
+TF32_OVER_BF16 = 1.1 / 2.25       # nominal dense tensor rates (PFLOP/s per GPU)
+FFMA_NOMINAL_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12   # 128 FP32 lanes/SM x 2 FLOP x 152 SMs x 2070 MHz
+
+
+def gemm_roofline(kind, precision, flops_per_launch, avg_ms, sustained, share):
+    """Roofline object for the dominant slice-GEMM kernel."""
+    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
+    pk = peaks()
+    if kind == "fp64":
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "k_gemm_slices<double> (FP64 DFMA, 3-multiply complex)",
+                "note": ("peak derived: 4 FP64 FLOP/clk/SM x 152 SMs x 2070 MHz (nominal). Algorithmic FLOPs count 8 "
+                         "per complex multiply-add; the kernel executes 6 (Gauss), so frac can reach 1.33. "
+                         f"Kernel share of the step: {share:.3f}")}
+    if precision == "mixed_fp32":
+        return {"bound": "alu", "achieved": achieved, "peak": FFMA_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FFMA_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "k_gemm_slices<float> (FP32 FFMA, 3-multiply complex)",
+                "note": f"peak derived: 2 FLOP x 128 lanes/SM x 152 SMs x 2070 MHz. Kernel share: {share:.3f}"}
+    bf = pk["bf16_sustained"] if sustained else pk["bf16_burst"]
+    peak = bf * (TF32_OVER_BF16 if precision == "mixed_tf32" else 1.0)
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": f"k_tc_sylv ({'TF32' if precision == 'mixed_tf32' else 'BF16'} tcgen05)",
+            "note": (f"peak: {pk['source']} BF16 {'sustained' if sustained else 'burst'}"
+                     + (" x nominal TF32/BF16 ratio 0.489" if precision == "mixed_tf32" else "")
+                     + f". Kernel share of the step: {share:.3f}")}
 
 
 def dist_env():
@@ -199,7 +253,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    cfg = inputs.WORKLOADS[a.workload]
+    cfg = workload_cfg(a)
     n, s, p, m = cfg["n"], cfg["s"], cfg["p"], cfg["restart"]
     seed = 1 + rank
     pr = inputs.dense_problem(n, s, p, seed=seed, scale=cfg["scale"])
@@ -213,6 +267,8 @@ def main():
     op0.close()
     X = torch.zeros_like(Cd)
     torch.cuda.synchronize()
+    if a.mode == "apply":
+        return run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev)
 
     def step(precision):
         op = ctx.op_create_dense(Ad, Bd)
@@ -256,17 +312,18 @@ def main():
     unknowns = n * s * p
     value = unknowns * world / (ms / 1e3)
 
-    # dominant kernel: the per-slice GEMM (FP64 pipe bound for the FP64 path)
-    gemm_avg_ms = st.gemm_ms / max(st.gemm_launches, 1)
-    flops_per_launch = st.gemm_flops / max(st.gemm_launches, 1)
-    achieved_tflops = flops_per_launch / (gemm_avg_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_NOMINAL_TFLOPS, "traffic": None,
-                "kernel": "k_gemm_slices<double> (FP64 DFMA, 3-multiply complex)",
-                "note": ("FP64 on CUDA cores; peak = 4 FLOP/clk/SM x 152 SMs x 2070 MHz (nominal). Algorithmic "
-                         "FLOPs count 8 per complex multiply-add; the kernel performs 6 (Gauss), so frac can "
-                         "exceed 0.75 of the FP64 pipe's own rate. GEMM share of the step: "
-                         f"{st.gemm_ms / (ms * a.steps):.3f}")}
+    # dominant kernel: whichever slice GEMM (FP64 or low precision) took more time
+    step_ms_total = ms * a.steps
+    if st.gemm_ms >= st.lowp_ms:
+        roofline = gemm_roofline("fp64", "fp64", st.gemm_flops / max(st.gemm_launches, 1),
+                                 st.gemm_ms / max(st.gemm_launches, 1), True, st.gemm_ms / step_ms_total)
+    else:
+        roofline = gemm_roofline("lowp", a.precision, st.lowp_flops / max(st.lowp_launches, 1),
+                                 st.lowp_ms / max(st.lowp_launches, 1), True, st.lowp_ms / step_ms_total)
+    kernel_times = {"fp64_gemm_ms": st.gemm_ms / a.steps, "lowp_gemm_ms": st.lowp_ms / a.steps,
+                    "fft_ms": st.fft_ms / a.steps, "fp64_gemm_launches": st.gemm_launches // a.steps,
+                    "lowp_gemm_launches": st.lowp_launches // a.steps,
+                    "fft_gbs": st.fft_bytes / max(st.fft_ms, 1e-9) / 1e6}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     C_h = Cd.cpu().pin_memory()
@@ -305,7 +362,7 @@ def main():
             variants[prec] = {"error": str(e)}
 
     cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and a.workload == "dense_n1024_s1024_p16":
         cpu = cpu_baseline(cfg, seed)
 
     if rank == 0:
@@ -320,11 +377,58 @@ def main():
                            "applies_fp64": last.info.applies_fp64, "relres_true": relres,
                            "err_vs_xstar": err_xstar},
                 "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-                "gpu_launches": int(st.launches), "variants": variants}
+                "gpu_launches": int(st.launches), "kernels_per_step": kernel_times, "variants": variants}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev):
+    """Operator applications only (FP64 ts_sylv_apply, or ts_sylv_apply_lowp): the kernel runs that the
+    profiles under profiles/ are taken on.  One step = one application of M."""
+    import torch
+    n, s, p = cfg["n"], cfg["s"], cfg["p"]
+    op = ctx.op_create_dense(Ad, Bd)
+    if a.precision == "fp64":
+        Xin = Xs
+        Y = torch.empty_like(Xs)
+        fn = lambda: ctx.sylv_apply(op, Xin, Y)  # noqa: E731
+    else:
+        Xin = Xs.float().contiguous()
+        Y = torch.empty_like(Xin)
+        fn = lambda: ctx.sylv_apply_lowp(op, Xin, a.precision, Y)  # noqa: E731
+    for _ in range(a.warmup):
+        fn()
+    torch.cuda.synchronize()
+    ctx.stats_reset()
+    ctx.stats_enable(True)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ctx.stats_enable(False)
+    st = ctx.stats_get()
+    ms = e0.elapsed_time(e1) / a.steps
+    if a.precision == "fp64":
+        rf = gemm_roofline("fp64", "fp64", st.gemm_flops / max(st.gemm_launches, 1),
+                           st.gemm_ms / max(st.gemm_launches, 1), False, st.gemm_ms / (ms * a.steps))
+    else:
+        rf = gemm_roofline("lowp", a.precision, st.lowp_flops / max(st.lowp_launches, 1),
+                           st.lowp_ms / max(st.lowp_launches, 1), False, st.lowp_ms / (ms * a.steps))
+    line = {"mode": "apply", "metric": "operator applications (unknowns/s)", "value": n * s * p / (ms / 1e3),
+            "unit": "unknowns/s", "ms_per_step": ms, "steps": a.steps, "warmup": a.warmup,
+            "config": {"workload": a.workload, "n": n, "s": s, "p": p, "precision": a.precision},
+            "roofline": rf, "fft_gbs": st.fft_bytes / max(st.fft_ms, 1e-9) / 1e6,
+            "fft_ms_per_step": st.fft_ms / a.steps, "clocks": clk, "gpu_launches": int(st.launches)}
+    print(json.dumps(line), flush=True)
+    op.close()
+    ctx.close()
 
 
 if __name__ == "__main__":

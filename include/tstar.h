@@ -150,9 +150,12 @@ ts_status ts_tfom_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X
  * by CUDA events recorded on the launching stream around each timed launch. */
 typedef struct {
   long long launches;      /* libtstar kernels launched since the last ts_stats_reset */
-  long long gemm_launches; /* per-Fourier-slice GEMM launches timed while enabled */
+  long long gemm_launches; /* FP64 per-Fourier-slice GEMM launches timed while enabled */
   double gemm_ms;          /* their summed event durations */
   double gemm_flops;       /* their algorithmic FLOPs: 8 per complex and 2 per real multiply-add */
+  long long lowp_launches; /* low-precision slice GEMM launches (FP32 CUDA cores or tcgen05) */
+  double lowp_ms;
+  double lowp_flops;
   long long fft_launches;  /* forward and inverse DFT launches timed while enabled */
   double fft_ms;
   double fft_bytes;        /* their algorithmic HBM bytes (input read + output written once) */

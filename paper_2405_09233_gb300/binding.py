@@ -42,7 +42,8 @@ class SolveInfo(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("gemm_launches", ctypes.c_longlong), ("gemm_ms", ctypes.c_double),
-                ("gemm_flops", ctypes.c_double), ("fft_launches", ctypes.c_longlong), ("fft_ms", ctypes.c_double),
+                ("gemm_flops", ctypes.c_double), ("lowp_launches", ctypes.c_longlong), ("lowp_ms", ctypes.c_double),
+                ("lowp_flops", ctypes.c_double), ("fft_launches", ctypes.c_longlong), ("fft_ms", ctypes.c_double),
                 ("fft_bytes", ctypes.c_double)]
 
 

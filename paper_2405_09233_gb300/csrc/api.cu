@@ -63,6 +63,10 @@ void KernelTimer::collect() {
       ++gemm_launches;
       gemm_ms += ms;
       gemm_flops += r.work;
+    } else if (r.kind == 2) {
+      ++lowp_launches;
+      lowp_ms += ms;
+      lowp_flops += r.work;
     } else {
       ++fft_launches;
       fft_ms += ms;
@@ -75,8 +79,8 @@ void KernelTimer::collect() {
 
 void KernelTimer::reset() {
   collect();
-  gemm_launches = fft_launches = 0;
-  gemm_ms = gemm_flops = fft_ms = fft_bytes = 0;
+  gemm_launches = fft_launches = lowp_launches = 0;
+  gemm_ms = gemm_flops = fft_ms = fft_bytes = lowp_ms = lowp_flops = 0;
 }
 
 void KernelTimer::destroy() {
@@ -386,6 +390,9 @@ ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out) {
   out->fft_launches = t.fft_launches;
   out->fft_ms = t.fft_ms;
   out->fft_bytes = t.fft_bytes;
+  out->lowp_launches = t.lowp_launches;
+  out->lowp_ms = t.lowp_ms;
+  out->lowp_flops = t.lowp_flops;
   return TS_OK;
   TS_API_END(ctx)
 }

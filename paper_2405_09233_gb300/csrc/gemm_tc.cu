@@ -546,7 +546,7 @@ void tc_apply(ts_ctx* ctx, ts_op* op, int precision, const float* X, float2* Yh,
   make_map(&maps.b_re, t.b_re, esz, t.lds, s, s, K, bn);
   make_map(&maps.b_im, t.b_im, esz, t.lds, s, s, K, bn);
   const int nyq = nyquist_index(p);
-  tm.begin(st, 0, gemm_flops_tc(n, s, K, nyq));
+  tm.begin(st, 2, gemm_flops_tc(n, s, K, nyq));
   if (esz == 2) {
     if (bn == 64) launch_tc<64, 2>(maps, Yh, n, s, K, nyq, err, st);
     else if (bn == 128) launch_tc<128, 2>(maps, Yh, n, s, K, nyq, err, st);

@@ -54,15 +54,15 @@ inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_
 // Event timing of selected kernels while a context has statistics enabled.
 struct TimedRegion {
   cudaEvent_t a, b;
-  int kind;        // 0 = GEMM, 1 = FFT
+  int kind;        // 0 = FP64 GEMM, 1 = FFT, 2 = low-precision GEMM
   double work;     // algorithmic FLOPs (GEMM) or bytes (FFT)
 };
 struct KernelTimer {
   bool enabled = false;
   std::vector<TimedRegion> done;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
-  long long gemm_launches = 0, fft_launches = 0;
-  double gemm_ms = 0, gemm_flops = 0, fft_ms = 0, fft_bytes = 0;
+  long long gemm_launches = 0, fft_launches = 0, lowp_launches = 0;
+  double gemm_ms = 0, gemm_flops = 0, fft_ms = 0, fft_bytes = 0, lowp_ms = 0, lowp_flops = 0;
   void begin(cudaStream_t st, int kind, double work);
   void end(cudaStream_t st);
   void collect();  // synchronise the recorded events and accumulate

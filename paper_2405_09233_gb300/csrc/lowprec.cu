@@ -41,7 +41,7 @@ void apply_low(ts_ctx* ctx, ts_op* op, int precision, const float* X, float* Y, 
   g.B2 = op->Bh32; g.sB2 = (long long)s * s; g.ldb2 = s; g.L2 = s;
   g.Y = Yh; g.sY = T; g.ldy = n;
   g.M = n; g.N = s; g.K = K; g.nyq = nyquist_index(p); g.sgn2 = -1.0;
-  tm.begin(st, 0, gemm_flops(n, s, n, s, K, g.nyq));
+  tm.begin(st, 2, gemm_flops(n, s, n, s, K, g.nyq));
   cgemm_slices_f32(g, st);
   tm.end(st);
   tm.begin(st, 1, 8.0 * K * T + 4.0 * T * p);

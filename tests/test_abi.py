@@ -36,7 +36,8 @@ def test_struct_layouts_match_header():
     """The ctypes mirrors of ts_solve_opts / ts_solve_info have the header's field order and sizes."""
     import re
     text = open(os.path.join(os.path.dirname(binding.LIB_PATH), "..", "include", "tstar.h")).read()
-    for cls, tag in ((binding.SolveOpts, "ts_solve_opts"), (binding.SolveInfo, "ts_solve_info")):
+    for cls, tag in ((binding.SolveOpts, "ts_solve_opts"), (binding.SolveInfo, "ts_solve_info"),
+                     (binding.Stats, "ts_stats")):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + tag + ";", text).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         names = []
