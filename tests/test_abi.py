@@ -45,6 +45,7 @@ def test_struct_layouts_match_header():
             decl = decl.strip()
             if not decl:
                 continue
-            parts = decl.replace("*", " ").split()
-            names += [n.strip(",") for n in " ".join(parts[1:]).split(",")]
+            chunks = decl.replace("*", " ").split(",")
+            names.append(chunks[0].split()[-1])          # "long long launches" -> "launches"
+            names += [c.strip() for c in chunks[1:]]
         assert [f[0] for f in cls._fields_] == [n.strip() for n in names if n.strip()], tag
