@@ -145,6 +145,26 @@ ts_status ts_tgmres_solve(ts_ctx* ctx, const ts_op* op, const double* C, double*
 ts_status ts_tfom_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X,
                         const ts_solve_opts* opts, ts_solve_info* info, ts_stream stream);
 
+/* ts_tstar without allocating: C = A*B exactly as ts_tstar computes it, for callers that cannot
+ * allocate device memory at call time -- code recorded under CUDA stream capture (cudaMalloc
+ * cannot be captured), latency-critical loops that must not risk an allocation's device-wide
+ * synchronisation, and processes whose device memory is already claimed by another allocator.
+ * The paper has no counterpart; this is a deployment variant of the T-product entry point.
+ *
+ * Scratch: a fixed array of TS_NOALLOC_MAX_COMPLEX complex doubles (32 MiB) in the library's own
+ * device memory, present on every GPU that loads the library until the process exits.  The call
+ * needs K*(n1*n2 + n2*m + n1*m) <= TS_NOALLOC_MAX_COMPLEX with K = p/2 + 1, else it returns
+ * TS_ERR_ARG without doing anything.  A, B and C must be device pointers on the current device
+ * (TS_ERR_ARG otherwise); no context is used and nothing is allocated or freed.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share the one
+ * array and every call overwrites what it uses, so calls whose work overlaps on the GPU (other
+ * streams, or other host threads) race and must be serialised by the caller.  Asynchronous on
+ * `stream`. */
+#define TS_NOALLOC_MAX_COMPLEX (2LL * 1024 * 1024)
+ts_status ts_tstar_noalloc(const double* A, int n1, int n2, const double* B, int m, int p, double* C,
+                           ts_stream stream);
+
 /* Kernel statistics, for measurement.  Launch counts are process-wide (every libtstar kernel
  * launch on any context); kernel timings are per context and only collected while enabled,
  * by CUDA events recorded on the launching stream around each timed launch. */

@@ -70,6 +70,7 @@ _SIGNATURES = {
     "ts_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "ts_tgmres_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
     "ts_tfom_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
+    "ts_tstar_noalloc": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp]),
     "ts_stats_enable": (_i, [_vp, _i]),
     "ts_stats_get": (_i, [_vp, ctypes.POINTER(Stats)]),
     "ts_stats_reset": (_i, [_vp]),
