@@ -81,6 +81,14 @@ ts_status ts_tstar(ts_ctx* ctx, const double* A, int n1, int n2, const double* B
  * caller and freed with ts_op_destroy before ts_destroy(ctx). */
 ts_status ts_op_create_dense(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p,
                              unsigned flags, ts_op** op, ts_stream stream);
+/* Prepare M(X) = A*X - X*B with a sparse A given by its p frontal slices in CSR form (host
+ * arrays): slice t (0-based) has row pointers rowptr[t*(n+1) .. t*(n+1)+n], which index the
+ * shared arrays col[] and val[] (0-based columns, duplicates summed).  The library forms the
+ * union of the p patterns and keeps, per Fourier slice k <= p/2, the complex values of A_k on it
+ * (a complex CSR matrix per slice).  B is dense s x s x p (host or device).  Sparse operators run
+ * in FP64 (ts_sylv_apply, ts_tgmres_solve, ts_tfom_solve, ts_tba_solve); s <= 64. */
+ts_status ts_op_create_csr(ts_ctx* ctx, int n, int p, const int* rowptr, const int* col, const double* val,
+                           const double* B, int s, unsigned flags, ts_op** op, ts_stream stream);
 /* Free an operator.  NULL is ignored. */
 void ts_op_destroy(ts_op* op);
 /* Sizes of a prepared operator (any output pointer may be NULL). */
@@ -164,6 +172,23 @@ ts_status ts_tfom_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X
 #define TS_NOALLOC_MAX_COMPLEX (2LL * 1024 * 1024)
 ts_status ts_tstar_noalloc(const double* A, int n1, int n2, const double* B, int m, int p, double* C,
                            ts_stream stream);
+
+/* Restarted TBAS(m) (§5.2, Algorithm 8): Tubal Block Arnoldi (Algorithm 7) on A with block width
+ * s, started from R0 = C - M(X0); the projected equation H_m*Y - Y*B = V_m^T*R0 (Eq. (46)) is
+ * solved by t-Bartels-Stewart; X = X0 + V_m*Y; restart until ||C - M(X)||_F <= tol ||C||_F.
+ * opts->restart is m (block steps per cycle, m*s <= 12000), opts->max_restarts the cycle budget;
+ * history receives the Proposition 5.2 estimate per cycle and true_history the true residual.
+ * FP64 only; s <= 64.  Arguments and results otherwise as ts_tgmres_solve. */
+ts_status ts_tba_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X, const ts_solve_opts* opts,
+                       ts_solve_info* info, ts_stream stream);
+
+/* t-Bartels-Stewart (§4, Algorithm 5) for a small dense STE A*X - X*B = C (A n x n x p,
+ * B s x s x p, C and X n x s x p, FP64): per Fourier slice k <= p/2, B_k = Q T Q^H (complex
+ * Schur), then column j of X_k Q solves (A_k - t_jj I) z_j = (C_k Q)_j + sum_{i<j} t_ij z_i.
+ * Needs K*s*n^2 <= 2^28 complex entries of workspace.  Returns TS_SINGULAR when A_k and B_k
+ * share an eigenvalue (Theorem 2.1's condition fails) or the Schur iteration does not converge. */
+ts_status ts_t_bartels_stewart(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p,
+                               const double* C, double* X, ts_stream stream);
 
 /* Kernel statistics, for measurement.  Launch counts are process-wide (every libtstar kernel
  * launch on any context); kernel timings are per context and only collected while enabled,

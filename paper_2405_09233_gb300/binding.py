@@ -63,6 +63,7 @@ _SIGNATURES = {
     "ts_status_string": (ctypes.c_char_p, [_i]),
     "ts_tstar": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _vp, _vp]),
     "ts_op_create_dense": (_i, [_vp, _vp, _i, _vp, _i, _i, _u, ctypes.POINTER(_vp), _vp]),
+    "ts_op_create_csr": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _i, _u, ctypes.POINTER(_vp), _vp]),
     "ts_op_destroy": (None, [_vp]),
     "ts_op_shape": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "ts_sylv_apply": (_i, [_vp, _vp, _vp, _vp, _vp]),
@@ -70,6 +71,8 @@ _SIGNATURES = {
     "ts_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "ts_tgmres_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
     "ts_tfom_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
+    "ts_tba_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
+    "ts_t_bartels_stewart": (_i, [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _vp]),
     "ts_tstar_noalloc": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp]),
     "ts_stats_enable": (_i, [_vp, _i]),
     "ts_stats_get": (_i, [_vp, ctypes.POINTER(Stats)]),
@@ -166,6 +169,30 @@ class Context:
                                              _stream(A, B)), "ts_op_create_dense")
         return Operator(self, h, n, s, p)
 
+    def op_create_csr(self, n, p, rowptr, col, val, B) -> "Operator":
+        """Sparse A from p CSR slices (numpy int32 rowptr of length p*(n+1) indexing the shared
+        int32 col / float64 val arrays); B: (p, s, s) float64 torch tensor."""
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        pB, s, s_ = B.shape
+        assert pB == p and s == s_ and rowptr.size == p * (n + 1)
+        h = _vp()
+        self._check(lib().ts_op_create_csr(self._h, n, p, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                           _ptr(B), s, 0, ctypes.byref(h), _stream(B)), "ts_op_create_csr")
+        return Operator(self, h, n, s, p)
+
+    def t_bartels_stewart(self, A, B, C, X=None):
+        """Small dense STE A*X - X*B = C by t-Bartels-Stewart; (p, n, n), (p, s, s), (p, s, n) tensors."""
+        import torch
+        p, n, _ = A.shape
+        s = B.shape[1]
+        if X is None:
+            X = torch.empty_like(C)
+        self._check(lib().ts_t_bartels_stewart(self._h, _ptr(A), n, _ptr(B), s, p, _ptr(C), _ptr(X),
+                                               _stream(A, B, C, X)), "ts_t_bartels_stewart")
+        return X
+
     def sylv_apply(self, op: "Operator", X, Y=None):
         import torch
         if Y is None:
@@ -208,6 +235,11 @@ class Context:
         """Restarted tGMRES(m); X holds X0 on entry and the solution on return."""
         return self._solve(lib().ts_tgmres_solve, "ts_tgmres_solve", op, C, X, restart, tol, max_restarts,
                            precision, inner_tol, max_outer, history_cap)
+
+    def tba_solve(self, op, C, X, restart=10, tol=1e-10, max_restarts=100, history_cap=4096):
+        """Restarted TBAS(m) (FP64); X holds X0 on entry and the solution on return."""
+        return self._solve(lib().ts_tba_solve, "ts_tba_solve", op, C, X, restart, tol, max_restarts,
+                           "fp64", 0.0, 0, history_cap)
 
     def tfom_solve(self, op, C, X, restart=20, tol=1e-10, max_restarts=200, history_cap=4096):
         """Restarted tFOM(m) (FP64)."""

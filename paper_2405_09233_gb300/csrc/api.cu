@@ -5,6 +5,7 @@
 #include "internal.cuh"
 #include "apply.cuh"
 #include "tc.cuh"
+#include "tba.cuh"
 
 namespace ts {
 
@@ -155,6 +156,15 @@ void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mod
                double* partials, cudaStream_t st) {
   const int n = op->n, s = op->s, p = op->p, K = op->K;
   const long long T = (long long)n * s;
+  if (op->sp) {
+    // Sparse A: SpMM path; the residual epilogue becomes a subtraction and a fixed-order norm.
+    apply_sparse_f64(ctx, op, X, Y, st);
+    if (mode == IRFFT_RESIDUAL) {
+      sub3<double>(C, Y, Y, T * p, st);
+      dot_partials<double>(Y, Y, T * p, partials, st);
+    }
+    return;
+  }
   double2* Xh = static_cast<double2*>(ctx->ws.get("apply_Xh", sizeof(double2) * (size_t)K * T));
   double2* Yh = static_cast<double2*>(ctx->ws.get("apply_Yh", sizeof(double2) * (size_t)K * T));
   KernelTimer& tm = ctx->timer;
@@ -327,6 +337,13 @@ void ts_op_destroy(ts_op* op) {
     op->tc->release();
     delete op->tc;
   }
+  if (op->sp) {
+    op->sp->release();
+    delete op->sp;
+  }
+  cudaFree(op->Bh_row);
+  cudaFree(op->schurT);
+  cudaFree(op->schurQ);
   delete op;
 }
 
@@ -354,6 +371,69 @@ ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y
   TS_API_END(ctx)
 }
 
+ts_status ts_op_create_csr(ts_ctx* ctx, int n, int p, const int* rowptr, const int* col, const double* val,
+                           const double* B, int s, unsigned flags, ts_op** out, ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  ts_op* op = nullptr;
+  try {
+    TS_REQUIRE(out, "ts_op_create_csr: null output");
+    *out = nullptr;
+    TS_REQUIRE(rowptr && col && val && B, "ts_op_create_csr: null pointer");
+    TS_REQUIRE(n >= 1 && s >= 1 && p >= 1, "ts_op_create_csr: sizes must be >= 1");
+    TS_REQUIRE(flags == 0, "ts_op_create_csr: flags must be 0");
+    TS_REQUIRE(!is_device_ptr(rowptr) && !is_device_ptr(col) && !is_device_ptr(val),
+               "ts_op_create_csr: the CSR arrays must be host memory");
+    TS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    op = new ts_op();
+    op->ctx = ctx;
+    op->n = n;
+    op->s = s;
+    op->p = p;
+    op->K = num_slices(p);
+    TS_CUDA(cudaMalloc(&op->Bh, sizeof(double2) * (size_t)op->K * s * s));
+    StagedIn b(ctx, "stage_B", B, (size_t)s * s * p, st);
+    rfft_tube<double, double2>(b.dev, op->Bh, (long long)s * s, p, st);
+    op_prepare_csr(op, rowptr, col, val, st);
+    *out = op;
+    return TS_OK;
+  } catch (const ts::Error& e) {
+    ctx->err = e.msg;
+    ts_op_destroy(op);
+    return e.status;
+  } catch (...) {
+    ctx->err = "unknown error";
+    ts_op_destroy(op);
+    return TS_ERR_NOMEM;
+  }
+}
+
+ts_status ts_tba_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X, const ts_solve_opts* opts,
+                       ts_solve_info* info, ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  return tba_entry(ctx, op, C, X, opts, info, stream);
+  TS_API_END(ctx)
+}
+
+ts_status ts_t_bartels_stewart(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p, const double* C,
+                               double* X, ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  TS_REQUIRE(A && B && C && X, "ts_t_bartels_stewart: null pointer");
+  TS_REQUIRE(n >= 1 && s >= 1 && p >= 1, "ts_t_bartels_stewart: sizes must be >= 1");
+  TS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  StagedIn a(ctx, "tbs_inA", A, (size_t)n * n * p, st);
+  StagedIn b(ctx, "tbs_inB", B, (size_t)s * s * p, st);
+  StagedIn c(ctx, "tbs_inC", C, (size_t)n * s * p, st);
+  StagedOut x(ctx, "tbs_outX", X, (size_t)n * s * p, false, st);
+  t_bartels_stewart_dev(ctx, a.dev, n, b.dev, s, p, c.dev, x.dev, st);
+  x.finish();
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
 ts_status ts_sylv_apply_lowp(ts_ctx* ctx, const ts_op* op, int precision, const float* X, float* Y,
                              ts_stream stream) {
   if (!ctx) return TS_ERR_ARG;
@@ -363,6 +443,7 @@ ts_status ts_sylv_apply_lowp(ts_ctx* ctx, const ts_op* op, int precision, const 
   TS_REQUIRE(precision == TS_MIXED_FP32 || precision == TS_MIXED_TF32 || precision == TS_MIXED_BF16,
              "ts_sylv_apply_lowp: precision must be a mixed precision");
   TS_REQUIRE(is_device_ptr(X) && is_device_ptr(Y), "ts_sylv_apply_lowp: X and Y must be device memory");
+  if (op->sp) throw Error{TS_ERR_UNSUPPORTED, "ts_sylv_apply_lowp: sparse operators run in FP64 only"};
   TS_CUDA(cudaSetDevice(ctx->device));
   apply_low(ctx, const_cast<ts_op*>(op), precision, X, Y, reinterpret_cast<cudaStream_t>(stream));
   return TS_OK;

@@ -32,6 +32,14 @@ void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mod
 // Algorithmic FLOPs of one fused slice-GEMM launch (8 per complex, 2 per real multiply-add).
 double gemm_flops(int M, int N, int L1, int L2, int K, int nyq);
 
+// Sparse operator: Y = M(X) (real FP64 in and out).
+void apply_sparse_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, cudaStream_t st);
+void op_prepare_csr(ts_op* op, const int* rowptr, const int* col, const double* val, cudaStream_t st);
+ts_status tba_entry(ts_ctx* ctx, const ts_op* op, const double* C, double* X, const ts_solve_opts* opts,
+                    ts_solve_info* info, ts_stream stream);
+void t_bartels_stewart_dev(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p, const double* C,
+                           double* X, cudaStream_t st);
+
 // Low-precision apply used by the inner solve of mixed precision: X, Y FP32.
 void apply_low(ts_ctx* ctx, ts_op* op, int precision, const float* X, float* Y, cudaStream_t st);
 

@@ -72,7 +72,7 @@ struct KernelTimer {
 
 }  // namespace ts
 
-namespace ts { struct TcOperands; }
+namespace ts { struct TcOperands; struct SparseOp; }
 
 struct ts_ctx {
   int device = 0;
@@ -93,6 +93,10 @@ struct ts_op {
   float2* Bh32 = nullptr;
   ts::TcOperands* tc = nullptr;  // tensor-core operand planes (BF16 or TF32), made on first use
   int tc_prec = -1;
+  ts::SparseOp* sp = nullptr;    // sparse A (union CSR pattern + Fourier slices of the values)
+  double2* Bh_row = nullptr;     // K slices of B_k, row-major (row kernels of TBAS)
+  double2* schurT = nullptr;     // K slices: complex Schur factor T of B_k
+  double2* schurQ = nullptr;     // K slices: Schur vectors Q of B_k
 };
 
 namespace ts {

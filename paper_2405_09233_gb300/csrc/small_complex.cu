@@ -1,0 +1,398 @@
+// Small dense complex FP64 kernels for the projected equation of TBAS and for t-Bartels-Stewart
+// (§4, Algorithm 5; §5.2, the projected equation H_m*Y - Y*B = C1).
+//
+// Per Fourier slice the tensor equation is the matrix Sylvester equation H_k Y_k - Y_k B_k = F_k.
+// It is solved by the Hessenberg-Schur form of Bartels-Stewart: only B_k (s x s) is reduced to
+// complex Schur form B_k = Q T Q^H (one warp per slice: Givens reduction to Hessenberg form, then
+// implicitly shifted single-shift QR with Wilkinson shifts and deflation); with Z = Y Q and G = F Q,
+// column j of Z solves (H_k - t_jj I) z_j = g_j + sum_{i<j} t_ij z_i.  The shifted matrices are
+// factorised in parallel (one CTA per (slice, j), LU with partial pivoting restricted to the lower
+// bandwidth, which is s for the block Hessenberg H_m of TBA and n-1 for a general matrix), then one
+// CTA per slice sweeps j in order.  All matrices are column-major complex (double2).
+#include "internal.cuh"
+#include "reduce.cuh"
+#include "tba.cuh"
+
+namespace ts {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  // Smith's algorithm
+  if (fabs(b.x) >= fabs(b.y)) {
+    const double r = b.y / b.x, d = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  }
+  const double r = b.x / b.y, d = b.y + b.x * r;
+  return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// Givens rotation G = [[c, s], [-conj(s), c]] (c real) with G [a; b] = [r; 0].
+__device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2& s) {
+  const double na = cabs2(a), nb = cabs2(b);
+  if (nb == 0.0) {
+    c = 1.0;
+    s = make_double2(0.0, 0.0);
+    return;
+  }
+  if (na == 0.0) {
+    c = 0.0;
+    s = cscale(cconj(b), 1.0 / nb);   // G [0; b] = [s b; c b] = [|b|; 0]
+    return;
+  }
+  const double nr = hypot(na, nb);
+  c = na / nr;
+  const double2 ua = cscale(a, 1.0 / na);  // a / |a|
+  s = cscale(cmul(ua, cconj(b)), 1.0 / nr);
+}
+
+// Rows (i, i+1), columns [c0, s):  row_i' = c row_i + s row_{i+1};  row_{i+1}' = -conj(s) row_i + c row_{i+1}
+__device__ void rot_rows(double2* T, int ld, int i, int c0, int c1, double c, double2 s) {
+  for (int q = c0 + (int)(threadIdx.x & 31); q < c1; q += 32) {
+    const double2 a = T[i + (long long)ld * q], b = T[i + 1 + (long long)ld * q];
+    T[i + (long long)ld * q] = cadd(cscale(a, c), cmul(s, b));
+    T[i + 1 + (long long)ld * q] = csub(cscale(b, c), cmul(cconj(s), a));
+  }
+  __syncwarp();
+}
+// Columns (i, i+1), rows [r0, r1): multiply on the right by G^H:
+//   col_i' = c col_i + conj(s) col_{i+1};  col_{i+1}' = -s col_i + c col_{i+1}
+__device__ void rot_cols(double2* T, int ld, int i, int r0, int r1, double c, double2 s) {
+  for (int r = r0 + (int)(threadIdx.x & 31); r < r1; r += 32) {
+    const double2 a = T[r + (long long)ld * i], b = T[r + (long long)ld * (i + 1)];
+    T[r + (long long)ld * i] = cadd(cscale(a, c), cmul(cconj(s), b));
+    T[r + (long long)ld * (i + 1)] = csub(cscale(b, c), cmul(s, a));
+  }
+  __syncwarp();
+}
+
+// Complex Schur form, one warp per matrix: B (s x s) = Q T Q^H, T upper triangular.
+// In: T holds B.  Out: T, Q.  err bit 1 on failure to converge.
+__global__ void k_schur_small(double2* __restrict__ Tall, double2* __restrict__ Qall, int s, int* err) {
+  double2* T = Tall + (long long)blockIdx.x * s * s;
+  double2* Q = Qall + (long long)blockIdx.x * s * s;
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < s * s; e += 32) Q[e] = make_double2((e % s) == (e / s) ? 1.0 : 0.0, 0.0);
+  __syncwarp();
+  // Hessenberg reduction by Givens rotations.
+  for (int c = 0; c + 2 < s; ++c) {
+    for (int r = s - 1; r >= c + 2; --r) {
+      double cs;
+      double2 sn;
+      givens(T[r - 1 + (long long)s * c], T[r + (long long)s * c], cs, sn);
+      rot_rows(T, s, r - 1, c, s, cs, sn);
+      rot_cols(T, s, r - 1, 0, s, cs, sn);
+      rot_cols(Q, s, r - 1, 0, s, cs, sn);
+      if (lane == 0) T[r + (long long)s * c] = make_double2(0.0, 0.0);
+      __syncwarp();
+    }
+  }
+  // Shifted QR on the active window [lo, hi].
+  const double eps = 2.220446049250313e-16;
+  int hi = s - 1, iter = 0, since = 0;
+  const int max_iter = 60 * s + 60;
+  while (hi > 0) {
+    if (iter++ > max_iter) {
+      if (lane == 0) atomicOr(err, 1);
+      break;
+    }
+    int lo = hi;
+    while (lo > 0) {
+      const double2 sub = T[lo + (long long)s * (lo - 1)];
+      double scale = cabs2(T[lo + (long long)s * lo]) + cabs2(T[lo - 1 + (long long)s * (lo - 1)]);
+      if (scale == 0.0) scale = 1.0;
+      if (cabs2(sub) <= eps * scale) {
+        if (lane == 0) T[lo + (long long)s * (lo - 1)] = make_double2(0.0, 0.0);
+        __syncwarp();
+        break;
+      }
+      --lo;
+    }
+    if (lo == hi) {
+      --hi;
+      since = 0;
+      continue;
+    }
+    // Wilkinson shift from the trailing 2 x 2 block of the window.
+    const double2 a = T[hi - 1 + (long long)s * (hi - 1)], b = T[hi - 1 + (long long)s * hi];
+    const double2 cc = T[hi + (long long)s * (hi - 1)], d = T[hi + (long long)s * hi];
+    double2 mu;
+    ++since;
+    if (since % 11 == 10) {
+      // exceptional shift
+      mu = cadd(d, make_double2(cabs2(cc), 0.0));
+    } else {
+      const double2 half = cscale(csub(a, d), 0.5);
+      const double2 disc2 = cadd(cmul(half, half), cmul(b, cc));
+      // principal square root of disc2
+      const double r = cabs2(disc2);
+      double2 sq = make_double2(sqrt(0.5 * (r + disc2.x)), 0.0);
+      const double im = sqrt(fmax(0.0, 0.5 * (r - disc2.x)));
+      sq.y = disc2.y < 0.0 ? -im : im;
+      const double2 m1 = cadd(cadd(d, half), sq), m2 = csub(cadd(d, half), sq);
+      mu = cabs2(csub(m1, d)) <= cabs2(csub(m2, d)) ? m1 : m2;
+    }
+    double2 x = csub(T[lo + (long long)s * lo], mu), y = T[lo + 1 + (long long)s * lo];
+    for (int i = lo; i < hi; ++i) {
+      double cs;
+      double2 sn;
+      givens(x, y, cs, sn);
+      const int c0 = i > lo ? i - 1 : lo;
+      rot_rows(T, s, i, c0, s, cs, sn);
+      const int r1 = (i + 3 <= hi + 1) ? i + 3 : hi + 1;
+      rot_cols(T, s, i, 0, r1, cs, sn);
+      rot_cols(Q, s, i, 0, s, cs, sn);
+      if (i > lo) {
+        if (lane == 0) T[i + 1 + (long long)s * (i - 1)] = make_double2(0.0, 0.0);
+        __syncwarp();
+      }
+      if (i + 1 < hi) {
+        x = T[i + 1 + (long long)s * i];
+        y = T[i + 2 + (long long)s * i];
+      }
+    }
+  }
+  for (int e = lane; e < s * s; e += 32)
+    if ((e % s) > (e / s)) T[e] = make_double2(0.0, 0.0);
+}
+
+// LU with partial pivoting of M = H_k - t_jj I, lower bandwidth bw, one CTA per (j, k).
+// LU[(k*s + j)] is an N x N column-major factor; piv holds the row chosen at each step.
+__global__ void __launch_bounds__(256) k_shifted_lu(const double2* __restrict__ H, long long sH,
+                                                    const double2* __restrict__ T, double2* __restrict__ LU,
+                                                    int* __restrict__ piv, int N, int bw, int s, int* err) {
+  const int j = blockIdx.x, k = blockIdx.y;
+  const double2* Hk = H + (long long)k * sH;
+  const double2 shift = T[(long long)k * s * s + (long long)j * s + j];
+  double2* M = LU + ((long long)k * s + j) * N * N;
+  int* pv = piv + ((long long)k * s + j) * N;
+  for (long long e = threadIdx.x; e < (long long)N * N; e += blockDim.x) {
+    double2 v = Hk[e];
+    if ((e % N) == (e / N)) v = csub(v, shift);
+    M[e] = v;
+  }
+  __shared__ int sp;
+  __shared__ double sbest[256];
+  __shared__ int sidx[256];
+  __syncthreads();
+  // max-norm of M: a pivot below N * 1e-14 * max|M| marks a (numerically) singular shift
+  double mx = 0.0;
+  for (long long e = threadIdx.x; e < (long long)N * N; e += blockDim.x) mx = fmax(mx, cabs2(M[e]));
+  sbest[threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m0 = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) m0 = fmax(m0, sbest[t]);
+    sbest[0] = m0;
+  }
+  __syncthreads();
+  const double tiny = 1e-14 * N * sbest[0];
+  __syncthreads();
+  for (int c = 0; c < N; ++c) {
+    const int rmax = (c + bw < N - 1) ? c + bw : N - 1;
+    // pivot search over rows c..rmax
+    double best = -1.0;
+    int bi = c;
+    for (int r = c + (int)threadIdx.x; r <= rmax; r += blockDim.x) {
+      const double v = cabs2(M[r + (long long)N * c]);
+      if (v > best) {
+        best = v;
+        bi = r;
+      }
+    }
+    sbest[threadIdx.x] = best;
+    sidx[threadIdx.x] = bi;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b0 = -1.0;
+      int i0 = c;
+      for (int t = 0; t < (int)blockDim.x; ++t)
+        if (sbest[t] > b0 || (sbest[t] == b0 && sidx[t] < i0)) {
+          b0 = sbest[t];
+          i0 = sidx[t];
+        }
+      sp = i0;
+      pv[c] = i0;
+      if (b0 <= tiny) atomicOr(err, 2);
+    }
+    __syncthreads();
+    const int p = sp;
+    if (p != c) {
+      for (int q = c + (int)threadIdx.x; q < N; q += blockDim.x) {
+        const double2 t0 = M[c + (long long)N * q];
+        M[c + (long long)N * q] = M[p + (long long)N * q];
+        M[p + (long long)N * q] = t0;
+      }
+    }
+    __syncthreads();
+    const double2 dinv = cdiv(make_double2(1.0, 0.0), M[c + (long long)N * c]);
+    const int nr = rmax - c;
+    for (int r = c + 1 + (int)threadIdx.x; r <= rmax; r += blockDim.x)
+      M[r + (long long)N * c] = cmul(M[r + (long long)N * c], dinv);
+    __syncthreads();
+    const long long work = (long long)nr * (N - c - 1);
+    for (long long w = threadIdx.x; w < work; w += blockDim.x) {
+      const int r = c + 1 + (int)(w % nr);
+      const int q = c + 1 + (int)(w / nr);
+      M[r + (long long)N * q] = csub(M[r + (long long)N * q], cmul(M[r + (long long)N * c], M[c + (long long)N * q]));
+    }
+    __syncthreads();
+  }
+}
+
+// One CTA per slice: Z[:, j] for j = 0..s-1 in order, using the factors of k_shifted_lu.
+// G (N x s) is the transformed right-hand side F Q; T the Schur factor of B_k.
+__global__ void __launch_bounds__(256) k_hs_solve(const double2* __restrict__ LU, const int* __restrict__ piv,
+                                                  const double2* __restrict__ G, const double2* __restrict__ T,
+                                                  double2* __restrict__ Z, int N, int bw, int s) {
+  const int k = blockIdx.x;
+  const double2* Gk = G + (long long)k * N * s;
+  const double2* Tk = T + (long long)k * s * s;
+  double2* Zk = Z + (long long)k * N * s;
+  extern __shared__ double2 rhs[];  // N entries
+  for (int j = 0; j < s; ++j) {
+    const double2* M = LU + ((long long)k * s + j) * N * N;
+    const int* pv = piv + ((long long)k * s + j) * N;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      double2 v = Gk[r + (long long)N * j];
+      for (int i = 0; i < j; ++i) v = cadd(v, cmul(Tk[i + (long long)s * j], Zk[r + (long long)N * i]));
+      rhs[r] = v;
+    }
+    __syncthreads();
+    for (int c = 0; c < N; ++c) {        // forward: row interchanges and unit lower factor
+      const int p = pv[c];
+      if (p != c) {
+        if (threadIdx.x == 0) {
+          const double2 t0 = rhs[c];
+          rhs[c] = rhs[p];
+          rhs[p] = t0;
+        }
+        __syncthreads();
+      }
+      const int rmax = (c + bw < N - 1) ? c + bw : N - 1;
+      const double2 rc = rhs[c];
+      for (int r = c + 1 + (int)threadIdx.x; r <= rmax; r += blockDim.x)
+        rhs[r] = csub(rhs[r], cmul(M[r + (long long)N * c], rc));
+      __syncthreads();
+    }
+    for (int c = N - 1; c >= 0; --c) {   // backward: upper factor
+      if (threadIdx.x == 0) rhs[c] = cdiv(rhs[c], M[c + (long long)N * c]);
+      __syncthreads();
+      const double2 zc = rhs[c];
+      for (int r = threadIdx.x; r < c; r += blockDim.x) rhs[r] = csub(rhs[r], cmul(M[r + (long long)N * c], zc));
+      __syncthreads();
+    }
+    for (int r = threadIdx.x; r < N; r += blockDim.x) Zk[r + (long long)N * j] = rhs[r];
+    __syncthreads();
+  }
+}
+
+// C = A * op(B) for small column-major complex matrices per slice: op = none or conjugate
+// transpose.  A: M x L (lda), B: L x Ncol (or Ncol x L when conjugate-transposed).
+__global__ void k_small_gemm(const double2* __restrict__ A, long long sA, int lda, const double2* __restrict__ B,
+                             long long sB, int ldb, int transB, double2* __restrict__ C, long long sC, int ldc, int M,
+                             int L, int Ncol, int accumulate) {
+  const int k = blockIdx.y;
+  const double2* Ak = A + (long long)k * sA;
+  const double2* Bk = B + (long long)k * sB;
+  double2* Ck = C + (long long)k * sC;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)M * Ncol;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M), j = (int)(e / M);
+    double2 acc = accumulate ? Ck[i + (long long)ldc * j] : make_double2(0.0, 0.0);
+    for (int l = 0; l < L; ++l) {
+      const double2 b = transB ? cconj(Bk[j + (long long)ldb * l]) : Bk[l + (long long)ldb * j];
+      acc = cadd(acc, cmul(Ak[i + (long long)lda * l], b));
+    }
+    Ck[i + (long long)ldc * j] = acc;
+  }
+}
+
+// Cholesky G = R^H R of a Hermitian positive definite s x s matrix per slice (one warp each).
+// R is written upper triangular (zeros below).  err bit 4 on a non-positive pivot.
+__global__ void k_cholesky(const double2* __restrict__ Gall, double2* __restrict__ Rall, int s, int* err,
+                           int* fail_slice) {
+  const double2* G = Gall + (long long)blockIdx.x * s * s;
+  double2* R = Rall + (long long)blockIdx.x * s * s;
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < s * s; e += 32) R[e] = make_double2(0.0, 0.0);
+  __syncwarp();
+  for (int j = 0; j < s; ++j) {
+    // r_jj = sqrt(g_jj - sum_{i<j} |r_ij|^2)
+    double d = G[j + (long long)s * j].x;
+    for (int i = 0; i < j; ++i) {
+      const double2 r = R[i + (long long)s * j];
+      d -= r.x * r.x + r.y * r.y;
+    }
+    if (!(d > 0.0)) {
+      if (lane == 0) {
+        atomicOr(err, 4);
+        if (fail_slice) fail_slice[blockIdx.x] = 1;
+      }
+      return;
+    }
+    const double rjj = sqrt(d);
+    if (lane == 0) R[j + (long long)s * j] = make_double2(rjj, 0.0);
+    // r_jq = (g_jq - sum_{i<j} conj(r_ij) r_iq) / r_jj for q > j
+    for (int q = j + 1 + lane; q < s; q += 32) {
+      double2 v = G[j + (long long)s * q];
+      for (int i = 0; i < j; ++i) v = csub(v, cmulc(R[i + (long long)s * j], R[i + (long long)s * q]));
+      R[j + (long long)s * q] = cscale(v, 1.0 / rjj);
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+void schur_small(double2* T, double2* Q, int s, int count, int* err, cudaStream_t st) {
+  k_schur_small<<<count, 32, 0, st>>>(T, Q, s, err);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void shifted_lu(const double2* H, long long sH, const double2* T, double2* LU, int* piv, int N, int bw, int s, int K,
+                int* err, cudaStream_t st) {
+  k_shifted_lu<<<dim3(s, K), 256, 0, st>>>(H, sH, T, LU, piv, N, bw, s, err);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void hs_solve(const double2* LU, const int* piv, const double2* G, const double2* T, double2* Z, int N, int bw, int s,
+              int K, cudaStream_t st) {
+  const size_t smem = sizeof(double2) * (size_t)N;
+  TS_REQUIRE(smem <= 200 * 1024, "projected system too large");
+  if (smem > 48 * 1024) TS_CUDA(cudaFuncSetAttribute(k_hs_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_hs_solve<<<K, 256, smem, st>>>(LU, piv, G, T, Z, N, bw, s);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void small_gemm(const double2* A, long long sA, int lda, const double2* B, long long sB, int ldb, bool transB, double2* C,
+                long long sC, int ldc, int M, int L, int Ncol, int K, bool accumulate, cudaStream_t st) {
+  long long tot = (long long)M * Ncol;
+  int g = (int)((tot + 255) / 256);
+  if (g > 1024) g = 1024;
+  k_small_gemm<<<dim3(g, K), 256, 0, st>>>(A, sA, lda, B, sB, ldb, transB ? 1 : 0, C, sC, ldc, M, L, Ncol,
+                                           accumulate ? 1 : 0);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void cholesky_small(const double2* G, double2* R, int s, int K, int* err, int* fail_slice, cudaStream_t st) {
+  k_cholesky<<<K, 32, 0, st>>>(G, R, s, err, fail_slice);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+}  // namespace ts

@@ -184,6 +184,8 @@ ts_status solve_entry(ts_ctx* ctx, const ts_op* cop, const double* C, double* X,
              "solve: negative history capacity");
   if (method == 1 && o.precision != TS_FP64)
     throw Error{TS_ERR_UNSUPPORTED, "tFOM runs in FP64 only"};
+  if (op->sp && o.precision != TS_FP64)
+    throw Error{TS_ERR_UNSUPPORTED, "sparse operators run in FP64 only"};
   TS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   ts_solve_info info{};

@@ -1,0 +1,798 @@
+// Tubal Block Arnoldi (Algorithm 7) and TBAS(m) (Algorithm 8), and t-Bartels-Stewart
+// (Algorithm 5), on one GB300 in FP64.
+//
+// Everything runs in the Fourier domain (Eq. (5)): the T-product decouples into K = p/2 + 1
+// independent complex slices, the T-transpose becomes the conjugate transpose of each slice, and
+// a tube becomes one complex number per slice.  So, slice by slice:
+//   * Tubal-QR (Algorithm 6) of an n x s block is the thin QR with a positive real diagonal --
+//     unique, whatever algorithm computes it.  It is computed by CholeskyQR2 (Gram matrix, small
+//     Cholesky, triangular multiply, twice), which keeps the work in GEMM-shaped passes.
+//   * The block MGS step H_ij = V_i^H W, W -= V_i H_ij is a tall-skinny Gram and an update.
+//   * The projected equation H_m Y - Y B = C1 (Eq. (46)) is solved per slice by Hessenberg-Schur
+//     (small_complex.cu) and X += V_m Y.
+// Block vectors are stored slice by slice as row-major n x s complex matrices, so that a warp
+// reading one row of V reads s contiguous entries: the sparse A_k V product (one warp per row,
+// union CSR pattern of all frontal slices, complex values per slice), the Gram and the updates are
+// all coalesced.  Norms use Parseval: ||X||^2 = (1/p) sum_k w_k ||X_k||^2, w = 1 for k = 0 and
+// k = p/2, 2 otherwise.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+#include "internal.cuh"
+#include "apply.cuh"
+#include "reduce.cuh"
+#include "tba.cuh"
+
+namespace ts {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a*b + c
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {  // conj(a)*b + c
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double slice_weight(int k, int p) {
+  return (k == 0 || (p % 2 == 0 && k == p / 2)) ? 1.0 : 2.0;
+}
+
+constexpr int kMaxS = 64;           // block width supported by the row kernels
+constexpr int kLanesT = kMaxS / 32;
+
+struct RowsArgs {
+  const int* rowptr;      // sparse pattern (nullptr: dense A_k column-major in Ad)
+  const int* col;
+  const double2* vals;    // K x nnz
+  const double2* Ad;      // K x n x n column-major (dense operator)
+  long long nnz;
+  const double2* V;       // K x n x s row-major
+  const double2* Brow;    // K x s x s row-major (B_k)
+  const double2* C;       // K x n x s row-major (residual mode)
+  double2* Out;           // K x n x s row-major
+  double* partials;       // residual mode: one per block
+  int n, s, K, p;
+};
+
+// MODE 0: Out = A_k V_k.  MODE 1: Out = A_k V_k - V_k B_k.  MODE 2: Out = C_k - (A_k V_k - V_k B_k)
+// and partials of the Parseval-weighted squared norm.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
+  const int k = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long ns = (long long)a.n * a.s;
+  const double2* Vk = a.V + k * ns;
+  double local = 0.0;
+  for (int i = blockIdx.x * 8 + warp; i < a.n; i += gridDim.x * 8) {
+    double2 acc[kLanesT];
+#pragma unroll
+    for (int t = 0; t < kLanesT; ++t) acc[t] = make_double2(0.0, 0.0);
+    if (a.rowptr) {
+      const double2* vk = a.vals + (long long)k * a.nnz;
+      for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+        const double2 av = vk[q];
+        const double2* vr = Vk + (long long)a.col[q] * a.s;
+#pragma unroll
+        for (int t = 0; t < kLanesT; ++t) {
+          const int j = lane + 32 * t;
+          if (j < a.s) acc[t] = cfma(av, vr[j], acc[t]);
+        }
+      }
+    } else {
+      const double2* Ak = a.Ad + (long long)k * a.n * a.n;
+      for (int l = 0; l < a.n; ++l) {
+        const double2 av = Ak[(long long)l * a.n + i];
+        const double2* vr = Vk + (long long)l * a.s;
+#pragma unroll
+        for (int t = 0; t < kLanesT; ++t) {
+          const int j = lane + 32 * t;
+          if (j < a.s) acc[t] = cfma(av, vr[j], acc[t]);
+        }
+      }
+    }
+    if (MODE >= 1) {
+      const double2* Bk = a.Brow + (long long)k * a.s * a.s;
+      const double2* xr = Vk + (long long)i * a.s;
+      for (int l = 0; l < a.s; ++l) {
+        const double2 xv = xr[l];
+        const double2 nx = make_double2(-xv.x, -xv.y);
+#pragma unroll
+        for (int t = 0; t < kLanesT; ++t) {
+          const int j = lane + 32 * t;
+          if (j < a.s) acc[t] = cfma(nx, Bk[(long long)l * a.s + j], acc[t]);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kLanesT; ++t) {
+      const int j = lane + 32 * t;
+      if (j < a.s) {
+        double2 v = acc[t];
+        const long long o = k * ns + (long long)i * a.s + j;
+        if (MODE == 2) {
+          const double2 c = a.C[o];
+          v = make_double2(c.x - v.x, c.y - v.y);
+          local += v.x * v.x + v.y * v.y;
+        }
+        a.Out[o] = v;
+      }
+    }
+  }
+  if (MODE == 2) {
+    const double tot = block_sum(local) * slice_weight(k, a.p) / a.p;
+    if (threadIdx.x == 0) a.partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  }
+}
+
+// Partial Gram matrices G_k = V_k^H W_k over row chunks: partials[(k*chunks + c)*s*s + a + s*b].
+__global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, const double2* __restrict__ W, int n, int s,
+                                              int rows_per_chunk, double2* __restrict__ partials) {
+  const int k = blockIdx.y, chunk = blockIdx.x, chunks = gridDim.x;
+  __shared__ double2 sv[16][kMaxS + 1], sw[16][kMaxS + 1];
+  const long long ns = (long long)n * s;
+  const double2* Vk = V + k * ns;
+  const double2* Wk = W + k * ns;
+  const int ss = s * s;
+  constexpr int kPer = (kMaxS * kMaxS) / 256;
+  double2 acc[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) acc[q] = make_double2(0.0, 0.0);
+  const int r_begin = chunk * rows_per_chunk;
+  const int r_end = min(n, r_begin + rows_per_chunk);
+  for (int r0 = r_begin; r0 < r_end; r0 += 16) {
+    for (int e = threadIdx.x; e < 16 * s; e += blockDim.x) {
+      const int rr = e / s, cc = e % s;
+      const int r = r0 + rr;
+      double2 v = make_double2(0.0, 0.0), w = v;
+      if (r < r_end) {
+        v = Vk[(long long)r * s + cc];
+        w = Wk[(long long)r * s + cc];
+      }
+      sv[rr][cc] = v;
+      sw[rr][cc] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int e = threadIdx.x + 256 * q;
+      if (e < ss) {
+        const int ai = e % s, bi = e / s;
+        double2 x = acc[q];
+#pragma unroll 4
+        for (int rr = 0; rr < 16; ++rr) x = cfmac(sv[rr][ai], sw[rr][bi], x);
+        acc[q] = x;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    if (e < ss) partials[((long long)k * chunks + chunk) * ss + e] = acc[q];
+  }
+}
+
+// out_k (column-major, leading dimension ldo) = sum over chunks of the partial Grams (fixed order).
+__global__ void k_gram_reduce(const double2* __restrict__ partials, int chunks, int s, double2* __restrict__ out,
+                              long long sOut, int ldo) {
+  const int k = blockIdx.x;
+  const int ss = s * s;
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = 0; c < chunks; ++c) {
+      const double2 v = partials[((long long)k * chunks + c) * ss + e];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    out[(long long)k * sOut + (e % s) + (long long)ldo * (e / s)] = acc;
+  }
+}
+
+// Out_k = (accumulate ? Out_k : 0) + alpha * In_k M_k, row by row (in place allowed), M_k an
+// s x s column-major block with leading dimension ldm.
+__global__ void __launch_bounds__(256) k_rows_mm(const double2* In, double2* Out, const double2* __restrict__ M,
+                                                 long long sM, int ldm, int n, int s, double alpha, int accumulate) {
+  const int k = blockIdx.y;
+  extern __shared__ double2 sm[];   // s x (s + 1), row-major copy of M_k
+  const int lds = s + 1;
+  const double2* Mk = M + (long long)k * sM;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int ai = e % s, bi = e / s;
+    sm[ai * lds + bi] = Mk[ai + (long long)ldm * bi];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long ns = (long long)n * s;
+  for (int i = blockIdx.x * 8 + warp; i < n; i += gridDim.x * 8) {
+    const long long ro = k * ns + (long long)i * s;
+    double2 x[kLanesT], y[kLanesT];
+#pragma unroll
+    for (int t = 0; t < kLanesT; ++t) {
+      const int j = lane + 32 * t;
+      x[t] = j < s ? In[ro + j] : make_double2(0.0, 0.0);
+      y[t] = make_double2(0.0, 0.0);
+    }
+    for (int ai = 0; ai < s; ++ai) {
+      double2 xa;
+      xa.x = __shfl_sync(0xffffffffu, x[ai >> 5].x, ai & 31);
+      xa.y = __shfl_sync(0xffffffffu, x[ai >> 5].y, ai & 31);
+#pragma unroll
+      for (int t = 0; t < kLanesT; ++t) {
+        const int j = lane + 32 * t;
+        if (j < s) y[t] = cfma(xa, sm[ai * lds + j], y[t]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kLanesT; ++t) {
+      const int j = lane + 32 * t;
+      if (j < s) {
+        double2 v = make_double2(alpha * y[t].x, alpha * y[t].y);
+        if (accumulate) {
+          const double2 o = Out[ro + j];
+          v.x += o.x;
+          v.y += o.y;
+        }
+        Out[ro + j] = v;
+      }
+    }
+  }
+}
+
+// Inverse of an upper triangular s x s matrix per slice (one warp; lanes over columns).
+__global__ void k_triinv(const double2* __restrict__ Rall, double2* __restrict__ Xall, int s) {
+  const double2* R = Rall + (long long)blockIdx.x * s * s;
+  double2* X = Xall + (long long)blockIdx.x * s * s;
+  for (int b = threadIdx.x; b < s; b += 32) {
+    for (int a = 0; a < s; ++a) X[a + (long long)s * b] = make_double2(0.0, 0.0);
+    // X[b][b] = 1 / R[b][b] (R has a real positive diagonal)
+    X[b + (long long)s * b] = make_double2(1.0 / R[b + (long long)s * b].x, 0.0);
+    for (int a = b - 1; a >= 0; --a) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int c = a + 1; c <= b; ++c) acc = cfma(R[a + (long long)s * c], X[c + (long long)s * b], acc);
+      const double inv = 1.0 / R[a + (long long)s * a].x;
+      X[a + (long long)s * b] = make_double2(-acc.x * inv, -acc.y * inv);
+    }
+  }
+}
+
+// Column-major spectral [k][j][i] <-> row-major [k][i][j], 32 x 32 tiles.
+__global__ void k_spec_transpose(const double2* __restrict__ in, double2* __restrict__ out, int rows, int cols) {
+  // in: K x (cols x rows) with rows fastest; out: K x (rows x cols) with cols fastest
+  __shared__ double2 tile[32][33];
+  const int k = blockIdx.z;
+  const long long off = (long long)k * rows * cols;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int r = r0 + threadIdx.x, c = c0 + q;
+    if (r < rows && c < cols) tile[q][threadIdx.x] = in[off + (long long)c * rows + r];
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int r = r0 + q, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) out[off + (long long)r * cols + c] = tile[threadIdx.x][q];
+  }
+}
+
+// sum_k w_k/p * (squared Frobenius norm of the s x s block k of E) -> out[0]; traces of G -> out.
+__global__ void k_weighted_fro(const double2* __restrict__ E, int s, int K, int p, double* out) {
+  double local = 0.0;
+  for (int e = threadIdx.x; e < K * s * s; e += blockDim.x) {
+    const int k = e / (s * s);
+    const double2 v = E[e];
+    local += (v.x * v.x + v.y * v.y) * slice_weight(k, p) / p;
+  }
+  const double tot = block_sum(local);
+  if (threadIdx.x == 0) out[0] = tot;
+}
+
+__global__ void k_weighted_trace(const double2* __restrict__ G, int s, int K, int p, double* out) {
+  double local = 0.0;
+  for (int e = threadIdx.x; e < K * s; e += blockDim.x) {
+    const int k = e / s, d = e % s;
+    local += G[(long long)k * s * s + d + (long long)s * d].x * slice_weight(k, p) / p;
+  }
+  const double tot = block_sum(local);
+  if (threadIdx.x == 0) out[0] = tot;
+}
+
+__global__ void k_fill_c1(const double2* __restrict__ H0, double2* __restrict__ C1, int s, int N, int K) {
+  // C1_k = [H0_k; 0] (N x s column-major)
+  const long long tot = (long long)K * N * s;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / ((long long)N * s));
+    const long long r = e % ((long long)N * s);
+    const int i = (int)(r % N), j = (int)(r / N);
+    C1[e] = i < s ? H0[(long long)k * s * s + i + (long long)s * j] : make_double2(0.0, 0.0);
+  }
+}
+
+// B_k (column-major) -> row-major copy.
+__global__ void k_row_major_small(const double2* __restrict__ B, double2* __restrict__ Br, int s, int K) {
+  const long long tot = (long long)K * s * s;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / ((long long)s * s));
+    const long long r = e % ((long long)s * s);
+    const int row = (int)(r / s), colj = (int)(r % s);
+    Br[e] = B[(long long)k * s * s + row + (long long)s * colj];
+  }
+}
+
+int grid1d(long long work) {
+  long long g = (work + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  return (int)(g < 1 ? 1 : g);
+}
+
+struct TbaWork {
+  int n, s, p, K, m;
+  long long blk;            // K * n * s
+  double2* V;               // (m + 1) blocks
+  double2* X;               // spectral X, row-major
+  double2* C;               // spectral C, row-major
+  double2* R;               // spectral residual
+  double2* tmp;             // column-major spectral scratch
+  double2* Hm;              // K x (ms x ms) column-major
+  double2* H0;              // K x s x s
+  double2* Hlast;           // K x s x s
+  double2* G;               // K x s x s (Gram / Cholesky scratch)
+  double2* R1;              // K x s x s
+  double2* Rinv;            // K x s x s
+  double2* R2;              // K x s x s
+  double2* gram_part;       // partial Grams
+  int chunks, rows_per_chunk;
+  double2* LU;              // K x s x N x N
+  int* piv;                 // K x s x N
+  double2* Gp;              // K x N x s
+  double2* Z;               // K x N x s
+  double2* Y;               // K x N x s
+  double2* E;               // K x s x s
+  double* P;                // kRedBlocks partials
+  double* sc;               // scalars
+  int* err;                 // error bits
+};
+
+}  // namespace
+
+void SparseOp::release() {
+  cudaFree(rowptr);
+  cudaFree(col);
+  cudaFree(vals);
+  rowptr = col = nullptr;
+  vals = nullptr;
+}
+
+void ensure_b_schur(ts_ctx* ctx, ts_op* op, cudaStream_t st) {
+  if (op->schurT) return;
+  const int s = op->s, K = op->K;
+  TS_CUDA(cudaMalloc(&op->schurT, sizeof(double2) * (size_t)K * s * s));
+  TS_CUDA(cudaMalloc(&op->schurQ, sizeof(double2) * (size_t)K * s * s));
+  TS_CUDA(cudaMemcpyAsync(op->schurT, op->Bh, sizeof(double2) * (size_t)K * s * s, cudaMemcpyDeviceToDevice, st));
+  int* err = static_cast<int*>(ctx->ws.get("schur_err", sizeof(int)));
+  TS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  schur_small(op->schurT, op->schurQ, s, K, err, st);
+  int e = 0;
+  TS_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  if (e) {
+    cudaFree(op->schurT);
+    cudaFree(op->schurQ);
+    op->schurT = op->schurQ = nullptr;
+    throw Error{TS_SINGULAR, "complex Schur iteration of B_k did not converge"};
+  }
+}
+
+namespace {
+
+void rows_call(int mode, const ts_op* op, const double2* V, const double2* C, double2* Out, double* partials, int n,
+               int s, int K, int p, cudaStream_t st) {
+  RowsArgs a{};
+  if (op->sp) {
+    a.rowptr = op->sp->rowptr;
+    a.col = op->sp->col;
+    a.vals = op->sp->vals;
+    a.nnz = op->sp->nnz;
+  } else {
+    a.Ad = op->Ah;
+  }
+  a.V = V;
+  a.Brow = op->Bh_row;
+  a.C = C;
+  a.Out = Out;
+  a.partials = partials;
+  a.n = n;
+  a.s = s;
+  a.K = K;
+  a.p = p;
+  if (mode == 2) {
+    const int gx = kRedBlocks / K;
+    TS_CUDA(cudaMemsetAsync(partials, 0, sizeof(double) * kRedBlocks, st));
+    k_sylv_rows<2><<<dim3(gx, K), 256, 0, st>>>(a);
+  } else {
+    const int gx = std::max(1, std::min((n + 7) / 8, 2 * 152 * 4 / K));
+    if (mode == 0) k_sylv_rows<0><<<dim3(gx, K), 256, 0, st>>>(a);
+    else k_sylv_rows<1><<<dim3(gx, K), 256, 0, st>>>(a);
+  }
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void rows_mm(const double2* In, double2* Out, const double2* M, long long sM, int ldm, int n, int s, int K, double alpha,
+             bool accumulate, cudaStream_t st) {
+  const int gx = std::max(1, std::min((n + 7) / 8, 2 * 152 * 4 / K));
+  const size_t smem = sizeof(double2) * (size_t)s * (s + 1);
+  static bool attr = false;
+  if (!attr) {
+    TS_CUDA(cudaFuncSetAttribute(k_rows_mm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(double2) * kMaxS * (kMaxS + 1))));
+    attr = true;
+  }
+  k_rows_mm<<<dim3(gx, K), 256, smem, st>>>(In, Out, M, sM, ldm, n, s, alpha, accumulate ? 1 : 0);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void gram(const TbaWork& w, const double2* V, const double2* W, double2* out, long long sOut, int ldo, cudaStream_t st) {
+  k_gram<<<dim3(w.chunks, w.K), 256, 0, st>>>(V, W, w.n, w.s, w.rows_per_chunk, w.gram_part);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+  k_gram_reduce<<<w.K, 256, 0, st>>>(w.gram_part, w.chunks, w.s, out, sOut, ldo);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void triinv(const double2* R, double2* X, int s, int K, cudaStream_t st) {
+  k_triinv<<<K, 32, 0, st>>>(R, X, s);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+// Tubal-QR of the block W (in place -> Q) by CholeskyQR2; R written to Rout (column-major, ldr).
+// Returns false on a failed Cholesky (rank-deficient block).
+bool tubal_qr(const TbaWork& w, double2* W, double2* Rout, long long sR, int ldr, cudaStream_t st) {
+  const int s = w.s, K = w.K;
+  const long long ss = (long long)s * s;
+  TS_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  gram(w, W, W, w.G, ss, s, st);
+  cholesky_small(w.G, w.R1, s, K, w.err, nullptr, st);
+  triinv(w.R1, w.Rinv, s, K, st);
+  rows_mm(W, W, w.Rinv, ss, s, w.n, s, K, 1.0, false, st);
+  gram(w, W, W, w.G, ss, s, st);
+  cholesky_small(w.G, w.R2, s, K, w.err, nullptr, st);
+  triinv(w.R2, w.Rinv, s, K, st);
+  rows_mm(W, W, w.Rinv, ss, s, w.n, s, K, 1.0, false, st);
+  small_gemm(w.R2, ss, s, w.R1, ss, s, false, Rout, sR, ldr, s, s, s, K, false, st);   // R = R2 R1
+  int e = 0;
+  TS_CUDA(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  return e == 0;
+}
+
+double read_scalar(const double* d, ts_ctx* ctx, cudaStream_t st) {
+  TS_CUDA(cudaMemcpyAsync(ctx->host_scalars + 32, d, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  return ctx->host_scalars[32];
+}
+
+double weighted_trace(const TbaWork& w, const double2* G, ts_ctx* ctx, cudaStream_t st) {
+  k_weighted_trace<<<1, 256, 0, st>>>(G, w.s, w.K, w.p, w.sc);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+  return read_scalar(w.sc, ctx, st);
+}
+
+// R = C - M(X) in the spectral row-major layout; returns ||R||_F (real space).
+double residual(ts_ctx* ctx, const ts_op* op, const TbaWork& w, cudaStream_t st) {
+  rows_call(2, op, w.X, w.C, w.R, w.P, w.n, w.s, w.K, w.p, st);
+  finalize_norm(w.P, w.sc, st);
+  return read_scalar(w.sc, ctx, st);
+}
+
+void to_rows(const double* real, double2* spec_rows, double2* tmp, int n, int s, int p, cudaStream_t st) {
+  const int K = num_slices(p);
+  rfft_tube<double, double2>(real, tmp, (long long)n * s, p, st);
+  k_spec_transpose<<<dim3((n + 31) / 32, (s + 31) / 32, K), dim3(32, 8), 0, st>>>(tmp, spec_rows, n, s);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+void from_rows(const double2* spec_rows, double* real, double2* tmp, int n, int s, int p, cudaStream_t st) {
+  const int K = num_slices(p);
+  // row-major (n x s) is column-major (s x n): transpose with rows = s, cols = n
+  k_spec_transpose<<<dim3((s + 31) / 32, (n + 31) / 32, K), dim3(32, 8), 0, st>>>(spec_rows, tmp, s, n);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+  irfft_tube<double, double2>(tmp, real, (long long)n * s, p, IRFFT_STORE, nullptr, nullptr, st);
+}
+
+void ensure_brow(ts_op* op, cudaStream_t st) {
+  if (op->Bh_row) return;
+  const size_t b = sizeof(double2) * (size_t)op->K * op->s * op->s;
+  TS_CUDA(cudaMalloc(&op->Bh_row, b));
+  k_row_major_small<<<grid1d((long long)op->K * op->s * op->s), 256, 0, st>>>(op->Bh, op->Bh_row, op->s, op->K);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+TbaWork tba_work(ts_ctx* ctx, const ts_op* op, int m) {
+  TbaWork w{};
+  w.n = op->n; w.s = op->s; w.p = op->p; w.K = op->K; w.m = m;
+  const int n = w.n, s = w.s, K = w.K, N = m * s;
+  w.blk = (long long)K * n * s;
+  const size_t blk = sizeof(double2) * (size_t)w.blk, ss = sizeof(double2) * (size_t)K * s * s;
+  auto get = [&](const char* name, size_t bytes) { return ctx->ws.get(name, bytes); };
+  w.V = (double2*)get("tba_V", blk * (m + 1));
+  w.X = (double2*)get("tba_X", blk);
+  w.C = (double2*)get("tba_C", blk);
+  w.R = (double2*)get("tba_R", blk);
+  w.tmp = (double2*)get("tba_tmp", blk);
+  w.Hm = (double2*)get("tba_Hm", sizeof(double2) * (size_t)K * N * N);
+  w.H0 = (double2*)get("tba_H0", ss);
+  w.Hlast = (double2*)get("tba_Hlast", ss);
+  w.G = (double2*)get("tba_G", ss);
+  w.R1 = (double2*)get("tba_R1", ss);
+  w.R2 = (double2*)get("tba_R2", ss);
+  w.Rinv = (double2*)get("tba_Rinv", ss);
+  w.chunks = std::max(1, std::min(2 * 152 / K, (n + 63) / 64));
+  w.rows_per_chunk = (n + w.chunks - 1) / w.chunks;
+  w.gram_part = (double2*)get("tba_gram_part", sizeof(double2) * (size_t)K * w.chunks * s * s);
+  w.LU = (double2*)get("tba_LU", sizeof(double2) * (size_t)K * s * N * N);
+  w.piv = (int*)get("tba_piv", sizeof(int) * (size_t)K * s * N);
+  w.Gp = (double2*)get("tba_Gp", sizeof(double2) * (size_t)K * N * s);
+  w.Z = (double2*)get("tba_Z", sizeof(double2) * (size_t)K * N * s);
+  w.Y = (double2*)get("tba_Y", sizeof(double2) * (size_t)K * N * s);
+  w.E = (double2*)get("tba_E", ss);
+  w.P = (double*)get("tba_P", sizeof(double) * kRedBlocks);
+  w.sc = (double*)get("tba_sc", sizeof(double) * 16);
+  w.err = (int*)get("tba_err", sizeof(int) * 4);
+  return w;
+}
+
+ts_status tbas_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const ts_solve_opts& o, ts_solve_info& info,
+                     cudaStream_t st) {
+  const int n = op->n, s = op->s, p = op->p, K = op->K, m = o.restart;
+  TS_REQUIRE(s <= kMaxS, "ts_tba_solve: block width s must be <= 64");
+  TS_REQUIRE((long long)m * s <= 12000, "ts_tba_solve: m*s too large for the projected solve");
+  ensure_brow(op, st);
+  ensure_b_schur(ctx, op, st);
+  TbaWork w = tba_work(ctx, op, m);
+  const long long ss = (long long)s * s;
+  int hist_len = 0, true_len = 0;
+  auto push_hist = [&](double v) {
+    if (o.history && hist_len < o.history_cap) o.history[hist_len] = v;
+    ++hist_len;
+  };
+  auto push_true = [&](double v) {
+    if (o.true_history && true_len < o.true_history_cap) o.true_history[true_len] = v;
+    ++true_len;
+  };
+  to_rows(C, w.C, w.tmp, n, s, p, st);
+  to_rows(X, w.X, w.tmp, n, s, p, st);
+  // ||C||^2 = (1/p) sum_k w_k trace(C_k^H C_k)  (Parseval)
+  gram(w, w.C, w.C, w.G, ss, s, st);
+  const double normC = std::sqrt(std::max(0.0, weighted_trace(w, w.G, ctx, st)));
+  double res = residual(ctx, op, w, st);
+  info.normC = normC;
+  info.applies_fp64 = 1;
+  push_true(res);
+  double last_est = res;
+  auto finish = [&](ts_status stt) {
+    from_rows(w.X, X, w.tmp, n, s, p, st);
+    TS_CUDA(cudaStreamSynchronize(st));
+    info.history_len = hist_len;
+    info.true_history_len = true_len;
+    info.relres_true = normC > 0 ? res / normC : res;
+    info.relres_est = normC > 0 ? last_est / normC : last_est;
+    return stt;
+  };
+  if (!std::isfinite(res) || !std::isfinite(normC)) return finish(TS_ERR_NONFINITE);
+  if (normC == 0.0 || res <= o.tol * normC) return finish(TS_OK);
+  const long long blk = w.blk;
+  for (int cycle = 0; cycle < o.max_restarts; ++cycle) {
+    // [V_1, H_0] = Tubal-QR(R0)
+    TS_CUDA(cudaMemcpyAsync(w.V, w.R, sizeof(double2) * blk, cudaMemcpyDeviceToDevice, st));
+    if (!tubal_qr(w, w.V, w.H0, ss, s, st)) return finish(TS_BREAKDOWN);
+    const int N = m * s;
+    TS_CUDA(cudaMemsetAsync(w.Hm, 0, sizeof(double2) * (size_t)K * N * N, st));
+    int mm = m;
+    for (int j = 0; j < m; ++j) {
+      double2* Vj = w.V + (long long)j * blk;
+      double2* Wb = w.V + (long long)(j + 1) * blk;
+      rows_call(0, op, Vj, nullptr, Wb, nullptr, n, s, K, p, st);              // W = A * V_j (A, not M)
+      ++info.applies_fp64;
+      for (int i = 0; i <= j; ++i) {                                            // block MGS
+        double2* Vi = w.V + (long long)i * blk;
+        double2* Hij = w.Hm + (long long)i * s + (long long)N * j * s;         // block (i, j) of H_m
+        gram(w, Vi, Wb, Hij, (long long)N * N, N, st);
+        rows_mm(Vi, Wb, Hij, (long long)N * N, N, n, s, K, -1.0, true, st);
+      }
+      gram(w, Wb, Wb, w.G, ss, s, st);
+      const double wn = std::sqrt(std::max(0.0, weighted_trace(w, w.G, ctx, st)));
+      ++info.iters;
+      if (wn <= 1e-13 * res) {                                                   // block breakdown
+        mm = j + 1;
+        TS_CUDA(cudaMemsetAsync(w.Hlast, 0, sizeof(double2) * (size_t)K * ss, st));
+        break;
+      }
+      double2* Hnext = (j + 1 < m) ? w.Hm + (long long)(j + 1) * s + (long long)N * j * s : w.Hlast;
+      const long long sH = (j + 1 < m) ? (long long)N * N : ss;
+      const int ldh = (j + 1 < m) ? N : s;
+      if (!tubal_qr(w, Wb, Hnext, sH, ldh, st)) return finish(TS_BREAKDOWN);
+    }
+    const int Nm = mm * s;
+    // Projected equation per slice: H_m Y - Y B = C1 = [H0; 0] by Hessenberg-Schur.
+    // When the block space broke down early the leading Nm x Nm part of H_m is used.
+    double2* Hproj = w.Hm;
+    long long sHp = (long long)N * N;
+    if (Nm != N) {
+      double2* Hc = (double2*)ctx->ws.get("tba_Hcompact", sizeof(double2) * (size_t)K * Nm * Nm);
+      for (int k = 0; k < K; ++k)
+        TS_CUDA(cudaMemcpy2DAsync(Hc + (long long)k * Nm * Nm, sizeof(double2) * Nm, w.Hm + (long long)k * N * N,
+                                  sizeof(double2) * N, sizeof(double2) * Nm, Nm, cudaMemcpyDeviceToDevice, st));
+      Hproj = Hc;
+      sHp = (long long)Nm * Nm;
+    }
+    k_fill_c1<<<grid1d((long long)K * Nm * s), 256, 0, st>>>(w.H0, w.Z, s, Nm, K);     // Z <- C1
+    count_launch();
+    TS_CUDA(cudaGetLastError());
+    small_gemm(w.Z, (long long)Nm * s, Nm, op->schurQ, ss, s, false, w.Gp, (long long)Nm * s, Nm, Nm, s, s, K, false,
+               st);                                                                     // G = C1 Q
+    TS_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    shifted_lu(Hproj, sHp, op->schurT, w.LU, w.piv, Nm, std::min(s, Nm - 1), s, K, w.err, st);
+    hs_solve(w.LU, w.piv, w.Gp, op->schurT, w.Z, Nm, std::min(s, Nm - 1), s, K, st);
+    small_gemm(w.Z, (long long)Nm * s, Nm, op->schurQ, ss, s, true, w.Y, (long long)Nm * s, Nm, Nm, s, s, K, false,
+               st);                                                                     // Y = Z Q^H
+    // Proposition 5.2 estimate ||H_{m+1,m} E_m Y||
+    small_gemm(w.Hlast, ss, s, w.Y + (long long)(mm - 1) * s, (long long)Nm * s, Nm, false, w.E, ss, s, s, s, s, K,
+               false, st);
+    k_weighted_fro<<<1, 256, 0, st>>>(w.E, s, K, p, w.sc + 4);
+    count_launch();
+    TS_CUDA(cudaGetLastError());
+    // X += V_m Y
+    for (int j = 0; j < mm; ++j)
+      rows_mm(w.V + (long long)j * blk, w.X, w.Y + (long long)j * s, (long long)Nm * s, Nm, n, s, K, 1.0, true, st);
+    int e = 0;
+    TS_CUDA(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    const double est = std::sqrt(std::max(0.0, read_scalar(w.sc + 4, ctx, st)));
+    if (e & 2) return finish(TS_SINGULAR);
+    last_est = est;
+    push_hist(est);
+    ++info.cycles;
+    res = residual(ctx, op, w, st);
+    ++info.applies_fp64;
+    push_true(res);
+    if (!std::isfinite(res)) return finish(TS_ERR_NONFINITE);
+    if (res <= o.tol * normC) return finish(TS_OK);
+  }
+  return finish(TS_NOT_CONVERGED);
+}
+
+}  // namespace
+
+ts_status tba_entry(ts_ctx* ctx, const ts_op* cop, const double* C, double* X, const ts_solve_opts* opts,
+                    ts_solve_info* info_out, ts_stream stream) {
+  ts_op* op = const_cast<ts_op*>(cop);
+  TS_REQUIRE(op && C && X && opts, "ts_tba_solve: null pointer");
+  const ts_solve_opts& o = *opts;
+  TS_REQUIRE(o.restart >= 1 && o.restart <= 256, "ts_tba_solve: restart must be in 1..256");
+  TS_REQUIRE(o.max_restarts >= 1, "ts_tba_solve: max_restarts must be >= 1");
+  TS_REQUIRE(o.tol > 0.0 && std::isfinite(o.tol), "ts_tba_solve: tol must be positive");
+  if (o.precision != TS_FP64) throw Error{TS_ERR_UNSUPPORTED, "TBAS runs in FP64 only"};
+  TS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ts_solve_info info{};
+  TS_CUDA(cudaEventRecord(ctx->ev0, st));
+  const size_t N = (size_t)op->n * op->s * op->p;
+  StagedIn c(ctx, "solve_inC", C, N, st);
+  StagedOut x(ctx, "solve_ioX", X, N, true, st);
+  ts_status s = tbas_solve(ctx, op, c.dev, x.dev, o, info, st);
+  x.finish();
+  TS_CUDA(cudaEventRecord(ctx->ev1, st));
+  TS_CUDA(cudaEventSynchronize(ctx->ev1));
+  float ms = 0.f;
+  TS_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  info.ms_total = ms;
+  if (info_out) *info_out = info;
+  return s;
+}
+
+// Dense operator apply for a sparse op (ts_sylv_apply / residuals): X real -> Y = M(X) real.
+void apply_sparse_f64(ts_ctx* ctx, const ts_op* cop, const double* X, double* Y, cudaStream_t st) {
+  ts_op* op = const_cast<ts_op*>(cop);
+  ensure_brow(op, st);
+  const int n = op->n, s = op->s, p = op->p, K = op->K;
+  TS_REQUIRE(s <= kMaxS, "sparse operator: s must be <= 64");
+  const size_t blk = sizeof(double2) * (size_t)K * n * s;
+  double2* a = (double2*)ctx->ws.get("sp_a", blk);
+  double2* b = (double2*)ctx->ws.get("sp_b", blk);
+  double2* t = (double2*)ctx->ws.get("sp_t", blk);
+  to_rows(X, a, t, n, s, p, st);
+  rows_call(1, op, a, nullptr, b, nullptr, n, s, K, p, st);
+  from_rows(b, Y, t, n, s, p, st);
+}
+
+// t-Bartels-Stewart (Algorithm 5) for small dense A (n x n x p), B (s x s x p): A*X - X*B = C.
+void t_bartels_stewart_dev(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p, const double* C,
+                           double* X, cudaStream_t st) {
+  const int K = num_slices(p);
+  TS_REQUIRE((long long)K * s * n * n <= (1ll << 28), "ts_t_bartels_stewart: K*s*n^2 too large (small solver)");
+  TS_REQUIRE(n <= 12000, "ts_t_bartels_stewart: n too large");
+  double2* Ah = (double2*)ctx->ws.get("bs_Ah", sizeof(double2) * (size_t)K * n * n);
+  double2* T = (double2*)ctx->ws.get("bs_T", sizeof(double2) * (size_t)K * s * s);
+  double2* Q = (double2*)ctx->ws.get("bs_Q", sizeof(double2) * (size_t)K * s * s);
+  double2* Ch = (double2*)ctx->ws.get("bs_Ch", sizeof(double2) * (size_t)K * n * s);
+  double2* Gp = (double2*)ctx->ws.get("bs_G", sizeof(double2) * (size_t)K * n * s);
+  double2* Z = (double2*)ctx->ws.get("bs_Z", sizeof(double2) * (size_t)K * n * s);
+  double2* LU = (double2*)ctx->ws.get("bs_LU", sizeof(double2) * (size_t)K * s * n * n);
+  int* piv = (int*)ctx->ws.get("bs_piv", sizeof(int) * (size_t)K * s * n);
+  int* err = (int*)ctx->ws.get("bs_err", sizeof(int));
+  rfft_tube<double, double2>(A, Ah, (long long)n * n, p, st);
+  rfft_tube<double, double2>(B, T, (long long)s * s, p, st);
+  rfft_tube<double, double2>(C, Ch, (long long)n * s, p, st);
+  TS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  schur_small(T, Q, s, K, err, st);                                                // B_k = Q T Q^H
+  const long long ss = (long long)s * s;
+  small_gemm(Ch, (long long)n * s, n, Q, ss, s, false, Gp, (long long)n * s, n, n, s, s, K, false, st);   // G = C Q
+  shifted_lu(Ah, (long long)n * n, T, LU, piv, n, n - 1, s, K, err, st);           // A_k - t_jj I
+  hs_solve(LU, piv, Gp, T, Z, n, n - 1, s, K, st);
+  small_gemm(Z, (long long)n * s, n, Q, ss, s, true, Ch, (long long)n * s, n, n, s, s, K, false, st);     // X = Z Q^H
+  irfft_tube<double, double2>(Ch, X, (long long)n * s, p, IRFFT_STORE, nullptr, nullptr, st);
+  int e = 0;
+  TS_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  if (e & 1) throw Error{TS_SINGULAR, "complex Schur iteration of B_k did not converge"};
+  if (e & 2) throw Error{TS_SINGULAR, "A_k - lambda I singular for an eigenvalue lambda of B_k (Theorem 2.1)"};
+}
+
+// Sparse operator from p CSR slices (host arrays): union pattern on the host, values' Fourier
+// slices on the device.
+void op_prepare_csr(ts_op* op, const int* rowptr, const int* col, const double* val, cudaStream_t st) {
+  const int n = op->n, p = op->p, K = op->K;
+  std::vector<int> urow(n + 1, 0);
+  std::vector<int> ucol;
+  std::vector<std::vector<int>> rows(n);
+  for (int t = 0; t < p; ++t) {
+    const int* rp = rowptr + (size_t)t * (n + 1);
+    for (int i = 0; i < n; ++i) {
+      TS_REQUIRE(rp[i] <= rp[i + 1], "ts_op_create_csr: row pointers must be non-decreasing");
+      for (int q = rp[i]; q < rp[i + 1]; ++q) {
+        TS_REQUIRE(col[q] >= 0 && col[q] < n, "ts_op_create_csr: column index out of range");
+        rows[i].push_back(col[q]);
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    std::sort(rows[i].begin(), rows[i].end());
+    rows[i].erase(std::unique(rows[i].begin(), rows[i].end()), rows[i].end());
+    urow[i + 1] = urow[i] + (int)rows[i].size();
+    ucol.insert(ucol.end(), rows[i].begin(), rows[i].end());
+  }
+  const int nnz = urow[n];
+  std::vector<double> uval((size_t)p * std::max(nnz, 1), 0.0);
+  for (int t = 0; t < p; ++t) {
+    const int* rp = rowptr + (size_t)t * (n + 1);
+    for (int i = 0; i < n; ++i)
+      for (int q = rp[i]; q < rp[i + 1]; ++q) {
+        const int* b = ucol.data() + urow[i];
+        const int* e = ucol.data() + urow[i + 1];
+        const int pos = (int)(std::lower_bound(b, e, col[q]) - ucol.data());
+        uval[(size_t)t * nnz + pos] += val[q];
+      }
+  }
+  op->sp = new SparseOp();
+  op->sp->nnz = nnz;
+  TS_CUDA(cudaMalloc(&op->sp->rowptr, sizeof(int) * (n + 1)));
+  TS_CUDA(cudaMalloc(&op->sp->col, sizeof(int) * std::max(nnz, 1)));
+  TS_CUDA(cudaMalloc(&op->sp->vals, sizeof(double2) * (size_t)K * std::max(nnz, 1)));
+  double* dval = (double*)op->ctx->ws.get("csr_stage_vals", sizeof(double) * (size_t)p * std::max(nnz, 1));
+  TS_CUDA(cudaMemcpyAsync(op->sp->rowptr, urow.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
+  if (nnz > 0) {
+    TS_CUDA(cudaMemcpyAsync(op->sp->col, ucol.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
+    TS_CUDA(cudaMemcpyAsync(dval, uval.data(), sizeof(double) * (size_t)p * nnz, cudaMemcpyHostToDevice, st));
+    rfft_tube<double, double2>(dval, op->sp->vals, nnz, p, st);
+  }
+  TS_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace ts
