@@ -9,6 +9,7 @@
 // k = 0 and Nyquist twiddles are exactly +-1 and 0 and those slices come out exactly real).
 #include "internal.cuh"
 #include "reduce.cuh"
+#include "fft_reg.cuh"
 
 namespace ts {
 namespace {
@@ -59,6 +60,55 @@ __global__ void __launch_bounds__(256) k_rfft(const Real* __restrict__ in, Cplx*
         out[k * T + e] = v;
       }
     }
+  }
+}
+
+// Power-of-two p: register radix-2 FFT (fft_reg.cuh), P compile-time.
+template <typename Real, typename Cplx, int P>
+__global__ void __launch_bounds__(256) k_rfft_pow2(const Real* __restrict__ in, Cplx* __restrict__ out, long long T) {
+  __shared__ Real tc[P], tsn[P];
+  load_twiddles(tc, tsn, P);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < T;
+       e += (long long)gridDim.x * blockDim.x) {
+    rfft_reg<Real, P>([&](int t) { return in[t * T + e]; },
+                      [&](int k, Real re, Real im) {
+                        Cplx v;
+                        v.x = re;
+                        v.y = im;
+                        out[k * T + e] = v;
+                      },
+                      tc, tsn);
+  }
+}
+
+template <typename Real, typename Cplx, int P, int MODE>
+__global__ void __launch_bounds__(256) k_irfft_pow2(const Cplx* __restrict__ in, Real* __restrict__ out, long long T,
+                                                    const Real* __restrict__ C, double* __restrict__ partials) {
+  __shared__ Real tc[P], tsn[P];
+  load_twiddles(tc, tsn, P);
+  const Real invp = Real(1) / Real(P);
+  double local = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < T;
+       e += (long long)gridDim.x * blockDim.x) {
+    irfft_reg<Real, P>(
+        [&](int k, Real& re, Real& im) {
+          const Cplx c = in[k * T + e];
+          re = c.x;
+          im = c.y;
+        },
+        [&](int t, Real v) {
+          v *= invp;
+          if (MODE == IRFFT_RESIDUAL) {
+            v = C[t * T + e] - v;
+            local += (double)v * (double)v;
+          }
+          out[t * T + e] = v;
+        },
+        tc, tsn);
+  }
+  if (MODE == IRFFT_RESIDUAL) {
+    const double tot = block_sum(local);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
   }
 }
 
@@ -198,7 +248,12 @@ int stream_grid(long long T) {
 template <typename Real, typename Cplx>
 void rfft_tube(const Real* in, Cplx* out, long long T, int p, cudaStream_t st) {
   const int g = stream_grid(T);
-  if (p <= 2) k_rfft<Real, Cplx, 2><<<g, 256, 0, st>>>(in, out, T, p);
+  if (p == 2) k_rfft_pow2<Real, Cplx, 2><<<g, 256, 0, st>>>(in, out, T);
+  else if (p == 4) k_rfft_pow2<Real, Cplx, 4><<<g, 256, 0, st>>>(in, out, T);
+  else if (p == 8) k_rfft_pow2<Real, Cplx, 8><<<g, 256, 0, st>>>(in, out, T);
+  else if (p == 16) k_rfft_pow2<Real, Cplx, 16><<<g, 256, 0, st>>>(in, out, T);
+  else if (p == 32) k_rfft_pow2<Real, Cplx, 32><<<g, 256, 0, st>>>(in, out, T);
+  else if (p <= 2) k_rfft<Real, Cplx, 2><<<g, 256, 0, st>>>(in, out, T, p);
   else if (p <= 4) k_rfft<Real, Cplx, 4><<<g, 256, 0, st>>>(in, out, T, p);
   else if (p <= 8) k_rfft<Real, Cplx, 8><<<g, 256, 0, st>>>(in, out, T, p);
   else if (p <= 16) k_rfft<Real, Cplx, 16><<<g, 256, 0, st>>>(in, out, T, p);
@@ -220,7 +275,19 @@ void irfft_tube(const Cplx* in, Real* out, long long T, int p, int mode, const R
     else                                                                                        \
       k_irfft<Real, Cplx, PM, IRFFT_STORE><<<g, 256, 0, st>>>(in, out, T, p, C, partials);      \
   } while (0)
-  if (p <= 2) TS_IRFFT(2);
+#define TS_IRFFT_POW2(PP)                                                                        \
+  do {                                                                                           \
+    if (mode == IRFFT_RESIDUAL)                                                                  \
+      k_irfft_pow2<Real, Cplx, PP, IRFFT_RESIDUAL><<<g, 256, 0, st>>>(in, out, T, C, partials);  \
+    else                                                                                         \
+      k_irfft_pow2<Real, Cplx, PP, IRFFT_STORE><<<g, 256, 0, st>>>(in, out, T, C, partials);     \
+  } while (0)
+  if (p == 2) TS_IRFFT_POW2(2);
+  else if (p == 4) TS_IRFFT_POW2(4);
+  else if (p == 8) TS_IRFFT_POW2(8);
+  else if (p == 16) TS_IRFFT_POW2(16);
+  else if (p == 32) TS_IRFFT_POW2(32);
+  else if (p <= 2) TS_IRFFT(2);
   else if (p <= 4) TS_IRFFT(4);
   else if (p <= 8) TS_IRFFT(8);
   else if (p <= 16) TS_IRFFT(16);
@@ -230,6 +297,7 @@ void irfft_tube(const Cplx* in, Real* out, long long T, int p, int mode, const R
   else
     k_irfft_any<Real, Cplx, IRFFT_STORE><<<g, 256, 2 * p * sizeof(Real), st>>>(in, out, T, p, C, partials);
 #undef TS_IRFFT
+#undef TS_IRFFT_POW2
   count_launch();
   TS_CUDA(cudaGetLastError());
 }

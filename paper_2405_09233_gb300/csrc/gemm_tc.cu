@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 #include "internal.cuh"
 #include "tc.cuh"
+#include "fft_reg.cuh"
 
 namespace ts {
 namespace {
@@ -387,6 +388,33 @@ __global__ void __launch_bounds__(256) k_rfft_planar(const float* __restrict__ X
   }
 }
 
+// Power-of-two p: register FFT version of k_rfft_planar.
+template <typename OpT, int P>
+__global__ void __launch_bounds__(256) k_rfft_planar_pow2(const float* __restrict__ X, OpT* __restrict__ re,
+                                                          OpT* __restrict__ im, int n, int s, int ldn) {
+  __shared__ float tc[P], tsn[P];
+  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    double sv, cv;
+    sincospi(2.0 * r / P, &sv, &cv);
+    tc[r] = (float)cv;
+    tsn[r] = (float)sv;
+  }
+  __syncthreads();
+  const long long T = (long long)n * s;
+  const long long Tp = (long long)ldn * s;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < Tp; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ldn);
+    const long long j = e / ldn;
+    const bool live = i < n;
+    rfft_reg<float, P>([&](int t) { return live ? X[t * T + j * n + i] : 0.f; },
+                       [&](int kk, float a, float b) {
+                         re[kk * Tp + e] = to_op<OpT>(a);
+                         im[kk * Tp + e] = to_op<OpT>(b);
+                       },
+                       tc, tsn);
+  }
+}
+
 // planes [k][j][ldn] (column-major X_k) -> planes [k][i][lds] (row-major X_k).
 template <typename OpT>
 __global__ void k_transpose_planes(const OpT* __restrict__ cre, const OpT* __restrict__ cim, OpT* __restrict__ rre,
@@ -483,7 +511,11 @@ void planar_dft(const float* X, TcWork& w, int n, int s, int p, int ldn, int lds
   int g = (int)((Tp + 255) / 256);
   if (g > 152 * 16) g = 152 * 16;
   OpT* cre = (OpT*)w.xc_re; OpT* cim = (OpT*)w.xc_im;
-  if (p <= 4) k_rfft_planar<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
+  if (p == 4) k_rfft_planar_pow2<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn);
+  else if (p == 8) k_rfft_planar_pow2<OpT, 8><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn);
+  else if (p == 16) k_rfft_planar_pow2<OpT, 16><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn);
+  else if (p == 32) k_rfft_planar_pow2<OpT, 32><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn);
+  else if (p <= 4) k_rfft_planar<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
   else if (p <= 8) k_rfft_planar<OpT, 8><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
   else if (p <= 16) k_rfft_planar<OpT, 16><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
   else if (p <= 32) k_rfft_planar<OpT, 32><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);

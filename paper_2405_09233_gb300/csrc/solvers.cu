@@ -71,17 +71,29 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
     ++true_len;
   };
 
-  // ||C|| and the initial residual R = C - M(X0) (Algorithm 3, step 3).
+  // ||C|| and the initial residual R = C - M(X0) (Algorithm 3, step 3).  M(0) = 0 exactly, so
+  // for X0 = 0 the residual is C itself and the FP64 apply is skipped.
   dot_partials<double>(C, C, N, P2, st);
   finalize_norm(P2, sc + 0, st);
-  apply_f64(ctx, op, X, R, IRFFT_RESIDUAL, C, P2, st);
-  finalize_norm(P2, sc + 2, st);
-  TS_CUDA(cudaMemcpyAsync(hs, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  dot_partials<double>(X, X, N, P2, st);
+  finalize_norm(P2, sc + 4, st);
+  TS_CUDA(cudaMemcpyAsync(hs, sc, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
   TS_CUDA(cudaStreamSynchronize(st));
   const double normC = hs[0];
-  double res = hs[2];
+  double res;
+  if (hs[4] == 0.0) {
+    TS_CUDA(cudaMemcpyAsync(R, C, sizeof(double) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    TS_CUDA(cudaMemcpyAsync(sc + 2, sc + 0, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    res = normC;
+  } else {
+    apply_f64(ctx, op, X, R, IRFFT_RESIDUAL, C, P2, st);
+    ++info.applies_fp64;
+    finalize_norm(P2, sc + 2, st);
+    TS_CUDA(cudaMemcpyAsync(hs, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TS_CUDA(cudaStreamSynchronize(st));
+    res = hs[2];
+  }
   info.normC = normC;
-  info.applies_fp64 = 1;
   push_true(res);
   ts_status status = TS_NOT_CONVERGED;
   double last_est = res;
