@@ -40,8 +40,9 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dense_n1024_s1024_p16")
-    ap.add_argument("--precision", default="fp64")
-    ap.add_argument("--variants", default="mixed_fp32,mixed_tf32,mixed_bf16",
+    ap.add_argument("--precision", default=None,
+                    help="default: fp64 for the dense n=s=1024 workload, mixed_fp32 for the others")
+    ap.add_argument("--variants", default="mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16",
                     help="comma list of extra precisions to time ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -94,12 +95,37 @@ def gemm_roofline(kind, precision, flops_per_launch, avg_ms, sustained, share):
                 "kernel": "k_gemm_slices<float> (FP32 FFMA, 3-multiply complex)",
                 "note": f"peak derived: 2 FLOP x 128 lanes/SM x 152 SMs x 2070 MHz. Kernel share: {share:.3f}"}
     bf = pk["bf16_sustained"] if sustained else pk["bf16_burst"]
-    peak = bf * (TF32_OVER_BF16 if precision == "mixed_tf32" else 1.0)
+    tf32 = precision in ("mixed_tf32", "mixed_tf32x3")
+    parts = 3 if precision == "mixed_tf32x3" else 1
+    peak = bf * (TF32_OVER_BF16 if tf32 else 1.0) / parts
+    name = {"mixed_tf32": "TF32", "mixed_bf16": "BF16", "mixed_tf32x3": "split TF32 x3"}[precision]
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": f"k_tc_sylv ({'TF32' if precision == 'mixed_tf32' else 'BF16'} tcgen05)",
+            "traffic": None, "kernel": f"k_tc_sylv ({name} tcgen05)",
             "note": (f"peak: {pk['source']} BF16 {'sustained' if sustained else 'burst'}"
-                     + (" x nominal TF32/BF16 ratio 0.489" if precision == "mixed_tf32" else "")
+                     + (" x nominal TF32/BF16 ratio 0.489" if tf32 else "")
+                     + (" / 3 products (split TF32)" if parts == 3 else "")
                      + f". Kernel share of the step: {share:.3f}")}
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The slowest rank's time: all-reduce MAX over the process group (NCCL on GPUs, gloo on CPU)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank processed its own units, the job took the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank solves its own instance of the workload family (weak scaling)."""
+    return 1 + rank
 
 
 def dist_env():
@@ -240,6 +266,8 @@ def run_reference(a):
 
 def main():
     a = args_parse()
+    if a.precision is None:
+        a.precision = "fp64" if a.workload in ("dense_n1024_s1024_p16", "sparse_lap128_s32_p8") else "mixed_fp32"
     if a.impl == "reference":
         run_reference(a)
         return
@@ -253,9 +281,14 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    if a.workload in ("batched_256", "sparse_lap128_s32_p8"):
+        (run_batched if a.workload == "batched_256" else run_tbas)(a, rank, world, local, dev)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     cfg = workload_cfg(a)
     n, s, p, m = cfg["n"], cfg["s"], cfg["p"], cfg["restart"]
-    seed = 1 + rank
+    seed = rank_seed(rank)
     pr = inputs.dense_problem(n, s, p, seed=seed, scale=cfg["scale"])
     A_h = torch.from_numpy(inputs.to_device_layout(pr.A)).pin_memory()
     B_h = torch.from_numpy(inputs.to_device_layout(pr.B)).pin_memory()
@@ -300,17 +333,13 @@ def main():
     clk = clocks.stop()
     ctx.stats_enable(False)
     st = ctx.stats_get()
-    ms = ev0.elapsed_time(ev1) / a.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dev)
     last = results[-1]
     assert all(r.status == 0 for r in results), results
     relres = last.info.relres_true
     err_xstar = float(torch.max(torch.abs(X - Xs)) / torch.max(torch.abs(Xs)))
     unknowns = n * s * p
-    value = unknowns * world / (ms / 1e3)
+    value = job_throughput(unknowns, world, ms)
 
     # dominant kernel: whichever slice GEMM (FP64 or low precision) took more time
     step_ms_total = ms * a.steps
@@ -329,7 +358,7 @@ def main():
     C_h = Cd.cpu().pin_memory()
     X_h = torch.zeros_like(C_h).pin_memory()
     e2e_times = []
-    for _ in range(a.e2e_steps):
+    for _ in range(max(a.e2e_steps, 0)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         op = ctx.op_create_dense(A_h, B_h)
@@ -338,7 +367,7 @@ def main():
         op.close()
         e2e_times.append(time.perf_counter() - t0)
         assert r.status == 0, r
-    e2e = {"value": unknowns * world / statistics.median(e2e_times), "unit": UNIT,
+    e2e = {"value": unknowns * world / statistics.median(e2e_times) if e2e_times else None, "unit": UNIT,
            "h2d_bytes_per_step": 8 * (n * n * p + s * s * p + 2 * n * s * p),
            "d2h_bytes_per_step": 8 * n * s * p}
 
@@ -382,6 +411,163 @@ def main():
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_batched(a, rank, world, local, dev):
+    """The batched workload: 256 instances (n log-uniform in [64, 1024], s uniform in [16, 128],
+    p in {4, 8, 16}), one step = one ts_batched_solve of all of them (operator setup included)."""
+    import torch
+    from paper_2405_09233_gb300 import Context, inputs
+    count = inputs.WORKLOADS["batched_256"]["count"]
+    specs = inputs.batched_specs(count, seed=4 + rank)
+    ctx = Context(local)
+    host = []
+    for sp in specs:
+        pr = inputs.dense_problem(sp.n, sp.s, sp.p, seed=sp.seed)
+        host.append((torch.from_numpy(inputs.to_device_layout(pr.A)).pin_memory(),
+                     torch.from_numpy(inputs.to_device_layout(pr.B)).pin_memory(),
+                     torch.from_numpy(inputs.to_device_layout(pr.Xstar)).pin_memory()))
+    dev_in = [(A.to(dev), B.to(dev), X.to(dev)) for A, B, X in host]
+    Cs = []
+    for A, B, Xst in dev_in:
+        op = ctx.op_create_dense(A, B)
+        Cs.append(ctx.sylv_apply(op, Xst))
+        op.close()
+    Xs = [torch.zeros_like(C) for C in Cs]
+    unknowns = sum(sp.n * sp.s * sp.p for sp in specs)
+    prec = a.precision
+
+    def step(precision):
+        ops = [ctx.op_create_dense(A, B) for A, B, _ in dev_in]
+        for X in Xs:
+            X.zero_()
+        st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, tol=1e-10, precision=precision)
+        for op in ops:
+            op.close()
+        return st, infos
+
+    for _ in range(a.warmup):
+        st, infos = step(prec)
+    assert st == 0
+    ctx.stats_reset()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        st, infos = step(prec)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stt = ctx.stats_get()
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+    relres = max(i.relres_true for i in infos)
+    err = max(float(torch.max(torch.abs(X - Xst))) for X, (_, _, Xst) in zip(Xs, dev_in))
+    # end to end: operators and right-hand sides from pinned host memory, solutions back to host
+    C_h = [C.cpu().pin_memory() for C in Cs]
+    X_h = [torch.zeros_like(C) for C in C_h]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ops = [ctx.op_create_dense(A, B) for A, B, _ in host]
+    Cd = [C.to(dev, non_blocking=True) for C in C_h]
+    Xd = [torch.zeros_like(C) for C in Cd]
+    st2, _, _ = ctx.batched_solve(ops, Cd, Xd, restart=20, tol=1e-10, precision=prec)
+    for Xh_, Xd_ in zip(X_h, Xd):
+        Xh_.copy_(Xd_)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    for op in ops:
+        op.close()
+    h2d = sum(8 * (A.numel() + B.numel() + C.numel()) for (A, B, _), C in zip(host, C_h))
+    d2h = sum(8 * X.numel() for X in X_h)
+    fp64 = None
+    if a.variants != "" and prec != "fp64":
+        torch.cuda.synchronize()
+        f0 = time.perf_counter()
+        stf, infof = step("fp64")
+        torch.cuda.synchronize()
+        fp64 = {"value": unknowns * world / (time.perf_counter() - f0), "status": stf,
+                "max_relres_true": max(i.relres_true for i in infof)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": unknowns * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if prec != "fp64" else "f64", "data": "synthetic",
+                "config": {"workload": "batched_256", "instances": count, "unknowns": unknowns, "restart": 20,
+                           "tol": 1e-10, "precision": prec, "method": "batched tGMRES",
+                           "max_relres_true": relres, "max_err_vs_xstar": err,
+                           "l2": "inputs larger than L2 (5 GB basis)"},
+                "e2e": {"value": unknowns * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "clocks": clk, "gpu_launches": int(stt.launches), "variants": {"fp64": fp64} if fp64 else {}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_tbas(a, rank, world, local, dev):
+    """The sparse workload: A^(1) = 5-point Laplacian on a 128 x 128 grid, A^(2..8) with 4 random
+    entries per row, B dense (s = 32, or --s), solved by TBAS(10) to 1e-10 in FP64.  One step =
+    one ts_op_create_csr + ts_tba_solve."""
+    import numpy as np
+    import torch
+    from paper_2405_09233_gb300 import Context, inputs
+    cfg = inputs.WORKLOADS["sparse_lap128_s32_p8"]
+    s_blk = a.s if a.s is not None else cfg["s"]
+    prob = inputs.sparse_problem(grid=cfg["grid"], s=s_blk, p=cfg["p"], seed=rank_seed(rank))
+    n, p = prob.n, prob.p
+    rowptr, cols, vals, base = [], [], [], 0
+    for sl in prob.slices:
+        rowptr.append(sl.rowptr.astype(np.int64) + base)
+        cols.append(sl.col)
+        vals.append(sl.val)
+        base += sl.col.size
+    rowptr = np.concatenate(rowptr).astype(np.int32)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    ctx = Context(local)
+    Bd = torch.from_numpy(inputs.to_device_layout(prob.B)).to(dev)
+    Xs = torch.from_numpy(inputs.to_device_layout(prob.Xstar)).to(dev)
+    op0 = ctx.op_create_csr(n, p, rowptr, cols, vals, Bd)
+    Cd = ctx.sylv_apply(op0, Xs)
+    op0.close()
+    X = torch.zeros_like(Cd)
+    m = 10
+
+    def step():
+        op = ctx.op_create_csr(n, p, rowptr, cols, vals, Bd)
+        X.zero_()
+        r = ctx.tba_solve(op, Cd, X, restart=m, tol=1e-10)
+        op.close()
+        return r
+
+    for _ in range(a.warmup):
+        r = step()
+    assert r.status == 0, r
+    ctx.stats_reset()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        r = step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stt = ctx.stats_get()
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+    unknowns = n * s_blk * p
+    if rank == 0:
+        line = {"metric": METRIC, "value": job_throughput(unknowns, world, ms), "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "sparse_lap128_s32_p8", "n": n, "s": s_blk, "p": p, "restart": m,
+                           "tol": 1e-10, "method": "TBAS", "cycles": r.info.cycles, "block_steps": r.info.iters,
+                           "relres_true": r.info.relres_true,
+                           "err_vs_xstar": float(torch.max(torch.abs(X - Xs)))},
+                "clocks": clk, "gpu_launches": int(stt.launches)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev):

@@ -49,7 +49,9 @@ typedef enum {
   TS_FP64 = 0,        /* every step in FP64 */
   TS_MIXED_FP32 = 1,  /* FP64 refinement around an FP32 inner tGMRES (FP32 CUDA-core GEMMs) */
   TS_MIXED_TF32 = 2,  /* inner GEMMs on tcgen05 tensor cores, TF32 inputs, FP32 accumulation */
-  TS_MIXED_BF16 = 3   /* inner GEMMs on tcgen05 tensor cores, BF16 inputs, FP32 accumulation */
+  TS_MIXED_BF16 = 3,  /* inner GEMMs on tcgen05 tensor cores, BF16 inputs, FP32 accumulation */
+  TS_MIXED_TF32X3 = 4 /* inner GEMMs on tcgen05 in split TF32 (hi*hi + hi*lo + lo*hi): FP32-level
+                         accuracy at tensor-core speed */
 } ts_precision;
 
 typedef struct ts_ctx ts_ctx; /* device, workspace, scratch, error text */
@@ -100,8 +102,8 @@ ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y
 
 /* Y = M(X) in a lower precision, the operator of the mixed-precision inner solve: X, Y are
  * FP32 device tensors (n x s x p).  precision TS_MIXED_FP32: FP32 DFT and FP32 CUDA-core slice
- * GEMMs; TS_MIXED_TF32 / TS_MIXED_BF16: the slice GEMMs run on the tcgen05 tensor cores with
- * TF32 / BF16 inputs and FP32 accumulation (p <= 32).  The first call with a precision builds
+ * GEMMs; TS_MIXED_TF32 / TS_MIXED_BF16 / TS_MIXED_TF32X3: the slice GEMMs run on the tcgen05
+ * tensor cores with TF32 / BF16 / split-TF32 inputs and FP32 accumulation (p <= 32).  The first call with a precision builds
  * that precision's copy of the operator's Fourier slices.  Asynchronous on `stream`. */
 ts_status ts_sylv_apply_lowp(ts_ctx* ctx, const ts_op* op, int precision, const float* X, float* Y,
                              ts_stream stream);
@@ -111,7 +113,8 @@ typedef struct {
   int max_restarts;      /* Iter_max (Algorithm 3): cycles allowed (per inner solve when mixed) */
   double tol;            /* stop when ||C - M(X)||_F <= tol * ||C||_F (true residual) */
   int precision;         /* ts_precision */
-  double inner_tol;      /* mixed precision: relative tolerance of each inner solve (0 = 1e-6 FP32, 1e-3 TF32, 1e-2 BF16) */
+  double inner_tol;      /* mixed precision: relative tolerance of each inner solve (0 = 1e-6 FP32 and split
+                            TF32, 1e-3 TF32, 1e-2 BF16) */
   int max_outer;         /* mixed precision: refinement steps allowed (0 = 50) */
   double* history;       /* optional host array: residual estimate after every inner step */
   int history_cap;       /* capacity of history (entries); extra entries are dropped */
@@ -152,6 +155,28 @@ ts_status ts_tgmres_solve(ts_ctx* ctx, const ts_op* op, const double* C, double*
  * results as ts_tgmres_solve; FP64 only (TS_ERR_UNSUPPORTED otherwise). */
 ts_status ts_tfom_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X,
                         const ts_solve_opts* opts, ts_solve_info* info, ts_stream stream);
+
+/* One instance of a batch: its prepared dense operator, right-hand side and initial guess /
+ * solution (device pointers, n x s x p of that operator), and its own relative tolerance
+ * (<= 0: opts->tol). */
+typedef struct {
+  const ts_op* op;
+  const double* C;
+  double* X;
+  double tol;
+} ts_instance;
+
+/* Many independent STEs of uneven (n, s, p) solved together by restarted tGMRES(m) (Algorithm 3)
+ * in lockstep: every phase of a restart cycle is one launch over all instances (block tables for
+ * the streaming phases and the mode-3 DFTs, a cost-ordered (instance, slice, tile) work list for
+ * the slice products), device-side masks retire converged instances, and one cycle is captured
+ * as a CUDA graph and replayed.  opts->precision: TS_FP64, or TS_MIXED_FP32 (FP32 Arnoldi cycle,
+ * FP64 residual and update; the cycle's inner tolerance is opts->inner_tol, default 1e-6).
+ * opts->restart <= 128; dense operators with p <= 64.  infos / statuses (count entries each, may
+ * be NULL) receive each instance's result; the call returns TS_OK when every instance reached its
+ * tolerance, TS_NOT_CONVERGED (or TS_ERR_NONFINITE) otherwise.  Synchronous. */
+ts_status ts_batched_solve(ts_ctx* ctx, int count, const ts_instance* insts, const ts_solve_opts* opts,
+                           ts_solve_info* infos, int* statuses, ts_stream stream);
 
 /* ts_tstar without allocating: C = A*B exactly as ts_tstar computes it, for callers that cannot
  * allocate device memory at call time -- code recorded under CUDA stream capture (cudaMalloc

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libtstar.so")
 
 TS_OK, TS_BREAKDOWN, TS_NOT_CONVERGED, TS_SINGULAR = 0, 1, 2, 3
 TS_ERR_ARG, TS_ERR_CUDA, TS_ERR_NOMEM, TS_ERR_NONFINITE, TS_ERR_TIMEOUT, TS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
-PRECISIONS = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
+PRECISIONS = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3, "mixed_tf32x3": 4}
 STATUS_NAMES = {0: "ok", 1: "breakdown", 2: "not_converged", 3: "singular", -1: "err_arg", -2: "err_cuda",
                 -3: "err_nomem", -4: "err_nonfinite", -5: "err_timeout", -6: "err_unsupported"}
 
@@ -38,6 +38,10 @@ class SolveInfo(ctypes.Structure):
                 ("applies_fp64", ctypes.c_int), ("applies_low", ctypes.c_int),
                 ("normC", ctypes.c_double), ("relres_true", ctypes.c_double), ("relres_est", ctypes.c_double),
                 ("ms_total", ctypes.c_double)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_void_p), ("C", ctypes.c_void_p), ("X", ctypes.c_void_p), ("tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -73,6 +77,8 @@ _SIGNATURES = {
     "ts_tfom_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
     "ts_tba_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
     "ts_t_bartels_stewart": (_i, [_vp, _vp, _i, _vp, _i, _i, _vp, _vp, _vp]),
+    "ts_batched_solve": (_i, [_vp, _i, ctypes.POINTER(Instance), ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo),
+                              ctypes.POINTER(_i), _vp]),
     "ts_tstar_noalloc": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp]),
     "ts_stats_enable": (_i, [_vp, _i]),
     "ts_stats_get": (_i, [_vp, ctypes.POINTER(Stats)]),
@@ -240,6 +246,28 @@ class Context:
         """Restarted TBAS(m) (FP64); X holds X0 on entry and the solution on return."""
         return self._solve(lib().ts_tba_solve, "ts_tba_solve", op, C, X, restart, tol, max_restarts,
                            "fp64", 0.0, 0, history_cap)
+
+    def batched_solve(self, ops, Cs, Xs, tols=None, restart=20, tol=1e-10, max_restarts=200, precision="fp64",
+                      inner_tol=0.0, max_outer=0):
+        """Solve len(ops) independent STEs together; Cs/Xs are CUDA float64 tensors (p, s, n) per instance.
+        Returns (status, [SolveInfo], [per-instance status])."""
+        count = len(ops)
+        arr = (Instance * count)()
+        for i, (op, C, X) in enumerate(zip(ops, Cs, Xs)):
+            arr[i].op = op._h.value if isinstance(op._h, ctypes.c_void_p) else op._h
+            arr[i].C = _ptr(C)
+            arr[i].X = _ptr(X)
+            arr[i].tol = -1.0 if tols is None else float(tols[i])
+        opts = SolveOpts()
+        lib().ts_solve_opts_default(ctypes.byref(opts))
+        opts.restart, opts.tol, opts.max_restarts = restart, tol, max_restarts
+        opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        opts.inner_tol, opts.max_outer = inner_tol, max_outer
+        infos = (SolveInfo * count)()
+        sts = (ctypes.c_int * count)()
+        st = self._check(lib().ts_batched_solve(self._h, count, arr, ctypes.byref(opts), infos, sts,
+                                                _stream(*Cs)), "ts_batched_solve")
+        return st, list(infos), list(sts)
 
     def tfom_solve(self, op, C, X, restart=20, tol=1e-10, max_restarts=200, history_cap=4096):
         """Restarted tFOM(m) (FP64)."""

@@ -255,6 +255,7 @@ void ts_destroy(ts_ctx* ctx) {
   cudaSetDevice(ctx->device);
   ctx->ws.release_all();
   ctx->timer.destroy();
+  if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
   if (ctx->host_scalars) cudaFreeHost(ctx->host_scalars);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -440,13 +441,22 @@ ts_status ts_sylv_apply_lowp(ts_ctx* ctx, const ts_op* op, int precision, const 
   TS_API_BEGIN
   TS_REQUIRE(op && X && Y, "ts_sylv_apply_lowp: null pointer");
   TS_REQUIRE(X != Y, "ts_sylv_apply_lowp: Y must not alias X");
-  TS_REQUIRE(precision == TS_MIXED_FP32 || precision == TS_MIXED_TF32 || precision == TS_MIXED_BF16,
+  TS_REQUIRE(precision == TS_MIXED_FP32 || precision == TS_MIXED_TF32 || precision == TS_MIXED_BF16 ||
+                 precision == TS_MIXED_TF32X3,
              "ts_sylv_apply_lowp: precision must be a mixed precision");
   TS_REQUIRE(is_device_ptr(X) && is_device_ptr(Y), "ts_sylv_apply_lowp: X and Y must be device memory");
   if (op->sp) throw Error{TS_ERR_UNSUPPORTED, "ts_sylv_apply_lowp: sparse operators run in FP64 only"};
   TS_CUDA(cudaSetDevice(ctx->device));
   apply_low(ctx, const_cast<ts_op*>(op), precision, X, Y, reinterpret_cast<cudaStream_t>(stream));
   return TS_OK;
+  TS_API_END(ctx)
+}
+
+ts_status ts_batched_solve(ts_ctx* ctx, int count, const ts_instance* insts, const ts_solve_opts* opts,
+                           ts_solve_info* infos, int* statuses, ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  return batched_entry(ctx, count, insts, opts, infos, statuses, stream);
   TS_API_END(ctx)
 }
 

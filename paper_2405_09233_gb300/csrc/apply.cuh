@@ -40,6 +40,9 @@ ts_status tba_entry(ts_ctx* ctx, const ts_op* op, const double* C, double* X, co
 void t_bartels_stewart_dev(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p, const double* C,
                            double* X, cudaStream_t st);
 
+ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const ts_solve_opts* opts,
+                        ts_solve_info* infos, int* statuses, ts_stream stream);
+
 // Low-precision apply used by the inner solve of mixed precision: X, Y FP32.
 void apply_low(ts_ctx* ctx, ts_op* op, int precision, const float* X, float* Y, cudaStream_t st);
 

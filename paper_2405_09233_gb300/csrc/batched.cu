@@ -1,0 +1,726 @@
+// Batched restarted tGMRES: many independent Sylvester tensor equations of uneven (n, s, p) solved
+// together on one GPU, FP64 or mixed precision (FP32 Arnoldi cycle, FP64 residual and update).
+//
+// All instances advance in lockstep through the restart cycle of Algorithm 3; every phase is ONE
+// launch over all instances:
+//   * streaming phases (scaling, inner products, MGS passes, X += V (*) y) run over a block table
+//     in which every block belongs to one instance (a chunk of its N = n s p unknowns), so each
+//     instance's inner product is the fixed-order sum of its own blocks' partials;
+//   * the mode-3 DFTs run over a tube-block table (one tube per thread, the instance's p);
+//   * the per-slice products run over a work list of (instance, Fourier slice, 64 x 64 tile)
+//     items, ordered by cost (largest first) so the tail of the launch stays short;
+//   * the Givens update is one block per instance.
+// Masks on the device (cycle participation, still iterating) let an instance stop its inner cycle
+// early or drop out of the batch without changing the launch sequence, so one restart cycle is
+// captured once as a CUDA graph and replayed; the host only reads the per-instance residuals at
+// the end of each cycle.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+#include "internal.cuh"
+#include "apply.cuh"
+#include "reduce.cuh"
+#include "fft_reg.cuh"
+#include "gemm_tile.cuh"
+
+namespace ts {
+
+void ensure_f32_operator(ts_op* op, cudaStream_t st);  // lowprec.cu
+
+namespace {
+
+constexpr int kChunk = 4096;      // unknowns per streaming block (256 threads x 16)
+constexpr int kTubes = 256;       // tubes per DFT block (one per thread)
+
+struct BInst {
+  double* X;
+  const double* C;
+  const double2* Ah;
+  const double2* Bh;
+  const float2* Ah32;
+  const float2* Bh32;
+  long long offN, offS;   // offsets in the concatenated unknown / spectral buffers
+  long long N, T;         // n s p and n s
+  int n, s, p, K, nyq;
+  int nb0, nb1;           // streaming-block range
+  int tb0, tb1;           // tube-block range
+  double tol;
+};
+
+// Per-instance scalars (16 doubles each).
+enum { SC_NORMC = 0, SC_RES = 1, SC_INVRES = 2, SC_EST = 3, SC_INVH = 4, SC_H = 5, SC_K = 6, SC_FLAGS = 7,
+       SC_ITERS = 8, SC_DONE = 9 };
+
+struct BDev {
+  const BInst* inst;
+  int count, m;
+  long long totN, totS;
+  const int* nb_inst;
+  const long long* nb_off;
+  const int* tb_inst;
+  const long long* tb_off;
+  const int* cyc;   // participates in the current cycle
+  int* act;         // still iterating in the current cycle
+  double* sc;
+  double* state;
+  long long stride;
+  double inner_tol;
+  int mixed;
+};
+
+struct StLayout {
+  int m;
+  __device__ long long H() const { return 0; }
+  __device__ long long R() const { return (long long)(m + 1) * m; }
+  __device__ long long cs() const { return 2ll * (m + 1) * m; }
+  __device__ long long sn() const { return cs() + m; }
+  __device__ long long g() const { return sn() + m; }
+  __device__ long long y() const { return g() + m + 1; }
+};
+long long state_stride(int m) { return 2ll * (m + 1) * m + 3ll * m + 1 + 8; }
+
+// Sum of an instance's block partials [b0, b1), identical in every block that calls it.
+__device__ __forceinline__ double inst_sum(const double* P, int b0, int b1) {
+  double v = 0.0;
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) v += P[b];
+  return block_sum(v);
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ T* basis(T* V, long long totN, int j) {
+  return V + (long long)j * totN;
+}
+
+// --- streaming phases ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_scale_R(BDev d, const double* __restrict__ R, T* __restrict__ V0) {
+  const int i = d.nb_inst[blockIdx.x];
+  if (!d.cyc[i]) return;
+  const BInst& in = d.inst[i];
+  const double sc = d.sc[16 * i + SC_INVRES];
+  const long long e0 = in.offN + d.nb_off[blockIdx.x];
+  const long long e1 = min(in.offN + in.N, e0 + kChunk);
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) V0[e] = (T)(R[e] * sc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_dot(BDev d, const T* __restrict__ x, const T* __restrict__ y,
+                                               double* __restrict__ P) {
+  const int i = d.nb_inst[blockIdx.x];
+  if (!d.act[i]) return;
+  const BInst& in = d.inst[i];
+  const long long e0 = in.offN + d.nb_off[blockIdx.x];
+  const long long e1 = min(in.offN + in.N, e0 + kChunk);
+  double acc = 0.0;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc += (double)x[e] * (double)y[e];
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) P[blockIdx.x] = t;
+}
+
+// ||C_i||^2 partials (C read through the instance pointer).
+__global__ void __launch_bounds__(256) k_b_normC(BDev d, double* __restrict__ P) {
+  const int i = d.nb_inst[blockIdx.x];
+  const BInst& in = d.inst[i];
+  const long long l0 = d.nb_off[blockIdx.x];
+  const long long l1 = min(in.N, l0 + kChunk);
+  double acc = 0.0;
+  for (long long e = l0 + threadIdx.x; e < l1; e += blockDim.x) acc += in.C[e] * in.C[e];
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) P[blockIdx.x] = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_mgs(BDev d, T* __restrict__ W, const T* __restrict__ Vi,
+                                               const T* __restrict__ Vn, const double* __restrict__ Pin,
+                                               double* __restrict__ Pout, int irow, int jcol) {
+  const int i = d.nb_inst[blockIdx.x];
+  if (!d.act[i]) return;
+  const BInst& in = d.inst[i];
+  const double h = inst_sum(Pin, in.nb0, in.nb1);
+  if (blockIdx.x == in.nb0 && threadIdx.x == 0) {
+    StLayout L{d.m};
+    d.state[i * d.stride + L.H() + irow + (long long)(d.m + 1) * jcol] = h;
+  }
+  const T hT = (T)h;
+  const long long e0 = in.offN + d.nb_off[blockIdx.x];
+  const long long e1 = min(in.offN + in.N, e0 + kChunk);
+  double acc = 0.0;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const T w = W[e] - hT * Vi[e];
+    W[e] = w;
+    acc += (double)(Vn ? Vn[e] : w) * (double)w;
+  }
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) Pout[blockIdx.x] = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_scale_W(BDev d, const T* __restrict__ W, T* __restrict__ Vn) {
+  const int i = d.nb_inst[blockIdx.x];
+  if (!d.act[i]) return;
+  const BInst& in = d.inst[i];
+  const T sc = (T)d.sc[16 * i + SC_INVH];
+  const long long e0 = in.offN + d.nb_off[blockIdx.x];
+  const long long e1 = min(in.offN + in.N, e0 + kChunk);
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) Vn[e] = W[e] * sc;
+}
+
+// X_i += sum_{q < k_i} y_q V_q  (X through the instance pointer, FP64).
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_axpy(BDev d, const T* __restrict__ V) {
+  const int i = d.nb_inst[blockIdx.x];
+  if (!d.cyc[i]) return;
+  const BInst& in = d.inst[i];
+  __shared__ double ys[256];
+  StLayout L{d.m};
+  const int k = (int)d.sc[16 * i + SC_K];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = d.state[i * d.stride + L.y() + q];
+  __syncthreads();
+  const long long l0 = d.nb_off[blockIdx.x];
+  const long long l1 = min(in.N, l0 + kChunk);
+  for (long long l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < k; ++q) acc = fma(ys[q], (double)V[(long long)q * d.totN + in.offN + l], acc);
+    in.X[l] += acc;
+  }
+}
+
+// --- DFT along mode 3 over the tube-block table ----------------------------------------------------
+// SRC 0: concatenated buffer `in` (offN); SRC 1: instance X (FP64).  MASK 0: act, 1: cyc.
+template <typename Real, typename Cplx, int SRC, int MASK>
+__global__ void __launch_bounds__(kTubes) k_b_rfft(BDev d, const Real* __restrict__ in, Cplx* __restrict__ out) {
+  const int i = d.tb_inst[blockIdx.x];
+  if (!(MASK ? d.cyc[i] : d.act[i])) return;
+  const BInst& ins = d.inst[i];
+  const int p = ins.p;
+  __shared__ Real tc[64], tsn[64];
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    double sv, cv;
+    sincospi(2.0 * r / p, &sv, &cv);
+    tc[r] = (Real)cv;
+    tsn[r] = (Real)sv;
+  }
+  __syncthreads();
+  const long long e = d.tb_off[blockIdx.x] + threadIdx.x;
+  if (e >= ins.T) return;
+  const Real* src = SRC == 0 ? in + ins.offN : reinterpret_cast<const Real*>(ins.X);
+  Cplx* dst = out + ins.offS;
+  const long long T = ins.T;
+  auto ld = [&](int t) { return src[t * T + e]; };
+  auto stv = [&](int k, Real re, Real im) {
+    Cplx v;
+    v.x = re;
+    v.y = im;
+    dst[k * T + e] = v;
+  };
+  switch (p) {
+    case 2: rfft_reg<Real, 2>(ld, stv, tc, tsn); break;
+    case 4: rfft_reg<Real, 4>(ld, stv, tc, tsn); break;
+    case 8: rfft_reg<Real, 8>(ld, stv, tc, tsn); break;
+    case 16: rfft_reg<Real, 16>(ld, stv, tc, tsn); break;
+    case 32: rfft_reg<Real, 32>(ld, stv, tc, tsn); break;
+    default: {
+      const int K = p / 2 + 1;
+      for (int k = 0; k < K; ++k) {
+        Real re = 0, im = 0;
+        int r = 0;
+        for (int t = 0; t < p; ++t) {
+          const Real x = src[t * T + e];
+          re = fma(x, tc[r], re);
+          im = fma(-x, tsn[r], im);
+          r += k;
+          if (r >= p) r -= p;
+        }
+        stv(k, re, im);
+      }
+    }
+  }
+}
+
+// MODE 0: out (concatenated) = y;  MODE 1: out = C_i - y (FP64) and per-block partial norms.
+template <typename Real, typename Cplx, int MODE>
+__global__ void __launch_bounds__(kTubes) k_b_irfft(BDev d, const Cplx* __restrict__ in, Real* __restrict__ out,
+                                                    double* __restrict__ P) {
+  const int i = d.tb_inst[blockIdx.x];
+  const bool on = MODE ? d.cyc[i] : d.act[i];
+  if (!on) return;
+  const BInst& ins = d.inst[i];
+  const int p = ins.p;
+  __shared__ Real tc[64], tsn[64];
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    double sv, cv;
+    sincospi(2.0 * r / p, &sv, &cv);
+    tc[r] = (Real)cv;
+    tsn[r] = (Real)sv;
+  }
+  __syncthreads();
+  const long long e = d.tb_off[blockIdx.x] + threadIdx.x;
+  double local = 0.0;
+  if (e < ins.T) {
+    const Cplx* src = in + ins.offS;
+    Real* dst = out + ins.offN;
+    const long long T = ins.T;
+    const Real invp = Real(1) / Real(p);
+    auto ld = [&](int k, Real& re, Real& im) {
+      const Cplx c = src[k * T + e];
+      re = c.x;
+      im = c.y;
+    };
+    auto stv = [&](int t, Real v) {
+      v *= invp;
+      if (MODE == 1) {
+        v = (Real)(ins.C[t * T + e] - (double)v);
+        local += (double)v * (double)v;
+      }
+      dst[t * T + e] = v;
+    };
+    switch (p) {
+      case 2: irfft_reg<Real, 2>(ld, stv, tc, tsn); break;
+      case 4: irfft_reg<Real, 4>(ld, stv, tc, tsn); break;
+      case 8: irfft_reg<Real, 8>(ld, stv, tc, tsn); break;
+      case 16: irfft_reg<Real, 16>(ld, stv, tc, tsn); break;
+      case 32: irfft_reg<Real, 32>(ld, stv, tc, tsn); break;
+      default: {
+        const int K = p / 2 + 1, nyq = (p % 2 == 0) ? p / 2 : -1;
+        for (int t = 0; t < p; ++t) {
+          Real y = 0;
+          for (int k = 0; k < K; ++k) {
+            const Cplx c = src[k * T + e];
+            const int r = (int)(((long long)k * t) % p);
+            if (k == 0 || k == nyq) {
+              y = fma(c.x, tc[r], y);
+            } else {
+              y = fma(Real(2) * c.x, tc[r], y);
+              y = fma(-Real(2) * c.y, tsn[r], y);
+            }
+          }
+          stv(t, y);
+        }
+      }
+    }
+  }
+  if (MODE == 1) {
+    const double t = block_sum(local);
+    if (threadIdx.x == 0) P[blockIdx.x] = t;
+  }
+}
+
+// --- per-slice products over the work list ---------------------------------------------------------
+template <typename Real, int MASK>
+__global__ void __launch_bounds__(kGemmNT, 1) k_b_gemm(BDev d, const int4* __restrict__ items,
+                                                       const typename CplxOf<Real>::T* __restrict__ Xh,
+                                                       typename CplxOf<Real>::T* __restrict__ Yh) {
+  using Cplx = typename CplxOf<Real>::T;
+  const int4 it = items[blockIdx.x];
+  const int i = it.x;
+  if (!(MASK ? d.cyc[i] : d.act[i])) return;
+  const BInst& in = d.inst[i];
+  GemmArgs<Cplx> a{};
+  const Cplx* Ah;
+  const Cplx* Bh;
+  if constexpr (sizeof(Real) == 8) {
+    Ah = reinterpret_cast<const Cplx*>(in.Ah);
+    Bh = reinterpret_cast<const Cplx*>(in.Bh);
+  } else {
+    Ah = reinterpret_cast<const Cplx*>(in.Ah32);
+    Bh = reinterpret_cast<const Cplx*>(in.Bh32);
+  }
+  const long long T = in.T;
+  a.A1 = Ah; a.sA1 = (long long)in.n * in.n; a.lda1 = in.n;
+  a.B1 = Xh + in.offS; a.sB1 = T; a.ldb1 = in.n; a.L1 = in.n;
+  a.A2 = Xh + in.offS; a.sA2 = T; a.lda2 = in.n;
+  a.B2 = Bh; a.sB2 = (long long)in.s * in.s; a.ldb2 = in.s; a.L2 = in.s;
+  a.Y = Yh + in.offS; a.sY = T; a.ldy = in.n;
+  a.M = in.n; a.N = in.s; a.K = in.K; a.nyq = in.nyq; a.sgn2 = -1.0;
+  gemm_tile<Real>(a, it.y, it.z, it.w);
+}
+
+// --- small per-instance kernels ---------------------------------------------------------------------
+__global__ void k_b_finalize_norm(BDev d, const double* __restrict__ P, int which) {
+  // which 0: ||C|| from streaming partials; 1: residual from tube-block partials
+  const int i = blockIdx.x;
+  const BInst& in = d.inst[i];
+  if (which == 1 && !d.cyc[i]) return;
+  const double v = which == 0 ? inst_sum(P, in.nb0, in.nb1) : inst_sum(P, in.tb0, in.tb1);
+  if (threadIdx.x == 0) {
+    double* sc = d.sc + 16 * i;
+    const double nv = sqrt(v);
+    if (which == 0) {
+      sc[SC_NORMC] = nv;
+    } else {
+      sc[SC_RES] = nv;
+      sc[SC_INVRES] = nv > 0.0 ? 1.0 / nv : 0.0;
+      const double tol = in.tol;
+      sc[SC_DONE] = (nv <= tol * sc[SC_NORMC] || !isfinite(nv)) ? 1.0 : 0.0;
+    }
+  }
+}
+
+__global__ void k_b_ks_init(BDev d) {
+  const int i = blockIdx.x;
+  if (!d.cyc[i]) return;
+  StLayout L{d.m};
+  double* st = d.state + i * d.stride;
+  const double beta = d.sc[16 * i + SC_RES];
+  for (long long e = threadIdx.x; e < 2ll * (d.m + 1) * d.m; e += blockDim.x) st[e] = 0.0;
+  for (int e = threadIdx.x; e <= d.m; e += blockDim.x) st[L.g() + e] = e == 0 ? beta : 0.0;
+  if (threadIdx.x == 0) {
+    d.sc[16 * i + SC_K] = 0.0;
+    d.sc[16 * i + SC_FLAGS] = 0.0;
+  }
+}
+
+// Givens update of column j for every still-iterating instance; retires instances whose
+// estimate passed, that broke down, or that reached the end of the cycle.
+__global__ void k_b_givens(BDev d, const double* __restrict__ Pnorm, int j) {
+  const int i = blockIdx.x;
+  if (!d.act[i]) return;
+  const BInst& in = d.inst[i];
+  const double hn = sqrt(inst_sum(Pnorm, in.nb0, in.nb1));
+  if (threadIdx.x != 0) return;
+  StLayout L{d.m};
+  const int m = d.m, ld = m + 1;
+  double* st = d.state + i * d.stride;
+  double* H = st + L.H();
+  double* R = st + L.R();
+  double* cs = st + L.cs();
+  double* sn = st + L.sn();
+  double* g = st + L.g();
+  double* sc = d.sc + 16 * i;
+  H[(j + 1) + ld * j] = hn;
+  for (int r = 0; r <= j + 1; ++r) R[r + ld * j] = H[r + ld * j];
+  for (int q = 0; q < j; ++q) {
+    const double a = R[q + ld * j], b = R[q + 1 + ld * j];
+    R[q + ld * j] = cs[q] * a + sn[q] * b;
+    R[q + 1 + ld * j] = -sn[q] * a + cs[q] * b;
+  }
+  const double a = R[j + ld * j], b = R[j + 1 + ld * j];
+  const double r = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (r > 0.0) {
+    c = a / r;
+    s = b / r;
+  }
+  cs[j] = c;
+  sn[j] = s;
+  R[j + ld * j] = r;
+  R[j + 1 + ld * j] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  const double est = fabs(g[j + 1]);
+  const double res = sc[SC_RES];
+  sc[SC_EST] = est;
+  sc[SC_H] = hn;
+  sc[SC_INVH] = hn > 0.0 ? 1.0 / hn : 0.0;
+  sc[SC_K] = j + 1;
+  sc[SC_ITERS] += 1.0;
+  const bool broke = hn <= 1e-14 * res;
+  if (!isfinite(est) || !isfinite(hn)) sc[SC_FLAGS] = 4.0;
+  if (broke || !isfinite(est) || est <= in.tol * sc[SC_NORMC] || (d.mixed && est <= d.inner_tol * res) ||
+      j + 1 == m)
+    d.act[i] = 0;
+}
+
+__global__ void k_b_solve_y(BDev d) {
+  const int i = blockIdx.x;
+  if (!d.cyc[i] || threadIdx.x != 0) return;
+  StLayout L{d.m};
+  const int m = d.m, ld = m + 1;
+  double* st = d.state + i * d.stride;
+  const double* R = st + L.R();
+  const double* g = st + L.g();
+  double* y = st + L.y();
+  const int k = (int)d.sc[16 * i + SC_K];
+  for (int r = k - 1; r >= 0; --r) {
+    double v = g[r];
+    for (int q = r + 1; q < k; ++q) v -= R[r + ld * q] * y[q];
+    y[r] = v / R[r + ld * r];
+  }
+}
+
+// --- host orchestration -----------------------------------------------------------------------------
+// Kernels are loaded lazily on first launch, and loading is not allowed while a stream is being
+// captured; every kernel of the captured cycle is therefore loaded (cudaFuncGetAttributes) first.
+template <typename T, typename Real2>
+void preload_cycle_kernels() {
+  cudaFuncAttributes fa;
+  const void* fns[] = {
+      (const void*)k_b_ks_init, (const void*)k_b_scale_R<T>, (const void*)k_b_rfft<T, Real2, 0, 0>,
+      (const void*)k_b_gemm<T, 0>, (const void*)k_b_irfft<T, Real2, 0>, (const void*)k_b_dot<T>,
+      (const void*)k_b_mgs<T>, (const void*)k_b_givens, (const void*)k_b_scale_W<T>, (const void*)k_b_solve_y,
+      (const void*)k_b_axpy<T>, (const void*)k_b_rfft<double, double2, 1, 1>, (const void*)k_b_gemm<double, 1>,
+      (const void*)k_b_irfft<double, double2, 1>, (const void*)k_b_finalize_norm};
+  for (const void* f : fns) TS_CUDA(cudaFuncGetAttributes(&fa, f));
+}
+
+struct BatchPlan {
+  std::vector<BInst> inst;
+  std::vector<int> nb_inst, tb_inst;
+  std::vector<long long> nb_off, tb_off;
+  std::vector<int4> items;
+  long long totN = 0, totS = 0;
+};
+
+// Records one restart cycle on `st`; returns the number of kernels it launched.
+template <typename T, typename Real2>
+int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Real2* Yh, double* R, double2* Xh64,
+                  double2* Yh64, const int4* items, double* P0, double* P1, double* Pt, cudaStream_t st) {
+  using Real = T;
+  const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size(), nit = (int)plan.items.size();
+  const int count = d.count, m = d.m;
+  double* Pp[2] = {P0, P1};
+  int kernels = 0;
+  k_b_ks_init<<<count, 256, 0, st>>>(d);
+  k_b_scale_R<T><<<nbs, 256, 0, st>>>(d, R, basis(V, d.totN, 0));
+  kernels += 2;
+  for (int j = 0; j < m; ++j) {
+    k_b_rfft<Real, Real2, 0, 0><<<ntb, kTubes, 0, st>>>(d, basis(V, d.totN, j), Xh);
+    k_b_gemm<Real, 0><<<nit, kGemmNT, 0, st>>>(d, items, Xh, Yh);
+    k_b_irfft<Real, Real2, 0><<<ntb, kTubes, 0, st>>>(d, Yh, W, nullptr);
+    k_b_dot<T><<<nbs, 256, 0, st>>>(d, basis(V, d.totN, 0), W, Pp[0]);
+    for (int i = 0; i <= j; ++i)
+      k_b_mgs<T><<<nbs, 256, 0, st>>>(d, W, basis(V, d.totN, i), i < j ? basis(V, d.totN, i + 1) : nullptr,
+                                      Pp[i & 1], Pp[(i + 1) & 1], i, j);
+    k_b_givens<<<count, 256, 0, st>>>(d, Pp[(j + 1) & 1], j);
+    k_b_scale_W<T><<<nbs, 256, 0, st>>>(d, W, basis(V, d.totN, j + 1));
+    kernels += 6 + j + 1;
+  }
+  k_b_solve_y<<<count, 32, 0, st>>>(d);
+  k_b_axpy<T><<<nbs, 256, 0, st>>>(d, V);
+  // true residual R = C - M(X) in FP64
+  k_b_rfft<double, double2, 1, 1><<<ntb, kTubes, 0, st>>>(d, nullptr, Xh64);
+  k_b_gemm<double, 1><<<nit, kGemmNT, 0, st>>>(d, items, Xh64, Yh64);
+  k_b_irfft<double, double2, 1><<<ntb, kTubes, 0, st>>>(d, Yh64, R, Pt);
+  k_b_finalize_norm<<<count, 256, 0, st>>>(d, Pt, 1);
+  kernels += 6;
+  TS_CUDA(cudaGetLastError());
+  return kernels;
+}
+
+}  // namespace
+
+ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const ts_solve_opts* opts,
+                        ts_solve_info* infos, int* statuses, ts_stream stream) {
+  TS_REQUIRE(count >= 1 && insts && opts, "ts_batched_solve: bad arguments");
+  const ts_solve_opts& o = *opts;
+  TS_REQUIRE(o.restart >= 1 && o.restart <= 128, "ts_batched_solve: restart must be in 1..128");
+  TS_REQUIRE(o.tol > 0.0, "ts_batched_solve: tol must be positive");
+  TS_REQUIRE(o.precision == TS_FP64 || o.precision == TS_MIXED_FP32,
+             "ts_batched_solve: precision must be TS_FP64 or TS_MIXED_FP32");
+  TS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  const bool mixed = o.precision == TS_MIXED_FP32;
+  const int m = o.restart;
+  BatchPlan plan;
+  plan.inst.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const ts_instance& u = insts[i];
+    TS_REQUIRE(u.op && u.C && u.X, "ts_batched_solve: instance with a null pointer");
+    ts_op* op = const_cast<ts_op*>(u.op);
+    TS_REQUIRE(!op->sp, "ts_batched_solve: dense operators only");
+    TS_REQUIRE(op->p <= 64, "ts_batched_solve: p must be <= 64");
+    TS_REQUIRE(is_device_ptr(u.C) && is_device_ptr(u.X), "ts_batched_solve: C and X must be device memory");
+    BInst& b = plan.inst[i];
+    b.X = u.X;
+    b.C = u.C;
+    b.Ah = op->Ah;
+    b.Bh = op->Bh;
+    if (mixed) {
+      ensure_f32_operator(op, user);
+      b.Ah32 = op->Ah32;
+      b.Bh32 = op->Bh32;
+    }
+    b.n = op->n; b.s = op->s; b.p = op->p; b.K = op->K; b.nyq = nyquist_index(op->p);
+    b.T = (long long)b.n * b.s;
+    b.N = b.T * b.p;
+    b.offN = plan.totN;
+    b.offS = plan.totS;
+    plan.totN += b.N;
+    plan.totS += (long long)b.K * b.T;
+    b.tol = u.tol > 0 ? u.tol : o.tol;
+    b.nb0 = (int)plan.nb_inst.size();
+    for (long long l = 0; l < b.N; l += kChunk) {
+      plan.nb_inst.push_back(i);
+      plan.nb_off.push_back(l);
+    }
+    b.nb1 = (int)plan.nb_inst.size();
+    b.tb0 = (int)plan.tb_inst.size();
+    for (long long t = 0; t < b.T; t += kTubes) {
+      plan.tb_inst.push_back(i);
+      plan.tb_off.push_back(t);
+    }
+    b.tb1 = (int)plan.tb_inst.size();
+    for (int k = 0; k < b.K; ++k)
+      for (int i0 = 0; i0 < b.n; i0 += kGemmBM)
+        for (int j0 = 0; j0 < b.s; j0 += kGemmBN) plan.items.push_back(make_int4(i, k, i0, j0));
+  }
+  // Largest tiles first (reduction length n + s; real slices are a quarter of the work).
+  std::stable_sort(plan.items.begin(), plan.items.end(), [&](const int4& a, const int4& b) {
+    auto cost = [&](const int4& q) {
+      const BInst& x = plan.inst[q.x];
+      const double w = (q.y == 0 || q.y == x.nyq) ? 1.0 : 4.0;
+      return w * (x.n + x.s);
+    };
+    return cost(a) > cost(b);
+  });
+  TS_REQUIRE(plan.items.size() < (size_t)INT32_MAX && plan.nb_inst.size() < (size_t)INT32_MAX, "batch too large");
+  const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+  auto get = [&](const char* name, size_t bytes) { return ctx->ws.get(name, bytes); };
+  char* base = (char*)get("b_tables", sizeof(BInst) * count + 16 * (plan.nb_inst.size() + plan.tb_inst.size()) +
+                                          sizeof(int4) * plan.items.size() + 1024);
+  BInst* d_inst = (BInst*)base;
+  int* d_nb_inst = (int*)(d_inst + count);
+  long long* d_nb_off = (long long*)(((uintptr_t)(d_nb_inst + plan.nb_inst.size()) + 15) & ~(uintptr_t)15);
+  int* d_tb_inst = (int*)(d_nb_off + plan.nb_off.size());
+  long long* d_tb_off = (long long*)(((uintptr_t)(d_tb_inst + plan.tb_inst.size()) + 15) & ~(uintptr_t)15);
+  int4* d_items = (int4*)(((uintptr_t)(d_tb_off + plan.tb_off.size()) + 15) & ~(uintptr_t)15);
+  // the tables are copied from pageable memory: synchronous, before anything is captured
+  TS_CUDA(cudaMemcpy(d_inst, plan.inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
+  TS_CUDA(cudaMemcpy(d_nb_inst, plan.nb_inst.data(), sizeof(int) * plan.nb_inst.size(), cudaMemcpyHostToDevice));
+  TS_CUDA(cudaMemcpy(d_nb_off, plan.nb_off.data(), sizeof(long long) * plan.nb_off.size(), cudaMemcpyHostToDevice));
+  TS_CUDA(cudaMemcpy(d_tb_inst, plan.tb_inst.data(), sizeof(int) * plan.tb_inst.size(), cudaMemcpyHostToDevice));
+  TS_CUDA(cudaMemcpy(d_tb_off, plan.tb_off.data(), sizeof(long long) * plan.tb_off.size(), cudaMemcpyHostToDevice));
+  TS_CUDA(cudaMemcpy(d_items, plan.items.data(), sizeof(int4) * plan.items.size(), cudaMemcpyHostToDevice));
+
+  void* V = get("b_V", tsz * (size_t)(m + 1) * plan.totN);
+  void* W = get("b_W", tsz * (size_t)plan.totN);
+  double* R = (double*)get("b_R", sizeof(double) * (size_t)plan.totN);
+  void* Xh = get("b_Xh", 2 * tsz * (size_t)plan.totS);
+  void* Yh = get("b_Yh", 2 * tsz * (size_t)plan.totS);
+  double2* Xh64 = mixed ? (double2*)get("b_Xh64", sizeof(double2) * (size_t)plan.totS) : (double2*)Xh;
+  double2* Yh64 = mixed ? (double2*)get("b_Yh64", sizeof(double2) * (size_t)plan.totS) : (double2*)Yh;
+  const size_t np = std::max(plan.nb_inst.size(), plan.tb_inst.size());
+  double* P0 = (double*)get("b_P0", sizeof(double) * np);
+  double* P1 = (double*)get("b_P1", sizeof(double) * np);
+  double* Pt = (double*)get("b_Pt", sizeof(double) * np);
+  double* sc = (double*)get("b_sc", sizeof(double) * 16 * count);
+  int* flags = (int*)get("b_flags", sizeof(int) * 2 * count);
+  const long long stride = state_stride(m);
+  double* state = (double*)get("b_state", sizeof(double) * (size_t)stride * count);
+
+  BDev d{};
+  d.inst = d_inst;
+  d.count = count;
+  d.m = m;
+  d.totN = plan.totN;
+  d.totS = plan.totS;
+  d.nb_inst = d_nb_inst;
+  d.nb_off = d_nb_off;
+  d.tb_inst = d_tb_inst;
+  d.tb_off = d_tb_off;
+  d.cyc = flags;
+  d.act = flags + count;
+  d.sc = sc;
+  d.state = state;
+  d.stride = stride;
+  d.inner_tol = mixed ? (o.inner_tol > 0 ? o.inner_tol : 1e-6) : 0.0;
+  d.mixed = mixed ? 1 : 0;
+
+  // A private stream for the captured cycle, ordered after the caller's stream.
+  if (!ctx->bstream) TS_CUDA(cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking));
+  cudaStream_t st = ctx->bstream;
+  TS_CUDA(cudaEventRecord(ctx->ev0, user));
+  TS_CUDA(cudaStreamWaitEvent(st, ctx->ev0, 0));
+  cudaEvent_t t0, t1;
+  TS_CUDA(cudaEventCreate(&t0));
+  TS_CUDA(cudaEventCreate(&t1));
+  TS_CUDA(cudaEventRecord(t0, st));
+
+  std::vector<int> hflags(2 * count, 1);
+  TS_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice, st));
+  TS_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * 16 * count, st));
+  const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size(), nit = (int)plan.items.size();
+  k_b_normC<<<nbs, 256, 0, st>>>(d, P0);
+  k_b_finalize_norm<<<count, 256, 0, st>>>(d, P0, 0);
+  k_b_rfft<double, double2, 1, 1><<<ntb, kTubes, 0, st>>>(d, nullptr, Xh64);
+  k_b_gemm<double, 1><<<nit, kGemmNT, 0, st>>>(d, d_items, Xh64, Yh64);
+  k_b_irfft<double, double2, 1><<<ntb, kTubes, 0, st>>>(d, Yh64, R, Pt);
+  k_b_finalize_norm<<<count, 256, 0, st>>>(d, Pt, 1);
+  count_launch(6);
+  TS_CUDA(cudaGetLastError());
+
+  std::vector<double> hsc(16 * count);
+  std::vector<int> done(count, 0), cycles(count, 0);
+  cudaGraphExec_t exec = nullptr;
+  int graph_kernels = 0;
+  int max_cycles = mixed ? (o.max_outer > 0 ? o.max_outer : 50) : o.max_restarts;
+  int launched = 0;
+  ts_status overall = TS_OK;
+  try {
+    for (int cycle = 0; cycle <= max_cycles; ++cycle) {
+      TS_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(double) * 16 * count, cudaMemcpyDeviceToHost, st));
+      TS_CUDA(cudaStreamSynchronize(st));
+      int remaining = 0;
+      for (int i = 0; i < count; ++i) {
+        done[i] = hsc[16 * i + SC_DONE] != 0.0 || hsc[16 * i + SC_FLAGS] != 0.0;
+        if (!done[i]) ++remaining;
+      }
+      if (remaining == 0 || cycle == max_cycles) break;
+      for (int i = 0; i < count; ++i) {
+        hflags[i] = done[i] ? 0 : 1;
+        hflags[count + i] = hflags[i];
+        if (!done[i]) ++cycles[i];
+      }
+      TS_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice, st));
+      TS_CUDA(cudaStreamSynchronize(st));
+      if (!exec) {
+        if (mixed) preload_cycle_kernels<float, float2>();
+        else preload_cycle_kernels<double, double2>();
+        cudaGraph_t graph;
+        TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        if (mixed)
+          graph_kernels = record_cycle<float, float2>(d, plan, (float*)V, (float*)W, (float2*)Xh, (float2*)Yh, R, Xh64, Yh64, d_items,
+                                      P0, P1, Pt, st);
+        else
+          graph_kernels = record_cycle<double, double2>(d, plan, (double*)V, (double*)W, (double2*)Xh, (double2*)Yh, R, Xh64, Yh64,
+                                        d_items, P0, P1, Pt, st);
+        TS_CUDA(cudaStreamEndCapture(st, &graph));
+        TS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        TS_CUDA(cudaGraphDestroy(graph));
+      }
+      TS_CUDA(cudaGraphLaunch(exec, st));
+      count_launch(graph_kernels);
+      ++launched;
+    }
+  } catch (...) {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    throw;
+  }
+  TS_CUDA(cudaEventRecord(t1, st));
+  TS_CUDA(cudaEventSynchronize(t1));
+  float ms = 0.f;
+  TS_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+  if (exec) TS_CUDA(cudaGraphExecDestroy(exec));
+  TS_CUDA(cudaEventDestroy(t0));
+  TS_CUDA(cudaEventDestroy(t1));
+  TS_CUDA(cudaEventRecord(ctx->ev1, st));
+  TS_CUDA(cudaStreamWaitEvent(user, ctx->ev1, 0));
+  for (int i = 0; i < count; ++i) {
+    const double* s = hsc.data() + 16 * i;
+    ts_status sti = TS_NOT_CONVERGED;
+    if (s[SC_FLAGS] != 0.0 || !std::isfinite(s[SC_RES])) sti = TS_ERR_NONFINITE;
+    else if (s[SC_DONE] != 0.0) sti = TS_OK;
+    if (statuses) statuses[i] = sti;
+    if (sti != TS_OK && overall == TS_OK) overall = sti == TS_ERR_NONFINITE ? TS_ERR_NONFINITE : TS_NOT_CONVERGED;
+    if (infos) {
+      ts_solve_info inf{};
+      inf.iters = (int)s[SC_ITERS];
+      inf.cycles = cycles[i];
+      inf.outer = mixed ? cycles[i] : 0;
+      inf.applies_fp64 = 1 + cycles[i] + (mixed ? 0 : inf.iters);
+      inf.applies_low = mixed ? inf.iters : 0;
+      inf.normC = s[SC_NORMC];
+      inf.relres_true = s[SC_NORMC] > 0 ? s[SC_RES] / s[SC_NORMC] : s[SC_RES];
+      inf.relres_est = s[SC_NORMC] > 0 ? s[SC_EST] / s[SC_NORMC] : s[SC_EST];
+      inf.ms_total = ms;
+      infos[i] = inf;
+    }
+  }
+  (void)launched;
+  return overall;
+}
+
+}  // namespace ts

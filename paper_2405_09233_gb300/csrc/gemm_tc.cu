@@ -140,6 +140,8 @@ struct TcMaps {
   CUtensorMap xc_re, xc_im;    // X_k column-major    [K][s][ldn]
   CUtensorMap xr_re, xr_im;    // X_k row-major       [K][n][lds]
   CUtensorMap b_re, b_im;      // B_k column-major    [K][s][lds]
+  // split TF32 (PARTS = 3): the low parts v - tf32(v) of the same planes
+  CUtensorMap a_re_lo, a_im_lo, xc_re_lo, xc_im_lo, xr_re_lo, xr_im_lo, b_re_lo, b_im_lo;
 };
 
 template <int BN, int ESZ>
@@ -154,7 +156,10 @@ struct TcCfg {
   static constexpr int kSubK = 128 / 32;                     // MMA K steps per stage (32 bytes each)
 };
 
-template <int BN, int ESZ>
+// PARTS = 1: one product per operand pair.  PARTS = 3 (split TF32): every l-block is visited three
+// times, hi*hi, hi*lo and lo*hi, accumulating in the same FP32 TMEM accumulators (FP32-level
+// accuracy on the TF32 tensor pipe).
+template <int BN, int ESZ, int PARTS>
 __global__ void __launch_bounds__(192, 1)
     k_tc_sylv(const __grid_constant__ TcMaps maps, float2* __restrict__ Y, int n, int s, int nyq, int* err) {
   using Cfg = TcCfg<BN, ESZ>;
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(192, 1)
   const bool real = (k == 0) || (k == nyq);
   const int it1 = (n + Cfg::kElemsK - 1) / Cfg::kElemsK;      // stages of the A_k X_k product
   const int it2 = (s + Cfg::kElemsK - 1) / Cfg::kElemsK;      // stages of the X_k B_k product
-  const int iters = it1 + it2;
+  const int iters = PARTS * (it1 + it2);
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < Cfg::kStages; ++q) {
@@ -202,18 +207,20 @@ __global__ void __launch_bounds__(192, 1)
         mbar_expect_tx(full, Cfg::kStage);
         const uint32_t sA = base + slot * Cfg::kStage;
         const uint32_t sAi = sA + Cfg::kTileA, sB = sA + 2 * Cfg::kTileA, sBi = sB + Cfg::kTileB;
-        if (it < it1) {
-          const int l0 = it * Cfg::kElemsK;
-          tma_load_3d(sA, &maps.a_re, l0, i0, k, full);
-          tma_load_3d(sAi, &maps.a_im, l0, i0, k, full);
-          tma_load_3d(sB, &maps.xc_re, l0, j0, k, full);
-          tma_load_3d(sBi, &maps.xc_im, l0, j0, k, full);
+        const int blk = it / PARTS, part = it % PARTS;
+        const bool alo = part == 2, blo = part == 1;
+        if (blk < it1) {
+          const int l0 = blk * Cfg::kElemsK;
+          tma_load_3d(sA, alo ? &maps.a_re_lo : &maps.a_re, l0, i0, k, full);
+          tma_load_3d(sAi, alo ? &maps.a_im_lo : &maps.a_im, l0, i0, k, full);
+          tma_load_3d(sB, blo ? &maps.xc_re_lo : &maps.xc_re, l0, j0, k, full);
+          tma_load_3d(sBi, blo ? &maps.xc_im_lo : &maps.xc_im, l0, j0, k, full);
         } else {
-          const int l0 = (it - it1) * Cfg::kElemsK;
-          tma_load_3d(sA, &maps.xr_re, l0, i0, k, full);
-          tma_load_3d(sAi, &maps.xr_im, l0, i0, k, full);
-          tma_load_3d(sB, &maps.b_re, l0, j0, k, full);
-          tma_load_3d(sBi, &maps.b_im, l0, j0, k, full);
+          const int l0 = (blk - it1) * Cfg::kElemsK;
+          tma_load_3d(sA, alo ? &maps.xr_re_lo : &maps.xr_re, l0, i0, k, full);
+          tma_load_3d(sAi, alo ? &maps.xr_im_lo : &maps.xr_im, l0, i0, k, full);
+          tma_load_3d(sB, blo ? &maps.b_re_lo : &maps.b_re, l0, j0, k, full);
+          tma_load_3d(sBi, blo ? &maps.b_im_lo : &maps.b_im, l0, j0, k, full);
         }
       }
     }
@@ -240,7 +247,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int kk = 0; kk < Cfg::kSubK; ++kk) {
           const uint64_t o = (uint64_t)(kk * 2);   // 32 bytes >> 4
           const uint32_t first = (it == 0 && kk == 0) ? 0u : 1u;
-          if (it < it1) {
+          if (it / PARTS < it1) {
             mma_issue(d_re, dAr + o, dBr + o, idp, first, ESZ == 4);
             if (!real) {
               mma_issue(d_re, dAi + o, dBi + o, idn, 1u, ESZ == 4);
@@ -307,9 +314,14 @@ template <> __device__ __forceinline__ float to_op<float>(float v) {
   return __uint_as_float(r);
 }
 
+// Low part of the split-TF32 representation: tf32(v - tf32(v)).
+__device__ __forceinline__ float tf32_lo(float v) { return to_op<float>(v - to_op<float>(v)); }
+
 // A_k (double2, column-major n x n) -> planes [k][i][ld] (row-major), via a 32 x 32 tile transpose.
+// With lo planes given, re/im receive tf32(v) and re_lo/im_lo receive tf32(v - tf32(v)).
 template <typename OpT>
-__global__ void k_prep_A(const double2* __restrict__ Ah, OpT* __restrict__ re, OpT* __restrict__ im, int n, int ld) {
+__global__ void k_prep_A(const double2* __restrict__ Ah, OpT* __restrict__ re, OpT* __restrict__ im, int n, int ld,
+                         float* __restrict__ re_lo, float* __restrict__ im_lo) {
   __shared__ float tr[32][33], ti[32][33];
   const int k = blockIdx.z;
   const int i0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
@@ -326,8 +338,13 @@ __global__ void k_prep_A(const double2* __restrict__ Ah, OpT* __restrict__ re, O
     const int i = i0 + q, l = l0 + threadIdx.x;
     if (i < n && l < ld) {
       const long long o = (long long)k * n * ld + (long long)i * ld + l;
-      re[o] = to_op<OpT>(l < n ? tr[threadIdx.x][q] : 0.f);
-      im[o] = to_op<OpT>(l < n ? ti[threadIdx.x][q] : 0.f);
+      const float vr = l < n ? tr[threadIdx.x][q] : 0.f, vi = l < n ? ti[threadIdx.x][q] : 0.f;
+      re[o] = to_op<OpT>(vr);
+      im[o] = to_op<OpT>(vi);
+      if (re_lo) {
+        re_lo[o] = tf32_lo(vr);
+        im_lo[o] = tf32_lo(vi);
+      }
     }
   }
 }
@@ -335,7 +352,7 @@ __global__ void k_prep_A(const double2* __restrict__ Ah, OpT* __restrict__ re, O
 // B_k (double2, column-major s x s) -> planes [k][j][ld] (no transpose), negative-free.
 template <typename OpT>
 __global__ void k_prep_B(const double2* __restrict__ Bh, OpT* __restrict__ re, OpT* __restrict__ im, int s, int ld,
-                         int K) {
+                         int K, float* __restrict__ re_lo, float* __restrict__ im_lo) {
   const long long total = (long long)K * s * ld;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const int l = (int)(e % ld);
@@ -345,13 +362,18 @@ __global__ void k_prep_B(const double2* __restrict__ Bh, OpT* __restrict__ re, O
     if (l < s) v = Bh[(long long)k * s * s + (long long)j * s + l];
     re[e] = to_op<OpT>((float)v.x);
     im[e] = to_op<OpT>((float)v.y);
+    if (re_lo) {
+      re_lo[e] = tf32_lo((float)v.x);
+      im_lo[e] = tf32_lo((float)v.y);
+    }
   }
 }
 
 // Planar DFT along mode 3 of an FP32 tensor: X (n x s x p) -> planes [k][j][ldn] (column-major X_k).
 template <typename OpT, int PMAX>
 __global__ void __launch_bounds__(256) k_rfft_planar(const float* __restrict__ X, OpT* __restrict__ re,
-                                                     OpT* __restrict__ im, int n, int s, int p, int ldn) {
+                                                     OpT* __restrict__ im, int n, int s, int p, int ldn,
+                                                     float* __restrict__ re_lo, float* __restrict__ im_lo) {
   __shared__ float tc[PMAX], tsn[PMAX];
   for (int r = threadIdx.x; r < p; r += blockDim.x) {
     double sv, cv;
@@ -384,6 +406,10 @@ __global__ void __launch_bounds__(256) k_rfft_planar(const float* __restrict__ X
       }
       re[kk * Tp + e] = to_op<OpT>(a);
       im[kk * Tp + e] = to_op<OpT>(b);
+      if (re_lo) {
+        re_lo[kk * Tp + e] = tf32_lo(a);
+        im_lo[kk * Tp + e] = tf32_lo(b);
+      }
     }
   }
 }
@@ -391,7 +417,8 @@ __global__ void __launch_bounds__(256) k_rfft_planar(const float* __restrict__ X
 // Power-of-two p: register FFT version of k_rfft_planar.
 template <typename OpT, int P>
 __global__ void __launch_bounds__(256) k_rfft_planar_pow2(const float* __restrict__ X, OpT* __restrict__ re,
-                                                          OpT* __restrict__ im, int n, int s, int ldn) {
+                                                          OpT* __restrict__ im, int n, int s, int ldn,
+                                                          float* __restrict__ re_lo, float* __restrict__ im_lo) {
   __shared__ float tc[P], tsn[P];
   for (int r = threadIdx.x; r < P; r += blockDim.x) {
     double sv, cv;
@@ -410,6 +437,10 @@ __global__ void __launch_bounds__(256) k_rfft_planar_pow2(const float* __restric
                        [&](int kk, float a, float b) {
                          re[kk * Tp + e] = to_op<OpT>(a);
                          im[kk * Tp + e] = to_op<OpT>(b);
+                         if (re_lo) {
+                           re_lo[kk * Tp + e] = tf32_lo(a);
+                           im_lo[kk * Tp + e] = tf32_lo(b);
+                         }
                        },
                        tc, tsn);
   }
@@ -476,16 +507,16 @@ void make_map(CUtensorMap* m, const void* base, int esz, int ld, int cols, int r
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-template <int BN, int ESZ>
+template <int BN, int ESZ, int PARTS>
 void launch_tc(const TcMaps& maps, float2* Y, int n, int s, int K, int nyq, int* err, cudaStream_t st) {
   using Cfg = TcCfg<BN, ESZ>;
   static bool attr_set = false;
   if (!attr_set) {
-    TS_CUDA(cudaFuncSetAttribute(k_tc_sylv<BN, ESZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+    TS_CUDA(cudaFuncSetAttribute(k_tc_sylv<BN, ESZ, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
     attr_set = true;
   }
   dim3 grid((s + BN - 1) / BN, (n + kTileM - 1) / kTileM, K);
-  k_tc_sylv<BN, ESZ><<<grid, 192, Cfg::kSmem, st>>>(maps, Y, n, s, nyq, err);
+  k_tc_sylv<BN, ESZ, PARTS><<<grid, 192, Cfg::kSmem, st>>>(maps, Y, n, s, nyq, err);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -494,13 +525,15 @@ template <typename OpT>
 void prepare_operator(ts_op* op, TcOperands& t, cudaStream_t st) {
   const int n = op->n, s = op->s, K = op->K;
   dim3 blk(32, 8);
-  k_prep_A<OpT><<<dim3((n + 31) / 32, (t.ldn + 31) / 32, K), blk, 0, st>>>(op->Ah, (OpT*)t.a_re, (OpT*)t.a_im, n, t.ldn);
+  k_prep_A<OpT><<<dim3((n + 31) / 32, (t.ldn + 31) / 32, K), blk, 0, st>>>(
+      op->Ah, (OpT*)t.a_re, (OpT*)t.a_im, n, t.ldn, (float*)t.a_re_lo, (float*)t.a_im_lo);
   count_launch();
   TS_CUDA(cudaGetLastError());
   const long long tot = (long long)K * s * t.lds;
   int g = (int)((tot + 255) / 256);
   if (g > 152 * 16) g = 152 * 16;
-  k_prep_B<OpT><<<g, 256, 0, st>>>(op->Bh, (OpT*)t.b_re, (OpT*)t.b_im, s, t.lds, K);
+  k_prep_B<OpT><<<g, 256, 0, st>>>(op->Bh, (OpT*)t.b_re, (OpT*)t.b_im, s, t.lds, K, (float*)t.b_re_lo,
+                                   (float*)t.b_im_lo);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -511,22 +544,43 @@ void planar_dft(const float* X, TcWork& w, int n, int s, int p, int ldn, int lds
   int g = (int)((Tp + 255) / 256);
   if (g > 152 * 16) g = 152 * 16;
   OpT* cre = (OpT*)w.xc_re; OpT* cim = (OpT*)w.xc_im;
-  if (p == 4) k_rfft_planar_pow2<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn);
-  else if (p == 8) k_rfft_planar_pow2<OpT, 8><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn);
-  else if (p == 16) k_rfft_planar_pow2<OpT, 16><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn);
-  else if (p == 32) k_rfft_planar_pow2<OpT, 32><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn);
-  else if (p <= 4) k_rfft_planar<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
-  else if (p <= 8) k_rfft_planar<OpT, 8><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
-  else if (p <= 16) k_rfft_planar<OpT, 16><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
-  else if (p <= 32) k_rfft_planar<OpT, 32><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn);
+  float* lre = (float*)w.xc_re_lo; float* lim = (float*)w.xc_im_lo;
+  if (p == 4) k_rfft_planar_pow2<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn, lre, lim);
+  else if (p == 8) k_rfft_planar_pow2<OpT, 8><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn, lre, lim);
+  else if (p == 16) k_rfft_planar_pow2<OpT, 16><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn, lre, lim);
+  else if (p == 32) k_rfft_planar_pow2<OpT, 32><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn, lre, lim);
+  else if (p <= 4) k_rfft_planar<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn, lre, lim);
+  else if (p <= 8) k_rfft_planar<OpT, 8><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn, lre, lim);
+  else if (p <= 16) k_rfft_planar<OpT, 16><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn, lre, lim);
+  else if (p <= 32) k_rfft_planar<OpT, 32><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn, lre, lim);
   else throw Error{TS_ERR_UNSUPPORTED, "tensor-core path supports p <= 32"};
   count_launch();
   TS_CUDA(cudaGetLastError());
   const int K = p / 2 + 1;
-  k_transpose_planes<OpT><<<dim3((n + 31) / 32, (lds + 31) / 32, K), dim3(32, 8), 0, st>>>(
-      cre, cim, (OpT*)w.xr_re, (OpT*)w.xr_im, n, s, ldn, lds);
+  const dim3 tg((n + 31) / 32, (lds + 31) / 32, K);
+  k_transpose_planes<OpT><<<tg, dim3(32, 8), 0, st>>>(cre, cim, (OpT*)w.xr_re, (OpT*)w.xr_im, n, s, ldn, lds);
   count_launch();
   TS_CUDA(cudaGetLastError());
+  if (lre) {
+    k_transpose_planes<float><<<tg, dim3(32, 8), 0, st>>>(lre, lim, (float*)w.xr_re_lo, (float*)w.xr_im_lo, n, s,
+                                                            ldn, lds);
+    count_launch();
+    TS_CUDA(cudaGetLastError());
+  }
+}
+
+template <int PARTS>
+void launch_by_bn(int esz, int bn, const TcMaps& maps, float2* Yh, int n, int s, int K, int nyq, int* err,
+                  cudaStream_t st) {
+  if (esz == 2) {
+    if (bn == 64) launch_tc<64, 2, PARTS>(maps, Yh, n, s, K, nyq, err, st);
+    else if (bn == 128) launch_tc<128, 2, PARTS>(maps, Yh, n, s, K, nyq, err, st);
+    else launch_tc<256, 2, PARTS>(maps, Yh, n, s, K, nyq, err, st);
+  } else {
+    if (bn == 64) launch_tc<64, 4, PARTS>(maps, Yh, n, s, K, nyq, err, st);
+    else if (bn == 128) launch_tc<128, 4, PARTS>(maps, Yh, n, s, K, nyq, err, st);
+    else launch_tc<256, 4, PARTS>(maps, Yh, n, s, K, nyq, err, st);
+  }
 }
 
 }  // namespace
@@ -535,10 +589,12 @@ void planar_dft(const float* X, TcWork& w, int n, int s, int p, int ldn, int lds
 void tc_prepare(ts_op* op, int precision, cudaStream_t st) {
   if (op->tc_prec == precision && op->tc) return;
   const int esz = precision == TS_MIXED_BF16 ? 2 : 4;
+  const bool split = precision == TS_MIXED_TF32X3;
   TcOperands* t = op->tc ? op->tc : new TcOperands();
   op->tc = t;
   t->release();
   t->esz = esz;
+  t->split = split;
   t->ldn = round_up(op->n, 64);
   t->lds = round_up(op->s, 64);
   const size_t na = (size_t)op->K * op->n * t->ldn * esz, nb = (size_t)op->K * op->s * t->lds * esz;
@@ -546,6 +602,12 @@ void tc_prepare(ts_op* op, int precision, cudaStream_t st) {
   TS_CUDA(cudaMalloc(&t->a_im, na));
   TS_CUDA(cudaMalloc(&t->b_re, nb));
   TS_CUDA(cudaMalloc(&t->b_im, nb));
+  if (split) {
+    TS_CUDA(cudaMalloc(&t->a_re_lo, na));
+    TS_CUDA(cudaMalloc(&t->a_im_lo, na));
+    TS_CUDA(cudaMalloc(&t->b_re_lo, nb));
+    TS_CUDA(cudaMalloc(&t->b_im_lo, nb));
+  }
   if (esz == 2) prepare_operator<__nv_bfloat16>(op, *t, st);
   else prepare_operator<float>(op, *t, st);
   op->tc_prec = precision;
@@ -561,9 +623,15 @@ void tc_apply(ts_ctx* ctx, ts_op* op, int precision, const float* X, float2* Yh,
   w.xc_im = ctx->ws.get("tc_xc_im", nx);
   w.xr_re = ctx->ws.get("tc_xr_re", nr);
   w.xr_im = ctx->ws.get("tc_xr_im", nr);
+  if (t.split) {
+    w.xc_re_lo = ctx->ws.get("tc_xc_re_lo", nx);
+    w.xc_im_lo = ctx->ws.get("tc_xc_im_lo", nx);
+    w.xr_re_lo = ctx->ws.get("tc_xr_re_lo", nr);
+    w.xr_im_lo = ctx->ws.get("tc_xr_im_lo", nr);
+  }
   int* err = static_cast<int*>(ctx->ws.get("tc_err", sizeof(int) * 4));
   KernelTimer& tm = ctx->timer;
-  tm.begin(st, 1, 4.0 * n * s * p + 2.0 * K * n * s * esz * 2);
+  tm.begin(st, 1, 4.0 * n * s * p + 2.0 * K * n * s * esz * 2 * (t.split ? 2 : 1));
   if (esz == 2) planar_dft<__nv_bfloat16>(X, w, n, s, p, t.ldn, t.lds, st);
   else planar_dft<float>(X, w, n, s, p, t.ldn, t.lds, st);
   tm.end(st);
@@ -577,17 +645,23 @@ void tc_apply(ts_ctx* ctx, ts_op* op, int precision, const float* X, float2* Yh,
   make_map(&maps.xr_im, w.xr_im, esz, t.lds, s, n, K, kTileM);
   make_map(&maps.b_re, t.b_re, esz, t.lds, s, s, K, bn);
   make_map(&maps.b_im, t.b_im, esz, t.lds, s, s, K, bn);
+  if (t.split) {
+    make_map(&maps.a_re_lo, t.a_re_lo, esz, t.ldn, n, n, K, kTileM);
+    make_map(&maps.a_im_lo, t.a_im_lo, esz, t.ldn, n, n, K, kTileM);
+    make_map(&maps.xc_re_lo, w.xc_re_lo, esz, t.ldn, n, s, K, bn);
+    make_map(&maps.xc_im_lo, w.xc_im_lo, esz, t.ldn, n, s, K, bn);
+    make_map(&maps.xr_re_lo, w.xr_re_lo, esz, t.lds, s, n, K, kTileM);
+    make_map(&maps.xr_im_lo, w.xr_im_lo, esz, t.lds, s, n, K, kTileM);
+    make_map(&maps.b_re_lo, t.b_re_lo, esz, t.lds, s, s, K, bn);
+    make_map(&maps.b_im_lo, t.b_im_lo, esz, t.lds, s, s, K, bn);
+  } else {
+    maps.a_re_lo = maps.a_re; maps.a_im_lo = maps.a_im; maps.xc_re_lo = maps.xc_re; maps.xc_im_lo = maps.xc_im;
+    maps.xr_re_lo = maps.xr_re; maps.xr_im_lo = maps.xr_im; maps.b_re_lo = maps.b_re; maps.b_im_lo = maps.b_im;
+  }
   const int nyq = nyquist_index(p);
   tm.begin(st, 2, gemm_flops_tc(n, s, K, nyq));
-  if (esz == 2) {
-    if (bn == 64) launch_tc<64, 2>(maps, Yh, n, s, K, nyq, err, st);
-    else if (bn == 128) launch_tc<128, 2>(maps, Yh, n, s, K, nyq, err, st);
-    else launch_tc<256, 2>(maps, Yh, n, s, K, nyq, err, st);
-  } else {
-    if (bn == 64) launch_tc<64, 4>(maps, Yh, n, s, K, nyq, err, st);
-    else if (bn == 128) launch_tc<128, 4>(maps, Yh, n, s, K, nyq, err, st);
-    else launch_tc<256, 4>(maps, Yh, n, s, K, nyq, err, st);
-  }
+  if (t.split) launch_by_bn<3>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
+  else launch_by_bn<1>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
   tm.end(st);
 }
 
@@ -602,7 +676,12 @@ void TcOperands::release() {
   cudaFree(a_im);
   cudaFree(b_re);
   cudaFree(b_im);
+  cudaFree(a_re_lo);
+  cudaFree(a_im_lo);
+  cudaFree(b_re_lo);
+  cudaFree(b_im_lo);
   a_re = a_im = b_re = b_im = nullptr;
+  a_re_lo = a_im_lo = b_re_lo = b_im_lo = nullptr;
 }
 
 }  // namespace ts

@@ -81,6 +81,7 @@ struct ts_ctx {
   ts::Workspace ws;
   double* host_scalars = nullptr;  // pinned, 256 doubles, for small device->host reads
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaStream_t bstream = nullptr;  // private stream of the batched solver (graph capture)
   ts::KernelTimer timer;
 };
 

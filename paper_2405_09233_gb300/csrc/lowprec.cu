@@ -6,7 +6,7 @@
 
 namespace ts {
 
-static void ensure_f32_operator(ts_op* op, cudaStream_t st) {
+void ensure_f32_operator(ts_op* op, cudaStream_t st) {
   if (op->Ah32) return;
   const size_t na = (size_t)op->K * op->n * op->n, nb = (size_t)op->K * op->s * op->s;
   TS_CUDA(cudaMalloc(&op->Ah32, sizeof(float2) * na));
@@ -22,7 +22,7 @@ void apply_low(ts_ctx* ctx, ts_op* op, int precision, const float* X, float* Y, 
   const long long T = (long long)n * s;
   float2* Yh = static_cast<float2*>(ctx->ws.get("low_Yh", sizeof(float2) * (size_t)K * T));
   KernelTimer& tm = ctx->timer;
-  if (precision == TS_MIXED_BF16 || precision == TS_MIXED_TF32) {
+  if (precision == TS_MIXED_BF16 || precision == TS_MIXED_TF32 || precision == TS_MIXED_TF32X3) {
     tc_apply(ctx, op, precision, X, Yh, st);
     tm.begin(st, 1, 8.0 * K * T + 4.0 * T * p);
     irfft_tube<float, float2>(Yh, Y, T, p, IRFFT_STORE, nullptr, nullptr, st);

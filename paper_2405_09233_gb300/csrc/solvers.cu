@@ -46,7 +46,8 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
   const int max_cycles = mixed ? (o.max_outer > 0 ? o.max_outer : 50) : o.max_restarts;
   // Default inner tolerance: a little above what the inner operator's rounding lets the inner
   // tGMRES resolve (FP32 ~1e-7, TF32 ~5e-4, BF16 ~4e-3 relative).
-  const double inner_default = prec == TS_MIXED_FP32 ? 1e-6 : (prec == TS_MIXED_TF32 ? 1e-3 : 1e-2);
+  const double inner_default =
+      (prec == TS_MIXED_FP32 || prec == TS_MIXED_TF32X3) ? 1e-6 : (prec == TS_MIXED_TF32 ? 1e-3 : 1e-2);
   const double inner_tol = mixed ? (o.inner_tol > 0 ? o.inner_tol : inner_default) : 0.0;
 
   T* V = static_cast<T*>(ctx->ws.get("krylov_V", sizeof(T) * (size_t)(m + 1) * N));
@@ -152,7 +153,7 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
       status = TS_ERR_NONFINITE;
       break;
     }
-    if (mixed && (prec == TS_MIXED_BF16 || prec == TS_MIXED_TF32)) {
+    if (mixed && prec != TS_MIXED_FP32) {
       int e = 0;
       TS_CUDA(cudaMemcpy(&e, tc_err, sizeof(int), cudaMemcpyDeviceToHost));
       if (e != 0) throw Error{TS_ERR_TIMEOUT, "tensor-core kernel wait expired (code " + std::to_string(e) + ")"};
@@ -191,7 +192,7 @@ ts_status solve_entry(ts_ctx* ctx, const ts_op* cop, const double* C, double* X,
   TS_REQUIRE(o.restart >= 1 && o.restart <= 256, "solve: restart must be in 1..256");
   TS_REQUIRE(o.max_restarts >= 1, "solve: max_restarts must be >= 1");
   TS_REQUIRE(o.tol > 0.0 && std::isfinite(o.tol), "solve: tol must be positive");
-  TS_REQUIRE(o.precision >= TS_FP64 && o.precision <= TS_MIXED_BF16, "solve: unknown precision");
+  TS_REQUIRE(o.precision >= TS_FP64 && o.precision <= TS_MIXED_TF32X3, "solve: unknown precision");
   TS_REQUIRE(!(o.history && o.history_cap < 0) && !(o.true_history && o.true_history_cap < 0),
              "solve: negative history capacity");
   if (method == 1 && o.precision != TS_FP64)

@@ -12,6 +12,11 @@ struct TcOperands {
   void* a_im = nullptr;
   void* b_re = nullptr;  // [K][s][lds]  column-major B_k
   void* b_im = nullptr;
+  bool split = false;       // split TF32: low parts v - tf32(v) below
+  void* a_re_lo = nullptr;
+  void* a_im_lo = nullptr;
+  void* b_re_lo = nullptr;
+  void* b_im_lo = nullptr;
   void release();
 };
 
@@ -21,6 +26,10 @@ struct TcWork {
   void* xc_im = nullptr;
   void* xr_re = nullptr;  // [K][n][lds]  row-major X_k
   void* xr_im = nullptr;
+  void* xc_re_lo = nullptr;  // split TF32 low parts (nullptr otherwise)
+  void* xc_im_lo = nullptr;
+  void* xr_re_lo = nullptr;
+  void* xr_im_lo = nullptr;
 };
 
 void tc_prepare(ts_op* op, int precision, cudaStream_t st);

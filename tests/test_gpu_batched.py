@@ -1,0 +1,102 @@
+"""GPU tests of the batched solver: many independent instances of uneven (n, s, p), each checked
+against the oracle's single-instance tGMRES (small sizes) or by its own true residual computed
+with the library's FP64 operator (the 256-instance workload)."""
+import numpy as np
+import pytest
+
+from oracle import krylov as kr, tproduct as tp
+from paper_2405_09233_gb300 import inputs
+from tests.gpu_helpers import to_dev, from_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2405_09233_gb300 import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+SHAPES = [(20, 4, 1), (33, 9, 3), (64, 16, 4), (70, 5, 7), (24, 24, 4), (40, 12, 8), (65, 3, 16), (17, 17, 2),
+          (50, 8, 5), (96, 20, 16)]
+
+
+def make_batch(ctx, shapes, seed0, scale=0.1):
+    import torch
+    probs, ops, Cs, Xs, Cn = [], [], [], [], []
+    for q, (n, s, p) in enumerate(shapes):
+        pr = inputs.dense_problem(n, s, p, seed=seed0 + q, scale=scale)
+        C = kr.sylv_apply(pr.A, pr.B, pr.Xstar)
+        probs.append(pr)
+        Cn.append(C)
+        ops.append(ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B)))
+        Cs.append(to_dev(C))
+        Xs.append(torch.zeros((p, s, n), dtype=torch.float64, device="cuda"))
+    return probs, ops, Cs, Xs, Cn
+
+
+@pytest.mark.parametrize("m", [20, 6])
+def test_batched_fp64_matches_single_instance_oracle(ctx, m):
+    probs, ops, Cs, Xs, Cn = make_batch(ctx, SHAPES, 100)
+    st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=m, tol=1e-10, precision="fp64")
+    assert st == 0 and all(v == 0 for v in sts), sts
+    for pr, C, X, info in zip(probs, Cn, Xs, infos):
+        ref = kr.tgmres(pr.A, pr.B, C, m=m, tol=1e-10)
+        Xh = from_dev(X)
+        assert tp.norm(C - kr.sylv_apply(pr.A, pr.B, Xh)) <= 1e-10 * tp.norm(C)
+        assert np.abs(Xh - ref.X).max() <= 1e-8 * np.abs(ref.X).max()
+        assert info.iters == ref.iters and info.cycles == ref.cycles, (info.iters, ref.iters)
+        assert abs(info.relres_true - ref.relres) <= 1e-11
+    for op in ops:
+        op.close()
+
+
+def test_batched_mixed_fp32_per_instance_tolerances(ctx):
+    probs, ops, Cs, Xs, Cn = make_batch(ctx, SHAPES, 200)
+    tols = [10.0 ** (-8 - 2 * q / (len(SHAPES) - 1)) for q in range(len(SHAPES))]   # 1e-8 .. 1e-10
+    st, infos, sts = ctx.batched_solve(ops, Cs, Xs, tols=tols, restart=20, precision="mixed_fp32")
+    assert st == 0 and all(v == 0 for v in sts), sts
+    for pr, C, X, tol, info in zip(probs, Cn, Xs, tols, infos):
+        Xh = from_dev(X)
+        assert tp.norm(C - kr.sylv_apply(pr.A, pr.B, Xh)) <= tol * tp.norm(C)
+        assert info.relres_true <= tol and info.outer >= 1
+    for op in ops:
+        op.close()
+
+
+def test_batched_matches_unbatched_gpu(ctx):
+    """Each instance of a batch reaches the same solution as a separate ts_tgmres_solve call."""
+    import torch
+    probs, ops, Cs, Xs, Cn = make_batch(ctx, SHAPES[:5], 300)
+    ctx.batched_solve(ops, Cs, Xs, restart=10, precision="fp64")
+    for op, C, X in zip(ops, Cs, Xs):
+        X1 = torch.zeros_like(X)
+        r = ctx.tgmres_solve(op, C, X1, restart=10)
+        assert r.status == 0
+        assert float(torch.max(torch.abs(X1 - X))) <= 1e-9 * float(torch.max(torch.abs(X1)))
+        op.close()
+
+
+def test_batched_256_instance_workload(ctx):
+    """256 instances, n log-uniform in [64, 1024], s uniform in [16, 128], p in {4, 8, 16}, FP32 inner
+    tGMRES(20) with FP64 refinement; every instance's true residual (library FP64 operator) <= 1e-10."""
+    import torch
+    specs = inputs.batched_specs(256, seed=4)
+    ops, Cs, Xs, Xstars = [], [], [], []
+    for sp in specs:
+        pr = inputs.dense_problem(sp.n, sp.s, sp.p, seed=sp.seed)
+        op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
+        Xst = to_dev(pr.Xstar)
+        ops.append(op)
+        Xstars.append(Xst)
+        Cs.append(ctx.sylv_apply(op, Xst))
+        Xs.append(torch.zeros_like(Xst))
+    st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, precision="mixed_fp32")
+    assert st == 0 and all(v == 0 for v in sts)
+    for op, C, X, Xst in zip(ops, Cs, Xs, Xstars):
+        R = C - ctx.sylv_apply(op, X)
+        assert float(torch.linalg.norm(R) / torch.linalg.norm(C)) <= 1e-10
+        assert float(torch.max(torch.abs(X - Xst))) < 1e-7
+        op.close()
