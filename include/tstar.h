@@ -42,7 +42,8 @@ typedef enum {
   TS_ERR_NOMEM = -3,     /* device or host allocation failed */
   TS_ERR_NONFINITE = -4, /* NaN/Inf met in a residual or norm */
   TS_ERR_TIMEOUT = -5,   /* a bounded device-side wait expired */
-  TS_ERR_UNSUPPORTED = -6
+  TS_ERR_UNSUPPORTED = -6,
+  TS_ERR_CORRUPTION = -7 /* a workspace guard band was overwritten (ts_workspace_check) */
 } ts_status;
 
 typedef enum {
@@ -214,6 +215,11 @@ ts_status ts_tba_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X,
  * share an eigenvalue (Theorem 2.1's condition fails) or the Schur iteration does not converge. */
 ts_status ts_t_bartels_stewart(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p,
                                const double* C, double* X, ts_stream stream);
+
+/* Verify the guard bands that follow every workspace buffer of ctx (4 KiB of a fixed pattern
+ * each): TS_ERR_CORRUPTION, with the buffer named by ts_last_error, when a kernel wrote past the
+ * end of a buffer.  Synchronises the device.  A debugging and testing aid. */
+ts_status ts_workspace_check(ts_ctx* ctx);
 
 /* Kernel statistics, for measurement.  Launch counts are process-wide (every libtstar kernel
  * launch on any context); kernel timings are per context and only collected while enabled,

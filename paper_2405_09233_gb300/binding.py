@@ -20,9 +20,10 @@ LIB_PATH = os.path.join(_PKG, "libtstar.so")
 
 TS_OK, TS_BREAKDOWN, TS_NOT_CONVERGED, TS_SINGULAR = 0, 1, 2, 3
 TS_ERR_ARG, TS_ERR_CUDA, TS_ERR_NOMEM, TS_ERR_NONFINITE, TS_ERR_TIMEOUT, TS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+TS_ERR_CORRUPTION = -7
 PRECISIONS = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3, "mixed_tf32x3": 4}
 STATUS_NAMES = {0: "ok", 1: "breakdown", 2: "not_converged", 3: "singular", -1: "err_arg", -2: "err_cuda",
-                -3: "err_nomem", -4: "err_nonfinite", -5: "err_timeout", -6: "err_unsupported"}
+                -3: "err_nomem", -4: "err_nonfinite", -5: "err_timeout", -6: "err_unsupported", -7: "err_corruption"}
 
 
 class SolveOpts(ctypes.Structure):
@@ -80,6 +81,7 @@ _SIGNATURES = {
     "ts_batched_solve": (_i, [_vp, _i, ctypes.POINTER(Instance), ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo),
                               ctypes.POINTER(_i), _vp]),
     "ts_tstar_noalloc": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp]),
+    "ts_workspace_check": (_i, [_vp]),
     "ts_stats_enable": (_i, [_vp, _i]),
     "ts_stats_get": (_i, [_vp, ctypes.POINTER(Stats)]),
     "ts_stats_reset": (_i, [_vp]),
@@ -141,6 +143,10 @@ class Context:
         if st < 0:
             raise TstarError(st, f"{what}: {lib().ts_last_error(self._h).decode()}")
         return st
+
+    def workspace_check(self):
+        """Raise TstarError if any workspace buffer was written past its end."""
+        self._check(lib().ts_workspace_check(self._h), "ts_workspace_check")
 
     # --- statistics ---------------------------------------------------------------------------
     def stats_enable(self, enable: bool = True):

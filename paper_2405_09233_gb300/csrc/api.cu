@@ -11,20 +11,34 @@ namespace ts {
 
 void* Workspace::get(const std::string& name, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) / 256 * 256;
   Buf& b = bufs[name];
   if (b.bytes < bytes) {
     if (b.ptr) TS_CUDA(cudaFree(b.ptr));
     b.ptr = nullptr;
     b.bytes = 0;
-    cudaError_t e = cudaMalloc(&b.ptr, bytes);
+    cudaError_t e = cudaMalloc(&b.ptr, bytes + kGuardBytes);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       throw Error{TS_ERR_NOMEM, "workspace '" + name + "': cudaMalloc(" + std::to_string(bytes) +
                                     ") failed: " + cudaGetErrorString(e)};
     }
+    TS_CUDA(cudaMemset(static_cast<char*>(b.ptr) + bytes, kGuardByte, kGuardBytes));
     b.bytes = bytes;
   }
   return b.ptr;
+}
+
+std::string Workspace::check() const {
+  std::vector<unsigned char> h(kGuardBytes);
+  for (const auto& kv : bufs) {
+    if (!kv.second.ptr) continue;
+    TS_CUDA(cudaMemcpy(h.data(), static_cast<const char*>(kv.second.ptr) + kv.second.bytes, kGuardBytes,
+                       cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < kGuardBytes; ++i)
+      if (h[i] != kGuardByte) return kv.first + " (guard byte " + std::to_string(i) + ")";
+  }
+  return "";
 }
 
 void Workspace::release_all() {
@@ -220,6 +234,7 @@ const char* ts_status_string(ts_status s) {
     case TS_ERR_NONFINITE: return "TS_ERR_NONFINITE";
     case TS_ERR_TIMEOUT: return "TS_ERR_TIMEOUT";
     case TS_ERR_UNSUPPORTED: return "TS_ERR_UNSUPPORTED";
+    case TS_ERR_CORRUPTION: return "TS_ERR_CORRUPTION";
   }
   return "TS_UNKNOWN";
 }
@@ -457,6 +472,20 @@ ts_status ts_batched_solve(ts_ctx* ctx, int count, const ts_instance* insts, con
   if (!ctx) return TS_ERR_ARG;
   TS_API_BEGIN
   return batched_entry(ctx, count, insts, opts, infos, statuses, stream);
+  TS_API_END(ctx)
+}
+
+ts_status ts_workspace_check(ts_ctx* ctx) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  TS_CUDA(cudaSetDevice(ctx->device));
+  TS_CUDA(cudaDeviceSynchronize());
+  const std::string bad = ctx->ws.check();
+  if (!bad.empty()) {
+    ctx->err = "workspace buffer written past its end: " + bad;
+    return TS_ERR_CORRUPTION;
+  }
+  return TS_OK;
   TS_API_END(ctx)
 }
 

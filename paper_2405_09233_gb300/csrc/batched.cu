@@ -69,16 +69,19 @@ struct BDev {
   int mixed;
 };
 
+// Per-instance Krylov state: H and its rotated copy R ((m+1) x m each), the rotations cs, sn (m),
+// the rotated right-hand side g (m+1) and the solution y (m).
 struct StLayout {
   int m;
-  __device__ long long H() const { return 0; }
-  __device__ long long R() const { return (long long)(m + 1) * m; }
-  __device__ long long cs() const { return 2ll * (m + 1) * m; }
-  __device__ long long sn() const { return cs() + m; }
-  __device__ long long g() const { return sn() + m; }
-  __device__ long long y() const { return g() + m + 1; }
+  __host__ __device__ long long H() const { return 0; }
+  __host__ __device__ long long R() const { return (long long)(m + 1) * m; }
+  __host__ __device__ long long cs() const { return 2ll * (m + 1) * m; }
+  __host__ __device__ long long sn() const { return cs() + m; }
+  __host__ __device__ long long g() const { return sn() + m; }
+  __host__ __device__ long long y() const { return g() + m + 1; }
+  __host__ __device__ long long end() const { return y() + m; }
 };
-long long state_stride(int m) { return 2ll * (m + 1) * m + 3ll * m + 1 + 8; }
+long long state_stride(int m) { return StLayout{m}.end(); }
 
 // Sum of an instance's block partials [b0, b1), identical in every block that calls it.
 __device__ __forceinline__ double inst_sum(const double* P, int b0, int b1) {

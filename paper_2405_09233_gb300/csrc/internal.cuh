@@ -34,10 +34,15 @@ struct Error {
 // ----------------------------------------------------------------------------------------------
 // Device workspace: named buffers that grow on demand and live as long as the context.
 // ----------------------------------------------------------------------------------------------
+// Every buffer carries a guard band of kGuardBytes filled with kGuardByte after its usable bytes;
+// check() reports a buffer whose guard was overwritten (an out-of-bounds write).
 struct Workspace {
+  static constexpr size_t kGuardBytes = 4096;
+  static constexpr unsigned char kGuardByte = 0xA5;
   struct Buf { void* ptr = nullptr; size_t bytes = 0; };
   std::map<std::string, Buf> bufs;
   void* get(const std::string& name, size_t bytes);
+  std::string check() const;   // "" when every guard is intact, else the first damaged buffer
   void release_all();
 };
 

@@ -16,6 +16,7 @@ def ctx():
     from paper_2405_09233_gb300 import Context
     c = Context(0)
     yield c
+    c.workspace_check()          # no kernel wrote past the end of a workspace buffer
     c.close()
 
 
@@ -77,6 +78,33 @@ def test_batched_matches_unbatched_gpu(ctx):
         assert r.status == 0
         assert float(torch.max(torch.abs(X1 - X))) <= 1e-9 * float(torch.max(torch.abs(X1)))
         op.close()
+
+
+def test_batched_repeated_calls_leave_operators_intact(ctx):
+    """Solving the same batch twice with fresh operators: the second solve must not write into any
+    other allocation (operators stay consistent with C) and must reach the same solutions."""
+    import torch
+    specs = inputs.batched_specs(24, seed=9, n_range=(40, 300), s_range=(8, 40))
+    dev_in, Cs = [], []
+    for sp in specs:
+        pr = inputs.dense_problem(sp.n, sp.s, sp.p, seed=sp.seed)
+        dev_in.append((to_dev(pr.A), to_dev(pr.B), to_dev(pr.Xstar)))
+    for A, B, Xst in dev_in:
+        op = ctx.op_create_dense(A, B)
+        Cs.append(ctx.sylv_apply(op, Xst))
+        op.close()
+    Xs = [torch.zeros_like(C) for C in Cs]
+    for rep in range(2):
+        ops = [ctx.op_create_dense(A, B) for A, B, _ in dev_in]
+        for X in Xs:
+            X.zero_()
+        st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, precision="mixed_fp32")
+        assert st == 0
+        ctx.workspace_check()
+        for op, C, X, (_, _, Xst) in zip(ops, Cs, Xs, dev_in):
+            assert float(torch.max(torch.abs(ctx.sylv_apply(op, Xst) - C))) <= 1e-9 * float(torch.max(torch.abs(C)))
+            assert float(torch.max(torch.abs(X - Xst))) < 1e-7
+            op.close()
 
 
 def test_batched_256_instance_workload(ctx):

@@ -21,6 +21,7 @@ def ctx():
     from paper_2405_09233_gb300 import Context
     c = Context(0)
     yield c
+    c.workspace_check()          # no kernel wrote past the end of a workspace buffer
     c.close()
 
 
