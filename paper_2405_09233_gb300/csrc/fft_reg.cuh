@@ -18,30 +18,50 @@ __host__ __device__ constexpr int bitrevc(int x, int bits) {
   return r;
 }
 
-// In-place decimation-in-time FFT; the inputs must already sit in bit-reversed order.
-template <typename Real, int P, bool INVERSE>
-__device__ __forceinline__ void fft_bitrev_inplace(Real (&xr)[P], Real (&xi)[P], const Real* __restrict__ tc,
-                                                   const Real* __restrict__ ts) {
+// One radix-2 stage of span LEN, then the next; LEN is a template argument so that every register
+// index is a compile-time constant (a runtime stage loop leaves the arrays in local memory).
+template <typename Real, int P, bool INVERSE, int LEN>
+struct FftStages {
+  static __device__ __forceinline__ void run(Real (&xr)[P], Real (&xi)[P], const Real* __restrict__ tc,
+                                             const Real* __restrict__ ts) {
+    constexpr int half = LEN / 2, stride = P / LEN;
 #pragma unroll
-  for (int len = 2; len <= P; len <<= 1) {
-    const int half = len >> 1;
-    const int stride = P / len;
-#pragma unroll
-    for (int start = 0; start < P; start += len) {
+    for (int start = 0; start < P; start += LEN) {
 #pragma unroll
       for (int q = 0; q < half; ++q) {
         const int a = start + q, b = start + q + half;
-        const Real wr = tc[q * stride];
-        const Real wi = INVERSE ? ts[q * stride] : -ts[q * stride];
-        const Real vr = xr[b] * wr - xi[b] * wi;
-        const Real vi = xr[b] * wi + xi[b] * wr;
+        Real vr, vi;
+        if (q == 0) {                       // twiddle 1
+          vr = xr[b];
+          vi = xi[b];
+        } else if (4 * q == LEN) {          // twiddle -+i
+          vr = INVERSE ? -xi[b] : xi[b];
+          vi = INVERSE ? xr[b] : -xr[b];
+        } else {
+          const Real wr = tc[q * stride];
+          const Real wi = INVERSE ? ts[q * stride] : -ts[q * stride];
+          vr = xr[b] * wr - xi[b] * wi;
+          vi = xr[b] * wi + xi[b] * wr;
+        }
         xr[b] = xr[a] - vr;
         xi[b] = xi[a] - vi;
         xr[a] = xr[a] + vr;
         xi[a] = xi[a] + vi;
       }
     }
+    FftStages<Real, P, INVERSE, 2 * LEN>::run(xr, xi, tc, ts);
   }
+};
+template <typename Real, int P, bool INVERSE>
+struct FftStages<Real, P, INVERSE, 2 * P> {
+  static __device__ __forceinline__ void run(Real (&)[P], Real (&)[P], const Real*, const Real*) {}
+};
+
+// In-place decimation-in-time FFT; the inputs must already sit in bit-reversed order.
+template <typename Real, int P, bool INVERSE>
+__device__ __forceinline__ void fft_bitrev_inplace(Real (&xr)[P], Real (&xi)[P], const Real* __restrict__ tc,
+                                                   const Real* __restrict__ ts) {
+  FftStages<Real, P, INVERSE, 2>::run(xr, xi, tc, ts);
 }
 
 // Forward transform of P real samples read by `load(t)`; writes the P/2+1 non-redundant outputs
