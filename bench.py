@@ -42,8 +42,11 @@ def args_parse():
     ap.add_argument("--workload", default="dense_n1024_s1024_p16")
     ap.add_argument("--precision", default=None,
                     help="default: fp64 for the dense n=s=1024 workload, mixed_fp32 for the others")
-    ap.add_argument("--variants", default="mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16",
-                    help="comma list of extra precisions to time ('' = none)")
+    ap.add_argument("--engine", choices=["dfma", "ozaki"], default="dfma",
+                    help="how FP64 applications run: FP64 CUDA cores, or emulated on the BF16 tensor cores")
+    ap.add_argument("--variants",
+                    default="mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16,fp64@ozaki,mixed_tf32x3@ozaki,mixed_bf16@ozaki",
+                    help="comma list of extra precision[@engine] runs to time ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
@@ -76,6 +79,21 @@ def peaks():
 
 TF32_OVER_BF16 = 1.1 / 2.25       # nominal dense tensor rates (PFLOP/s per GPU)
 FFMA_NOMINAL_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12   # 128 FP32 lanes/SM x 2 FLOP x 152 SMs x 2070 MHz
+
+
+def ozaki_roofline(flops_per_launch, avg_ms, sustained, share, digits=6):
+    """Emulated FP64 slice products: the tensor pipe executes S(S+1)/2 BF16 digit-pair products per
+    algorithmic FP64 product; achieved = those BF16 FLOPs / launch time (digit split included)."""
+    pk = peaks()
+    peak = pk["bf16_sustained"] if sustained else pk["bf16_burst"]
+    pairs = digits * (digits + 1) // 2
+    achieved = pairs * flops_per_launch / (avg_ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_oz_sylv (emulated FP64: %d BF16 digit-pair products on tcgen05)" % pairs,
+            "note": "peak: %s BF16 %s; FP64-equivalent rate %.2f TFLOP/s. Kernel share of the step: %.3f"
+                    % (pk["source"], "sustained" if sustained else "burst",
+                       flops_per_launch / (avg_ms * 1e-3) / 1e12, share)}
 
 
 def gemm_roofline(kind, precision, flops_per_launch, avg_ms, sustained, share):
@@ -303,10 +321,10 @@ def main():
     if a.mode == "apply":
         return run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev)
 
-    def step(precision):
+    def step(precision, engine=a.engine):
         op = ctx.op_create_dense(Ad, Bd)
         X.zero_()
-        r = ctx.tgmres_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision)
+        r = ctx.tgmres_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision, engine=engine)
         op.close()
         return r
 
@@ -341,16 +359,22 @@ def main():
     unknowns = n * s * p
     value = job_throughput(unknowns, world, ms)
 
-    # dominant kernel: whichever slice GEMM (FP64 or low precision) took more time
+    # dominant kernel: whichever slice-GEMM class (FP64 DFMA, emulated FP64, low precision) took most time
     step_ms_total = ms * a.steps
-    if st.gemm_ms >= st.lowp_ms:
+    top = max(("fp64", st.gemm_ms), ("oz", st.oz_ms), ("lowp", st.lowp_ms), key=lambda t: t[1])[0]
+    if top == "fp64":
         roofline = gemm_roofline("fp64", "fp64", st.gemm_flops / max(st.gemm_launches, 1),
                                  st.gemm_ms / max(st.gemm_launches, 1), True, st.gemm_ms / step_ms_total)
+    elif top == "oz":
+        roofline = ozaki_roofline(st.oz_flops / max(st.oz_launches, 1), st.oz_ms / max(st.oz_launches, 1),
+                                  True, st.oz_ms / step_ms_total)
     else:
         roofline = gemm_roofline("lowp", a.precision, st.lowp_flops / max(st.lowp_launches, 1),
                                  st.lowp_ms / max(st.lowp_launches, 1), True, st.lowp_ms / step_ms_total)
-    kernel_times = {"fp64_gemm_ms": st.gemm_ms / a.steps, "lowp_gemm_ms": st.lowp_ms / a.steps,
+    kernel_times = {"fp64_gemm_ms": st.gemm_ms / a.steps, "ozaki_gemm_ms": st.oz_ms / a.steps,
+                    "lowp_gemm_ms": st.lowp_ms / a.steps,
                     "fft_ms": st.fft_ms / a.steps, "fp64_gemm_launches": st.gemm_launches // a.steps,
+                    "ozaki_gemm_launches": st.oz_launches // a.steps,
                     "lowp_gemm_launches": st.lowp_launches // a.steps,
                     "fft_gbs": st.fft_bytes / max(st.fft_ms, 1e-9) / 1e6}
 
@@ -363,7 +387,7 @@ def main():
         t0 = time.perf_counter()
         op = ctx.op_create_dense(A_h, B_h)
         X_h.zero_()
-        r = ctx.tgmres_solve(op, C_h, X_h, restart=m, tol=1e-10, precision=a.precision)
+        r = ctx.tgmres_solve(op, C_h, X_h, restart=m, tol=1e-10, precision=a.precision, engine=a.engine)
         op.close()
         e2e_times.append(time.perf_counter() - t0)
         assert r.status == 0, r
@@ -372,23 +396,26 @@ def main():
            "d2h_bytes_per_step": 8 * n * s * p}
 
     variants = {}
-    for prec in [v for v in a.variants.split(",") if v and v != a.precision]:
+    primary = a.precision + ("" if a.engine == "dfma" else "@" + a.engine)
+    for name in [v for v in a.variants.split(",") if v and v != primary]:
+        prec, _, eng = name.partition("@")
+        eng = eng or "dfma"
         try:
-            step(prec)
+            step(prec, eng)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            rv = step(prec)
+            rv = step(prec, eng)
             e1.record()
             torch.cuda.synchronize()
             tv = e0.elapsed_time(e1)
-            variants[prec] = {"value": unknowns * world / (tv / 1e3), "ms_per_step": tv,
+            variants[name] = {"value": unknowns * world / (tv / 1e3), "ms_per_step": tv,
                               "status": rv.status_name, "relres_true": rv.info.relres_true,
                               "outer": rv.info.outer, "inner_iters": rv.info.iters,
                               "applies_fp64": rv.info.applies_fp64, "applies_low": rv.info.applies_low,
                               "err_vs_xstar": float(torch.max(torch.abs(X - Xs)) / torch.max(torch.abs(Xs)))}
         except Exception as e:  # report, do not hide
-            variants[prec] = {"error": str(e)}
+            variants[name] = {"error": str(e)}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline and a.workload == "dense_n1024_s1024_p16":
@@ -400,7 +427,8 @@ def main():
                 "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32+f64",
                 "data": "synthetic",
                 "config": {"workload": a.workload, "n": n, "s": s, "p": p, "restart": m, "tol": 1e-10,
-                           "precision": a.precision, "method": "tGMRES", "l2": "inputs larger than L2 "
+                           "precision": a.precision, "fp64_engine": a.engine, "method": "tGMRES",
+                           "l2": "inputs larger than L2 "
                            "(A-hat 151 MB, Krylov basis 4.2 GB at n=s=1024, p=16)",
                            "iters": last.info.iters, "cycles": last.info.cycles,
                            "applies_fp64": last.info.applies_fp64, "relres_true": relres,

@@ -101,6 +101,12 @@ ts_status ts_op_shape(const ts_op* op, int* n, int* s, int* p);
  * not alias X.  Asynchronous when X and Y are device pointers. */
 ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, ts_stream stream);
 
+/* Y = M(X) as ts_sylv_apply, with the slice products on the emulated-FP64 tensor-core engine
+ * (TS_ENGINE_OZAKI) and `digits` digits per value (3..8; 0 = 6).  Dense operators, p <= any.  The
+ * first call with a digit count builds the operator's digit planes. */
+ts_status ts_sylv_apply_ozaki(ts_ctx* ctx, const ts_op* op, int digits, const double* X, double* Y,
+                              ts_stream stream);
+
 /* Y = M(X) in a lower precision, the operator of the mixed-precision inner solve: X, Y are
  * FP32 device tensors (n x s x p).  precision TS_MIXED_FP32: FP32 DFT and FP32 CUDA-core slice
  * GEMMs; TS_MIXED_TF32 / TS_MIXED_BF16 / TS_MIXED_TF32X3: the slice GEMMs run on the tcgen05
@@ -108,6 +114,15 @@ ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y
  * that precision's copy of the operator's Fourier slices.  Asynchronous on `stream`. */
 ts_status ts_sylv_apply_lowp(ts_ctx* ctx, const ts_op* op, int precision, const float* X, float* Y,
                              ts_stream stream);
+
+/* How FP64 operator applications are computed.  TS_ENGINE_DFMA: FP64 CUDA-core slice GEMMs.
+ * TS_ENGINE_OZAKI: the slice products are emulated on the BF16 tensor cores (Ozaki scheme):
+ * every FP64 Fourier slice is split into `ozaki_digits` 8-bit integer digits under one exponent
+ * per slice, the digit products are summed exactly in FP32 tensor memory and combined in 64-bit
+ * fixed point.  Its error is below 2^(-8 ozaki_digits + 2) max|A_k| max|X_k| per term of the
+ * reduction (n + s terms per slice entry), i.e. at FP64 level for 6 digits, in normwise rather than
+ * componentwise form.  The mode-3 DFTs stay FP64. */
+typedef enum { TS_ENGINE_DFMA = 0, TS_ENGINE_OZAKI = 1 } ts_fp64_engine;
 
 typedef struct {
   int restart;           /* m, the Krylov dimension per cycle (Algorithm 3), 1..256 */
@@ -121,6 +136,9 @@ typedef struct {
   int history_cap;       /* capacity of history (entries); extra entries are dropped */
   double* true_history;  /* optional host array: true residual norm at every restart / outer step */
   int true_history_cap;
+  int fp64_engine;       /* ts_fp64_engine of every FP64 application (the whole FP64 solve, or the true
+                            residuals of mixed precision); dense operators of ts_tgmres/ts_tfom only */
+  int ozaki_digits;      /* TS_ENGINE_OZAKI: digits per value, 3..8 (0 = 6) */
 } ts_solve_opts;
 
 typedef struct {
@@ -235,6 +253,9 @@ typedef struct {
   long long fft_launches;  /* forward and inverse DFT launches timed while enabled */
   double fft_ms;
   double fft_bytes;        /* their algorithmic HBM bytes (input read + output written once) */
+  long long oz_launches;   /* emulated FP64 slice products (TS_ENGINE_OZAKI), digit split included */
+  double oz_ms;
+  double oz_flops;         /* their algorithmic FLOPs, counted as for gemm_flops */
 } ts_stats;
 
 /* Enable (1) or disable (0) per-kernel event timing on ctx. */

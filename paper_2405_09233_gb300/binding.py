@@ -22,6 +22,7 @@ TS_OK, TS_BREAKDOWN, TS_NOT_CONVERGED, TS_SINGULAR = 0, 1, 2, 3
 TS_ERR_ARG, TS_ERR_CUDA, TS_ERR_NOMEM, TS_ERR_NONFINITE, TS_ERR_TIMEOUT, TS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 TS_ERR_CORRUPTION = -7
 PRECISIONS = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3, "mixed_tf32x3": 4}
+ENGINES = {"dfma": 0, "ozaki": 1}
 STATUS_NAMES = {0: "ok", 1: "breakdown", 2: "not_converged", 3: "singular", -1: "err_arg", -2: "err_cuda",
                 -3: "err_nomem", -4: "err_nonfinite", -5: "err_timeout", -6: "err_unsupported", -7: "err_corruption"}
 
@@ -30,7 +31,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_restarts", ctypes.c_int), ("tol", ctypes.c_double),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int),
-                ("true_history", ctypes.POINTER(ctypes.c_double)), ("true_history_cap", ctypes.c_int)]
+                ("true_history", ctypes.POINTER(ctypes.c_double)), ("true_history_cap", ctypes.c_int),
+                ("fp64_engine", ctypes.c_int), ("ozaki_digits", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -49,7 +51,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("gemm_launches", ctypes.c_longlong), ("gemm_ms", ctypes.c_double),
                 ("gemm_flops", ctypes.c_double), ("lowp_launches", ctypes.c_longlong), ("lowp_ms", ctypes.c_double),
                 ("lowp_flops", ctypes.c_double), ("fft_launches", ctypes.c_longlong), ("fft_ms", ctypes.c_double),
-                ("fft_bytes", ctypes.c_double)]
+                ("fft_bytes", ctypes.c_double), ("oz_launches", ctypes.c_longlong), ("oz_ms", ctypes.c_double),
+                ("oz_flops", ctypes.c_double)]
 
 
 class TstarError(RuntimeError):
@@ -73,6 +76,7 @@ _SIGNATURES = {
     "ts_op_shape": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "ts_sylv_apply": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "ts_sylv_apply_lowp": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    "ts_sylv_apply_ozaki": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "ts_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "ts_tgmres_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
     "ts_tfom_solve": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), _vp]),
@@ -212,6 +216,15 @@ class Context:
         self._check(lib().ts_sylv_apply(self._h, op._h, _ptr(X), _ptr(Y), _stream(X, Y)), "ts_sylv_apply")
         return Y
 
+    def sylv_apply_ozaki(self, op: "Operator", X, Y=None, digits=0):
+        """Y = M(X) in FP64 with the slice products on the emulated-FP64 tensor-core engine."""
+        import torch
+        if Y is None:
+            Y = torch.empty_like(X)
+        self._check(lib().ts_sylv_apply_ozaki(self._h, op._h, int(digits), _ptr(X), _ptr(Y), _stream(X, Y)),
+                    "ts_sylv_apply_ozaki")
+        return Y
+
     def sylv_apply_lowp(self, op: "Operator", X, precision="mixed_bf16", Y=None):
         """Y = M(X) in low precision; X, Y float32 CUDA tensors of shape (p, s, n)."""
         import torch
@@ -224,12 +237,14 @@ class Context:
         return Y
 
     def _solve(self, fn, name, op, C, X, restart, tol, max_restarts, precision, inner_tol, max_outer,
-               history_cap):
+               history_cap, engine="dfma", ozaki_digits=0):
         opts = SolveOpts()
         lib().ts_solve_opts_default(ctypes.byref(opts))
         opts.restart, opts.tol, opts.max_restarts = restart, tol, max_restarts
         opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opts.inner_tol, opts.max_outer = inner_tol, max_outer
+        opts.fp64_engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
+        opts.ozaki_digits = ozaki_digits
         hist = np.zeros(history_cap)
         thist = np.zeros(history_cap)
         opts.history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -243,10 +258,11 @@ class Context:
                            thist[:min(info.true_history_len, history_cap)].copy())
 
     def tgmres_solve(self, op, C, X, restart=20, tol=1e-10, max_restarts=200, precision="fp64",
-                     inner_tol=0.0, max_outer=0, history_cap=4096):
-        """Restarted tGMRES(m); X holds X0 on entry and the solution on return."""
+                     inner_tol=0.0, max_outer=0, history_cap=4096, engine="dfma", ozaki_digits=0):
+        """Restarted tGMRES(m); X holds X0 on entry and the solution on return.  engine selects how
+        FP64 applications are computed ("dfma" or "ozaki")."""
         return self._solve(lib().ts_tgmres_solve, "ts_tgmres_solve", op, C, X, restart, tol, max_restarts,
-                           precision, inner_tol, max_outer, history_cap)
+                           precision, inner_tol, max_outer, history_cap, engine, ozaki_digits)
 
     def tba_solve(self, op, C, X, restart=10, tol=1e-10, max_restarts=100, history_cap=4096):
         """Restarted TBAS(m) (FP64); X holds X0 on entry and the solution on return."""
@@ -275,10 +291,11 @@ class Context:
                                                 _stream(*Cs)), "ts_batched_solve")
         return st, list(infos), list(sts)
 
-    def tfom_solve(self, op, C, X, restart=20, tol=1e-10, max_restarts=200, history_cap=4096):
+    def tfom_solve(self, op, C, X, restart=20, tol=1e-10, max_restarts=200, history_cap=4096, engine="dfma",
+                   ozaki_digits=0):
         """Restarted tFOM(m) (FP64)."""
         return self._solve(lib().ts_tfom_solve, "ts_tfom_solve", op, C, X, restart, tol, max_restarts,
-                           "fp64", 0.0, 0, history_cap)
+                           "fp64", 0.0, 0, history_cap, engine, ozaki_digits)
 
 
 class Operator:

@@ -6,6 +6,7 @@
 #include "apply.cuh"
 #include "tc.cuh"
 #include "tba.cuh"
+#include "oz.cuh"
 
 namespace ts {
 
@@ -82,6 +83,10 @@ void KernelTimer::collect() {
       ++lowp_launches;
       lowp_ms += ms;
       lowp_flops += r.work;
+    } else if (r.kind == 3) {
+      ++oz_launches;
+      oz_ms += ms;
+      oz_flops += r.work;
     } else {
       ++fft_launches;
       fft_ms += ms;
@@ -94,8 +99,8 @@ void KernelTimer::collect() {
 
 void KernelTimer::reset() {
   collect();
-  gemm_launches = fft_launches = lowp_launches = 0;
-  gemm_ms = gemm_flops = fft_ms = fft_bytes = lowp_ms = lowp_flops = 0;
+  gemm_launches = fft_launches = lowp_launches = oz_launches = 0;
+  gemm_ms = gemm_flops = fft_ms = fft_bytes = lowp_ms = lowp_flops = oz_ms = oz_flops = 0;
 }
 
 void KernelTimer::destroy() {
@@ -177,6 +182,10 @@ void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mod
       sub3<double>(C, Y, Y, T * p, st);
       dot_partials<double>(Y, Y, T * p, partials, st);
     }
+    return;
+  }
+  if (ctx->f64_engine == TS_ENGINE_OZAKI) {
+    apply_f64_oz(ctx, op, X, Y, mode, C, partials, ctx->oz_digits, st);
     return;
   }
   double2* Xh = static_cast<double2*>(ctx->ws.get("apply_Xh", sizeof(double2) * (size_t)K * T));
@@ -349,6 +358,10 @@ void ts_op_destroy(ts_op* op) {
   cudaFree(op->Bh);
   cudaFree(op->Ah32);
   cudaFree(op->Bh32);
+  if (op->oz) {
+    op->oz->release();
+    delete op->oz;
+  }
   if (op->tc) {
     op->tc->release();
     delete op->tc;
@@ -381,6 +394,26 @@ ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y
   const size_t N = (size_t)op->n * op->s * op->p;
   StagedIn x(ctx, "apply_inX", X, N, st);
   StagedOut y(ctx, "apply_outY", Y, N, false, st);
+  apply_f64(ctx, op, x.dev, y.dev, IRFFT_STORE, nullptr, nullptr, st);
+  y.finish();
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
+ts_status ts_sylv_apply_ozaki(ts_ctx* ctx, const ts_op* op, int digits, const double* X, double* Y,
+                              ts_stream stream) {
+  if (!ctx) return TS_ERR_ARG;
+  TS_API_BEGIN
+  TS_REQUIRE(op && X && Y, "ts_sylv_apply_ozaki: null pointer");
+  TS_REQUIRE(X != Y, "ts_sylv_apply_ozaki: Y must not alias X");
+  TS_REQUIRE(digits == 0 || (digits >= 3 && digits <= 8), "ts_sylv_apply_ozaki: digits must be 3..8 (or 0)");
+  if (op->sp) throw Error{TS_ERR_UNSUPPORTED, "ts_sylv_apply_ozaki: dense operators only"};
+  TS_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t N = (size_t)op->n * op->s * op->p;
+  StagedIn x(ctx, "apply_inX", X, N, st);
+  StagedOut y(ctx, "apply_outY", Y, N, false, st);
+  EngineScope scope(ctx, TS_ENGINE_OZAKI, digits == 0 ? 6 : digits);
   apply_f64(ctx, op, x.dev, y.dev, IRFFT_STORE, nullptr, nullptr, st);
   y.finish();
   return TS_OK;
@@ -513,6 +546,9 @@ ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out) {
   out->lowp_launches = t.lowp_launches;
   out->lowp_ms = t.lowp_ms;
   out->lowp_flops = t.lowp_flops;
+  out->oz_launches = t.oz_launches;
+  out->oz_ms = t.oz_ms;
+  out->oz_flops = t.oz_flops;
   return TS_OK;
   TS_API_END(ctx)
 }

@@ -24,6 +24,20 @@ struct StagedOut {
   void finish();
 };
 
+// Sets the FP64 engine of ctx for the duration of one API call.
+struct EngineScope {
+  ts_ctx* c;
+  int e0, d0;
+  EngineScope(ts_ctx* ctx, int engine, int digits) : c(ctx), e0(ctx->f64_engine), d0(ctx->oz_digits) {
+    c->f64_engine = engine;
+    c->oz_digits = digits;
+  }
+  ~EngineScope() {
+    c->f64_engine = e0;
+    c->oz_digits = d0;
+  }
+};
+
 // Y = M(X) in FP64 (rfft -> fused per-slice GEMMs -> irfft).  mode IRFFT_RESIDUAL writes
 // Y = C - M(X) and the kRedBlocks partial sums of Y^2 to `partials`.
 void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,

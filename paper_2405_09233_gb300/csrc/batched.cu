@@ -513,6 +513,8 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
              "ts_batched_solve: precision must be TS_FP64 or TS_MIXED_FP32");
   TS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  if (o.fp64_engine != TS_ENGINE_DFMA)
+    throw Error{TS_ERR_UNSUPPORTED, "ts_batched_solve runs on the FP64 DFMA engine only"};
   const bool mixed = o.precision == TS_MIXED_FP32;
   const int m = o.restart;
   BatchPlan plan;

@@ -59,15 +59,16 @@ inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_
 // Event timing of selected kernels while a context has statistics enabled.
 struct TimedRegion {
   cudaEvent_t a, b;
-  int kind;        // 0 = FP64 GEMM, 1 = FFT, 2 = low-precision GEMM
+  int kind;        // 0 = FP64 GEMM, 1 = FFT, 2 = low-precision GEMM, 3 = emulated FP64 GEMM
   double work;     // algorithmic FLOPs (GEMM) or bytes (FFT)
 };
 struct KernelTimer {
   bool enabled = false;
   std::vector<TimedRegion> done;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
-  long long gemm_launches = 0, fft_launches = 0, lowp_launches = 0;
+  long long gemm_launches = 0, fft_launches = 0, lowp_launches = 0, oz_launches = 0;
   double gemm_ms = 0, gemm_flops = 0, fft_ms = 0, fft_bytes = 0, lowp_ms = 0, lowp_flops = 0;
+  double oz_ms = 0, oz_flops = 0;
   void begin(cudaStream_t st, int kind, double work);
   void end(cudaStream_t st);
   void collect();  // synchronise the recorded events and accumulate
@@ -77,7 +78,7 @@ struct KernelTimer {
 
 }  // namespace ts
 
-namespace ts { struct TcOperands; struct SparseOp; }
+namespace ts { struct TcOperands; struct SparseOp; struct OzOperands; }
 
 struct ts_ctx {
   int device = 0;
@@ -87,6 +88,8 @@ struct ts_ctx {
   double* host_scalars = nullptr;  // pinned, 256 doubles, for small device->host reads
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t bstream = nullptr;  // private stream of the batched solver (graph capture)
+  int f64_engine = 0;              // how the current call computes FP64 applications (ts_fp64_engine)
+  int oz_digits = 6;               // digits per value of the emulated FP64 product
   ts::KernelTimer timer;
 };
 
@@ -98,6 +101,7 @@ struct ts_op {
   float2* Ah32 = nullptr;  // FP32 copies, made on first mixed-precision use
   float2* Bh32 = nullptr;
   ts::TcOperands* tc = nullptr;  // tensor-core operand planes (BF16 or TF32), made on first use
+  ts::OzOperands* oz = nullptr;  // BF16 digit planes of the emulated FP64 product, made on first use
   int tc_prec = -1;
   ts::SparseOp* sp = nullptr;    // sparse A (union CSR pattern + Fourier slices of the values)
   double2* Bh_row = nullptr;     // K slices of B_k, row-major (row kernels of TBAS)

@@ -60,7 +60,8 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
   void* state = ctx->ws.get("krylov_state", krylov_state_bytes(m));
   double* hs = ctx->host_scalars;
   int* tc_err = static_cast<int*>(ctx->ws.get("tc_err", sizeof(int) * 4));
-  if (mixed) TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
+  const bool ozaki = ctx->f64_engine == TS_ENGINE_OZAKI;
+  if (mixed || ozaki) TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
 
   int hist_len = 0, true_len = 0;
   auto push_hist = [&](double v) {
@@ -153,7 +154,7 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
       status = TS_ERR_NONFINITE;
       break;
     }
-    if (mixed && prec != TS_MIXED_FP32) {
+    if ((mixed && prec != TS_MIXED_FP32) || ozaki) {
       int e = 0;
       TS_CUDA(cudaMemcpy(&e, tc_err, sizeof(int), cudaMemcpyDeviceToHost));
       if (e != 0) throw Error{TS_ERR_TIMEOUT, "tensor-core kernel wait expired (code " + std::to_string(e) + ")"};
@@ -199,6 +200,11 @@ ts_status solve_entry(ts_ctx* ctx, const ts_op* cop, const double* C, double* X,
     throw Error{TS_ERR_UNSUPPORTED, "tFOM runs in FP64 only"};
   if (op->sp && o.precision != TS_FP64)
     throw Error{TS_ERR_UNSUPPORTED, "sparse operators run in FP64 only"};
+  TS_REQUIRE(o.fp64_engine == TS_ENGINE_DFMA || o.fp64_engine == TS_ENGINE_OZAKI, "solve: unknown fp64_engine");
+  TS_REQUIRE(o.ozaki_digits == 0 || (o.ozaki_digits >= 3 && o.ozaki_digits <= 8), "solve: ozaki_digits must be 3..8");
+  if (op->sp && o.fp64_engine != TS_ENGINE_DFMA)
+    throw Error{TS_ERR_UNSUPPORTED, "the emulated FP64 engine takes dense operators only"};
+  EngineScope scope(ctx, o.fp64_engine, o.ozaki_digits == 0 ? 6 : o.ozaki_digits);
   TS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   ts_solve_info info{};

@@ -679,6 +679,7 @@ ts_status tba_entry(ts_ctx* ctx, const ts_op* cop, const double* C, double* X, c
   TS_REQUIRE(o.max_restarts >= 1, "ts_tba_solve: max_restarts must be >= 1");
   TS_REQUIRE(o.tol > 0.0 && std::isfinite(o.tol), "ts_tba_solve: tol must be positive");
   if (o.precision != TS_FP64) throw Error{TS_ERR_UNSUPPORTED, "TBAS runs in FP64 only"};
+  if (o.fp64_engine != TS_ENGINE_DFMA) throw Error{TS_ERR_UNSUPPORTED, "TBAS runs on the FP64 DFMA engine only"};
   TS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   ts_solve_info info{};
