@@ -604,7 +604,11 @@ def run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev):
     import torch
     n, s, p = cfg["n"], cfg["s"], cfg["p"]
     op = ctx.op_create_dense(Ad, Bd)
-    if a.precision == "fp64":
+    if a.precision == "fp64" and a.engine == "ozaki":
+        Xin = Xs
+        Y = torch.empty_like(Xs)
+        fn = lambda: ctx.sylv_apply_ozaki(op, Xin, Y)  # noqa: E731
+    elif a.precision == "fp64":
         Xin = Xs
         Y = torch.empty_like(Xs)
         fn = lambda: ctx.sylv_apply(op, Xin, Y)  # noqa: E731
@@ -629,7 +633,10 @@ def run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev):
     ctx.stats_enable(False)
     st = ctx.stats_get()
     ms = e0.elapsed_time(e1) / a.steps
-    if a.precision == "fp64":
+    if a.precision == "fp64" and a.engine == "ozaki":
+        rf = ozaki_roofline(st.oz_flops / max(st.oz_launches, 1), st.oz_ms / max(st.oz_launches, 1), False,
+                            st.oz_ms / (ms * a.steps))
+    elif a.precision == "fp64":
         rf = gemm_roofline("fp64", "fp64", st.gemm_flops / max(st.gemm_launches, 1),
                            st.gemm_ms / max(st.gemm_launches, 1), False, st.gemm_ms / (ms * a.steps))
     else:
@@ -637,7 +644,8 @@ def run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev):
                            st.lowp_ms / max(st.lowp_launches, 1), False, st.lowp_ms / (ms * a.steps))
     line = {"mode": "apply", "metric": "operator applications (unknowns/s)", "value": n * s * p / (ms / 1e3),
             "unit": "unknowns/s", "ms_per_step": ms, "steps": a.steps, "warmup": a.warmup,
-            "config": {"workload": a.workload, "n": n, "s": s, "p": p, "precision": a.precision},
+            "config": {"workload": a.workload, "n": n, "s": s, "p": p, "precision": a.precision,
+                       "fp64_engine": a.engine},
             "roofline": rf, "fft_gbs": st.fft_bytes / max(st.fft_ms, 1e-9) / 1e6,
             "fft_ms_per_step": st.fft_ms / a.steps, "clocks": clk, "gpu_launches": int(st.launches)}
     print(json.dumps(line), flush=True)

@@ -22,10 +22,12 @@
 //    Units with 8g > F are added with a rounded right shift.
 //  * Y = double(acc) 2^(E_op + E_x - F): one rounding.
 //
-// One CTA computes a 128 x 64 output tile of one slice.  Warp roles (320 threads):
+// One CTA computes a 128 x 64 output tile of one slice; each MMA (N = 128) produces its Re and Im
+// columns together from a B operand stored as three 64-row blocks (see the MMA warp).  Warp roles
+// (320 threads):
 //   warps 0-7  epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +31 (output rows) and columns
 //              32 (w div 4) .. +31 of the tile; holds 2 x 32 int64 accumulators per thread
-//   warp 8     TMA producer (A-operand Re/Im tiles 128 x 64, B-operand Re/Im tiles 64 x 64)
+//   warp 8     TMA producer (A-operand Re/Im tiles 128 x 64, three B-operand blocks 64 x 64)
 //   warp 9     TMEM allocator and MMA issuer (one elected lane)
 // Two TMEM accumulator buffers (Re 64 + Im 64 columns each) alternate between units, so the MMAs
 // of one unit overlap the epilogue of the previous one.  Every wait is bounded.
@@ -46,8 +48,8 @@ constexpr int kOzN = 64;                                // tile columns
 constexpr int kOzKB = 64;                               // k-block: BF16 elements per 128-byte row
 constexpr int kOzStages = 4;
 constexpr int kOzTileA = kOzM * 128;                    // bytes of one A-operand plane tile
-constexpr int kOzTileB = kOzN * 128;                    // bytes of one B-operand plane tile
-constexpr int kOzStage = 2 * kOzTileA + 2 * kOzTileB;   // Re and Im of both operands
+constexpr int kOzTileB = kOzN * 128;                    // bytes of one 64-row B-operand block
+constexpr int kOzStage = 2 * kOzTileA + 3 * kOzTileB;   // A Re, A Im; B blocks [P; Q; R]
 constexpr int kOzSmem = kOzStages * kOzStage + 1024 + 256;
 constexpr int kOzUnitBlocks = 8;                        // k-blocks per exact accumulator run
 constexpr int kOzTmemCols = 256;                        // 2 buffers x (Re 64 + Im 64)
@@ -57,8 +59,10 @@ constexpr int kOzBadExp = INT_MAX;                      // slice with a non-fini
 struct OzMaps {
   CUtensorMap a_re, a_im;     // A digits  [S*K][n][ldn]  row-major A_k         (A operand of A X)
   CUtensorMap xc_re, xc_im;   // X digits  [S*K][s][ldn]  column-major X_k      (B operand of A X)
+  CUtensorMap xc_nim;         //   and the digits of -Im X_k
   CUtensorMap xr_re, xr_im;   // X digits  [S*K][n][lds]  row-major X_k         (A operand of X B)
   CUtensorMap b_re, b_im;     // B digits  [S*K][s][lds]  column-major B_k      (B operand of X B)
+  CUtensorMap b_nre;          //   and the digits of -Re B_k
 };
 
 // The stage sequence of one tile: for g = 2 .. S+1, the kbA k-blocks of A_k X_k for each digit
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           const uint32_t full = bar_full + 8 * slot;
           mbar_expect_tx(full, kOzStage);
           const uint32_t sA = base + slot * kOzStage;
-          const uint32_t sAi = sA + kOzTileA, sB = sA + 2 * kOzTileA, sBi = sB + kOzTileB;
+          const uint32_t sAi = sA + kOzTileA, sP = sA + 2 * kOzTileA, sQ = sP + kOzTileB, sR = sQ + kOzTileB;
           bool ax;
           int u, lb;
           seq.decode(g, idx, ax, u, lb);
@@ -178,26 +182,34 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           if (ax) {
             tma_load_3d(sA, &maps.a_re, l0, i0, pa, full);
             tma_load_3d(sAi, &maps.a_im, l0, i0, pa, full);
-            tma_load_3d(sB, &maps.xc_re, l0, j0, pb, full);
-            tma_load_3d(sBi, &maps.xc_im, l0, j0, pb, full);
+            tma_load_3d(sP, &maps.xc_nim, l0, j0, pb, full);   // [P; Q; R] = [-Xi; Xr; Xi]
+            tma_load_3d(sQ, &maps.xc_re, l0, j0, pb, full);
+            tma_load_3d(sR, &maps.xc_im, l0, j0, pb, full);
           } else {
             tma_load_3d(sA, &maps.xr_re, l0, i0, pa, full);
             tma_load_3d(sAi, &maps.xr_im, l0, i0, pa, full);
-            tma_load_3d(sB, &maps.b_re, l0, j0, pb, full);
-            tma_load_3d(sBi, &maps.b_im, l0, j0, pb, full);
+            tma_load_3d(sP, &maps.b_re, l0, j0, pb, full);     // [P; Q; R] = [Br; Bi; -Br]
+            tma_load_3d(sQ, &maps.b_im, l0, j0, pb, full);
+            tma_load_3d(sR, &maps.b_nre, l0, j0, pb, full);
           }
         }
       }
     }
   } else if (warp == 9) {
     if (lane == 0) {
-      constexpr uint32_t idp = make_idesc(1, kOzM, kOzN, false);
-      constexpr uint32_t idn = make_idesc(1, kOzM, kOzN, true);
+      // One accumulator covers [Re | Im] (N = 128): with the B blocks [P; Q; R] of a stage,
+      //   A X:  D += Ar [Xr | Xi] + Ai [-Xi | Xr]        (blocks Q-R, then P-Q)
+      //   X B:  D += -Xr [Br | Bi] + Xi [Bi | -Br]       (blocks P-Q, then Q-R)
+      // Real slices use the Re half only (N = 64).
+      constexpr uint32_t idp = make_idesc(1, kOzM, 2 * kOzN, false);
+      constexpr uint32_t idn = make_idesc(1, kOzM, 2 * kOzN, true);
+      constexpr uint32_t idp1 = make_idesc(1, kOzM, kOzN, false);
+      constexpr uint32_t idn1 = make_idesc(1, kOzM, kOzN, true);
       int it = 0, uc = 0;
       bool ok = true;
       for (int g = 2; g <= S + 1 && ok; ++g) {
         const int ns = seq.stages(g);
-        uint32_t d_re = tmem, d_im = tmem + kOzN;
+        uint32_t d = tmem;
         for (int idx = 0; idx < ns; ++idx, ++it) {
           const bool ufirst = (idx % kOzUnitBlocks) == 0;
           const bool ulast = (idx % kOzUnitBlocks) == kOzUnitBlocks - 1 || idx == ns - 1;
@@ -208,8 +220,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            d_re = tmem + (uint32_t)(b * 2 * kOzN);
-            d_im = d_re + kOzN;
+            d = tmem + (uint32_t)(b * 2 * kOzN);
           }
           const int slot = it % kOzStages;
           const uint32_t phase = (uint32_t)(it / kOzStages) & 1u;
@@ -223,25 +234,25 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           seq.decode(g, idx, ax, u, lb);
           const uint32_t sA = base + slot * kOzStage;
           const uint64_t dAr = smem_desc_sw128(sA), dAi = smem_desc_sw128(sA + kOzTileA);
-          const uint64_t dBr = smem_desc_sw128(sA + 2 * kOzTileA);
-          const uint64_t dBi = smem_desc_sw128(sA + 2 * kOzTileA + kOzTileB);
+          const uint64_t dP = smem_desc_sw128(sA + 2 * kOzTileA);
+          const uint64_t dQ = smem_desc_sw128(sA + 2 * kOzTileA + kOzTileB);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t o = (uint64_t)(kk * 2);   // 32 bytes >> 4
             const uint32_t acc = (ufirst && kk == 0) ? 0u : 1u;
-            if (ax) {   // Re += Ar Xr - Ai Xi,  Im += Ai Xr + Ar Xi
-              mma_issue(d_re, dAr + o, dBr + o, idp, acc, 0);
-              if (!real) {
-                mma_issue(d_re, dAi + o, dBi + o, idn, 1u, 0);
-                mma_issue(d_im, dAi + o, dBr + o, idp, acc, 0);
-                mma_issue(d_im, dAr + o, dBi + o, idp, 1u, 0);
+            if (ax) {
+              if (real) {
+                mma_issue(d, dAr + o, dQ + o, idp1, acc, 0);
+              } else {
+                mma_issue(d, dAr + o, dQ + o, idp, acc, 0);
+                mma_issue(d, dAi + o, dP + o, idp, 1u, 0);
               }
-            } else {    // Re -= Xr Br - Xi Bi,  Im -= Xr Bi + Xi Br
-              mma_issue(d_re, dAr + o, dBr + o, idn, acc, 0);
-              if (!real) {
-                mma_issue(d_re, dAi + o, dBi + o, idp, 1u, 0);
-                mma_issue(d_im, dAr + o, dBi + o, idn, acc, 0);
-                mma_issue(d_im, dAi + o, dBr + o, idn, 1u, 0);
+            } else {
+              if (real) {
+                mma_issue(d, dAr + o, dP + o, idn1, acc, 0);
+              } else {
+                mma_issue(d, dAr + o, dP + o, idn, acc, 0);
+                mma_issue(d, dAi + o, dQ + o, idp, 1u, 0);
               }
             }
           }
@@ -369,12 +380,13 @@ __device__ __forceinline__ long long oz_fixed(double v, int E, int S) {
 // Digit planes of K complex slices.  Slice k of src is a column-major R x C matrix (entry (r, c) at
 // src[k*sstride + c*R + r]).  TRANS = false: output rows c, contiguous index r; TRANS = true: output
 // rows r, contiguous index c.  Digit t (0 = most significant) of slice k lands in plane t*K + k of
-// plane_elems entries with row pitch ld.  Entries beyond R or C are not written (the tensor maps
-// read them as zero).
+// plane_elems entries with row pitch ld.  nre / nim (optional) receive the digits of -Re / -Im.
+// Entries beyond R or C are not written (the tensor maps read them as zero).
 template <bool TRANS>
 __global__ void k_oz_split(const double2* __restrict__ src, long long sstride, int R, int C, int K,
                            const int* __restrict__ E, int S, __nv_bfloat16* __restrict__ re,
-                           __nv_bfloat16* __restrict__ im, int ld, long long plane_elems) {
+                           __nv_bfloat16* __restrict__ im, __nv_bfloat16* __restrict__ nre,
+                           __nv_bfloat16* __restrict__ nim, int ld, long long plane_elems) {
   __shared__ double2 tile[32][33];
   const int k = blockIdx.z, r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   const double2* Sk = src + (long long)k * sstride;
@@ -410,10 +422,14 @@ __global__ void k_oz_split(const double2* __restrict__ src, long long sstride, i
       const long long po = ((long long)t * K + k) * plane_elems + o;
       re[po] = __int2bfloat16_rn(dr);
       im[po] = __int2bfloat16_rn(di);
+      if (nre) nre[po] = __int2bfloat16_rn(-dr);
+      if (nim) nim[po] = __int2bfloat16_rn(-di);
     }
     const long long po = (long long)k * plane_elems + o;
     re[po] = __int2bfloat16_rn((int)qr);
     im[po] = __int2bfloat16_rn((int)qi);
+    if (nre) nre[po] = __int2bfloat16_rn(-(int)qr);
+    if (nim) nim[po] = __int2bfloat16_rn(-(int)qi);
   }
 }
 
@@ -434,11 +450,11 @@ void exponents(const unsigned long long* mx, int K, int* E, cudaStream_t st) {
 }
 
 template <bool TRANS>
-void split(const double2* src, long long sstride, int R, int C, int K, const int* E, int S, void* re, void* im, int ld,
-           long long plane_elems, cudaStream_t st) {
+void split(const double2* src, long long sstride, int R, int C, int K, const int* E, int S, void* re, void* im,
+           void* nre, void* nim, int ld, long long plane_elems, cudaStream_t st) {
   k_oz_split<TRANS><<<dim3((R + 31) / 32, (C + 31) / 32, K), dim3(32, 8), 0, st>>>(
-      src, sstride, R, C, K, E, S, static_cast<__nv_bfloat16*>(re), static_cast<__nv_bfloat16*>(im), ld,
-      plane_elems);
+      src, sstride, R, C, K, E, S, static_cast<__nv_bfloat16*>(re), static_cast<__nv_bfloat16*>(im),
+      static_cast<__nv_bfloat16*>(nre), static_cast<__nv_bfloat16*>(nim), ld, plane_elems);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -450,9 +466,10 @@ void OzOperands::release() {
   cudaFree(a_im);
   cudaFree(b_re);
   cudaFree(b_im);
+  cudaFree(b_nre);
   cudaFree(Eop);
   cudaFree(mx);
-  a_re = a_im = b_re = b_im = nullptr;
+  a_re = a_im = b_re = b_im = b_nre = nullptr;
   Eop = nullptr;
   mx = nullptr;
   S = 0;
@@ -471,6 +488,7 @@ void oz_prepare(ts_op* op, int S, cudaStream_t st) {
   TS_CUDA(cudaMalloc(&t->a_im, na));
   TS_CUDA(cudaMalloc(&t->b_re, nb));
   TS_CUDA(cudaMalloc(&t->b_im, nb));
+  TS_CUDA(cudaMalloc(&t->b_nre, nb));
   TS_CUDA(cudaMalloc(&t->Eop, sizeof(int) * K));
   TS_CUDA(cudaMalloc(&t->mx, sizeof(unsigned long long) * K));
   // A_k and B_k share one exponent per slice, so both products of Eq. (2) land on one fixed point.
@@ -479,8 +497,10 @@ void oz_prepare(ts_op* op, int S, cudaStream_t st) {
   slice_maxabs(op->Ah, (long long)n * n, K, mxb, st);
   slice_maxabs(op->Bh, (long long)s * s, K, mxb, st);
   exponents(mxb, K, t->Eop, st);
-  split<true>(op->Ah, (long long)n * n, n, n, K, t->Eop, S, t->a_re, t->a_im, t->ldn, (long long)n * t->ldn, st);
-  split<false>(op->Bh, (long long)s * s, s, s, K, t->Eop, S, t->b_re, t->b_im, t->lds, (long long)s * t->lds, st);
+  split<true>(op->Ah, (long long)n * n, n, n, K, t->Eop, S, t->a_re, t->a_im, nullptr, nullptr, t->ldn,
+              (long long)n * t->ldn, st);
+  split<false>(op->Bh, (long long)s * s, s, s, K, t->Eop, S, t->b_re, t->b_im, t->b_nre, nullptr, t->lds,
+               (long long)s * t->lds, st);
   t->S = S;
 }
 
@@ -503,6 +523,7 @@ void apply_f64_oz(ts_ctx* ctx, const ts_op* cop, const double* X, double* Y, int
   const size_t nxc = (size_t)S * K * s * t.ldn * 2, nxr = (size_t)S * K * n * t.lds * 2;
   void* xc_re = ctx->ws.get("oz_xc_re", nxc);
   void* xc_im = ctx->ws.get("oz_xc_im", nxc);
+  void* xc_nim = ctx->ws.get("oz_xc_nim", nxc);
   void* xr_re = ctx->ws.get("oz_xr_re", nxr);
   void* xr_im = ctx->ws.get("oz_xr_im", nxr);
   unsigned long long* mx = static_cast<unsigned long long*>(ctx->ws.get("oz_mx", sizeof(unsigned long long) * K));
@@ -518,17 +539,19 @@ void apply_f64_oz(ts_ctx* ctx, const ts_op* cop, const double* X, double* Y, int
   TS_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * K, st));
   slice_maxabs(Xh, T, K, mx, st);
   exponents(mx, K, Ex, st);
-  split<false>(Xh, T, n, s, K, Ex, S, xc_re, xc_im, t.ldn, (long long)s * t.ldn, st);
-  split<true>(Xh, T, n, s, K, Ex, S, xr_re, xr_im, t.lds, (long long)n * t.lds, st);
+  split<false>(Xh, T, n, s, K, Ex, S, xc_re, xc_im, nullptr, xc_nim, t.ldn, (long long)s * t.ldn, st);
+  split<true>(Xh, T, n, s, K, Ex, S, xr_re, xr_im, nullptr, nullptr, t.lds, (long long)n * t.lds, st);
   OzMaps maps;
   make_map(&maps.a_re, t.a_re, 2, t.ldn, n, n, S * K, kOzM);
   make_map(&maps.a_im, t.a_im, 2, t.ldn, n, n, S * K, kOzM);
   make_map(&maps.xc_re, xc_re, 2, t.ldn, n, s, S * K, kOzN);
   make_map(&maps.xc_im, xc_im, 2, t.ldn, n, s, S * K, kOzN);
+  make_map(&maps.xc_nim, xc_nim, 2, t.ldn, n, s, S * K, kOzN);
   make_map(&maps.xr_re, xr_re, 2, t.lds, s, n, S * K, kOzM);
   make_map(&maps.xr_im, xr_im, 2, t.lds, s, n, S * K, kOzM);
   make_map(&maps.b_re, t.b_re, 2, t.lds, s, s, S * K, kOzN);
   make_map(&maps.b_im, t.b_im, 2, t.lds, s, s, S * K, kOzN);
+  make_map(&maps.b_nre, t.b_nre, 2, t.lds, s, s, S * K, kOzN);
   // Fixed point 2^(E_op + E_x - F): |partial sums| < 2 (n + s) 2^(E_op + E_x - 2) <= 2^(E_op + E_x + 62 - F).
   int lg = 0;
   while ((1ll << lg) < 2ll * (n + s)) ++lg;

@@ -12,6 +12,7 @@ struct OzOperands {
   void* a_im = nullptr;
   void* b_re = nullptr;            // [S][K][s][lds]  column-major B_k digits
   void* b_im = nullptr;
+  void* b_nre = nullptr;           // digits of -Re B_k
   int* Eop = nullptr;              // [K] shared exponent of A_k and B_k
   unsigned long long* mx = nullptr;
   void release();
