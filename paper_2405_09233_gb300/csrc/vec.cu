@@ -1,20 +1,37 @@
 // Streaming kernels of the Arnoldi process (Algorithm 2) and of the solution update: inner
 // products and norms (Definition 2.3), the modified Gram-Schmidt sweep, scaling and the
-// (*) product of §3.1.  All are HBM-bound: grid-stride loops over 16-byte vectors, a fixed grid
-// of kRedBlocks blocks wherever a sum is formed, FP64 accumulation whatever the storage type.
+// (*) product of §3.1.  All are HBM-bound: grid-stride loops over packs of 4 elements (16- or
+// 32-byte loads, two packs in flight per thread) when N is a multiple of 4 and the tensors are
+// 16-byte aligned, scalar loops otherwise; a fixed grid of kRedBlocks blocks wherever a sum is
+// formed; FP64 accumulation whatever the storage type.
 //
 // Reductions never use atomics: each block writes one partial sum, and whoever needs the total
 // (the next MGS pass, the Givens kernel) adds the kRedBlocks partials in a fixed order.  The
 // results are therefore bitwise reproducible from run to run.
+#include <initializer_list>
+#include <cstdint>
 #include "internal.cuh"
 #include "reduce.cuh"
 
 namespace ts {
 namespace {
 
-template <typename T> struct V2;
-template <> struct V2<double> { using T = double2; };
-template <> struct V2<float> { using T = float2; };
+// 4 consecutive elements as one or two 16-byte accesses.
+__device__ __forceinline__ void ld4(const float* p, long long e, float (&v)[4]) {
+  const float4 q = reinterpret_cast<const float4*>(p)[e];
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, long long e, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[2 * e], b = reinterpret_cast<const double2*>(p)[2 * e + 1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, long long e, const float (&v)[4]) {
+  reinterpret_cast<float4*>(p)[e] = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, long long e, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[2 * e] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[2 * e + 1] = make_double2(v[2], v[3]);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const T* __restrict__ x, const T* __restrict__ y,
@@ -23,6 +40,33 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(const T* __restrict__ x, co
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride)
     acc += (double)x[e] * (double)y[e];
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// Packed form of k_dot: N4 packs of 4.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_dot4(const T* __restrict__ x, const T* __restrict__ y,
+                                                      long long N4, double* __restrict__ partials) {
+  double acc = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N4; e += 2 * stride) {
+    const long long e1 = e + stride;
+    T a0[4], b0[4], a1[4], b1[4];
+    ld4(x, e, a0);
+    ld4(y, e, b0);
+    const bool two = e1 < N4;
+    if (two) {
+      ld4(x, e1, a1);
+      ld4(y, e1, b1);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc += (double)a0[c] * (double)b0[c];
+    if (two) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc += (double)a1[c] * (double)b1[c];
+    }
+  }
   const double tot = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
@@ -49,12 +93,68 @@ __global__ void __launch_bounds__(kRedThreads) k_mgs(T* __restrict__ W, const T*
   if (threadIdx.x == 0) Pout[blockIdx.x] = tot;
 }
 
+// Packed form of k_mgs: N4 packs of 4.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_mgs4(T* __restrict__ W, const T* __restrict__ Vi,
+                                                      const T* __restrict__ Vn, long long N4,
+                                                      const double* __restrict__ Pin, double* __restrict__ h_out,
+                                                      double* __restrict__ Pout) {
+  const double h = finalize_partials(Pin);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *h_out = h;
+  const T hT = (T)h;
+  double acc = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N4; e += 2 * stride) {
+    const long long e1 = e + stride;
+    const bool two = e1 < N4;
+    T w0[4], v0[4], o0[4], w1[4], v1[4], o1[4];
+    ld4(W, e, w0);
+    ld4(Vi, e, v0);
+    if (Vn) ld4(Vn, e, o0);
+    if (two) {
+      ld4(W, e1, w1);
+      ld4(Vi, e1, v1);
+      if (Vn) ld4(Vn, e1, o1);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      w0[c] = w0[c] - hT * v0[c];
+      acc += (double)(Vn ? o0[c] : w0[c]) * (double)w0[c];
+    }
+    st4(W, e, w0);
+    if (two) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        w1[c] = w1[c] - hT * v1[c];
+        acc += (double)(Vn ? o1[c] : w1[c]) * (double)w1[c];
+      }
+      st4(W, e1, w1);
+    }
+  }
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) Pout[blockIdx.x] = tot;
+}
+
 template <typename T, typename U>
 __global__ void k_scale(const T* __restrict__ x, U* __restrict__ y, long long N, const double* __restrict__ s) {
   const double sc = *s;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride)
     y[e] = (U)((double)x[e] * sc);
+}
+
+template <typename T, typename U>
+__global__ void k_scale4(const T* __restrict__ x, U* __restrict__ y, long long N4, const double* __restrict__ s) {
+  const double sc = *s;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N4; e += stride) {
+    T a[4];
+    U b[4];
+    ld4(x, e, a);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) b[c] = (U)((double)a[c] * sc);
+    st4(y, e, b);
+  }
 }
 
 // X += alpha * sum_{i<k} y_i V_i ; alpha = alpha_scale * (*alpha_dev if given).
@@ -71,6 +171,31 @@ __global__ void k_multi_axpy(U* __restrict__ X, const T* __restrict__ V, long lo
     double acc = 0.0;
     for (int i = 0; i < k; ++i) acc = fma(ys[i], (double)V[(long long)i * ldv + e], acc);
     X[e] = (U)((double)X[e] + acc);
+  }
+}
+
+template <typename T, typename U>
+__global__ void k_multi_axpy4(U* __restrict__ X, const T* __restrict__ V, long long ldv, long long N4,
+                              const double* __restrict__ y, int k, double alpha_scale,
+                              const double* __restrict__ alpha_dev) {
+  __shared__ double ys[256];
+  const double alpha = alpha_scale * (alpha_dev ? *alpha_dev : 1.0);
+  for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) ys[i] = y[i] * alpha;
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N4; e += stride) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < k; ++i) {
+      T v[4];
+      ld4(V + (long long)i * ldv, e, v);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[c] = fma(ys[i], (double)v[c], acc[c]);
+    }
+    U x[4];
+    ld4(X, e, x);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = (U)((double)x[c] + acc[c]);
+    st4(X, e, x);
   }
 }
 
@@ -95,6 +220,15 @@ __global__ void k_convert(const T* __restrict__ x, U* __restrict__ y, long long 
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride) y[e] = (U)x[e];
 }
 
+// Packed kernels need N % 4 == 0 and 16-byte aligned tensors (then every basis vector V + i N is
+// aligned too).
+bool packable(long long N, std::initializer_list<const void*> ptrs) {
+  if (N % 4 != 0) return false;
+  for (const void* p : ptrs)
+    if (p && (reinterpret_cast<uintptr_t>(p) & 15) != 0) return false;
+  return true;
+}
+
 int grid_for(long long N) {
   long long b = (N + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -105,7 +239,8 @@ int grid_for(long long N) {
 
 template <typename T>
 void dot_partials(const T* x, const T* y, long long N, double* partials, cudaStream_t st) {
-  k_dot<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, y, N, partials);
+  if (packable(N, {x, y})) k_dot4<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, y, N / 4, partials);
+  else k_dot<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, y, N, partials);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -113,14 +248,16 @@ void dot_partials(const T* x, const T* y, long long N, double* partials, cudaStr
 template <typename T>
 void mgs_pass(T* W, const T* Vi, const T* Vnext, long long N, const double* Pin, double* h_out, double* Pout,
               cudaStream_t st) {
-  k_mgs<T><<<kRedBlocks, kRedThreads, 0, st>>>(W, Vi, Vnext, N, Pin, h_out, Pout);
+  if (packable(N, {W, Vi, Vnext})) k_mgs4<T><<<kRedBlocks, kRedThreads, 0, st>>>(W, Vi, Vnext, N / 4, Pin, h_out, Pout);
+  else k_mgs<T><<<kRedBlocks, kRedThreads, 0, st>>>(W, Vi, Vnext, N, Pin, h_out, Pout);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
 
 template <typename T, typename U>
 void scale_dev(const T* x, U* y, long long N, const double* scale, cudaStream_t st) {
-  k_scale<T, U><<<grid_for(N), 256, 0, st>>>(x, y, N, scale);
+  if (packable(N, {x, y})) k_scale4<T, U><<<grid_for(N / 4), 256, 0, st>>>(x, y, N / 4, scale);
+  else k_scale<T, U><<<grid_for(N), 256, 0, st>>>(x, y, N, scale);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -130,7 +267,10 @@ void multi_axpy(U* X, const T* V, long long ldv, long long N, const double* y, i
                 const double* alpha_dev, cudaStream_t st) {
   TS_REQUIRE(k <= 256, "multi_axpy: at most 256 basis vectors");
   if (k <= 0) return;
-  k_multi_axpy<T, U><<<grid_for(N), 256, 0, st>>>(X, V, ldv, N, y, k, alpha_scale, alpha_dev);
+  if (packable(N, {X, V}) && ldv % 4 == 0)
+    k_multi_axpy4<T, U><<<grid_for(N / 4), 256, 0, st>>>(X, V, ldv / 4 * 4, N / 4, y, k, alpha_scale, alpha_dev);
+  else
+    k_multi_axpy<T, U><<<grid_for(N), 256, 0, st>>>(X, V, ldv, N, y, k, alpha_scale, alpha_dev);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
