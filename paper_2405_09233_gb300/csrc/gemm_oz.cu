@@ -16,7 +16,7 @@
 //    every partial sum is an integer below 2^24, so the tensor core sums them exactly.
 //  * Digit pairs (u, v) with u + v = g share the scale 2^(E_op + E_x - 8g); the pairs with
 //    g <= S + 1 are kept (the dropped ones are below the truncation error of the digits).  Each
-//    accumulator run ("unit": up to 8 k-blocks of 64 inside one g) is read from TMEM, converted to
+//    accumulator run ("unit": up to 8 k-blocks of 64 of one digit pair) is read from TMEM, converted to
 //    int32 and added into per-thread int64 accumulators at the common fixed point
 //    2^(E_op + E_x - F), F = 63 - ceil(log2(2 (n + s))), which keeps every partial sum below 2^62.
 //    Units with 8g > F are added with a rounded right shift.
@@ -65,27 +65,31 @@ struct OzMaps {
   CUtensorMap b_nre;          //   and the digits of -Re B_k
 };
 
-// The stage sequence of one tile: for g = 2 .. S+1, the kbA k-blocks of A_k X_k for each digit
-// pair (u, g-u), then the kbB k-blocks of X_k B_k for each pair.  A unit is a run of at most
-// kOzUnitBlocks consecutive stages of one g.
+// The work of one tile as a list of units, each an exact accumulator run over at most
+// kOzUnitBlocks k-blocks of one digit pair: the A X part, then the X B part; within a part, for
+// each chunk of kOzUnitBlocks k-blocks, every kept digit pair (u, v), u + v <= S + 1, in the order
+// (1,1) .. (1,S), (2,1) .. (2,S-1), ...  Consecutive units therefore reuse one chunk of every
+// operand, which keeps the operands in flight across the grid small enough for L2.
 struct OzSeq {
   int S, kbA, kbB;
-  __device__ __forceinline__ int ulo(int g) const { return g - S > 1 ? g - S : 1; }
-  __device__ __forceinline__ int npairs(int g) const { return (g - 1 < S ? g - 1 : S) - ulo(g) + 1; }
-  __device__ __forceinline__ int stages(int g) const { return npairs(g) * (kbA + kbB); }
-  // Stage idx of group g -> (A X or X B, digit u of the A operand, k-block).
-  __device__ __forceinline__ void decode(int g, int idx, bool& ax, int& u, int& lb) const {
-    const int np = npairs(g);
-    if (idx < np * kbA) {
-      ax = true;
-      u = ulo(g) + idx / kbA;
-      lb = idx % kbA;
-    } else {
-      idx -= np * kbA;
-      ax = false;
-      u = ulo(g) + idx / kbB;
-      lb = idx % kbB;
+  __device__ __forceinline__ int npairs() const { return S * (S + 1) / 2; }
+  __device__ __forceinline__ int chunks(int kb) const { return (kb + kOzUnitBlocks - 1) / kOzUnitBlocks; }
+  __device__ __forceinline__ int units() const { return npairs() * (chunks(kbA) + chunks(kbB)); }
+  // Unit q -> (A X or X B, digit u of the A operand, digit v of the B operand, first k-block, count).
+  __device__ __forceinline__ void unit(int q, bool& ax, int& u, int& v, int& lb0, int& nb) const {
+    const int P = npairs(), qa = P * chunks(kbA);
+    ax = q < qa;
+    const int r = ax ? q : q - qa;
+    int p = r % P;
+    u = 1;
+    while (u < S && p >= S + 1 - u) {
+      p -= S + 1 - u;
+      ++u;
     }
+    v = p + 1;
+    const int kb = ax ? kbA : kbB;
+    lb0 = (r / P) * kOzUnitBlocks;
+    nb = kb - lb0 < kOzUnitBlocks ? kb - lb0 : kOzUnitBlocks;
   }
 };
 
@@ -160,9 +164,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int g = 2; g <= S + 1 && ok; ++g) {
-        const int ns = seq.stages(g);
-        for (int idx = 0; idx < ns; ++idx, ++it) {
+      const int U = seq.units();
+      for (int q = 0; q < U && ok; ++q) {
+        bool ax;
+        int u, v, lb0, nb;
+        seq.unit(q, ax, u, v, lb0, nb);
+        const int pa = (u - 1) * K + k, pb = (v - 1) * K + k;
+        for (int t = 0; t < nb; ++t, ++it) {
           const int slot = it % kOzStages;
           const uint32_t phase = (uint32_t)(it / kOzStages) & 1u;
           if (!mbar_wait(bar_empty + 8 * slot, phase ^ 1u, err, 11)) {
@@ -173,12 +181,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           mbar_expect_tx(full, kOzStage);
           const uint32_t sA = base + slot * kOzStage;
           const uint32_t sAi = sA + kOzTileA, sP = sA + 2 * kOzTileA, sQ = sP + kOzTileB, sR = sQ + kOzTileB;
-          bool ax;
-          int u, lb;
-          seq.decode(g, idx, ax, u, lb);
-          const int v = g - u;
-          const int l0 = lb * kOzKB;
-          const int pa = (u - 1) * K + k, pb = (v - 1) * K + k;
+          const int l0 = (lb0 + t) * kOzKB;
           if (ax) {
             tma_load_3d(sA, &maps.a_re, l0, i0, pa, full);
             tma_load_3d(sAi, &maps.a_im, l0, i0, pa, full);
@@ -205,23 +208,21 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       constexpr uint32_t idn = make_idesc(1, kOzM, 2 * kOzN, true);
       constexpr uint32_t idp1 = make_idesc(1, kOzM, kOzN, false);
       constexpr uint32_t idn1 = make_idesc(1, kOzM, kOzN, true);
-      int it = 0, uc = 0;
+      int it = 0;
       bool ok = true;
-      for (int g = 2; g <= S + 1 && ok; ++g) {
-        const int ns = seq.stages(g);
-        uint32_t d = tmem;
-        for (int idx = 0; idx < ns; ++idx, ++it) {
-          const bool ufirst = (idx % kOzUnitBlocks) == 0;
-          const bool ulast = (idx % kOzUnitBlocks) == kOzUnitBlocks - 1 || idx == ns - 1;
-          if (ufirst) {
-            const int b = uc & 1;
-            if (uc >= 2 && !mbar_wait(bar_free + 8 * b, (uint32_t)((uc >> 1) - 1) & 1u, err, 12)) {
-              ok = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            d = tmem + (uint32_t)(b * 2 * kOzN);
-          }
+      const int U = seq.units();
+      for (int q = 0; q < U && ok; ++q) {
+        bool ax;
+        int u, v, lb0, nb;
+        seq.unit(q, ax, u, v, lb0, nb);
+        const int b = q & 1;
+        if (q >= 2 && !mbar_wait(bar_free + 8 * b, (uint32_t)((q >> 1) - 1) & 1u, err, 12)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * 2 * kOzN);
+        for (int t = 0; t < nb; ++t, ++it) {
           const int slot = it % kOzStages;
           const uint32_t phase = (uint32_t)(it / kOzStages) & 1u;
           if (!mbar_wait(bar_full + 8 * slot, phase, err, 13)) {
@@ -229,9 +230,6 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          bool ax;
-          int u, lb;
-          seq.decode(g, idx, ax, u, lb);
           const uint32_t sA = base + slot * kOzStage;
           const uint64_t dAr = smem_desc_sw128(sA), dAi = smem_desc_sw128(sA + kOzTileA);
           const uint64_t dP = smem_desc_sw128(sA + 2 * kOzTileA);
@@ -239,7 +237,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t o = (uint64_t)(kk * 2);   // 32 bytes >> 4
-            const uint32_t acc = (ufirst && kk == 0) ? 0u : 1u;
+            const uint32_t acc = (t == 0 && kk == 0) ? 0u : 1u;
             if (ax) {
               if (real) {
                 mma_issue(d, dAr + o, dQ + o, idp1, acc, 0);
@@ -257,11 +255,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             }
           }
           mma_commit(bar_empty + 8 * slot);
-          if (ulast) {
-            mma_commit(bar_acc + 8 * (uc & 1));
-            ++uc;
-          }
         }
+        if (ok) mma_commit(bar_acc + 8 * b);
       }
     }
   } else {
@@ -272,28 +267,28 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 #pragma unroll
     for (int c = 0; c < 32; ++c) ar[c] = ai[c] = 0;
     bool ok = true;
-    int uc = 0;
-    for (int g = 2; g <= S + 1 && ok; ++g) {
-      const int nunits = (seq.stages(g) + kOzUnitBlocks - 1) / kOzUnitBlocks;
-      const int shift = F - 8 * g;
-      for (int un = 0; un < nunits; ++un, ++uc) {
-        const int b = uc & 1;
-        if (!mbar_wait(bar_acc + 8 * b, (uint32_t)(uc >> 1) & 1u, err, 14)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t tre = lane_base + (uint32_t)(b * 2 * kOzN);
-        acc_add16<0>(ar, tre, shift);
-        acc_add16<16>(ar, tre + 16, shift);
-        if (!real) {
-          acc_add16<0>(ai, tre + kOzN, shift);
-          acc_add16<16>(ai, tre + kOzN + 16, shift);
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar_free + 8 * b);
+    const int U = seq.units();
+    for (int q = 0; q < U; ++q) {
+      bool ax;
+      int u, v, lb0, nb;
+      seq.unit(q, ax, u, v, lb0, nb);
+      const int shift = F - 8 * (u + v);
+      const int b = q & 1;
+      if (!mbar_wait(bar_acc + 8 * b, (uint32_t)(q >> 1) & 1u, err, 14)) {
+        ok = false;
+        break;
       }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tre = lane_base + (uint32_t)(b * 2 * kOzN);
+      acc_add16<0>(ar, tre, shift);
+      acc_add16<16>(ar, tre + 16, shift);
+      if (!real) {
+        acc_add16<0>(ai, tre + kOzN, shift);
+        acc_add16<16>(ai, tre + kOzN + 16, shift);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_free + 8 * b);
     }
     const int row = i0 + quad * 32 + lane;
     if (ok && row < n) {
