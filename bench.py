@@ -44,9 +44,9 @@ def args_parse():
                     help="default: fp64 for the dense n=s=1024 workload, mixed_fp32 for the others")
     ap.add_argument("--engine", choices=["dfma", "ozaki"], default="dfma",
                     help="how FP64 applications run: FP64 CUDA cores, or emulated on the BF16 tensor cores")
-    ap.add_argument("--variants",
-                    default="mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16,fp64@ozaki,mixed_tf32x3@ozaki,mixed_bf16@ozaki",
-                    help="comma list of extra precision[@engine] runs to time ('' = none)")
+    ap.add_argument("--variants", default=None,
+                    help="comma list of extra precision[@engine] runs to time ('' = none; default: every "
+                         "precision and engine the workload supports)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
@@ -55,6 +55,10 @@ def args_parse():
     ap.add_argument("--s", type=int)
     ap.add_argument("--p", type=int)
     return ap.parse_args()
+
+
+DENSE_VARIANTS = "mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16,fp64@ozaki,mixed_tf32x3@ozaki,mixed_bf16@ozaki"
+BATCHED_VARIANTS_DEFAULT_MARK = "<batched-default>"
 
 
 def workload_cfg(a):
@@ -284,6 +288,8 @@ def run_reference(a):
 
 def main():
     a = args_parse()
+    if a.variants is None:
+        a.variants = BATCHED_VARIANTS_DEFAULT_MARK if a.workload == "batched_256" else DENSE_VARIANTS
     if a.precision is None:
         a.precision = "fp64" if a.workload in ("dense_n1024_s1024_p16", "sparse_lap128_s32_p8") else "mixed_fp32"
     if a.impl == "reference":
@@ -465,11 +471,11 @@ def run_batched(a, rank, world, local, dev):
     unknowns = sum(sp.n * sp.s * sp.p for sp in specs)
     prec = a.precision
 
-    def step(precision):
+    def step(precision, engine=a.engine):
         ops = [ctx.op_create_dense(A, B) for A, B, _ in dev_in]
         for X in Xs:
             X.zero_()
-        st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, tol=1e-10, precision=precision)
+        st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, tol=1e-10, precision=precision, engine=engine)
         for op in ops:
             op.close()
         return st, infos
@@ -500,7 +506,7 @@ def run_batched(a, rank, world, local, dev):
     ops = [ctx.op_create_dense(A, B) for A, B, _ in host]
     Cd = [C.to(dev, non_blocking=True) for C in C_h]
     Xd = [torch.zeros_like(C) for C in Cd]
-    st2, _, _ = ctx.batched_solve(ops, Cd, Xd, restart=20, tol=1e-10, precision=prec)
+    st2, _, _ = ctx.batched_solve(ops, Cd, Xd, restart=20, tol=1e-10, precision=prec, engine=a.engine)
     for Xh_, Xd_ in zip(X_h, Xd):
         Xh_.copy_(Xd_)
     torch.cuda.synchronize()
@@ -509,25 +515,35 @@ def run_batched(a, rank, world, local, dev):
         op.close()
     h2d = sum(8 * (A.numel() + B.numel() + C.numel()) for (A, B, _), C in zip(host, C_h))
     d2h = sum(8 * X.numel() for X in X_h)
-    fp64 = None
-    if a.variants != "" and prec != "fp64":
-        torch.cuda.synchronize()
-        f0 = time.perf_counter()
-        stf, infof = step("fp64")
-        torch.cuda.synchronize()
-        fp64 = {"value": unknowns * world / (time.perf_counter() - f0), "status": stf,
-                "max_relres_true": max(i.relres_true for i in infof)}
+    variants = {}
+    primary = prec + ("" if a.engine == "dfma" else "@" + a.engine)
+    names = a.variants.split(",") if a.variants else []
+    if a.variants == BATCHED_VARIANTS_DEFAULT_MARK:
+        names = ["fp64", "mixed_fp32", "fp64@ozaki", "mixed_fp32@ozaki"]
+    for name in [v for v in names if v and v != primary and v.partition("@")[0] in ("fp64", "mixed_fp32")]:
+        vp, _, ve = name.partition("@")
+        try:
+            torch.cuda.synchronize()
+            f0 = time.perf_counter()
+            stf, infof = step(vp, ve or "dfma")
+            torch.cuda.synchronize()
+            variants[name] = {"value": unknowns * world / (time.perf_counter() - f0), "status": stf,
+                              "max_relres_true": max(i.relres_true for i in infof),
+                              "max_err_vs_xstar": max(float(torch.max(torch.abs(X - Xst)))
+                                                      for X, (_, _, Xst) in zip(Xs, dev_in))}
+        except Exception as e:  # report, do not hide
+            variants[name] = {"error": str(e)}
     if rank == 0:
         line = {"metric": METRIC, "value": unknowns * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64" if prec != "fp64" else "f64", "data": "synthetic",
                 "config": {"workload": "batched_256", "instances": count, "unknowns": unknowns, "restart": 20,
-                           "tol": 1e-10, "precision": prec, "method": "batched tGMRES",
+                           "tol": 1e-10, "precision": prec, "fp64_engine": a.engine, "method": "batched tGMRES",
                            "max_relres_true": relres, "max_err_vs_xstar": err,
                            "l2": "inputs larger than L2 (5 GB basis)"},
                 "e2e": {"value": unknowns * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "clocks": clk, "gpu_launches": int(stt.launches), "variants": {"fp64": fp64} if fp64 else {}}
+                "clocks": clk, "gpu_launches": int(stt.launches), "variants": variants}
         print(json.dumps(line), flush=True)
     ctx.close()
 

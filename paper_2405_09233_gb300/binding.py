@@ -270,7 +270,7 @@ class Context:
                            "fp64", 0.0, 0, history_cap)
 
     def batched_solve(self, ops, Cs, Xs, tols=None, restart=20, tol=1e-10, max_restarts=200, precision="fp64",
-                      inner_tol=0.0, max_outer=0):
+                      inner_tol=0.0, max_outer=0, engine="dfma", ozaki_digits=0):
         """Solve len(ops) independent STEs together; Cs/Xs are CUDA float64 tensors (p, s, n) per instance.
         Returns (status, [SolveInfo], [per-instance status])."""
         count = len(ops)
@@ -285,6 +285,8 @@ class Context:
         opts.restart, opts.tol, opts.max_restarts = restart, tol, max_restarts
         opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opts.inner_tol, opts.max_outer = inner_tol, max_outer
+        opts.fp64_engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
+        opts.ozaki_digits = ozaki_digits
         infos = (SolveInfo * count)()
         sts = (ctypes.c_int * count)()
         st = self._check(lib().ts_batched_solve(self._h, count, arr, ctypes.byref(opts), infos, sts,

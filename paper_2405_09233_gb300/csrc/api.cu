@@ -49,6 +49,7 @@ void Workspace::release_all() {
 }
 
 std::atomic<long long> g_launches{0};
+thread_local int g_count_suppress = 0;
 
 void KernelTimer::begin(cudaStream_t st, int kind, double work) {
   if (!enabled) return;

@@ -19,6 +19,7 @@
 #include <numeric>
 #include <vector>
 #include "internal.cuh"
+#include "oz.cuh"
 #include "apply.cuh"
 #include "reduce.cuh"
 #include "fft_reg.cuh"
@@ -466,9 +467,12 @@ struct BatchPlan {
 };
 
 // Records one restart cycle on `st`; returns the number of kernels it launched.
-template <typename T, typename Real2>
+// `residual_products(st)` issues the FP64 slice products of the true residual (Xh64 -> Yh64) and
+// returns how many kernels it launched.
+template <typename T, typename Real2, typename ResidualProducts>
 int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Real2* Yh, double* R, double2* Xh64,
-                  double2* Yh64, const int4* items, double* P0, double* P1, double* Pt, cudaStream_t st) {
+                 double2* Yh64, const int4* items, double* P0, double* P1, double* Pt,
+                 const ResidualProducts& residual_products, cudaStream_t st) {
   using Real = T;
   const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size(), nit = (int)plan.items.size();
   const int count = d.count, m = d.m;
@@ -493,10 +497,10 @@ int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Re
   k_b_axpy<T><<<nbs, 256, 0, st>>>(d, V);
   // true residual R = C - M(X) in FP64
   k_b_rfft<double, double2, 1, 1><<<ntb, kTubes, 0, st>>>(d, nullptr, Xh64);
-  k_b_gemm<double, 1><<<nit, kGemmNT, 0, st>>>(d, items, Xh64, Yh64);
+  kernels += residual_products(st);
   k_b_irfft<double, double2, 1><<<ntb, kTubes, 0, st>>>(d, Yh64, R, Pt);
   k_b_finalize_norm<<<count, 256, 0, st>>>(d, Pt, 1);
-  kernels += 6;
+  kernels += 5;
   TS_CUDA(cudaGetLastError());
   return kernels;
 }
@@ -513,9 +517,14 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
              "ts_batched_solve: precision must be TS_FP64 or TS_MIXED_FP32");
   TS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-  if (o.fp64_engine != TS_ENGINE_DFMA)
-    throw Error{TS_ERR_UNSUPPORTED, "ts_batched_solve runs on the FP64 DFMA engine only"};
+  TS_REQUIRE(o.fp64_engine == TS_ENGINE_DFMA || o.fp64_engine == TS_ENGINE_OZAKI,
+             "ts_batched_solve: unknown fp64_engine");
+  TS_REQUIRE(o.ozaki_digits == 0 || (o.ozaki_digits >= 3 && o.ozaki_digits <= 8),
+             "ts_batched_solve: ozaki_digits must be 3..8");
+  const bool ozaki = o.fp64_engine == TS_ENGINE_OZAKI;
+  const int oz_digits = o.ozaki_digits == 0 ? 6 : o.ozaki_digits;
   const bool mixed = o.precision == TS_MIXED_FP32;
+  std::vector<ts_op*> ops(count);
   const int m = o.restart;
   BatchPlan plan;
   plan.inst.resize(count);
@@ -523,6 +532,7 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
     const ts_instance& u = insts[i];
     TS_REQUIRE(u.op && u.C && u.X, "ts_batched_solve: instance with a null pointer");
     ts_op* op = const_cast<ts_op*>(u.op);
+    ops[i] = op;
     TS_REQUIRE(!op->sp, "ts_batched_solve: dense operators only");
     TS_REQUIRE(op->p <= 64, "ts_batched_solve: p must be <= 64");
     TS_REQUIRE(is_device_ptr(u.C) && is_device_ptr(u.X), "ts_batched_solve: C and X must be device memory");
@@ -603,6 +613,29 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   int* flags = (int*)get("b_flags", sizeof(int) * 2 * count);
   const long long stride = state_stride(m);
   double* state = (double*)get("b_state", sizeof(double) * (size_t)stride * count);
+  // Emulated FP64 residual products: digit planes of every operator and one scratch set sized for
+  // the largest instance, all made before anything is captured.
+  OzBuffers ozb;
+  int* tc_err = (int*)get("tc_err", sizeof(int) * 4);
+  if (ozaki) {
+    OzBufferSizes zmax;
+    for (int i = 0; i < count; ++i) {
+      oz_prepare(ops[i], oz_digits, user);
+      const OzBufferSizes z = oz_buffer_sizes(ops[i]->n, ops[i]->s, ops[i]->K, oz_digits);
+      zmax.xc = std::max(zmax.xc, z.xc);
+      zmax.xr = std::max(zmax.xr, z.xr);
+      zmax.K = std::max(zmax.K, z.K);
+    }
+    oz_preload();
+    ozb.xc_re = get("b_oz_xc_re", zmax.xc);
+    ozb.xc_im = get("b_oz_xc_im", zmax.xc);
+    ozb.xc_nim = get("b_oz_xc_nim", zmax.xc);
+    ozb.xr_re = get("b_oz_xr_re", zmax.xr);
+    ozb.xr_im = get("b_oz_xr_im", zmax.xr);
+    ozb.mx = (unsigned long long*)get("b_oz_mx", sizeof(unsigned long long) * zmax.K);
+    ozb.Ex = (int*)get("b_oz_Ex", sizeof(int) * zmax.K);
+    TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, user));
+  }
 
   BDev d{};
   d.inst = d_inst;
@@ -636,13 +669,25 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   TS_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice, st));
   TS_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * 16 * count, st));
   const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size(), nit = (int)plan.items.size();
+  // FP64 slice products of a true residual: the (instance, slice, tile) work list on CUDA cores, or
+  // one emulated-FP64 product per instance (each gated by the instance's cycle flag).
+  auto residual_products = [&](cudaStream_t s2) -> int {
+    if (!ozaki) {
+      k_b_gemm<double, 1><<<nit, kGemmNT, 0, s2>>>(d, d_items, Xh64, Yh64);
+      TS_CUDA(cudaGetLastError());
+      return 1;
+    }
+    for (int i = 0; i < count; ++i)
+      oz_products(ops[i], Xh64 + plan.inst[i].offS, Yh64 + plan.inst[i].offS, oz_digits, ozb, d.cyc + i, tc_err, s2);
+    return 5 * count;
+  };
   k_b_normC<<<nbs, 256, 0, st>>>(d, P0);
   k_b_finalize_norm<<<count, 256, 0, st>>>(d, P0, 0);
   k_b_rfft<double, double2, 1, 1><<<ntb, kTubes, 0, st>>>(d, nullptr, Xh64);
-  k_b_gemm<double, 1><<<nit, kGemmNT, 0, st>>>(d, d_items, Xh64, Yh64);
+  const int first = residual_products(st);
   k_b_irfft<double, double2, 1><<<ntb, kTubes, 0, st>>>(d, Yh64, R, Pt);
   k_b_finalize_norm<<<count, 256, 0, st>>>(d, Pt, 1);
-  count_launch(6);
+  count_launch(ozaki ? 5 : 5 + first);   // the emulated products count their own launches
   TS_CUDA(cudaGetLastError());
 
   std::vector<double> hsc(16 * count);
@@ -673,13 +718,14 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
         if (mixed) preload_cycle_kernels<float, float2>();
         else preload_cycle_kernels<double, double2>();
         cudaGraph_t graph;
+        CountSuppress no_count;   // the replays below count the recorded kernels
         TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         if (mixed)
-          graph_kernels = record_cycle<float, float2>(d, plan, (float*)V, (float*)W, (float2*)Xh, (float2*)Yh, R, Xh64, Yh64, d_items,
-                                      P0, P1, Pt, st);
+          graph_kernels = record_cycle<float, float2>(d, plan, (float*)V, (float*)W, (float2*)Xh, (float2*)Yh, R, Xh64,
+                                                      Yh64, d_items, P0, P1, Pt, residual_products, st);
         else
-          graph_kernels = record_cycle<double, double2>(d, plan, (double*)V, (double*)W, (double2*)Xh, (double2*)Yh, R, Xh64, Yh64,
-                                        d_items, P0, P1, Pt, st);
+          graph_kernels = record_cycle<double, double2>(d, plan, (double*)V, (double*)W, (double2*)Xh, (double2*)Yh, R,
+                                                        Xh64, Yh64, d_items, P0, P1, Pt, residual_products, st);
         TS_CUDA(cudaStreamEndCapture(st, &graph));
         TS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         TS_CUDA(cudaGraphDestroy(graph));
@@ -699,6 +745,15 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   float ms = 0.f;
   TS_CUDA(cudaEventElapsedTime(&ms, t0, t1));
   if (exec) TS_CUDA(cudaGraphExecDestroy(exec));
+  if (ozaki) {
+    int e = 0;
+    TS_CUDA(cudaMemcpy(&e, tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+      TS_CUDA(cudaEventDestroy(t0));
+      TS_CUDA(cudaEventDestroy(t1));
+      throw Error{TS_ERR_TIMEOUT, "tensor-core kernel wait expired (code " + std::to_string(e) + ")"};
+    }
+  }
   TS_CUDA(cudaEventDestroy(t0));
   TS_CUDA(cudaEventDestroy(t1));
   TS_CUDA(cudaEventRecord(ctx->ev1, st));

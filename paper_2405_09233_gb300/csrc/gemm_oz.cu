@@ -123,7 +123,8 @@ __device__ __forceinline__ void acc_add16(long long (&acc)[32], uint32_t taddr, 
 
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_oz_sylv(const __grid_constant__ OzMaps maps, double2* __restrict__ Y, int n, int s, int K, int nyq, int S,
-              int F, const int* __restrict__ Eop, const int* __restrict__ Ex, int* err) {
+              int F, const int* __restrict__ Eop, const int* __restrict__ Ex, const int* __restrict__ gate, int* err) {
+  if (gate && *gate == 0) return;   // instance of a batch that has left the current cycle
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -322,7 +323,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 // ------------------------------------------------------------------------------------------------
 // Per-slice max(|Re|, |Im|) of K complex slices of T entries, as FP64 bit patterns (monotone for
 // non-negative values) combined with atomicMax; a non-finite entry makes the slice's value +inf.
-__global__ void k_oz_maxabs(const double2* __restrict__ Z, long long T, unsigned long long* __restrict__ out) {
+__global__ void k_oz_maxabs(const double2* __restrict__ Z, long long T, unsigned long long* __restrict__ out,
+                            const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
   const int k = blockIdx.y;
   const double2* Zk = Z + (long long)k * T;
   double m = 0.0;
@@ -381,7 +384,8 @@ template <bool TRANS>
 __global__ void k_oz_split(const double2* __restrict__ src, long long sstride, int R, int C, int K,
                            const int* __restrict__ E, int S, __nv_bfloat16* __restrict__ re,
                            __nv_bfloat16* __restrict__ im, __nv_bfloat16* __restrict__ nre,
-                           __nv_bfloat16* __restrict__ nim, int ld, long long plane_elems) {
+                           __nv_bfloat16* __restrict__ nim, int ld, long long plane_elems, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
   __shared__ double2 tile[32][33];
   const int k = blockIdx.z, r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   const double2* Sk = src + (long long)k * sstride;
@@ -430,10 +434,11 @@ __global__ void k_oz_split(const double2* __restrict__ src, long long sstride, i
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-void slice_maxabs(const double2* Z, long long T, int K, unsigned long long* out, cudaStream_t st) {
+void slice_maxabs(const double2* Z, long long T, int K, unsigned long long* out, cudaStream_t st,
+                  const int* gate = nullptr) {
   long long b = (T + 255) / 256;
   if (b > 64) b = 64;
-  k_oz_maxabs<<<dim3((unsigned)b, K), 256, 0, st>>>(Z, T, out);
+  k_oz_maxabs<<<dim3((unsigned)b, K), 256, 0, st>>>(Z, T, out, gate);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -446,10 +451,10 @@ void exponents(const unsigned long long* mx, int K, int* E, cudaStream_t st) {
 
 template <bool TRANS>
 void split(const double2* src, long long sstride, int R, int C, int K, const int* E, int S, void* re, void* im,
-           void* nre, void* nim, int ld, long long plane_elems, cudaStream_t st) {
+           void* nre, void* nim, int ld, long long plane_elems, cudaStream_t st, const int* gate = nullptr) {
   k_oz_split<TRANS><<<dim3((R + 31) / 32, (C + 31) / 32, K), dim3(32, 8), 0, st>>>(
       src, sstride, R, C, K, E, S, static_cast<__nv_bfloat16*>(re), static_cast<__nv_bfloat16*>(im),
-      static_cast<__nv_bfloat16*>(nre), static_cast<__nv_bfloat16*>(nim), ld, plane_elems);
+      static_cast<__nv_bfloat16*>(nre), static_cast<__nv_bfloat16*>(nim), ld, plane_elems, gate);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -506,44 +511,47 @@ double oz_bf16_flops(int n, int s, int K, int nyq, int S) {
   return pairs * per * (8.0 * (K - nreal) + 2.0 * nreal);
 }
 
-void apply_f64_oz(ts_ctx* ctx, const ts_op* cop, const double* X, double* Y, int mode, const double* C,
-                  double* partials, int S, cudaStream_t st) {
-  ts_op* op = const_cast<ts_op*>(cop);   // the digit planes are cached on first use
-  oz_prepare(op, S, st);
-  OzOperands& t = *op->oz;
-  const int n = op->n, s = op->s, p = op->p, K = op->K;
-  const long long T = (long long)n * s;
-  double2* Xh = static_cast<double2*>(ctx->ws.get("apply_Xh", sizeof(double2) * (size_t)K * T));
-  double2* Yh = static_cast<double2*>(ctx->ws.get("apply_Yh", sizeof(double2) * (size_t)K * T));
-  const size_t nxc = (size_t)S * K * s * t.ldn * 2, nxr = (size_t)S * K * n * t.lds * 2;
-  void* xc_re = ctx->ws.get("oz_xc_re", nxc);
-  void* xc_im = ctx->ws.get("oz_xc_im", nxc);
-  void* xc_nim = ctx->ws.get("oz_xc_nim", nxc);
-  void* xr_re = ctx->ws.get("oz_xr_re", nxr);
-  void* xr_im = ctx->ws.get("oz_xr_im", nxr);
-  unsigned long long* mx = static_cast<unsigned long long*>(ctx->ws.get("oz_mx", sizeof(unsigned long long) * K));
-  int* Ex = static_cast<int*>(ctx->ws.get("oz_Ex", sizeof(int) * K));
-  int* err = static_cast<int*>(ctx->ws.get("tc_err", sizeof(int) * 4));
-  KernelTimer& tm = ctx->timer;
+void oz_preload() {
+  const void* fns[] = {(const void*)k_oz_maxabs, (const void*)k_oz_exponents, (const void*)k_oz_split<false>,
+                       (const void*)k_oz_split<true>, (const void*)k_oz_sylv};
+  for (const void* f : fns) {
+    cudaFuncAttributes fa;
+    TS_CUDA(cudaFuncGetAttributes(&fa, f));
+  }
+  static bool attr_set = false;
+  if (!attr_set) {
+    TS_CUDA(cudaFuncSetAttribute(k_oz_sylv, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem));
+    attr_set = true;
+  }
+}
 
-  tm.begin(st, 1, 8.0 * T * p + 16.0 * K * T);
-  rfft_tube<double, double2>(X, Xh, T, p, st);
-  tm.end(st);
-  const int nyq = nyquist_index(p);
-  tm.begin(st, 3, gemm_flops(n, s, n, s, K, nyq));
-  TS_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * K, st));
-  slice_maxabs(Xh, T, K, mx, st);
-  exponents(mx, K, Ex, st);
-  split<false>(Xh, T, n, s, K, Ex, S, xc_re, xc_im, nullptr, xc_nim, t.ldn, (long long)s * t.ldn, st);
-  split<true>(Xh, T, n, s, K, Ex, S, xr_re, xr_im, nullptr, nullptr, t.lds, (long long)n * t.lds, st);
+OzBufferSizes oz_buffer_sizes(int n, int s, int K, int S) {
+  OzBufferSizes z;
+  z.xc = (size_t)S * K * s * round_up(n, 64) * 2;
+  z.xr = (size_t)S * K * n * round_up(s, 64) * 2;
+  z.K = K;
+  return z;
+}
+
+void oz_products(const ts_op* cop, const double2* Xh, double2* Yh, int S, const OzBuffers& b, const int* gate,
+                 int* err, cudaStream_t st) {
+  const OzOperands& t = *cop->oz;
+  TS_REQUIRE(t.S == S, "oz_products: operator digits not prepared");
+  const int n = cop->n, s = cop->s, p = cop->p, K = cop->K;
+  const long long T = (long long)n * s;
+  TS_CUDA(cudaMemsetAsync(b.mx, 0, sizeof(unsigned long long) * K, st));
+  slice_maxabs(Xh, T, K, b.mx, st, gate);
+  exponents(b.mx, K, b.Ex, st);
+  split<false>(Xh, T, n, s, K, b.Ex, S, b.xc_re, b.xc_im, nullptr, b.xc_nim, t.ldn, (long long)s * t.ldn, st, gate);
+  split<true>(Xh, T, n, s, K, b.Ex, S, b.xr_re, b.xr_im, nullptr, nullptr, t.lds, (long long)n * t.lds, st, gate);
   OzMaps maps;
   make_map(&maps.a_re, t.a_re, 2, t.ldn, n, n, S * K, kOzM);
   make_map(&maps.a_im, t.a_im, 2, t.ldn, n, n, S * K, kOzM);
-  make_map(&maps.xc_re, xc_re, 2, t.ldn, n, s, S * K, kOzN);
-  make_map(&maps.xc_im, xc_im, 2, t.ldn, n, s, S * K, kOzN);
-  make_map(&maps.xc_nim, xc_nim, 2, t.ldn, n, s, S * K, kOzN);
-  make_map(&maps.xr_re, xr_re, 2, t.lds, s, n, S * K, kOzM);
-  make_map(&maps.xr_im, xr_im, 2, t.lds, s, n, S * K, kOzM);
+  make_map(&maps.xc_nim, b.xc_nim, 2, t.ldn, n, s, S * K, kOzN);
+  make_map(&maps.xc_re, b.xc_re, 2, t.ldn, n, s, S * K, kOzN);
+  make_map(&maps.xc_im, b.xc_im, 2, t.ldn, n, s, S * K, kOzN);
+  make_map(&maps.xr_re, b.xr_re, 2, t.lds, s, n, S * K, kOzM);
+  make_map(&maps.xr_im, b.xr_im, 2, t.lds, s, n, S * K, kOzM);
   make_map(&maps.b_re, t.b_re, 2, t.lds, s, s, S * K, kOzN);
   make_map(&maps.b_im, t.b_im, 2, t.lds, s, s, S * K, kOzN);
   make_map(&maps.b_nre, t.b_nre, 2, t.lds, s, s, S * K, kOzN);
@@ -551,15 +559,37 @@ void apply_f64_oz(ts_ctx* ctx, const ts_op* cop, const double* X, double* Y, int
   int lg = 0;
   while ((1ll << lg) < 2ll * (n + s)) ++lg;
   const int F = 63 - lg;
-  static bool attr_set = false;
-  if (!attr_set) {
-    TS_CUDA(cudaFuncSetAttribute(k_oz_sylv, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem));
-    attr_set = true;
-  }
   dim3 grid((s + kOzN - 1) / kOzN, (n + kOzM - 1) / kOzM, K);
-  k_oz_sylv<<<grid, kOzThreads, kOzSmem, st>>>(maps, Yh, n, s, K, nyq, S, F, t.Eop, Ex, err);
+  k_oz_sylv<<<grid, kOzThreads, kOzSmem, st>>>(maps, Yh, n, s, K, nyquist_index(p), S, F, t.Eop, b.Ex, gate, err);
   count_launch();
   TS_CUDA(cudaGetLastError());
+}
+
+void apply_f64_oz(ts_ctx* ctx, const ts_op* cop, const double* X, double* Y, int mode, const double* C,
+                  double* partials, int S, cudaStream_t st) {
+  ts_op* op = const_cast<ts_op*>(cop);   // the digit planes are cached on first use
+  oz_prepare(op, S, st);
+  oz_preload();
+  const int n = op->n, s = op->s, p = op->p, K = op->K;
+  const long long T = (long long)n * s;
+  double2* Xh = static_cast<double2*>(ctx->ws.get("apply_Xh", sizeof(double2) * (size_t)K * T));
+  double2* Yh = static_cast<double2*>(ctx->ws.get("apply_Yh", sizeof(double2) * (size_t)K * T));
+  const OzBufferSizes z = oz_buffer_sizes(n, s, K, S);
+  OzBuffers b;
+  b.xc_re = ctx->ws.get("oz_xc_re", z.xc);
+  b.xc_im = ctx->ws.get("oz_xc_im", z.xc);
+  b.xc_nim = ctx->ws.get("oz_xc_nim", z.xc);
+  b.xr_re = ctx->ws.get("oz_xr_re", z.xr);
+  b.xr_im = ctx->ws.get("oz_xr_im", z.xr);
+  b.mx = static_cast<unsigned long long*>(ctx->ws.get("oz_mx", sizeof(unsigned long long) * K));
+  b.Ex = static_cast<int*>(ctx->ws.get("oz_Ex", sizeof(int) * K));
+  int* err = static_cast<int*>(ctx->ws.get("tc_err", sizeof(int) * 4));
+  KernelTimer& tm = ctx->timer;
+  tm.begin(st, 1, 8.0 * T * p + 16.0 * K * T);
+  rfft_tube<double, double2>(X, Xh, T, p, st);
+  tm.end(st);
+  tm.begin(st, 3, gemm_flops(n, s, n, s, K, nyquist_index(p)));
+  oz_products(op, Xh, Yh, S, b, nullptr, err, st);
   tm.end(st);
   tm.begin(st, 1, 16.0 * K * T + 8.0 * T * p * (mode == IRFFT_RESIDUAL ? 2 : 1));
   irfft_tube<double, double2>(Yh, Y, T, p, mode, C, partials, st);

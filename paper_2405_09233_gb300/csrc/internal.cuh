@@ -54,7 +54,16 @@ constexpr int kRedThreads = 256;
 
 // Process-wide count of kernel launches (reported by ts_stats_get).
 extern std::atomic<long long> g_launches;
-inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// Launches recorded into a CUDA graph are counted when the graph is replayed, not while it is
+// captured: CountSuppress turns counting off on this thread for its lifetime.
+extern thread_local int g_count_suppress;
+inline void count_launch(long long n = 1) {
+  if (!g_count_suppress) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+struct CountSuppress {
+  CountSuppress() { ++g_count_suppress; }
+  ~CountSuppress() { --g_count_suppress; }
+};
 
 // Event timing of selected kernels while a context has statistics enabled.
 struct TimedRegion {

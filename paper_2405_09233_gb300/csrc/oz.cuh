@@ -18,7 +18,30 @@ struct OzOperands {
   void release();
 };
 
+// Per-application digit planes of X_k (caller-owned, sized by oz_buffer_sizes).
+struct OzBuffers {
+  void* xc_re = nullptr;           // [S][K][s][ldn]  column-major X_k digits
+  void* xc_im = nullptr;
+  void* xc_nim = nullptr;          //   digits of -Im X_k
+  void* xr_re = nullptr;           // [S][K][n][lds]  row-major X_k digits
+  void* xr_im = nullptr;
+  unsigned long long* mx = nullptr;   // [K] slice maxima (FP64 bit patterns)
+  int* Ex = nullptr;                  // [K] slice exponents
+};
+struct OzBufferSizes {
+  size_t xc = 0, xr = 0;           // bytes of each xc_* / xr_* plane set
+  int K = 0;                       // entries of mx and Ex
+};
+OzBufferSizes oz_buffer_sizes(int n, int s, int K, int S);
+
 void oz_prepare(ts_op* op, int S, cudaStream_t st);
+// Loads the kernels and sets their attributes (call before any stream capture that records them).
+void oz_preload();
+// Yh_k = A_k Xh_k - Xh_k B_k for the K spectral slices of op (double2, column-major n x s each),
+// emulated FP64; op must be prepared with S digits.  gate (device, may be null): when *gate == 0
+// every kernel returns at once.  Captures into a CUDA graph (no allocation, no synchronisation).
+void oz_products(const ts_op* op, const double2* Xh, double2* Yh, int S, const OzBuffers& b, const int* gate,
+                 int* err, cudaStream_t st);
 // Y = M(X) in FP64 through the emulated product (same contract as apply_f64).
 void apply_f64_oz(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
                   double* partials, int S, cudaStream_t st);

@@ -107,6 +107,25 @@ def test_batched_repeated_calls_leave_operators_intact(ctx):
             op.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp32"])
+def test_batched_ozaki_residuals(ctx, prec):
+    """The batch with its FP64 products on the emulated-FP64 engine: every instance reaches its
+    tolerance (checked by the oracle) and matches the DFMA-engine batch to 1e-8 relative."""
+    import torch
+    probs, ops, Cs, Xs, Cn = make_batch(ctx, SHAPES, 400)
+    st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=12, precision=prec, engine="ozaki")
+    assert st == 0 and all(v == 0 for v in sts), sts
+    Xd = [torch.zeros_like(X) for X in Xs]
+    st2, _, _ = ctx.batched_solve(ops, Cs, Xd, restart=12, precision=prec)
+    assert st2 == 0
+    for pr, C, X, X2 in zip(probs, Cn, Xs, Xd):
+        Xh = from_dev(X)
+        assert tp.norm(C - kr.sylv_apply(pr.A, pr.B, Xh)) <= 1e-10 * tp.norm(C)
+        assert float(torch.max(torch.abs(X - X2))) <= 1e-8 * float(torch.max(torch.abs(X2)))
+    for op in ops:
+        op.close()
+
+
 def test_batched_256_instance_workload(ctx):
     """256 instances, n log-uniform in [64, 1024], s uniform in [16, 128], p in {4, 8, 16}, FP32 inner
     tGMRES(20) with FP64 refinement; every instance's true residual (library FP64 operator) <= 1e-10."""
