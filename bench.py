@@ -588,6 +588,7 @@ def run_tbas(a, rank, world, local, dev):
         r = step()
     assert r.status == 0, r
     ctx.stats_reset()
+    ctx.stats_enable(True)
     clocks = ClockSampler(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -598,9 +599,18 @@ def run_tbas(a, rank, world, local, dev):
     e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    ctx.stats_enable(False)
     stt = ctx.stats_get()
     ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
     unknowns = n * s_blk * p
+    blk_ms = stt.tba_ms / max(stt.tba_launches, 1)
+    blk_tf = stt.tba_flops / max(stt.tba_launches, 1) / (blk_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": blk_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": blk_tf / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "k_gram / k_rows_mm (TBAS tubal Gram and block update, FP64 complex, n x s blocks)",
+                "note": ("peak derived: 4 FP64 FLOP/clk/SM x 152 SMs x 2070 MHz (nominal); 8 n s^2 FLOP per slice "
+                         "product. Share of the step: %.3f (timed with events around each product, which adds "
+                         "event overhead)" % (stt.tba_ms / (ms * a.steps)))}
     if rank == 0:
         line = {"metric": METRIC, "value": job_throughput(unknowns, world, ms), "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -609,7 +619,7 @@ def run_tbas(a, rank, world, local, dev):
                            "tol": 1e-10, "method": "TBAS", "cycles": r.info.cycles, "block_steps": r.info.iters,
                            "relres_true": r.info.relres_true,
                            "err_vs_xstar": float(torch.max(torch.abs(X - Xs)))},
-                "clocks": clk, "gpu_launches": int(stt.launches)}
+                "roofline": roofline, "clocks": clk, "gpu_launches": int(stt.launches)}
         print(json.dumps(line), flush=True)
     ctx.close()
 

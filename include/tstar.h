@@ -256,6 +256,9 @@ typedef struct {
   long long oz_launches;   /* emulated FP64 slice products (TS_ENGINE_OZAKI), digit split included */
   double oz_ms;
   double oz_flops;         /* their algorithmic FLOPs, counted as for gemm_flops */
+  long long tba_launches;  /* TBAS tubal Gram and block products (V^H W, W - V H), FP64 */
+  double tba_ms;
+  double tba_flops;        /* 8 n s^2 per complex slice product */
 } ts_stats;
 
 /* Enable (1) or disable (0) per-kernel event timing on ctx. */

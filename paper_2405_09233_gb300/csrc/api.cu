@@ -88,6 +88,10 @@ void KernelTimer::collect() {
       ++oz_launches;
       oz_ms += ms;
       oz_flops += r.work;
+    } else if (r.kind == 4) {
+      ++tba_launches;
+      tba_ms += ms;
+      tba_flops += r.work;
     } else {
       ++fft_launches;
       fft_ms += ms;
@@ -100,8 +104,8 @@ void KernelTimer::collect() {
 
 void KernelTimer::reset() {
   collect();
-  gemm_launches = fft_launches = lowp_launches = oz_launches = 0;
-  gemm_ms = gemm_flops = fft_ms = fft_bytes = lowp_ms = lowp_flops = oz_ms = oz_flops = 0;
+  gemm_launches = fft_launches = lowp_launches = oz_launches = tba_launches = 0;
+  gemm_ms = gemm_flops = fft_ms = fft_bytes = lowp_ms = lowp_flops = oz_ms = oz_flops = tba_ms = tba_flops = 0;
 }
 
 void KernelTimer::destroy() {
@@ -550,6 +554,9 @@ ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out) {
   out->oz_launches = t.oz_launches;
   out->oz_ms = t.oz_ms;
   out->oz_flops = t.oz_flops;
+  out->tba_launches = t.tba_launches;
+  out->tba_ms = t.tba_ms;
+  out->tba_flops = t.tba_flops;
   return TS_OK;
   TS_API_END(ctx)
 }

@@ -68,7 +68,7 @@ struct CountSuppress {
 // Event timing of selected kernels while a context has statistics enabled.
 struct TimedRegion {
   cudaEvent_t a, b;
-  int kind;        // 0 = FP64 GEMM, 1 = FFT, 2 = low-precision GEMM, 3 = emulated FP64 GEMM
+  int kind;        // 0 = FP64 GEMM, 1 = FFT, 2 = low-precision GEMM, 3 = emulated FP64 GEMM, 4 = TBAS block products
   double work;     // algorithmic FLOPs (GEMM) or bytes (FFT)
 };
 struct KernelTimer {
@@ -78,6 +78,8 @@ struct KernelTimer {
   long long gemm_launches = 0, fft_launches = 0, lowp_launches = 0, oz_launches = 0;
   double gemm_ms = 0, gemm_flops = 0, fft_ms = 0, fft_bytes = 0, lowp_ms = 0, lowp_flops = 0;
   double oz_ms = 0, oz_flops = 0;
+  long long tba_launches = 0;
+  double tba_ms = 0, tba_flops = 0;
   void begin(cudaStream_t st, int kind, double work);
   void end(cudaStream_t st);
   void collect();  // synchronise the recorded events and accumulate

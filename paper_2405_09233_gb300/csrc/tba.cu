@@ -127,51 +127,121 @@ __global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
 }
 
 // Partial Gram matrices G_k = V_k^H W_k over row chunks: partials[(k*chunks + c)*s*s + a + s*b].
+// Gauss's three-multiplication form: with u = conj(v), u w = (T1 - T3) + i (T1 + T2) where
+// T1 = sum w_re (u_re + u_im), T2 = sum u_re (w_im - w_re), T3 = sum u_im (w_re + w_im); the sums
+// of the factors are formed once per entry while staging, so a complex multiply-add costs three
+// DFMA.  Each thread owns a 4 x 4 block of G; 256 / (s/4)^2 row groups split a staged row batch
+// and are summed in shared memory at the end.
 __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, const double2* __restrict__ W, int n, int s,
                                               int rows_per_chunk, double2* __restrict__ partials) {
+  constexpr int RB = 16;                                 // rows staged per batch
   const int k = blockIdx.y, chunk = blockIdx.x, chunks = gridDim.x;
-  __shared__ double2 sv[16][kMaxS + 1], sw[16][kMaxS + 1];
+  // staged planes: u_re, u_im, u_re + u_im of V; w_re, w_im - w_re, w_re + w_im of W (one array, so
+  // the final reduction can reuse it as one contiguous buffer)
+  __shared__ double stage[6][RB][kMaxS];
+  double (*vp1)[kMaxS] = stage[0];
+  double (*vp2)[kMaxS] = stage[1];
+  double (*vp3)[kMaxS] = stage[2];
+  double (*wq1)[kMaxS] = stage[3];
+  double (*wq2)[kMaxS] = stage[4];
+  double (*wq3)[kMaxS] = stage[5];
   const long long ns = (long long)n * s;
   const double2* Vk = V + k * ns;
   const double2* Wk = W + k * ns;
-  const int ss = s * s;
-  constexpr int kPer = (kMaxS * kMaxS) / 256;
-  double2 acc[kPer];
+  const int sg = (s + 3) / 4;                            // 4-wide groups per side
+  const int tiles = sg * sg;
+  const int groups = blockDim.x / tiles;                 // row groups (>= 1 since s <= 64)
+  const int t = threadIdx.x % tiles, grp = threadIdx.x / tiles;
+  const int a0 = (t % sg) * 4, b0 = (t / sg) * 4;
+  const bool live = grp < groups;
+  double T1[4][4], T2[4][4], T3[4][4];
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) acc[q] = make_double2(0.0, 0.0);
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) T1[x][y] = T2[x][y] = T3[x][y] = 0.0;
   const int r_begin = chunk * rows_per_chunk;
   const int r_end = min(n, r_begin + rows_per_chunk);
-  for (int r0 = r_begin; r0 < r_end; r0 += 16) {
-    for (int e = threadIdx.x; e < 16 * s; e += blockDim.x) {
-      const int rr = e / s, cc = e % s;
+  for (int r0 = r_begin; r0 < r_end; r0 += RB) {
+    for (int e = threadIdx.x; e < RB * kMaxS; e += blockDim.x) {
+      const int rr = e / kMaxS, cc = e % kMaxS;
       const int r = r0 + rr;
       double2 v = make_double2(0.0, 0.0), w = v;
-      if (r < r_end) {
+      if (r < r_end && cc < s) {
         v = Vk[(long long)r * s + cc];
         w = Wk[(long long)r * s + cc];
       }
-      sv[rr][cc] = v;
-      sw[rr][cc] = w;
+      vp1[rr][cc] = v.x;
+      vp2[rr][cc] = -v.y;
+      vp3[rr][cc] = v.x - v.y;
+      wq1[rr][cc] = w.x;
+      wq2[rr][cc] = w.y - w.x;
+      wq3[rr][cc] = w.x + w.y;
     }
     __syncthreads();
+    if (live) {
+      for (int rr = grp; rr < RB; rr += groups) {
+        double p1[4], p2[4], p3[4], q1[4], q2[4], q3[4];
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int e = threadIdx.x + 256 * q;
-      if (e < ss) {
-        const int ai = e % s, bi = e / s;
-        double2 x = acc[q];
-#pragma unroll 4
-        for (int rr = 0; rr < 16; ++rr) x = cfmac(sv[rr][ai], sw[rr][bi], x);
-        acc[q] = x;
+        for (int x = 0; x < 4; ++x) {
+          const int a = min(a0 + x, kMaxS - 1), b = min(b0 + x, kMaxS - 1);
+          p1[x] = vp1[rr][a];
+          p2[x] = vp2[rr][a];
+          p3[x] = vp3[rr][a];
+          q1[x] = wq1[rr][b];
+          q2[x] = wq2[rr][b];
+          q3[x] = wq3[rr][b];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            T1[x][y] = fma(q1[y], p3[x], T1[x][y]);
+            T2[x][y] = fma(p1[x], q2[y], T2[x][y]);
+            T3[x][y] = fma(p2[x], q3[y], T3[x][y]);
+          }
       }
     }
     __syncthreads();
   }
+  const int ss = s * s;
+  double2* Pk = partials + ((long long)k * chunks + chunk) * ss;
+  if (groups == 1) {
+    if (live) {
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int e = threadIdx.x + 256 * q;
-    if (e < ss) partials[((long long)k * chunks + chunk) * ss + e] = acc[q];
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          if (a0 + x < s && b0 + y < s)
+            Pk[(a0 + x) + s * (b0 + y)] = make_double2(T1[x][y] - T3[x][y], T1[x][y] + T2[x][y]);
+    }
+    return;
   }
+  // Several row groups (then s <= 44, so 2 s^2 doubles fit in the staging arrays): sum them in a
+  // fixed order through shared memory.
+  double* red = &stage[0][0][0];
+  for (int g = 0; g < groups; ++g) {
+    if (live && grp == g) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int a = a0 + x, b = b0 + y;
+          if (a < s && b < s) {
+            const double re = T1[x][y] - T3[x][y], im = T1[x][y] + T2[x][y];
+            const int e = a + s * b;
+            if (g == 0) {
+              red[2 * e] = re;
+              red[2 * e + 1] = im;
+            } else {
+              red[2 * e] += re;
+              red[2 * e + 1] += im;
+            }
+          }
+        }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) Pk[e] = make_double2(red[2 * e], red[2 * e + 1]);
 }
 
 // out_k (column-major, leading dimension ldo) = sum over chunks of the partial Grams (fixed order).
@@ -190,51 +260,72 @@ __global__ void k_gram_reduce(const double2* __restrict__ partials, int chunks, 
   }
 }
 
-// Out_k = (accumulate ? Out_k : 0) + alpha * In_k M_k, row by row (in place allowed), M_k an
-// s x s column-major block with leading dimension ldm.
+// Out_k = (accumulate ? Out_k : 0) + alpha * In_k M_k (in place allowed), M_k an s x s column-major
+// block with leading dimension ldm.  kRowCols consecutive columns of one row per thread, all
+// threads of a row in one warp; Gauss's form with the planes M_re, M_im - M_re, M_re + M_im of M_k in
+// shared memory: Re = T1 - T3, Im = T1 + T2 with T1 = sum (a_re + a_im) m_re, T2 = sum a_re (m_im - m_re),
+// T3 = sum a_im (m_re + m_im), three DFMA per complex multiply-add.
+constexpr int kRowCols = 8;
 __global__ void __launch_bounds__(256) k_rows_mm(const double2* In, double2* Out, const double2* __restrict__ M,
                                                  long long sM, int ldm, int n, int s, double alpha, int accumulate) {
   const int k = blockIdx.y;
-  extern __shared__ double2 sm[];   // s x (s + 1), row-major copy of M_k
-  const int lds = s + 1;
+  extern __shared__ double smm[];   // three s x s planes, l-major: plane[l * s + j]
+  double* mr = smm;
+  double* md = smm + s * s;
+  double* mq = smm + 2 * s * s;
   const double2* Mk = M + (long long)k * sM;
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-    const int ai = e % s, bi = e / s;
-    sm[ai * lds + bi] = Mk[ai + (long long)ldm * bi];
+    const int l = e % s, j = e / s;
+    const double2 v = Mk[l + (long long)ldm * j];
+    mr[l * s + j] = v.x;
+    md[l * s + j] = v.y - v.x;
+    mq[l * s + j] = v.x + v.y;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // Threads per row: a power of two (1, 2, 4, 8), so a row never straddles two warps.
+  int tpr = 1;
+  while (tpr * kRowCols < s) tpr *= 2;
+  const int cpt = (s + tpr - 1) / tpr;                   // columns per thread (<= kRowCols)
+  const int rows_per_block = blockDim.x / tpr;
+  const int rloc = threadIdx.x / tpr, cg = threadIdx.x % tpr;
+  const int c0 = cg * cpt;
+  const int c1 = min(c0 + cpt, s);
   const long long ns = (long long)n * s;
-  for (int i = blockIdx.x * 8 + warp; i < n; i += gridDim.x * 8) {
+  const bool live_thread = rloc < rows_per_block;
+  for (int rbase = blockIdx.x * rows_per_block; rbase < n; rbase += gridDim.x * rows_per_block) {
+    const int i = rbase + rloc;
+    const bool live = live_thread && i < n;
+    double T1[kRowCols], T2[kRowCols], T3[kRowCols];
+#pragma unroll
+    for (int c = 0; c < kRowCols; ++c) T1[c] = T2[c] = T3[c] = 0.0;
     const long long ro = k * ns + (long long)i * s;
-    double2 x[kLanesT], y[kLanesT];
+    if (live) {
+      for (int l = 0; l < s; ++l) {
+        const double2 a = In[ro + l];
+        const double sa = a.x + a.y;
 #pragma unroll
-    for (int t = 0; t < kLanesT; ++t) {
-      const int j = lane + 32 * t;
-      x[t] = j < s ? In[ro + j] : make_double2(0.0, 0.0);
-      y[t] = make_double2(0.0, 0.0);
-    }
-    for (int ai = 0; ai < s; ++ai) {
-      double2 xa;
-      xa.x = __shfl_sync(0xffffffffu, x[ai >> 5].x, ai & 31);
-      xa.y = __shfl_sync(0xffffffffu, x[ai >> 5].y, ai & 31);
-#pragma unroll
-      for (int t = 0; t < kLanesT; ++t) {
-        const int j = lane + 32 * t;
-        if (j < s) y[t] = cfma(xa, sm[ai * lds + j], y[t]);
+        for (int c = 0; c < kRowCols; ++c) {
+          const int j = min(c0 + c, c1 - 1);
+          T1[c] = fma(sa, mr[l * s + j], T1[c]);
+          T2[c] = fma(a.x, md[l * s + j], T2[c]);
+          T3[c] = fma(a.y, mq[l * s + j], T3[c]);
+        }
       }
     }
+    __syncwarp();   // every thread of the row has read In before any writes Out (in place)
+    if (live) {
 #pragma unroll
-    for (int t = 0; t < kLanesT; ++t) {
-      const int j = lane + 32 * t;
-      if (j < s) {
-        double2 v = make_double2(alpha * y[t].x, alpha * y[t].y);
-        if (accumulate) {
-          const double2 o = Out[ro + j];
-          v.x += o.x;
-          v.y += o.y;
+      for (int c = 0; c < kRowCols; ++c) {
+        const int j = c0 + c;
+        if (j < c1) {
+          double2 v = make_double2(alpha * (T1[c] - T3[c]), alpha * (T1[c] + T2[c]));
+          if (accumulate) {
+            const double2 o = Out[ro + j];
+            v.x += o.x;
+            v.y += o.y;
+          }
+          Out[ro + j] = v;
         }
-        Out[ro + j] = v;
       }
     }
   }
@@ -351,6 +442,7 @@ struct TbaWork {
   double* P;                // kRedBlocks partials
   double* sc;               // scalars
   int* err;                 // error bits
+  KernelTimer* tm;          // per-kernel timing (kind 4: tubal Gram and block products)
 };
 
 }  // namespace
@@ -420,12 +512,16 @@ void rows_call(int mode, const ts_op* op, const double2* V, const double2* C, do
 
 void rows_mm(const double2* In, double2* Out, const double2* M, long long sM, int ldm, int n, int s, int K, double alpha,
              bool accumulate, cudaStream_t st) {
-  const int gx = std::max(1, std::min((n + 7) / 8, 2 * 152 * 4 / K));
-  const size_t smem = sizeof(double2) * (size_t)s * (s + 1);
+  TS_REQUIRE(s <= kMaxS, "rows_mm: block width above kMaxS");
+  int tpr = 1;
+  while (tpr * kRowCols < s) tpr *= 2;
+  const int rows_per_block = 256 / tpr;
+  const int gx = std::max(1, std::min((n + rows_per_block - 1) / rows_per_block, 4 * 152 * 4 / K));
+  const size_t smem = sizeof(double) * 3 * (size_t)s * s;
   static bool attr = false;
   if (!attr) {
     TS_CUDA(cudaFuncSetAttribute(k_rows_mm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(double2) * kMaxS * (kMaxS + 1))));
+                                 (int)(sizeof(double) * 3 * kMaxS * kMaxS)));
     attr = true;
   }
   k_rows_mm<<<dim3(gx, K), 256, smem, st>>>(In, Out, M, sM, ldm, n, s, alpha, accumulate ? 1 : 0);
@@ -433,13 +529,25 @@ void rows_mm(const double2* In, double2* Out, const double2* M, long long sM, in
   TS_CUDA(cudaGetLastError());
 }
 
+// Algorithmic FLOPs of one (n x s)^H (n x s) or (n x s)(s x s) complex product over K slices.
+double block_flops(const TbaWork& w) { return 8.0 * w.n * w.s * w.s * w.K; }
+
 void gram(const TbaWork& w, const double2* V, const double2* W, double2* out, long long sOut, int ldo, cudaStream_t st) {
+  w.tm->begin(st, 4, block_flops(w));
   k_gram<<<dim3(w.chunks, w.K), 256, 0, st>>>(V, W, w.n, w.s, w.rows_per_chunk, w.gram_part);
   count_launch();
   TS_CUDA(cudaGetLastError());
   k_gram_reduce<<<w.K, 256, 0, st>>>(w.gram_part, w.chunks, w.s, out, sOut, ldo);
   count_launch();
   TS_CUDA(cudaGetLastError());
+  w.tm->end(st);
+}
+
+void rows_mm_timed(const TbaWork& w, const double2* In, double2* Out, const double2* M, long long sM, int ldm,
+                   double alpha, bool accumulate, cudaStream_t st) {
+  w.tm->begin(st, 4, block_flops(w));
+  rows_mm(In, Out, M, sM, ldm, w.n, w.s, w.K, alpha, accumulate, st);
+  w.tm->end(st);
 }
 
 void triinv(const double2* R, double2* X, int s, int K, cudaStream_t st) {
@@ -457,11 +565,11 @@ bool tubal_qr(const TbaWork& w, double2* W, double2* Rout, long long sR, int ldr
   gram(w, W, W, w.G, ss, s, st);
   cholesky_small(w.G, w.R1, s, K, w.err, nullptr, st);
   triinv(w.R1, w.Rinv, s, K, st);
-  rows_mm(W, W, w.Rinv, ss, s, w.n, s, K, 1.0, false, st);
+  rows_mm_timed(w, W, W, w.Rinv, ss, s, 1.0, false, st);
   gram(w, W, W, w.G, ss, s, st);
   cholesky_small(w.G, w.R2, s, K, w.err, nullptr, st);
   triinv(w.R2, w.Rinv, s, K, st);
-  rows_mm(W, W, w.Rinv, ss, s, w.n, s, K, 1.0, false, st);
+  rows_mm_timed(w, W, W, w.Rinv, ss, s, 1.0, false, st);
   small_gemm(w.R2, ss, s, w.R1, ss, s, false, Rout, sR, ldr, s, s, s, K, false, st);   // R = R2 R1
   int e = 0;
   TS_CUDA(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -546,6 +654,7 @@ TbaWork tba_work(ts_ctx* ctx, const ts_op* op, int m) {
   w.P = (double*)get("tba_P", sizeof(double) * kRedBlocks);
   w.sc = (double*)get("tba_sc", sizeof(double) * 16);
   w.err = (int*)get("tba_err", sizeof(int) * 4);
+  w.tm = &ctx->timer;
   return w;
 }
 
@@ -605,7 +714,7 @@ ts_status tbas_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const t
         double2* Vi = w.V + (long long)i * blk;
         double2* Hij = w.Hm + (long long)i * s + (long long)N * j * s;         // block (i, j) of H_m
         gram(w, Vi, Wb, Hij, (long long)N * N, N, st);
-        rows_mm(Vi, Wb, Hij, (long long)N * N, N, n, s, K, -1.0, true, st);
+        rows_mm_timed(w, Vi, Wb, Hij, (long long)N * N, N, -1.0, true, st);
       }
       gram(w, Wb, Wb, w.G, ss, s, st);
       const double wn = std::sqrt(std::max(0.0, weighted_trace(w, w.G, ctx, st)));
