@@ -291,7 +291,8 @@ def main():
     if a.variants is None:
         a.variants = BATCHED_VARIANTS_DEFAULT_MARK if a.workload == "batched_256" else DENSE_VARIANTS
     if a.precision is None:
-        a.precision = "fp64" if a.workload in ("dense_n1024_s1024_p16", "sparse_lap128_s32_p8") else "mixed_fp32"
+        a.precision = ("fp64" if a.workload in ("dense_n24_s24_p4", "dense_n1024_s1024_p16", "sparse_lap128_s32_p8")
+                       else "mixed_fp32")
     if a.impl == "reference":
         run_reference(a)
         return
@@ -422,6 +423,32 @@ def main():
                               "err_vs_xstar": float(torch.max(torch.abs(X - Xs)) / torch.max(torch.abs(Xs)))}
         except Exception as e:  # report, do not hide
             variants[name] = {"error": str(e)}
+
+    if n * s * p <= 1 << 16:
+        # small problems are launch-latency bound: also time the graph-replayed form (the batched
+        # solver on this single instance: one CUDA graph per restart cycle, no per-step host sync)
+        try:
+            ops1 = [ctx.op_create_dense(Ad, Bd)]
+            for _ in range(3):
+                X.zero_()
+                ctx.batched_solve(ops1, [Cd], [X], restart=m, tol=1e-10, precision=a.precision)
+            torch.cuda.synchronize()
+            reps = 20
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                X.zero_()
+                stb, infb, _ = ctx.batched_solve(ops1, [Cd], [X], restart=m, tol=1e-10, precision=a.precision)
+            e1.record()
+            torch.cuda.synchronize()
+            tb = e0.elapsed_time(e1) / reps
+            variants["graph_replay"] = {"value": unknowns * world / (tb / 1e3), "ms_per_step": tb, "status": stb,
+                                        "inner_iters": infb[0].iters, "relres_true": infb[0].relres_true,
+                                        "us_per_inner_step": 1e3 * tb / max(infb[0].iters, 1)}
+            ops1[0].close()
+        except Exception as e:  # report, do not hide
+            variants["graph_replay"] = {"error": str(e)}
+        variants["us_per_inner_step"] = 1e3 * ms / max(last.info.iters, 1)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline and a.workload == "dense_n1024_s1024_p16":
