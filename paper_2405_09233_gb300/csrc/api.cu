@@ -285,6 +285,7 @@ void ts_destroy(ts_ctx* ctx) {
   ctx->ws.release_all();
   ctx->timer.destroy();
   if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
+  for (cudaStream_t q : ctx->side) cudaStreamDestroy(q);
   if (ctx->host_scalars) cudaFreeHost(ctx->host_scalars);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);

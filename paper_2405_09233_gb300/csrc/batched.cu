@@ -18,6 +18,7 @@
 #include <cmath>
 #include <numeric>
 #include <vector>
+#include <string>
 #include "internal.cuh"
 #include "oz.cuh"
 #include "apply.cuh"
@@ -613,10 +614,16 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   int* flags = (int*)get("b_flags", sizeof(int) * 2 * count);
   const long long stride = state_stride(m);
   double* state = (double*)get("b_state", sizeof(double) * (size_t)stride * count);
-  // Emulated FP64 residual products: digit planes of every operator and one scratch set sized for
-  // the largest instance, all made before anything is captured.
-  OzBuffers ozb;
+  // Emulated FP64 residual products: digit planes of every operator; the instances' products run
+  // on kOzBranches side streams (parallel branches of the captured graph, since one small
+  // instance fills few SMs), each branch with its own scratch set sized for the largest instance.
+  // Everything is made before anything is captured.
+  constexpr int kOzBranches = 8;
+  std::vector<OzBuffers> ozb(kOzBranches);
+  std::vector<int> order(count);
   int* tc_err = (int*)get("tc_err", sizeof(int) * 4);
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
   if (ozaki) {
     OzBufferSizes zmax;
     for (int i = 0; i < count; ++i) {
@@ -627,15 +634,40 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       zmax.K = std::max(zmax.K, z.K);
     }
     oz_preload();
-    ozb.xc_re = get("b_oz_xc_re", zmax.xc);
-    ozb.xc_im = get("b_oz_xc_im", zmax.xc);
-    ozb.xc_nim = get("b_oz_xc_nim", zmax.xc);
-    ozb.xr_re = get("b_oz_xr_re", zmax.xr);
-    ozb.xr_im = get("b_oz_xr_im", zmax.xr);
-    ozb.mx = (unsigned long long*)get("b_oz_mx", sizeof(unsigned long long) * zmax.K);
-    ozb.Ex = (int*)get("b_oz_Ex", sizeof(int) * zmax.K);
+    for (int q = 0; q < kOzBranches; ++q) {
+      const std::string sfx = "_" + std::to_string(q);
+      ozb[q].xc_re = get(("b_oz_xc_re" + sfx).c_str(), zmax.xc);
+      ozb[q].xc_im = get(("b_oz_xc_im" + sfx).c_str(), zmax.xc);
+      ozb[q].xc_nim = get(("b_oz_xc_nim" + sfx).c_str(), zmax.xc);
+      ozb[q].xr_re = get(("b_oz_xr_re" + sfx).c_str(), zmax.xr);
+      ozb[q].xr_im = get(("b_oz_xr_im" + sfx).c_str(), zmax.xr);
+      ozb[q].mx = (unsigned long long*)get(("b_oz_mx" + sfx).c_str(), sizeof(unsigned long long) * zmax.K);
+      ozb[q].Ex = (int*)get(("b_oz_Ex" + sfx).c_str(), sizeof(int) * zmax.K);
+    }
+    while ((int)ctx->side.size() < kOzBranches) {
+      cudaStream_t q;
+      TS_CUDA(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+      ctx->side.push_back(q);
+    }
+    TS_CUDA(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    join_ev.resize(kOzBranches);
+    for (auto& e : join_ev) TS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    // largest products first, dealt round-robin over the branches
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      auto cost = [&](int i) { return (double)ops[i]->K * ops[i]->n * ops[i]->s * (ops[i]->n + ops[i]->s); };
+      return cost(a) > cost(b);
+    });
     TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, user));
   }
+  struct EventGuard {
+    cudaEvent_t& f;
+    std::vector<cudaEvent_t>& j;
+    ~EventGuard() {
+      if (f) cudaEventDestroy(f);
+      for (auto e : j) cudaEventDestroy(e);
+    }
+  } ev_guard{fork_ev, join_ev};
 
   BDev d{};
   d.inst = d_inst;
@@ -677,8 +709,18 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       TS_CUDA(cudaGetLastError());
       return 1;
     }
-    for (int i = 0; i < count; ++i)
-      oz_products(ops[i], Xh64 + plan.inst[i].offS, Yh64 + plan.inst[i].offS, oz_digits, ozb, d.cyc + i, tc_err, s2);
+    // fork: every branch waits for the products' input; join: s2 waits for every branch
+    TS_CUDA(cudaEventRecord(fork_ev, s2));
+    for (int q = 0; q < kOzBranches; ++q) TS_CUDA(cudaStreamWaitEvent(ctx->side[q], fork_ev, 0));
+    for (int r = 0; r < count; ++r) {
+      const int i = order[r], q = r % kOzBranches;
+      oz_products(ops[i], Xh64 + plan.inst[i].offS, Yh64 + plan.inst[i].offS, oz_digits, ozb[q], d.cyc + i, tc_err,
+                  ctx->side[q]);
+    }
+    for (int q = 0; q < kOzBranches; ++q) {
+      TS_CUDA(cudaEventRecord(join_ev[q], ctx->side[q]));
+      TS_CUDA(cudaStreamWaitEvent(s2, join_ev[q], 0));
+    }
     return 5 * count;
   };
   k_b_normC<<<nbs, 256, 0, st>>>(d, P0);
