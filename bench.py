@@ -546,8 +546,8 @@ def run_batched(a, rank, world, local, dev):
     primary = prec + ("" if a.engine == "dfma" else "@" + a.engine)
     names = a.variants.split(",") if a.variants else []
     if a.variants == BATCHED_VARIANTS_DEFAULT_MARK:
-        names = ["fp64", "mixed_fp32", "fp64@ozaki", "mixed_fp32@ozaki"]
-    for name in [v for v in names if v and v != primary and v.partition("@")[0] in ("fp64", "mixed_fp32")]:
+        names = ["fp64", "mixed_fp32", "fp64@ozaki", "mixed_fp32@ozaki", "mixed_tf32x3@ozaki", "mixed_bf16@ozaki"]
+    for name in [v for v in names if v and v != primary]:
         vp, _, ve = name.partition("@")
         try:
             torch.cuda.synchronize()

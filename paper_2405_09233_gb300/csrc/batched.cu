@@ -21,6 +21,7 @@
 #include <string>
 #include "internal.cuh"
 #include "oz.cuh"
+#include "tc.cuh"
 #include "apply.cuh"
 #include "reduce.cuh"
 #include "fft_reg.cuh"
@@ -470,12 +471,13 @@ struct BatchPlan {
 // Records one restart cycle on `st`; returns the number of kernels it launched.
 // `residual_products(st)` issues the FP64 slice products of the true residual (Xh64 -> Yh64) and
 // returns how many kernels it launched.
-template <typename T, typename Real2, typename ResidualProducts>
+// `inner_products(st)` issues the inner operator's slice products (Xh -> Yh) likewise.
+template <typename T, typename Real2, typename InnerProducts, typename ResidualProducts>
 int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Real2* Yh, double* R, double2* Xh64,
-                 double2* Yh64, const int4* items, double* P0, double* P1, double* Pt,
+                 double2* Yh64, double* P0, double* P1, double* Pt, const InnerProducts& inner_products,
                  const ResidualProducts& residual_products, cudaStream_t st) {
   using Real = T;
-  const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size(), nit = (int)plan.items.size();
+  const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size();
   const int count = d.count, m = d.m;
   double* Pp[2] = {P0, P1};
   int kernels = 0;
@@ -484,7 +486,7 @@ int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Re
   kernels += 2;
   for (int j = 0; j < m; ++j) {
     k_b_rfft<Real, Real2, 0, 0><<<ntb, kTubes, 0, st>>>(d, basis(V, d.totN, j), Xh);
-    k_b_gemm<Real, 0><<<nit, kGemmNT, 0, st>>>(d, items, Xh, Yh);
+    kernels += inner_products(st);
     k_b_irfft<Real, Real2, 0><<<ntb, kTubes, 0, st>>>(d, Yh, W, nullptr);
     k_b_dot<T><<<nbs, 256, 0, st>>>(d, basis(V, d.totN, 0), W, Pp[0]);
     for (int i = 0; i <= j; ++i)
@@ -492,7 +494,7 @@ int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Re
                                       Pp[i & 1], Pp[(i + 1) & 1], i, j);
     k_b_givens<<<count, 256, 0, st>>>(d, Pp[(j + 1) & 1], j);
     k_b_scale_W<T><<<nbs, 256, 0, st>>>(d, W, basis(V, d.totN, j + 1));
-    kernels += 6 + j + 1;
+    kernels += 5 + j + 1;
   }
   k_b_solve_y<<<count, 32, 0, st>>>(d);
   k_b_axpy<T><<<nbs, 256, 0, st>>>(d, V);
@@ -514,8 +516,7 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   const ts_solve_opts& o = *opts;
   TS_REQUIRE(o.restart >= 1 && o.restart <= 128, "ts_batched_solve: restart must be in 1..128");
   TS_REQUIRE(o.tol > 0.0, "ts_batched_solve: tol must be positive");
-  TS_REQUIRE(o.precision == TS_FP64 || o.precision == TS_MIXED_FP32,
-             "ts_batched_solve: precision must be TS_FP64 or TS_MIXED_FP32");
+  TS_REQUIRE(o.precision >= TS_FP64 && o.precision <= TS_MIXED_TF32X3, "ts_batched_solve: unknown precision");
   TS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
   TS_REQUIRE(o.fp64_engine == TS_ENGINE_DFMA || o.fp64_engine == TS_ENGINE_OZAKI,
@@ -524,7 +525,9 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
              "ts_batched_solve: ozaki_digits must be 3..8");
   const bool ozaki = o.fp64_engine == TS_ENGINE_OZAKI;
   const int oz_digits = o.ozaki_digits == 0 ? 6 : o.ozaki_digits;
-  const bool mixed = o.precision == TS_MIXED_FP32;
+  const bool mixed = o.precision != TS_FP64;
+  // tensor-core inner products (BF16, TF32 or split TF32); FP32 CUDA cores for TS_MIXED_FP32
+  const bool tcin = mixed && o.precision != TS_MIXED_FP32;
   std::vector<ts_op*> ops(count);
   const int m = o.restart;
   BatchPlan plan;
@@ -543,7 +546,8 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
     b.Ah = op->Ah;
     b.Bh = op->Bh;
     if (mixed) {
-      ensure_f32_operator(op, user);
+      if (tcin) tc_prepare(op, o.precision, user);
+      else ensure_f32_operator(op, user);
       b.Ah32 = op->Ah32;
       b.Bh32 = op->Bh32;
     }
@@ -684,7 +688,10 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   d.sc = sc;
   d.state = state;
   d.stride = stride;
-  d.inner_tol = mixed ? (o.inner_tol > 0 ? o.inner_tol : 1e-6) : 0.0;
+  // default inner tolerances as in the single-instance solver (FP32 / split TF32, TF32, BF16)
+  const double inner_default =
+      o.precision == TS_MIXED_TF32 ? 1e-3 : (o.precision == TS_MIXED_BF16 ? 1e-2 : 1e-6);
+  d.inner_tol = mixed ? (o.inner_tol > 0 ? o.inner_tol : inner_default) : 0.0;
   d.mixed = mixed ? 1 : 0;
 
   // A private stream for the captured cycle, ordered after the caller's stream.
@@ -701,6 +708,76 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   TS_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice, st));
   TS_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * 16 * count, st));
   const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size(), nit = (int)plan.items.size();
+  // Tensor-core inner products: every instance's planar X copies, tensor maps and work lists,
+  // made before anything is captured.
+  const TcMaps* d_tcmaps = nullptr;
+  const BTcInst* d_tcinst = nullptr;
+  const BTcPlanes* d_tcplanes = nullptr;
+  const int4* d_titems = nullptr;
+  const int4* d_pitems = nullptr;
+  int n_titems = 0, n_pitems = 0;
+  if (tcin) {
+    std::vector<size_t> poff(count);
+    size_t ptot = 0;
+    for (int i = 0; i < count; ++i) {
+      poff[i] = ptot;
+      ptot += tc_batch_plane_bytes(ops[i]->n, ops[i]->s, ops[i]->K, o.precision);
+    }
+    char* planes = (char*)get("b_tc_planes", ptot);
+    std::vector<TcMaps> hmaps(count);
+    std::vector<BTcPlanes> hplanes(count);
+    std::vector<BTcInst> hinst(count);
+    std::vector<int4> titems, pitems;
+    for (int i = 0; i < count; ++i) {
+      const BInst& b = plan.inst[i];
+      tc_batch_instance(ops[i], o.precision, (const float2*)Xh + b.offS, planes + poff[i], &hplanes[i], &hmaps[i]);
+      hinst[i] = BTcInst{(float2*)Yh + b.offS, b.n, b.s, b.nyq};
+      for (int k = 0; k < b.K; ++k) {
+        for (int i0 = 0; i0 < b.n; i0 += 128)
+          for (int j0 = 0; j0 < b.s; j0 += kBatchTcBN) titems.push_back(make_int4(i, k, i0, j0));
+        for (int i0 = 0; i0 < b.n; i0 += 32)
+          for (int j0 = 0; j0 < b.s; j0 += 32) pitems.push_back(make_int4(i, k, i0, j0));
+      }
+    }
+    std::stable_sort(titems.begin(), titems.end(), [&](const int4& a, const int4& b) {
+      auto cost = [&](const int4& q) {
+        const BInst& x = plan.inst[q.x];
+        return ((q.y == 0 || q.y == x.nyq) ? 1.0 : 4.0) * (x.n + x.s);
+      };
+      return cost(a) > cost(b);
+    });
+    n_titems = (int)titems.size();
+    n_pitems = (int)pitems.size();
+    char* tab = (char*)get("b_tc_tables", sizeof(TcMaps) * count + sizeof(BTcPlanes) * count + sizeof(BTcInst) * count +
+                                              sizeof(int4) * (titems.size() + pitems.size()) + 1024);
+    TcMaps* m_ = (TcMaps*)tab;                                    // 2 KB each: 64-byte aligned tensor maps
+    BTcPlanes* p_ = (BTcPlanes*)(m_ + count);
+    BTcInst* in_ = (BTcInst*)(((uintptr_t)(p_ + count) + 15) & ~(uintptr_t)15);
+    int4* ti_ = (int4*)(((uintptr_t)(in_ + count) + 15) & ~(uintptr_t)15);
+    int4* pi_ = ti_ + titems.size();
+    TS_CUDA(cudaMemcpy(m_, hmaps.data(), sizeof(TcMaps) * count, cudaMemcpyHostToDevice));
+    TS_CUDA(cudaMemcpy(p_, hplanes.data(), sizeof(BTcPlanes) * count, cudaMemcpyHostToDevice));
+    TS_CUDA(cudaMemcpy(in_, hinst.data(), sizeof(BTcInst) * count, cudaMemcpyHostToDevice));
+    TS_CUDA(cudaMemcpy(ti_, titems.data(), sizeof(int4) * titems.size(), cudaMemcpyHostToDevice));
+    TS_CUDA(cudaMemcpy(pi_, pitems.data(), sizeof(int4) * pitems.size(), cudaMemcpyHostToDevice));
+    d_tcmaps = m_;
+    d_tcplanes = p_;
+    d_tcinst = in_;
+    d_titems = ti_;
+    d_pitems = pi_;
+    if (!ozaki) TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, user));
+  }
+  auto inner_products = [&](cudaStream_t s2) -> int {
+    if (tcin) {
+      tc_batch_products(o.precision, d_tcplanes, d_pitems, n_pitems, d_tcmaps, d_tcinst, d.act, d_titems, n_titems,
+                        tc_err, s2);
+      return 2;
+    }
+    if (mixed) k_b_gemm<float, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, (float2*)Xh, (float2*)Yh);
+    else k_b_gemm<double, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, (double2*)Xh, (double2*)Yh);
+    TS_CUDA(cudaGetLastError());
+    return 1;
+  };
   // FP64 slice products of a true residual: the (instance, slice, tile) work list on CUDA cores, or
   // one emulated-FP64 product per instance (each gated by the instance's cycle flag).
   auto residual_products = [&](cudaStream_t s2) -> int {
@@ -759,15 +836,16 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       if (!exec) {
         if (mixed) preload_cycle_kernels<float, float2>();
         else preload_cycle_kernels<double, double2>();
+        if (tcin) tc_batch_preload(o.precision);
         cudaGraph_t graph;
         CountSuppress no_count;   // the replays below count the recorded kernels
         TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         if (mixed)
           graph_kernels = record_cycle<float, float2>(d, plan, (float*)V, (float*)W, (float2*)Xh, (float2*)Yh, R, Xh64,
-                                                      Yh64, d_items, P0, P1, Pt, residual_products, st);
+                                                      Yh64, P0, P1, Pt, inner_products, residual_products, st);
         else
           graph_kernels = record_cycle<double, double2>(d, plan, (double*)V, (double*)W, (double2*)Xh, (double2*)Yh, R,
-                                                        Xh64, Yh64, d_items, P0, P1, Pt, residual_products, st);
+                                                        Xh64, Yh64, P0, P1, Pt, inner_products, residual_products, st);
         TS_CUDA(cudaStreamEndCapture(st, &graph));
         TS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         TS_CUDA(cudaGraphDestroy(graph));
@@ -787,7 +865,7 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   float ms = 0.f;
   TS_CUDA(cudaEventElapsedTime(&ms, t0, t1));
   if (exec) TS_CUDA(cudaGraphExecDestroy(exec));
-  if (ozaki) {
+  if (ozaki || tcin) {
     int e = 0;
     TS_CUDA(cudaMemcpy(&e, tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e != 0) {

@@ -39,14 +39,7 @@ constexpr int kTileM = 128;
 constexpr int kStageBytesMax = 200 * 1024;
 using namespace tcg;
 
-struct TcMaps {
-  CUtensorMap a_re, a_im;      // A_k planes          [K][n][ldn]
-  CUtensorMap xc_re, xc_im;    // X_k column-major    [K][s][ldn]
-  CUtensorMap xr_re, xr_im;    // X_k row-major       [K][n][lds]
-  CUtensorMap b_re, b_im;      // B_k column-major    [K][s][lds]
-  // split TF32 (PARTS = 3): the low parts v - tf32(v) of the same planes
-  CUtensorMap a_re_lo, a_im_lo, xc_re_lo, xc_im_lo, xr_re_lo, xr_im_lo, b_re_lo, b_im_lo;
-};
+
 
 template <int BN, int ESZ>
 struct TcCfg {
@@ -63,9 +56,11 @@ struct TcCfg {
 // PARTS = 1: one product per operand pair.  PARTS = 3 (split TF32): every l-block is visited three
 // times, hi*hi, hi*lo and lo*hi, accumulating in the same FP32 TMEM accumulators (FP32-level
 // accuracy on the TF32 tensor pipe).
+// One 128 x BN output tile (rows i0.., columns j0..) of slice k; Y holds K slices of column-major
+// n x s float2 matrices.  `maps` may live in kernel parameter space or in global memory.
 template <int BN, int ESZ, int PARTS>
-__global__ void __launch_bounds__(192, 1)
-    k_tc_sylv(const __grid_constant__ TcMaps maps, float2* __restrict__ Y, int n, int s, int nyq, int* err) {
+__device__ __forceinline__ void tc_sylv_tile(const TcMaps& maps, float2* __restrict__ Y, int n, int s, int nyq,
+                                             int k, int i0, int j0, int* err) {
   using Cfg = TcCfg<BN, ESZ>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -77,7 +72,6 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t bar_acc = smem_u32(bars + 2 * Cfg::kStages);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j0 = blockIdx.x * BN, i0 = blockIdx.y * kTileM, k = blockIdx.z;
   const bool real = (k == 0) || (k == nyq);
   const int it1 = (n + Cfg::kElemsK - 1) / Cfg::kElemsK;      // stages of the A_k X_k product
   const int it2 = (s + Cfg::kElemsK - 1) / Cfg::kElemsK;      // stages of the X_k B_k product
@@ -207,9 +201,12 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
-// ------------------------------------------------------------------------------------------------
-// Operand preparation
-// ------------------------------------------------------------------------------------------------
+template <int BN, int ESZ, int PARTS>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_sylv(const __grid_constant__ TcMaps maps, float2* __restrict__ Y, int n, int s, int nyq, int* err) {
+  tc_sylv_tile<BN, ESZ, PARTS>(maps, Y, n, s, nyq, blockIdx.z, blockIdx.y * kTileM, blockIdx.x * BN, err);
+}
+
 template <typename OpT> __device__ __forceinline__ OpT to_op(float v);
 template <> __device__ __forceinline__ __nv_bfloat16 to_op<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 template <> __device__ __forceinline__ float to_op<float>(float v) {
@@ -221,6 +218,69 @@ template <> __device__ __forceinline__ float to_op<float>(float v) {
 // Low part of the split-TF32 representation: tf32(v - tf32(v)).
 __device__ __forceinline__ float tf32_lo(float v) { return to_op<float>(v - to_op<float>(v)); }
 
+// ------------------------------------------------------------------------------------------------
+// Batched form: one CTA per (instance, slice, tile) work item; every instance has its own tensor
+// maps (a table in global memory, written from the host before the launch) and output.
+// ------------------------------------------------------------------------------------------------
+template <int BN, int ESZ, int PARTS>
+__global__ void __launch_bounds__(192, 1)
+    k_b_tc(const TcMaps* __restrict__ maps, const BTcInst* __restrict__ inst, const int* __restrict__ active,
+           const int4* __restrict__ items, int* err) {
+  const int4 it = items[blockIdx.x];
+  if (!active[it.x]) return;   // instance not in the current inner cycle (uniform over the CTA)
+  const BTcInst& b = inst[it.x];
+  tc_sylv_tile<BN, ESZ, PARTS>(maps[it.x], b.Y, b.n, b.s, b.nyq, it.y, it.z, it.w, err);
+}
+
+// Planar copies of the FP32 spectra of a batch: per (instance, slice, 32 x 32 tile) work item,
+// column-major planes [k][j][ldn] and row-major planes [k][i][lds] of Re and Im (TF32 or BF16), and
+// with SPLIT the low parts v - tf32(v) of both.
+template <typename OpT, bool SPLIT>
+__global__ void __launch_bounds__(256) k_b_planes(const BTcPlanes* __restrict__ pl, const int* __restrict__ active,
+                                                  const int4* __restrict__ items) {
+  __shared__ float tr[32][33], ti[32][33];
+  const int4 it = items[blockIdx.x];
+  if (!active[it.x]) return;
+  const BTcPlanes& P = pl[it.x];
+  const int k = it.y, i0 = it.z, j0 = it.w;
+  const float2* Xk = P.Xh + (long long)k * P.n * P.s;
+  const long long oc = (long long)k * P.s * P.ldn, orow = (long long)k * P.n * P.lds;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {     // column j0 + q, rows i0 + tx
+    const int i = i0 + threadIdx.x, j = j0 + q;
+    float2 v = make_float2(0.f, 0.f);
+    if (i < P.n && j < P.s) v = Xk[(long long)j * P.n + i];
+    if (k == 0 || k == P.nyq) v.y = 0.f;
+    tr[q][threadIdx.x] = v.x;
+    ti[q][threadIdx.x] = v.y;
+    if (i < P.n && j < P.s) {
+      const long long o = oc + (long long)j * P.ldn + i;
+      static_cast<OpT*>(P.xc_re)[o] = to_op<OpT>(v.x);
+      static_cast<OpT*>(P.xc_im)[o] = to_op<OpT>(v.y);
+      if (SPLIT) {
+        static_cast<float*>(P.xc_re_lo)[o] = tf32_lo(v.x);
+        static_cast<float*>(P.xc_im_lo)[o] = tf32_lo(v.y);
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {     // row i0 + q, columns j0 + tx
+    const int i = i0 + q, j = j0 + threadIdx.x;
+    if (i < P.n && j < P.s) {
+      const long long o = orow + (long long)i * P.lds + j;
+      const float vr = tr[threadIdx.x][q], vi = ti[threadIdx.x][q];
+      static_cast<OpT*>(P.xr_re)[o] = to_op<OpT>(vr);
+      static_cast<OpT*>(P.xr_im)[o] = to_op<OpT>(vi);
+      if (SPLIT) {
+        static_cast<float*>(P.xr_re_lo)[o] = tf32_lo(vr);
+        static_cast<float*>(P.xr_im_lo)[o] = tf32_lo(vi);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Operand preparation
+// ------------------------------------------------------------------------------------------------
 // A_k (double2, column-major n x n) -> planes [k][i][ld] (row-major), via a 32 x 32 tile transpose.
 // With lo planes given, re/im receive tf32(v) and re_lo/im_lo receive tf32(v - tf32(v)).
 template <typename OpT>
@@ -571,6 +631,104 @@ void tc_apply(ts_ctx* ctx, ts_op* op, int precision, const float* X, float2* Yh,
   if (t.split) launch_by_bn<3>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
   else launch_by_bn<1>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
   tm.end(st);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Batched tensor-core products (host side)
+// ------------------------------------------------------------------------------------------------
+namespace {
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+template <typename OpT, int ESZ, int PARTS, bool SPLIT>
+void batch_preload_t() {
+  using Cfg = TcCfg<kBatchTcBN, ESZ>;
+  cudaFuncAttributes fa;
+  TS_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_b_planes<OpT, SPLIT>));
+  TS_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_b_tc<kBatchTcBN, ESZ, PARTS>));
+  TS_CUDA(cudaFuncSetAttribute(k_b_tc<kBatchTcBN, ESZ, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+}
+
+template <typename OpT, int ESZ, int PARTS, bool SPLIT>
+void batch_products_t(const BTcPlanes* planes, const int4* pitems, int npitems, const TcMaps* maps,
+                      const BTcInst* inst, const int* active, const int4* items, int nitems, int* err,
+                      cudaStream_t st) {
+  using Cfg = TcCfg<kBatchTcBN, ESZ>;
+  k_b_planes<OpT, SPLIT><<<npitems, dim3(32, 8), 0, st>>>(planes, active, pitems);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+  k_b_tc<kBatchTcBN, ESZ, PARTS><<<nitems, 192, Cfg::kSmem, st>>>(maps, inst, active, items, err);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+}  // namespace
+
+size_t tc_batch_plane_bytes(int n, int s, int K, int precision) {
+  const int esz = precision == TS_MIXED_BF16 ? 2 : 4;
+  const bool split = precision == TS_MIXED_TF32X3;
+  const size_t nx = align256((size_t)K * s * round_up(n, 64) * esz);
+  const size_t nr = align256((size_t)K * n * round_up(s, 64) * esz);
+  return (split ? 4 : 2) * (nx + nr);
+}
+
+void tc_batch_instance(ts_op* op, int precision, const float2* Xh, void* base, BTcPlanes* pl, TcMaps* maps) {
+  TS_REQUIRE(op->tc && op->tc_prec == precision, "tc_batch_instance: operator planes not prepared");
+  const TcOperands& t = *op->tc;
+  const int n = op->n, s = op->s, K = op->K, esz = t.esz;
+  const size_t nx = align256((size_t)K * s * t.ldn * esz), nr = align256((size_t)K * n * t.lds * esz);
+  char* b = static_cast<char*>(base);
+  *pl = BTcPlanes{};
+  pl->Xh = Xh;
+  pl->xc_re = b; b += nx;
+  pl->xc_im = b; b += nx;
+  pl->xr_re = b; b += nr;
+  pl->xr_im = b; b += nr;
+  if (t.split) {
+    pl->xc_re_lo = b; b += nx;
+    pl->xc_im_lo = b; b += nx;
+    pl->xr_re_lo = b; b += nr;
+    pl->xr_im_lo = b; b += nr;
+  }
+  pl->n = n; pl->s = s; pl->ldn = t.ldn; pl->lds = t.lds; pl->nyq = nyquist_index(op->p);
+  const int bn = kBatchTcBN;
+  make_map(&maps->a_re, t.a_re, esz, t.ldn, n, n, K, kTileM);
+  make_map(&maps->a_im, t.a_im, esz, t.ldn, n, n, K, kTileM);
+  make_map(&maps->xc_re, pl->xc_re, esz, t.ldn, n, s, K, bn);
+  make_map(&maps->xc_im, pl->xc_im, esz, t.ldn, n, s, K, bn);
+  make_map(&maps->xr_re, pl->xr_re, esz, t.lds, s, n, K, kTileM);
+  make_map(&maps->xr_im, pl->xr_im, esz, t.lds, s, n, K, kTileM);
+  make_map(&maps->b_re, t.b_re, esz, t.lds, s, s, K, bn);
+  make_map(&maps->b_im, t.b_im, esz, t.lds, s, s, K, bn);
+  if (t.split) {
+    make_map(&maps->a_re_lo, t.a_re_lo, esz, t.ldn, n, n, K, kTileM);
+    make_map(&maps->a_im_lo, t.a_im_lo, esz, t.ldn, n, n, K, kTileM);
+    make_map(&maps->xc_re_lo, pl->xc_re_lo, esz, t.ldn, n, s, K, bn);
+    make_map(&maps->xc_im_lo, pl->xc_im_lo, esz, t.ldn, n, s, K, bn);
+    make_map(&maps->xr_re_lo, pl->xr_re_lo, esz, t.lds, s, n, K, kTileM);
+    make_map(&maps->xr_im_lo, pl->xr_im_lo, esz, t.lds, s, n, K, kTileM);
+    make_map(&maps->b_re_lo, t.b_re_lo, esz, t.lds, s, s, K, bn);
+    make_map(&maps->b_im_lo, t.b_im_lo, esz, t.lds, s, s, K, bn);
+  } else {
+    maps->a_re_lo = maps->a_re; maps->a_im_lo = maps->a_im; maps->xc_re_lo = maps->xc_re;
+    maps->xc_im_lo = maps->xc_im; maps->xr_re_lo = maps->xr_re; maps->xr_im_lo = maps->xr_im;
+    maps->b_re_lo = maps->b_re; maps->b_im_lo = maps->b_im;
+  }
+}
+
+void tc_batch_preload(int precision) {
+  if (precision == TS_MIXED_BF16) batch_preload_t<__nv_bfloat16, 2, 1, false>();
+  else if (precision == TS_MIXED_TF32) batch_preload_t<float, 4, 1, false>();
+  else batch_preload_t<float, 4, 3, true>();
+}
+
+void tc_batch_products(int precision, const BTcPlanes* planes, const int4* pitems, int npitems, const TcMaps* maps,
+                       const BTcInst* inst, const int* active, const int4* items, int nitems, int* err,
+                       cudaStream_t st) {
+  if (precision == TS_MIXED_BF16)
+    batch_products_t<__nv_bfloat16, 2, 1, false>(planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
+  else if (precision == TS_MIXED_TF32)
+    batch_products_t<float, 4, 1, false>(planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
+  else
+    batch_products_t<float, 4, 3, true>(planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
 }
 
 double gemm_flops_tc(int n, int s, int K, int nyq) {

@@ -126,6 +126,22 @@ def test_batched_ozaki_residuals(ctx, prec):
         op.close()
 
 
+@pytest.mark.parametrize("prec,engine", [("mixed_tf32x3", "dfma"), ("mixed_tf32x3", "ozaki"), ("mixed_bf16", "ozaki"),
+                                         ("mixed_tf32", "dfma")])
+def test_batched_tensor_core_inner(ctx, prec, engine):
+    """Inner products of the batch on the tcgen05 tensor cores (per-instance tensor maps, one work
+    list over all instances): every instance reaches 1e-10 (checked by the oracle)."""
+    probs, ops, Cs, Xs, Cn = make_batch(ctx, SHAPES + [(300, 128, 16), (129, 65, 8)], 500)
+    st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, precision=prec, engine=engine)
+    assert st == 0 and all(v == 0 for v in sts), sts
+    for pr, C, X, info in zip(probs, Cn, Xs, infos):
+        Xh = from_dev(X)
+        assert tp.norm(C - kr.sylv_apply(pr.A, pr.B, Xh)) <= 1e-10 * tp.norm(C)
+        assert info.outer >= 1 and info.applies_low > 0
+    for op in ops:
+        op.close()
+
+
 def test_batched_256_instance_workload(ctx):
     """256 instances, n log-uniform in [64, 1024], s uniform in [16, 128], p in {4, 8, 16}, FP32 inner
     tGMRES(20) with FP64 refinement; every instance's true residual (library FP64 operator) <= 1e-10."""
