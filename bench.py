@@ -51,6 +51,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
                     help="solve: full solves (the benchmark); apply: operator applications only (kernel runs)")
+    ap.add_argument("--count", type=int, default=None, help="instances of the batched workload (default 256)")
     ap.add_argument("--n", type=int)
     ap.add_argument("--s", type=int)
     ap.add_argument("--p", type=int)
@@ -479,7 +480,7 @@ def run_batched(a, rank, world, local, dev):
     p in {4, 8, 16}), one step = one ts_batched_solve of all of them (operator setup included)."""
     import torch
     from paper_2405_09233_gb300 import Context, inputs
-    count = inputs.WORKLOADS["batched_256"]["count"]
+    count = a.count if a.count else inputs.WORKLOADS["batched_256"]["count"]
     specs = inputs.batched_specs(count, seed=4 + rank)
     ctx = Context(local)
     host = []
@@ -564,7 +565,8 @@ def run_batched(a, rank, world, local, dev):
         line = {"metric": METRIC, "value": unknowns * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64" if prec != "fp64" else "f64", "data": "synthetic",
-                "config": {"workload": "batched_256", "instances": count, "unknowns": unknowns, "restart": 20,
+                "config": {"workload": "batched_256" if count == 256 else "batched_%d" % count, "instances": count,
+                           "unknowns": unknowns, "restart": 20,
                            "tol": 1e-10, "precision": prec, "fp64_engine": a.engine, "method": "batched tGMRES",
                            "max_relres_true": relres, "max_err_vs_xstar": err,
                            "l2": "inputs larger than L2 (5 GB basis)"},
