@@ -24,6 +24,7 @@
 #include "tc.cuh"
 #include "apply.cuh"
 #include "reduce.cuh"
+#include "pack.cuh"
 #include "fft_reg.cuh"
 #include "gemm_tile.cuh"
 
@@ -110,6 +111,9 @@ __global__ void __launch_bounds__(256) k_b_scale_R(BDev d, const double* __restr
   for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) V0[e] = (T)(R[e] * sc);
 }
 
+// Instance offsets are multiples of 4 and chunks are kChunk long, so a block's range starts
+// 16-byte aligned: the streaming kernels below move packs of 4 and finish a ragged instance tail
+// element by element.
 template <typename T>
 __global__ void __launch_bounds__(256) k_b_dot(BDev d, const T* __restrict__ x, const T* __restrict__ y,
                                                double* __restrict__ P) {
@@ -118,8 +122,17 @@ __global__ void __launch_bounds__(256) k_b_dot(BDev d, const T* __restrict__ x, 
   const BInst& in = d.inst[i];
   const long long e0 = in.offN + d.nb_off[blockIdx.x];
   const long long e1 = min(in.offN + in.N, e0 + kChunk);
+  const long long n4 = (e1 - e0) / 4, p0 = e0 / 4;
   double acc = 0.0;
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc += (double)x[e] * (double)y[e];
+#pragma unroll 4
+  for (long long q = threadIdx.x; q < n4; q += blockDim.x) {
+    T a[4], c[4];
+    ld4(x, p0 + q, a);
+    ld4(y, p0 + q, c);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) acc += (double)a[t] * (double)c[t];
+  }
+  for (long long e = e0 + 4 * n4 + threadIdx.x; e < e1; e += blockDim.x) acc += (double)x[e] * (double)y[e];
   const double t = block_sum(acc);
   if (threadIdx.x == 0) P[blockIdx.x] = t;
 }
@@ -151,8 +164,22 @@ __global__ void __launch_bounds__(256) k_b_mgs(BDev d, T* __restrict__ W, const 
   const T hT = (T)h;
   const long long e0 = in.offN + d.nb_off[blockIdx.x];
   const long long e1 = min(in.offN + in.N, e0 + kChunk);
+  const long long n4 = (e1 - e0) / 4, p0 = e0 / 4;
   double acc = 0.0;
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+#pragma unroll 4
+  for (long long q = threadIdx.x; q < n4; q += blockDim.x) {
+    T w[4], v[4], o[4];
+    ld4(W, p0 + q, w);
+    ld4(Vi, p0 + q, v);
+    if (Vn) ld4(Vn, p0 + q, o);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      w[t] = w[t] - hT * v[t];
+      acc += (double)(Vn ? o[t] : w[t]) * (double)w[t];
+    }
+    st4(W, p0 + q, w);
+  }
+  for (long long e = e0 + 4 * n4 + threadIdx.x; e < e1; e += blockDim.x) {
     const T w = W[e] - hT * Vi[e];
     W[e] = w;
     acc += (double)(Vn ? Vn[e] : w) * (double)w;
@@ -554,9 +581,9 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
     b.n = op->n; b.s = op->s; b.p = op->p; b.K = op->K; b.nyq = nyquist_index(op->p);
     b.T = (long long)b.n * b.s;
     b.N = b.T * b.p;
-    b.offN = plan.totN;
+    b.offN = (plan.totN + 3) / 4 * 4;   // 16-byte aligned start: the streaming kernels move packs of 4
     b.offS = plan.totS;
-    plan.totN += b.N;
+    plan.totN = b.offN + b.N;
     plan.totS += (long long)b.K * b.T;
     b.tol = u.tol > 0 ? u.tol : o.tol;
     b.nb0 = (int)plan.nb_inst.size();
@@ -575,6 +602,7 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       for (int i0 = 0; i0 < b.n; i0 += kGemmBM)
         for (int j0 = 0; j0 < b.s; j0 += kGemmBN) plan.items.push_back(make_int4(i, k, i0, j0));
   }
+  plan.totN = (plan.totN + 3) / 4 * 4;   // every basis vector V + j totN starts 16-byte aligned
   // Largest tiles first (reduction length n + s; real slices are a quarter of the work).
   std::stable_sort(plan.items.begin(), plan.items.end(), [&](const int4& a, const int4& b) {
     auto cost = [&](const int4& q) {
