@@ -250,8 +250,17 @@ __global__ void __launch_bounds__(256) k_shifted_lu(const double2* __restrict__ 
   }
 }
 
-// One CTA per slice: Z[:, j] for j = 0..s-1 in order, using the factors of k_shifted_lu.
-// G (N x s) is the transformed right-hand side F Q; T the Schur factor of B_k.
+// One CTA per slice: Z[:, j] for j = 0..s-1 in order, using the factors of k_shifted_lu.  Both
+// triangular solves are blocked by kHsB columns so that the long dependent chains run inside one
+// warp on shared memory:
+//   forward  for each block of columns: stage the pivots and, for bands up to kHsBandStage wide,
+//            the L band (rows c+1 .. c+bw), then one warp applies the row interchanges and
+//            eliminations of the block in order (the same operations, in the same order, as the
+//            unblocked solve); wider bands (t-Bartels-Stewart, bw = n - 1) are read from global memory;
+//   backward for each block from the last: stage the diagonal kHsB x kHsB block of U, one warp
+//            solves it, then all threads subtract the block's columns from the rows above (GEMV).
+constexpr int kHsB = 32;
+constexpr int kHsBandStage = 64;
 __global__ void __launch_bounds__(256) k_hs_solve(const double2* __restrict__ LU, const int* __restrict__ piv,
                                                   const double2* __restrict__ G, const double2* __restrict__ T,
                                                   double2* __restrict__ Z, int N, int bw, int s) {
@@ -259,7 +268,13 @@ __global__ void __launch_bounds__(256) k_hs_solve(const double2* __restrict__ LU
   const double2* Gk = G + (long long)k * N * s;
   const double2* Tk = T + (long long)k * s * s;
   double2* Zk = Z + (long long)k * N * s;
-  extern __shared__ double2 rhs[];  // N entries
+  extern __shared__ double2 hs_smem[];
+  double2* rhs = hs_smem;                       // N
+  const bool stage = bw <= kHsBandStage;
+  double2* Lb = rhs + N;                        // kHsB x bw  (band of the block's L columns), if staged
+  double2* Ub = Lb + (stage ? (size_t)kHsB * bw : 0);   // kHsB x (kHsB + 1)
+  __shared__ int spv[kHsB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int j = 0; j < s; ++j) {
     const double2* M = LU + ((long long)k * s + j) * N * N;
     const int* pv = piv + ((long long)k * s + j) * N;
@@ -269,27 +284,58 @@ __global__ void __launch_bounds__(256) k_hs_solve(const double2* __restrict__ LU
       rhs[r] = v;
     }
     __syncthreads();
-    for (int c = 0; c < N; ++c) {        // forward: row interchanges and unit lower factor
-      const int p = pv[c];
-      if (p != c) {
-        if (threadIdx.x == 0) {
-          const double2 t0 = rhs[c];
-          rhs[c] = rhs[p];
-          rhs[p] = t0;
-        }
-        __syncthreads();
+    // forward: row interchanges and the unit lower factor
+    for (int c0 = 0; c0 < N; c0 += kHsB) {
+      const int nb = min(kHsB, N - c0);
+      for (int e = threadIdx.x; stage && e < nb * bw; e += blockDim.x) {
+        const int cc = e / bw, t = e % bw, c = c0 + cc, r = c + 1 + t;
+        Lb[e] = r < N ? M[r + (long long)N * c] : make_double2(0.0, 0.0);
       }
-      const int rmax = (c + bw < N - 1) ? c + bw : N - 1;
-      const double2 rc = rhs[c];
-      for (int r = c + 1 + (int)threadIdx.x; r <= rmax; r += blockDim.x)
-        rhs[r] = csub(rhs[r], cmul(M[r + (long long)N * c], rc));
+      for (int cc = threadIdx.x; cc < nb; cc += blockDim.x) spv[cc] = pv[c0 + cc];
+      __syncthreads();
+      if (warp == 0) {
+        for (int cc = 0; cc < nb; ++cc) {
+          const int c = c0 + cc, p = spv[cc];
+          if (p != c && lane == 0) {
+            const double2 t0 = rhs[c];
+            rhs[c] = rhs[p];
+            rhs[p] = t0;
+          }
+          __syncwarp();
+          const double2 rc = rhs[c];
+          const int nr = min(bw, N - 1 - c);
+          for (int t = lane; t < nr; t += 32) {
+            const double2 l = stage ? Lb[cc * bw + t] : M[(c + 1 + t) + (long long)N * c];
+            rhs[c + 1 + t] = csub(rhs[c + 1 + t], cmul(l, rc));
+          }
+          __syncwarp();
+        }
+      }
       __syncthreads();
     }
-    for (int c = N - 1; c >= 0; --c) {   // backward: upper factor
-      if (threadIdx.x == 0) rhs[c] = cdiv(rhs[c], M[c + (long long)N * c]);
+    // backward: the upper factor, by blocks from the last
+    for (int c1 = N; c1 > 0; c1 -= kHsB) {
+      const int c0 = max(0, c1 - kHsB), nb = c1 - c0;
+      for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int rr = e % nb, cc = e / nb;
+        Ub[rr + (kHsB + 1) * cc] = M[(c0 + rr) + (long long)N * (c0 + cc)];
+      }
       __syncthreads();
-      const double2 zc = rhs[c];
-      for (int r = threadIdx.x; r < c; r += blockDim.x) rhs[r] = csub(rhs[r], cmul(M[r + (long long)N * c], zc));
+      if (warp == 0) {
+        for (int cc = nb - 1; cc >= 0; --cc) {
+          if (lane == 0) rhs[c0 + cc] = cdiv(rhs[c0 + cc], Ub[cc + (kHsB + 1) * cc]);
+          __syncwarp();
+          const double2 zc = rhs[c0 + cc];
+          if (lane < cc) rhs[c0 + lane] = csub(rhs[c0 + lane], cmul(Ub[lane + (kHsB + 1) * cc], zc));
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < c0; r += blockDim.x) {
+        double2 v = rhs[r];
+        for (int cc = 0; cc < nb; ++cc) v = csub(v, cmul(M[r + (long long)N * (c0 + cc)], rhs[c0 + cc]));
+        rhs[r] = v;
+      }
       __syncthreads();
     }
     for (int r = threadIdx.x; r < N; r += blockDim.x) Zk[r + (long long)N * j] = rhs[r];
@@ -370,7 +416,8 @@ void shifted_lu(const double2* H, long long sH, const double2* T, double2* LU, i
 
 void hs_solve(const double2* LU, const int* piv, const double2* G, const double2* T, double2* Z, int N, int bw, int s,
               int K, cudaStream_t st) {
-  const size_t smem = sizeof(double2) * (size_t)N;
+  const size_t band = bw <= kHsBandStage ? (size_t)kHsB * bw : 0;
+  const size_t smem = sizeof(double2) * ((size_t)N + band + (size_t)kHsB * (kHsB + 1));
   TS_REQUIRE(smem <= 200 * 1024, "projected system too large");
   if (smem > 48 * 1024) TS_CUDA(cudaFuncSetAttribute(k_hs_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_hs_solve<<<K, 256, smem, st>>>(LU, piv, G, T, Z, N, bw, s);
