@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
 // Gauss's three-multiplication form: with u = conj(v), u w = (T1 - T3) + i (T1 + T2) where
 // T1 = sum w_re (u_re + u_im), T2 = sum u_re (w_im - w_re), T3 = sum u_im (w_re + w_im); the sums
 // of the factors are formed once per entry while staging, so a complex multiply-add costs three
-// DFMA.  Each thread owns a 4 x 4 block of G; 256 / (s/4)^2 row groups split a staged row batch
-// and are summed in shared memory at the end.
+// DFMA.  Each thread owns a 4 x 4 block of G; min(256 / (s/4)^2, 16) row groups split a staged row
+// batch and are summed in shared memory at the end.
 __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, const double2* __restrict__ W, int n, int s,
                                               int rows_per_chunk, double2* __restrict__ partials) {
   constexpr int RB = 16;                                 // rows staged per batch
@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, con
   const double2* Wk = W + k * ns;
   const int sg = (s + 3) / 4;                            // 4-wide groups per side
   const int tiles = sg * sg;
-  const int groups = blockDim.x / tiles;                 // row groups (>= 1 since s <= 64)
+  // Row groups (>= 1 since s <= 64), at most one per staged row: more would sit idle and lengthen
+  // the serial group reduction below, whose FP64 adds are expensive on this part.
+  const int groups = min((int)blockDim.x / tiles, RB);
   const int t = threadIdx.x % tiles, grp = threadIdx.x / tiles;
   const int a0 = (t % sg) * 4, b0 = (t / sg) * 4;
   const bool live = grp < groups;
