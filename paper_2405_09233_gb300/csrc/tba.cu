@@ -58,65 +58,79 @@ struct RowsArgs {
 
 // MODE 0: Out = A_k V_k.  MODE 1: Out = A_k V_k - V_k B_k.  MODE 2: Out = C_k - (A_k V_k - V_k B_k)
 // and partials of the Parseval-weighted squared norm.
-template <int MODE>
+// Lane layout: LT = 1 (s <= 32): the warp's lanes form groups of sp = s rounded up to a power of two,
+// one group per row and one lane per column, so a warp works on 32 / sp rows at once (an idle
+// FP64 lane costs as much as a busy one); LT = 2 (32 < s <= 64): one row per warp, two columns per
+// lane.
+template <int MODE, int LT>
 __global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
   const int k = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int sp = 32;
+  if (LT == 1)
+    while (sp / 2 >= a.s && sp > 1) sp /= 2;
+  const int rpw = 32 / sp;                       // rows per warp
+  const int sub = lane / sp, jl = lane % sp;
   const long long ns = (long long)a.n * a.s;
   const double2* Vk = a.V + k * ns;
   double local = 0.0;
-  for (int i = blockIdx.x * 8 + warp; i < a.n; i += gridDim.x * 8) {
-    double2 acc[kLanesT];
+  const int rows_step = gridDim.x * 8 * rpw;
+  for (int ibase = (blockIdx.x * 8 + warp) * rpw; ibase < a.n; ibase += rows_step) {
+    const int i = ibase + sub;
+    const bool live = i < a.n;
+    double2 acc[LT];
 #pragma unroll
-    for (int t = 0; t < kLanesT; ++t) acc[t] = make_double2(0.0, 0.0);
-    if (a.rowptr) {
-      const double2* vk = a.vals + (long long)k * a.nnz;
-      for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-        const double2 av = vk[q];
-        const double2* vr = Vk + (long long)a.col[q] * a.s;
+    for (int t = 0; t < LT; ++t) acc[t] = make_double2(0.0, 0.0);
+    if (live) {
+      if (a.rowptr) {
+        const double2* vk = a.vals + (long long)k * a.nnz;
+        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+          const double2 av = vk[q];
+          const double2* vr = Vk + (long long)a.col[q] * a.s;
 #pragma unroll
-        for (int t = 0; t < kLanesT; ++t) {
-          const int j = lane + 32 * t;
-          if (j < a.s) acc[t] = cfma(av, vr[j], acc[t]);
+          for (int t = 0; t < LT; ++t) {
+            const int j = jl + 32 * t;
+            if (j < a.s) acc[t] = cfma(av, vr[j], acc[t]);
+          }
+        }
+      } else {
+        const double2* Ak = a.Ad + (long long)k * a.n * a.n;
+        for (int l = 0; l < a.n; ++l) {
+          const double2 av = Ak[(long long)l * a.n + i];
+          const double2* vr = Vk + (long long)l * a.s;
+#pragma unroll
+          for (int t = 0; t < LT; ++t) {
+            const int j = jl + 32 * t;
+            if (j < a.s) acc[t] = cfma(av, vr[j], acc[t]);
+          }
         }
       }
-    } else {
-      const double2* Ak = a.Ad + (long long)k * a.n * a.n;
-      for (int l = 0; l < a.n; ++l) {
-        const double2 av = Ak[(long long)l * a.n + i];
-        const double2* vr = Vk + (long long)l * a.s;
+      if (MODE >= 1) {
+        const double2* Bk = a.Brow + (long long)k * a.s * a.s;
+        const double2* xr = Vk + (long long)i * a.s;
+        for (int l = 0; l < a.s; ++l) {
+          const double2 xv = xr[l];
+          const double2 nx = make_double2(-xv.x, -xv.y);
 #pragma unroll
-        for (int t = 0; t < kLanesT; ++t) {
-          const int j = lane + 32 * t;
-          if (j < a.s) acc[t] = cfma(av, vr[j], acc[t]);
+          for (int t = 0; t < LT; ++t) {
+            const int j = jl + 32 * t;
+            if (j < a.s) acc[t] = cfma(nx, Bk[(long long)l * a.s + j], acc[t]);
+          }
         }
       }
-    }
-    if (MODE >= 1) {
-      const double2* Bk = a.Brow + (long long)k * a.s * a.s;
-      const double2* xr = Vk + (long long)i * a.s;
-      for (int l = 0; l < a.s; ++l) {
-        const double2 xv = xr[l];
-        const double2 nx = make_double2(-xv.x, -xv.y);
 #pragma unroll
-        for (int t = 0; t < kLanesT; ++t) {
-          const int j = lane + 32 * t;
-          if (j < a.s) acc[t] = cfma(nx, Bk[(long long)l * a.s + j], acc[t]);
+      for (int t = 0; t < LT; ++t) {
+        const int j = jl + 32 * t;
+        if (j < a.s) {
+          double2 v = acc[t];
+          const long long o = k * ns + (long long)i * a.s + j;
+          if (MODE == 2) {
+            const double2 c = a.C[o];
+            v = make_double2(c.x - v.x, c.y - v.y);
+            local += v.x * v.x + v.y * v.y;
+          }
+          a.Out[o] = v;
         }
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < kLanesT; ++t) {
-      const int j = lane + 32 * t;
-      if (j < a.s) {
-        double2 v = acc[t];
-        const long long o = k * ns + (long long)i * a.s + j;
-        if (MODE == 2) {
-          const double2 c = a.C[o];
-          v = make_double2(c.x - v.x, c.y - v.y);
-          local += v.x * v.x + v.y * v.y;
-        }
-        a.Out[o] = v;
       }
     }
   }
@@ -499,15 +513,25 @@ void rows_call(int mode, const ts_op* op, const double2* V, const double2* C, do
   a.s = s;
   a.K = K;
   a.p = p;
+  const bool wide = s > 32;
+  int sp = 32;
+  while (!wide && sp / 2 >= s && sp > 1) sp /= 2;
+  const int rows_per_block = 8 * (32 / sp);
+#define TS_SYLV_ROWS(M, GX)                                                           \
+  do {                                                                                \
+    if (wide) k_sylv_rows<M, 2><<<dim3((GX), K), 256, 0, st>>>(a);                    \
+    else k_sylv_rows<M, 1><<<dim3((GX), K), 256, 0, st>>>(a);                         \
+  } while (0)
   if (mode == 2) {
     const int gx = kRedBlocks / K;
     TS_CUDA(cudaMemsetAsync(partials, 0, sizeof(double) * kRedBlocks, st));
-    k_sylv_rows<2><<<dim3(gx, K), 256, 0, st>>>(a);
+    TS_SYLV_ROWS(2, gx);
   } else {
-    const int gx = std::max(1, std::min((n + 7) / 8, 2 * 152 * 4 / K));
-    if (mode == 0) k_sylv_rows<0><<<dim3(gx, K), 256, 0, st>>>(a);
-    else k_sylv_rows<1><<<dim3(gx, K), 256, 0, st>>>(a);
+    const int gx = std::max(1, std::min((n + rows_per_block - 1) / rows_per_block, 2 * 152 * 4 / K));
+    if (mode == 0) TS_SYLV_ROWS(0, gx);
+    else TS_SYLV_ROWS(1, gx);
   }
+#undef TS_SYLV_ROWS
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
