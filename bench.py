@@ -606,10 +606,10 @@ def run_tbas(a, rank, world, local, dev):
     X = torch.zeros_like(Cd)
     m = 10
 
-    def step():
+    def step(precision=a.precision):
         op = ctx.op_create_csr(n, p, rowptr, cols, vals, Bd)
         X.zero_()
-        r = ctx.tba_solve(op, Cd, X, restart=m, tol=1e-10)
+        r = ctx.tba_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision)
         op.close()
         return r
 
@@ -640,15 +640,34 @@ def run_tbas(a, rank, world, local, dev):
                 "note": ("peak derived: 4 FP64 FLOP/clk/SM x 152 SMs x 2070 MHz (nominal); 8 n s^2 FLOP per slice "
                          "product. Share of the step: %.3f (timed with events around each product, which adds "
                          "event overhead)" % (stt.tba_ms / (ms * a.steps)))}
+    variants = {}
+    other = "mixed_fp32" if a.precision == "fp64" else "fp64"
+    if a.variants != "":
+        try:
+            step(other)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record()
+            rv = step(other)
+            v1.record()
+            torch.cuda.synchronize()
+            tv = v0.elapsed_time(v1)
+            variants[other] = {"value": unknowns * world / (tv / 1e3), "ms_per_step": tv, "status": rv.status_name,
+                               "cycles": rv.info.cycles, "relres_true": rv.info.relres_true,
+                               "err_vs_xstar": float(torch.max(torch.abs(X - Xs)))}
+        except Exception as e:  # report, do not hide
+            variants[other] = {"error": str(e)}
     if rank == 0:
         line = {"metric": METRIC, "value": job_throughput(unknowns, world, ms), "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32+f64",
+                "data": "synthetic",
                 "config": {"workload": "sparse_lap128_s32_p8", "n": n, "s": s_blk, "p": p, "restart": m,
+                           "precision": a.precision,
                            "tol": 1e-10, "method": "TBAS", "cycles": r.info.cycles, "block_steps": r.info.iters,
                            "relres_true": r.info.relres_true,
                            "err_vs_xstar": float(torch.max(torch.abs(X - Xs)))},
-                "roofline": roofline, "clocks": clk, "gpu_launches": int(stt.launches)}
+                "roofline": roofline, "clocks": clk, "gpu_launches": int(stt.launches), "variants": variants}
         print(json.dumps(line), flush=True)
     ctx.close()
 

@@ -222,7 +222,10 @@ ts_status ts_tstar_noalloc(const double* A, int n1, int n2, const double* B, int
  * solved by t-Bartels-Stewart; X = X0 + V_m*Y; restart until ||C - M(X)||_F <= tol ||C||_F.
  * opts->restart is m (block steps per cycle, m*s <= 12000), opts->max_restarts the cycle budget;
  * history receives the Proposition 5.2 estimate per cycle and true_history the true residual.
- * FP64 only; s <= 64.  Arguments and results otherwise as ts_tgmres_solve. */
+ * opts->precision TS_FP64, or TS_MIXED_FP32: the block Krylov basis, the SpMM and the block
+ * products of every cycle run in FP32 while the Gram results, H_m, the projected solve, X and the
+ * true residual of every restart stay FP64, so the restarts are steps of iterative refinement
+ * (info->outer = cycles).  s <= 64.  Arguments and results otherwise as ts_tgmres_solve. */
 ts_status ts_tba_solve(ts_ctx* ctx, const ts_op* op, const double* C, double* X, const ts_solve_opts* opts,
                        ts_solve_info* info, ts_stream stream);
 

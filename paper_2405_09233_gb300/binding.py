@@ -265,10 +265,11 @@ class Context:
         return self._solve(lib().ts_tgmres_solve, "ts_tgmres_solve", op, C, X, restart, tol, max_restarts,
                            precision, inner_tol, max_outer, history_cap, engine, ozaki_digits)
 
-    def tba_solve(self, op, C, X, restart=10, tol=1e-10, max_restarts=100, history_cap=4096):
-        """Restarted TBAS(m) (FP64); X holds X0 on entry and the solution on return."""
+    def tba_solve(self, op, C, X, restart=10, tol=1e-10, max_restarts=100, history_cap=4096, precision="fp64"):
+        """Restarted TBAS(m); X holds X0 on entry and the solution on return.  precision "fp64", or
+        "mixed_fp32" (FP32 block Krylov cycles, FP64 true residuals and solution)."""
         return self._solve(lib().ts_tba_solve, "ts_tba_solve", op, C, X, restart, tol, max_restarts,
-                           "fp64", 0.0, 0, history_cap)
+                           precision, 0.0, 0, history_cap)
 
     def batched_solve(self, ops, Cs, Xs, tols=None, restart=20, tol=1e-10, max_restarts=200, precision="fp64",
                       inner_tol=0.0, max_outer=0, engine="dfma", ozaki_digits=0):

@@ -18,12 +18,14 @@
 #include <algorithm>
 #include <cmath>
 #include <vector>
+#include <type_traits>
 #include "internal.cuh"
 #include "apply.cuh"
 #include "reduce.cuh"
 #include "tba.cuh"
 
 namespace ts {
+void ensure_f32_operator(ts_op* op, cudaStream_t st);  // lowprec.cu
 namespace {
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -35,6 +37,16 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a
 __device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {  // conj(a)*b + c
   return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
 }
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // a*b + c, FP32
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+template <typename C2> struct RealOf;
+template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<float2> { using T = float; };
+__device__ __forceinline__ double2 to_c2(double2 v, double2*) { return v; }
+__device__ __forceinline__ float2 to_c2(double2 v, float2*) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ double2 widen(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 widen(double2 v) { return v; }
 __device__ __forceinline__ double slice_weight(int k, int p) {
   return (k == 0 || (p % 2 == 0 && k == p / 2)) ? 1.0 : 2.0;
 }
@@ -42,19 +54,22 @@ __device__ __forceinline__ double slice_weight(int k, int p) {
 constexpr int kMaxS = 64;           // block width supported by the row kernels
 constexpr int kLanesT = kMaxS / 32;
 
-struct RowsArgs {
+// C2: double2 (FP64), or float2 for the FP32 inner cycle of mixed-precision TBAS (MODE 0 only).
+template <typename C2>
+struct RowsArgsT {
   const int* rowptr;      // sparse pattern (nullptr: dense A_k column-major in Ad)
   const int* col;
-  const double2* vals;    // K x nnz
-  const double2* Ad;      // K x n x n column-major (dense operator)
+  const C2* vals;         // K x nnz
+  const C2* Ad;           // K x n x n column-major (dense operator)
   long long nnz;
-  const double2* V;       // K x n x s row-major
+  const C2* V;            // K x n x s row-major
   const double2* Brow;    // K x s x s row-major (B_k)
   const double2* C;       // K x n x s row-major (residual mode)
-  double2* Out;           // K x n x s row-major
+  C2* Out;                // K x n x s row-major
   double* partials;       // residual mode: one per block
   int n, s, K, p;
 };
+using RowsArgs = RowsArgsT<double2>;
 
 // MODE 0: Out = A_k V_k.  MODE 1: Out = A_k V_k - V_k B_k.  MODE 2: Out = C_k - (A_k V_k - V_k B_k)
 // and partials of the Parseval-weighted squared norm.
@@ -62,8 +77,9 @@ struct RowsArgs {
 // one group per row and one lane per column, so a warp works on 32 / sp rows at once (an idle
 // FP64 lane costs as much as a busy one); LT = 2 (32 < s <= 64): one row per warp, two columns per
 // lane.
-template <int MODE, int LT>
-__global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
+template <int MODE, int LT, typename C2>
+__global__ void __launch_bounds__(256) k_sylv_rows(RowsArgsT<C2> a) {
+  static_assert(MODE == 0 || sizeof(C2) == 16, "the operator with B_k and the residual run in FP64");
   const int k = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int sp = 32;
@@ -72,21 +88,21 @@ __global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
   const int rpw = 32 / sp;                       // rows per warp
   const int sub = lane / sp, jl = lane % sp;
   const long long ns = (long long)a.n * a.s;
-  const double2* Vk = a.V + k * ns;
+  const C2* Vk = a.V + k * ns;
   double local = 0.0;
   const int rows_step = gridDim.x * 8 * rpw;
   for (int ibase = (blockIdx.x * 8 + warp) * rpw; ibase < a.n; ibase += rows_step) {
     const int i = ibase + sub;
     const bool live = i < a.n;
-    double2 acc[LT];
+    C2 acc[LT];
 #pragma unroll
-    for (int t = 0; t < LT; ++t) acc[t] = make_double2(0.0, 0.0);
+    for (int t = 0; t < LT; ++t) acc[t] = C2{0, 0};
     if (live) {
       if (a.rowptr) {
-        const double2* vk = a.vals + (long long)k * a.nnz;
+        const C2* vk = a.vals + (long long)k * a.nnz;
         for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-          const double2 av = vk[q];
-          const double2* vr = Vk + (long long)a.col[q] * a.s;
+          const C2 av = vk[q];
+          const C2* vr = Vk + (long long)a.col[q] * a.s;
 #pragma unroll
           for (int t = 0; t < LT; ++t) {
             const int j = jl + 32 * t;
@@ -94,10 +110,10 @@ __global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
           }
         }
       } else {
-        const double2* Ak = a.Ad + (long long)k * a.n * a.n;
+        const C2* Ak = a.Ad + (long long)k * a.n * a.n;
         for (int l = 0; l < a.n; ++l) {
-          const double2 av = Ak[(long long)l * a.n + i];
-          const double2* vr = Vk + (long long)l * a.s;
+          const C2 av = Ak[(long long)l * a.n + i];
+          const C2* vr = Vk + (long long)l * a.s;
 #pragma unroll
           for (int t = 0; t < LT; ++t) {
             const int j = jl + 32 * t;
@@ -105,7 +121,7 @@ __global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
           }
         }
       }
-      if (MODE >= 1) {
+      if constexpr (MODE >= 1) {
         const double2* Bk = a.Brow + (long long)k * a.s * a.s;
         const double2* xr = Vk + (long long)i * a.s;
         for (int l = 0; l < a.s; ++l) {
@@ -122,9 +138,9 @@ __global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
       for (int t = 0; t < LT; ++t) {
         const int j = jl + 32 * t;
         if (j < a.s) {
-          double2 v = acc[t];
+          C2 v = acc[t];
           const long long o = k * ns + (long long)i * a.s + j;
-          if (MODE == 2) {
+          if constexpr (MODE == 2) {
             const double2 c = a.C[o];
             v = make_double2(c.x - v.x, c.y - v.y);
             local += v.x * v.x + v.y * v.y;
@@ -146,22 +162,26 @@ __global__ void __launch_bounds__(256) k_sylv_rows(RowsArgs a) {
 // of the factors are formed once per entry while staging, so a complex multiply-add costs three
 // DFMA.  Each thread owns a 4 x 4 block of G; min(256 / (s/4)^2, 16) row groups split a staged row
 // batch and are summed in shared memory at the end.
-__global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, const double2* __restrict__ W, int n, int s,
+// C2 = float2: FP32 inputs and accumulation (the inner cycle of mixed-precision TBAS); the partial
+// Grams are written in FP64 either way.
+template <typename C2>
+__global__ void __launch_bounds__(256) k_gram(const C2* __restrict__ V, const C2* __restrict__ W, int n, int s,
                                               int rows_per_chunk, double2* __restrict__ partials) {
+  using R = typename RealOf<C2>::T;
   constexpr int RB = 16;                                 // rows staged per batch
   const int k = blockIdx.y, chunk = blockIdx.x, chunks = gridDim.x;
   // staged planes: u_re, u_im, u_re + u_im of V; w_re, w_im - w_re, w_re + w_im of W (one array, so
   // the final reduction can reuse it as one contiguous buffer)
-  __shared__ double stage[6][RB][kMaxS];
-  double (*vp1)[kMaxS] = stage[0];
-  double (*vp2)[kMaxS] = stage[1];
-  double (*vp3)[kMaxS] = stage[2];
-  double (*wq1)[kMaxS] = stage[3];
-  double (*wq2)[kMaxS] = stage[4];
-  double (*wq3)[kMaxS] = stage[5];
+  __shared__ R stage[6][RB][kMaxS];
+  R (*vp1)[kMaxS] = stage[0];
+  R (*vp2)[kMaxS] = stage[1];
+  R (*vp3)[kMaxS] = stage[2];
+  R (*wq1)[kMaxS] = stage[3];
+  R (*wq2)[kMaxS] = stage[4];
+  R (*wq3)[kMaxS] = stage[5];
   const long long ns = (long long)n * s;
-  const double2* Vk = V + k * ns;
-  const double2* Wk = W + k * ns;
+  const C2* Vk = V + k * ns;
+  const C2* Wk = W + k * ns;
   const int sg = (s + 3) / 4;                            // 4-wide groups per side
   const int tiles = sg * sg;
   // Row groups (>= 1 since s <= 64), at most one per staged row: more would sit idle and lengthen
@@ -170,18 +190,18 @@ __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, con
   const int t = threadIdx.x % tiles, grp = threadIdx.x / tiles;
   const int a0 = (t % sg) * 4, b0 = (t / sg) * 4;
   const bool live = grp < groups;
-  double T1[4][4], T2[4][4], T3[4][4];
+  R T1[4][4], T2[4][4], T3[4][4];
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) T1[x][y] = T2[x][y] = T3[x][y] = 0.0;
+    for (int y = 0; y < 4; ++y) T1[x][y] = T2[x][y] = T3[x][y] = R(0);
   const int r_begin = chunk * rows_per_chunk;
   const int r_end = min(n, r_begin + rows_per_chunk);
   for (int r0 = r_begin; r0 < r_end; r0 += RB) {
     for (int e = threadIdx.x; e < RB * kMaxS; e += blockDim.x) {
       const int rr = e / kMaxS, cc = e % kMaxS;
       const int r = r0 + rr;
-      double2 v = make_double2(0.0, 0.0), w = v;
+      C2 v{0, 0}, w{0, 0};
       if (r < r_end && cc < s) {
         v = Vk[(long long)r * s + cc];
         w = Wk[(long long)r * s + cc];
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, con
     __syncthreads();
     if (live) {
       for (int rr = grp; rr < RB; rr += groups) {
-        double p1[4], p2[4], p3[4], q1[4], q2[4], q3[4];
+        R p1[4], p2[4], p3[4], q1[4], q2[4], q3[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
           const int a = min(a0 + x, kMaxS - 1), b = min(b0 + x, kMaxS - 1);
@@ -228,13 +248,14 @@ __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, con
 #pragma unroll
         for (int y = 0; y < 4; ++y)
           if (a0 + x < s && b0 + y < s)
-            Pk[(a0 + x) + s * (b0 + y)] = make_double2(T1[x][y] - T3[x][y], T1[x][y] + T2[x][y]);
+            Pk[(a0 + x) + s * (b0 + y)] =
+                make_double2((double)T1[x][y] - (double)T3[x][y], (double)T1[x][y] + (double)T2[x][y]);
     }
     return;
   }
   // Several row groups (then s <= 44, so 2 s^2 doubles fit in the staging arrays): sum them in a
   // fixed order through shared memory.
-  double* red = &stage[0][0][0];
+  R* red = &stage[0][0][0];
   for (int g = 0; g < groups; ++g) {
     if (live && grp == g) {
 #pragma unroll
@@ -243,7 +264,7 @@ __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, con
         for (int y = 0; y < 4; ++y) {
           const int a = a0 + x, b = b0 + y;
           if (a < s && b < s) {
-            const double re = T1[x][y] - T3[x][y], im = T1[x][y] + T2[x][y];
+            const R re = T1[x][y] - T3[x][y], im = T1[x][y] + T2[x][y];
             const int e = a + s * b;
             if (g == 0) {
               red[2 * e] = re;
@@ -257,7 +278,7 @@ __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ V, con
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < ss; e += blockDim.x) Pk[e] = make_double2(red[2 * e], red[2 * e + 1]);
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) Pk[e] = make_double2((double)red[2 * e], (double)red[2 * e + 1]);
 }
 
 // out_k (column-major, leading dimension ldo) = sum over chunks of the partial Grams (fixed order).
@@ -281,21 +302,25 @@ __global__ void k_gram_reduce(const double2* __restrict__ partials, int chunks, 
 // threads of a row in one warp; Gauss's form with the planes M_re, M_im - M_re, M_re + M_im of M_k in
 // shared memory: Re = T1 - T3, Im = T1 + T2 with T1 = sum (a_re + a_im) m_re, T2 = sum a_re (m_im - m_re),
 // T3 = sum a_im (m_re + m_im), three DFMA per complex multiply-add.
+// Cin = float2 (the FP32 basis of mixed-precision TBAS): products in FP32; Cout may be double2 (the
+// FP64 solution update X += V Y) or float2.
 constexpr int kRowCols = 8;
-__global__ void __launch_bounds__(256) k_rows_mm(const double2* In, double2* Out, const double2* __restrict__ M,
+template <typename Cin, typename Cout>
+__global__ void __launch_bounds__(256) k_rows_mm(const Cin* In, Cout* Out, const double2* __restrict__ M,
                                                  long long sM, int ldm, int n, int s, double alpha, int accumulate) {
+  using R = typename RealOf<Cin>::T;
   const int k = blockIdx.y;
-  extern __shared__ double smm[];   // three s x s planes, l-major: plane[l * s + j]
-  double* mr = smm;
-  double* md = smm + s * s;
-  double* mq = smm + 2 * s * s;
+  extern __shared__ unsigned char smm_raw[];   // three s x s planes, l-major: plane[l * s + j]
+  R* mr = reinterpret_cast<R*>(smm_raw);
+  R* md = mr + s * s;
+  R* mq = mr + 2 * s * s;
   const double2* Mk = M + (long long)k * sM;
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
     const int l = e % s, j = e / s;
     const double2 v = Mk[l + (long long)ldm * j];
-    mr[l * s + j] = v.x;
-    md[l * s + j] = v.y - v.x;
-    mq[l * s + j] = v.x + v.y;
+    mr[l * s + j] = (R)v.x;
+    md[l * s + j] = (R)(v.y - v.x);
+    mq[l * s + j] = (R)(v.x + v.y);
   }
   __syncthreads();
   // Threads per row: a power of two (1, 2, 4, 8), so a row never straddles two warps.
@@ -311,14 +336,14 @@ __global__ void __launch_bounds__(256) k_rows_mm(const double2* In, double2* Out
   for (int rbase = blockIdx.x * rows_per_block; rbase < n; rbase += gridDim.x * rows_per_block) {
     const int i = rbase + rloc;
     const bool live = live_thread && i < n;
-    double T1[kRowCols], T2[kRowCols], T3[kRowCols];
+    R T1[kRowCols], T2[kRowCols], T3[kRowCols];
 #pragma unroll
-    for (int c = 0; c < kRowCols; ++c) T1[c] = T2[c] = T3[c] = 0.0;
+    for (int c = 0; c < kRowCols; ++c) T1[c] = T2[c] = T3[c] = R(0);
     const long long ro = k * ns + (long long)i * s;
     if (live) {
       for (int l = 0; l < s; ++l) {
-        const double2 a = In[ro + l];
-        const double sa = a.x + a.y;
+        const Cin a = In[ro + l];
+        const R sa = a.x + a.y;
 #pragma unroll
         for (int c = 0; c < kRowCols; ++c) {
           const int j = min(c0 + c, c1 - 1);
@@ -334,13 +359,13 @@ __global__ void __launch_bounds__(256) k_rows_mm(const double2* In, double2* Out
       for (int c = 0; c < kRowCols; ++c) {
         const int j = c0 + c;
         if (j < c1) {
-          double2 v = make_double2(alpha * (T1[c] - T3[c]), alpha * (T1[c] + T2[c]));
+          double2 v = make_double2(alpha * (double)(T1[c] - T3[c]), alpha * (double)(T1[c] + T2[c]));
           if (accumulate) {
-            const double2 o = Out[ro + j];
+            const double2 o = widen(Out[ro + j]);
             v.x += o.x;
             v.y += o.y;
           }
-          Out[ro + j] = v;
+          Out[ro + j] = to_c2(v, (Cout*)nullptr);
         }
       }
     }
@@ -467,8 +492,10 @@ void SparseOp::release() {
   cudaFree(rowptr);
   cudaFree(col);
   cudaFree(vals);
+  cudaFree(vals32);
   rowptr = col = nullptr;
   vals = nullptr;
+  vals32 = nullptr;
 }
 
 void ensure_b_schur(ts_ctx* ctx, ts_op* op, cudaStream_t st) {
@@ -492,6 +519,42 @@ void ensure_b_schur(ts_ctx* ctx, ts_op* op, cudaStream_t st) {
 }
 
 namespace {
+
+// W = A_k V_k in FP32 (the inner cycle of mixed-precision TBAS); FP32 copies of the operator's
+// values are made on first use.
+void rows_call_f32(ts_op* op, const float2* V, float2* Out, int n, int s, int K, int p, cudaStream_t st) {
+  RowsArgsT<float2> a{};
+  if (op->sp) {
+    SparseOp& sp = *op->sp;
+    if (!sp.vals32) {
+      TS_CUDA(cudaMalloc(&sp.vals32, sizeof(float2) * (size_t)K * sp.nnz));
+      convert<double, float>(reinterpret_cast<const double*>(sp.vals), reinterpret_cast<float*>(sp.vals32),
+                             2ll * K * sp.nnz, st);
+    }
+    a.rowptr = sp.rowptr;
+    a.col = sp.col;
+    a.vals = sp.vals32;
+    a.nnz = sp.nnz;
+  } else {
+    ensure_f32_operator(op, st);
+    a.Ad = op->Ah32;
+  }
+  a.V = V;
+  a.Out = Out;
+  a.n = n;
+  a.s = s;
+  a.K = K;
+  a.p = p;
+  const bool wide = s > 32;
+  int sp = 32;
+  while (!wide && sp / 2 >= s && sp > 1) sp /= 2;
+  const int rows_per_block = 8 * (32 / sp);
+  const int gx = std::max(1, std::min((n + rows_per_block - 1) / rows_per_block, 2 * 152 * 4 / K));
+  if (wide) k_sylv_rows<0, 2><<<dim3(gx, K), 256, 0, st>>>(a);
+  else k_sylv_rows<0, 1><<<dim3(gx, K), 256, 0, st>>>(a);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
 
 void rows_call(int mode, const ts_op* op, const double2* V, const double2* C, double2* Out, double* partials, int n,
                int s, int K, int p, cudaStream_t st) {
@@ -536,21 +599,23 @@ void rows_call(int mode, const ts_op* op, const double2* V, const double2* C, do
   TS_CUDA(cudaGetLastError());
 }
 
-void rows_mm(const double2* In, double2* Out, const double2* M, long long sM, int ldm, int n, int s, int K, double alpha,
+template <typename Cin, typename Cout>
+void rows_mm(const Cin* In, Cout* Out, const double2* M, long long sM, int ldm, int n, int s, int K, double alpha,
              bool accumulate, cudaStream_t st) {
+  using R = typename RealOf<Cin>::T;
   TS_REQUIRE(s <= kMaxS, "rows_mm: block width above kMaxS");
   int tpr = 1;
   while (tpr * kRowCols < s) tpr *= 2;
   const int rows_per_block = 256 / tpr;
   const int gx = std::max(1, std::min((n + rows_per_block - 1) / rows_per_block, 4 * 152 * 4 / K));
-  const size_t smem = sizeof(double) * 3 * (size_t)s * s;
+  const size_t smem = sizeof(R) * 3 * (size_t)s * s;
   static bool attr = false;
   if (!attr) {
-    TS_CUDA(cudaFuncSetAttribute(k_rows_mm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(double) * 3 * kMaxS * kMaxS)));
+    TS_CUDA(cudaFuncSetAttribute(k_rows_mm<Cin, Cout>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(R) * 3 * kMaxS * kMaxS)));
     attr = true;
   }
-  k_rows_mm<<<dim3(gx, K), 256, smem, st>>>(In, Out, M, sM, ldm, n, s, alpha, accumulate ? 1 : 0);
+  k_rows_mm<Cin, Cout><<<dim3(gx, K), 256, smem, st>>>(In, Out, M, sM, ldm, n, s, alpha, accumulate ? 1 : 0);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -558,9 +623,10 @@ void rows_mm(const double2* In, double2* Out, const double2* M, long long sM, in
 // Algorithmic FLOPs of one (n x s)^H (n x s) or (n x s)(s x s) complex product over K slices.
 double block_flops(const TbaWork& w) { return 8.0 * w.n * w.s * w.s * w.K; }
 
-void gram(const TbaWork& w, const double2* V, const double2* W, double2* out, long long sOut, int ldo, cudaStream_t st) {
+template <typename C2>
+void gram(const TbaWork& w, const C2* V, const C2* W, double2* out, long long sOut, int ldo, cudaStream_t st) {
   w.tm->begin(st, 4, block_flops(w));
-  k_gram<<<dim3(w.chunks, w.K), 256, 0, st>>>(V, W, w.n, w.s, w.rows_per_chunk, w.gram_part);
+  k_gram<C2><<<dim3(w.chunks, w.K), 256, 0, st>>>(V, W, w.n, w.s, w.rows_per_chunk, w.gram_part);
   count_launch();
   TS_CUDA(cudaGetLastError());
   k_gram_reduce<<<w.K, 256, 0, st>>>(w.gram_part, w.chunks, w.s, out, sOut, ldo);
@@ -569,7 +635,8 @@ void gram(const TbaWork& w, const double2* V, const double2* W, double2* out, lo
   w.tm->end(st);
 }
 
-void rows_mm_timed(const TbaWork& w, const double2* In, double2* Out, const double2* M, long long sM, int ldm,
+template <typename Cin, typename Cout>
+void rows_mm_timed(const TbaWork& w, const Cin* In, Cout* Out, const double2* M, long long sM, int ldm,
                    double alpha, bool accumulate, cudaStream_t st) {
   w.tm->begin(st, 4, block_flops(w));
   rows_mm(In, Out, M, sM, ldm, w.n, w.s, w.K, alpha, accumulate, st);
@@ -584,7 +651,8 @@ void triinv(const double2* R, double2* X, int s, int K, cudaStream_t st) {
 
 // Tubal-QR of the block W (in place -> Q) by CholeskyQR2; R written to Rout (column-major, ldr).
 // Returns false on a failed Cholesky (rank-deficient block).
-bool tubal_qr(const TbaWork& w, double2* W, double2* Rout, long long sR, int ldr, cudaStream_t st) {
+template <typename C2>
+bool tubal_qr(const TbaWork& w, C2* W, double2* Rout, long long sR, int ldr, cudaStream_t st) {
   const int s = w.s, K = w.K;
   const long long ss = (long long)s * s;
   TS_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
@@ -717,6 +785,7 @@ ts_status tbas_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const t
     TS_CUDA(cudaStreamSynchronize(st));
     info.history_len = hist_len;
     info.true_history_len = true_len;
+    if (o.precision == TS_MIXED_FP32) info.outer = info.cycles;
     info.relres_true = normC > 0 ? res / normC : res;
     info.relres_est = normC > 0 ? last_est / normC : last_est;
     return stt;
@@ -724,37 +793,58 @@ ts_status tbas_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const t
   if (!std::isfinite(res) || !std::isfinite(normC)) return finish(TS_ERR_NONFINITE);
   if (normC == 0.0 || res <= o.tol * normC) return finish(TS_OK);
   const long long blk = w.blk;
+  // Mixed precision (TS_MIXED_FP32): the block Krylov basis, the SpMM and the block products of each
+  // cycle run in FP32; the Gram results, H_m, the projected solve, X and the true residual of every
+  // restart stay FP64, so the restarts are steps of iterative refinement.
+  const bool low = o.precision == TS_MIXED_FP32;
+  float2* V32 = low ? (float2*)ctx->ws.get("tba_V32", sizeof(float2) * (size_t)blk * (m + 1)) : nullptr;
+  const double breakdown_rel = low ? 1e-6 : 1e-13;
   for (int cycle = 0; cycle < o.max_restarts; ++cycle) {
-    // [V_1, H_0] = Tubal-QR(R0)
-    TS_CUDA(cudaMemcpyAsync(w.V, w.R, sizeof(double2) * blk, cudaMemcpyDeviceToDevice, st));
-    if (!tubal_qr(w, w.V, w.H0, ss, s, st)) return finish(TS_BREAKDOWN);
     const int N = m * s;
-    TS_CUDA(cudaMemsetAsync(w.Hm, 0, sizeof(double2) * (size_t)K * N * N, st));
     int mm = m;
-    for (int j = 0; j < m; ++j) {
-      double2* Vj = w.V + (long long)j * blk;
-      double2* Wb = w.V + (long long)(j + 1) * blk;
-      rows_call(0, op, Vj, nullptr, Wb, nullptr, n, s, K, p, st);              // W = A * V_j (A, not M)
-      ++info.applies_fp64;
-      for (int i = 0; i <= j; ++i) {                                            // block MGS
-        double2* Vi = w.V + (long long)i * blk;
-        double2* Hij = w.Hm + (long long)i * s + (long long)N * j * s;         // block (i, j) of H_m
-        gram(w, Vi, Wb, Hij, (long long)N * N, N, st);
-        rows_mm_timed(w, Vi, Wb, Hij, (long long)N * N, N, -1.0, true, st);
+    // One Tubal Block Arnoldi cycle on the basis V (double2 or float2): V_1 = Tubal-QR(R0), W = A V_j,
+    // block MGS, Tubal-QR of W.  Returns false on a failed Tubal-QR.
+    auto arnoldi = [&](auto* V) -> bool {
+      using C2 = std::remove_pointer_t<decltype(V)>;
+      if constexpr (sizeof(C2) == 16) {
+        TS_CUDA(cudaMemcpyAsync(V, w.R, sizeof(double2) * blk, cudaMemcpyDeviceToDevice, st));
+      } else {
+        convert<double, float>(reinterpret_cast<const double*>(w.R), reinterpret_cast<float*>(V), 2 * blk, st);
       }
-      gram(w, Wb, Wb, w.G, ss, s, st);
-      const double wn = std::sqrt(std::max(0.0, weighted_trace(w, w.G, ctx, st)));
-      ++info.iters;
-      if (wn <= 1e-13 * res) {                                                   // block breakdown
-        mm = j + 1;
-        TS_CUDA(cudaMemsetAsync(w.Hlast, 0, sizeof(double2) * (size_t)K * ss, st));
-        break;
+      if (!tubal_qr(w, V, w.H0, ss, s, st)) return false;
+      TS_CUDA(cudaMemsetAsync(w.Hm, 0, sizeof(double2) * (size_t)K * N * N, st));
+      for (int j = 0; j < m; ++j) {
+        C2* Vj = V + (long long)j * blk;
+        C2* Wb = V + (long long)(j + 1) * blk;
+        if constexpr (sizeof(C2) == 16) {
+          rows_call(0, op, Vj, nullptr, Wb, nullptr, n, s, K, p, st);          // W = A * V_j (A, not M)
+          ++info.applies_fp64;
+        } else {
+          rows_call_f32(op, Vj, Wb, n, s, K, p, st);
+          ++info.applies_low;
+        }
+        for (int i = 0; i <= j; ++i) {                                          // block MGS
+          C2* Vi = V + (long long)i * blk;
+          double2* Hij = w.Hm + (long long)i * s + (long long)N * j * s;       // block (i, j) of H_m
+          gram(w, Vi, Wb, Hij, (long long)N * N, N, st);
+          rows_mm_timed(w, Vi, Wb, Hij, (long long)N * N, N, -1.0, true, st);
+        }
+        gram(w, Wb, Wb, w.G, ss, s, st);
+        const double wn = std::sqrt(std::max(0.0, weighted_trace(w, w.G, ctx, st)));
+        ++info.iters;
+        if (wn <= breakdown_rel * res) {                                        // block breakdown
+          mm = j + 1;
+          TS_CUDA(cudaMemsetAsync(w.Hlast, 0, sizeof(double2) * (size_t)K * ss, st));
+          break;
+        }
+        double2* Hnext = (j + 1 < m) ? w.Hm + (long long)(j + 1) * s + (long long)N * j * s : w.Hlast;
+        const long long sH = (j + 1 < m) ? (long long)N * N : ss;
+        const int ldh = (j + 1 < m) ? N : s;
+        if (!tubal_qr(w, Wb, Hnext, sH, ldh, st)) return false;
       }
-      double2* Hnext = (j + 1 < m) ? w.Hm + (long long)(j + 1) * s + (long long)N * j * s : w.Hlast;
-      const long long sH = (j + 1 < m) ? (long long)N * N : ss;
-      const int ldh = (j + 1 < m) ? N : s;
-      if (!tubal_qr(w, Wb, Hnext, sH, ldh, st)) return finish(TS_BREAKDOWN);
-    }
+      return true;
+    };
+    if (!(low ? arnoldi(V32) : arnoldi(w.V))) return finish(TS_BREAKDOWN);
     const int Nm = mm * s;
     // Projected equation per slice: H_m Y - Y B = C1 = [H0; 0] by Hessenberg-Schur.
     // When the block space broke down early the leading Nm x Nm part of H_m is used.
@@ -785,8 +875,12 @@ ts_status tbas_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const t
     count_launch();
     TS_CUDA(cudaGetLastError());
     // X += V_m Y
-    for (int j = 0; j < mm; ++j)
-      rows_mm(w.V + (long long)j * blk, w.X, w.Y + (long long)j * s, (long long)Nm * s, Nm, n, s, K, 1.0, true, st);
+    for (int j = 0; j < mm; ++j) {
+      if (low)
+        rows_mm(V32 + (long long)j * blk, w.X, w.Y + (long long)j * s, (long long)Nm * s, Nm, n, s, K, 1.0, true, st);
+      else
+        rows_mm(w.V + (long long)j * blk, w.X, w.Y + (long long)j * s, (long long)Nm * s, Nm, n, s, K, 1.0, true, st);
+    }
     int e = 0;
     TS_CUDA(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     const double est = std::sqrt(std::max(0.0, read_scalar(w.sc + 4, ctx, st)));
@@ -813,7 +907,8 @@ ts_status tba_entry(ts_ctx* ctx, const ts_op* cop, const double* C, double* X, c
   TS_REQUIRE(o.restart >= 1 && o.restart <= 256, "ts_tba_solve: restart must be in 1..256");
   TS_REQUIRE(o.max_restarts >= 1, "ts_tba_solve: max_restarts must be >= 1");
   TS_REQUIRE(o.tol > 0.0 && std::isfinite(o.tol), "ts_tba_solve: tol must be positive");
-  if (o.precision != TS_FP64) throw Error{TS_ERR_UNSUPPORTED, "TBAS runs in FP64 only"};
+  if (o.precision != TS_FP64 && o.precision != TS_MIXED_FP32)
+    throw Error{TS_ERR_UNSUPPORTED, "TBAS runs in FP64 or TS_MIXED_FP32 only"};
   if (o.fp64_engine != TS_ENGINE_DFMA) throw Error{TS_ERR_UNSUPPORTED, "TBAS runs on the FP64 DFMA engine only"};
   TS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

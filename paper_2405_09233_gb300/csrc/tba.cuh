@@ -11,6 +11,7 @@ struct SparseOp {
   int* rowptr = nullptr;     // n + 1
   int* col = nullptr;        // nnz
   double2* vals = nullptr;   // K x nnz (slice k at vals + k*nnz)
+  float2* vals32 = nullptr;  // FP32 copy for the inner cycle of mixed-precision TBAS, made on first use
   void release();
 };
 

@@ -143,3 +143,44 @@ def test_tbas_sparse_full_size_lap128(ctx, s):
     assert float(torch.linalg.norm(R) / torch.linalg.norm(Cd)) <= 1e-10
     assert float(torch.max(torch.abs(Xd - Xs))) < 1e-8
     op.close()
+
+
+@pytest.mark.parametrize("case", [(40, 4, 4, 4, 1), (60, 3, 2, 6, 3), (64, 8, 8, 3, 4), (24, 24, 4, 3, 0)],
+                         ids=lambda c: "n%d_s%d_p%d_m%d" % c[:4])
+def test_tbas_mixed_fp32_dense(ctx, case):
+    """Mixed-precision TBAS (FP32 block Krylov cycles, FP64 residuals and solution) reaches a true
+    relative residual of 1e-10 and the oracle's FP64 TBAS solution."""
+    import torch
+    n, s, p, m, seed = case
+    pr = inputs.dense_problem(n, s, p, seed=seed)
+    C = kr.sylv_apply(pr.A, pr.B, pr.Xstar)
+    ref = tb.tbas(pr.A, pr.B, C, m=m, tol=1e-10)
+    op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
+    Xd = torch.zeros((p, s, n), dtype=torch.float64, device="cuda")
+    res = ctx.tba_solve(op, to_dev(C), Xd, restart=m, tol=1e-10, precision="mixed_fp32")
+    X = from_dev(Xd)
+    assert res.status == 0, res
+    assert tp.norm(C - kr.sylv_apply(pr.A, pr.B, X)) <= 1e-10 * tp.norm(C)
+    np.testing.assert_allclose(X, ref.X, rtol=0, atol=1e-8 * np.abs(ref.X).max())
+    assert res.info.applies_low > 0 and res.info.outer == res.info.cycles
+    op.close()
+
+
+@pytest.mark.parametrize("s", [32, 4])
+def test_tbas_mixed_fp32_sparse_lap128(ctx, s):
+    """The sparse workload at full size with mixed-precision TBAS(10): true relative residual
+    1e-10 (FP64 operator) and the manufactured solution."""
+    import torch
+    prob = inputs.sparse_problem(grid=128, s=s, p=8, seed=1)
+    rowptr, col, val = csr_arrays(prob)
+    op = ctx.op_create_csr(prob.n, 8, rowptr, col, val, to_dev(prob.B))
+    Xs = to_dev(prob.Xstar)
+    Cd = ctx.sylv_apply(op, Xs)
+    Xd = torch.zeros_like(Cd)
+    res = ctx.tba_solve(op, Cd, Xd, restart=10, tol=1e-10, precision="mixed_fp32")
+    assert res.status == 0, res
+    R = Cd - ctx.sylv_apply(op, Xd)
+    assert float(torch.linalg.norm(R) / torch.linalg.norm(Cd)) <= 1e-10
+    assert float(torch.max(torch.abs(Xd - Xs))) < 1e-8
+    op.close()
+
