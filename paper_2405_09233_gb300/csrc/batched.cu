@@ -22,6 +22,7 @@
 #include "internal.cuh"
 #include "oz.cuh"
 #include "tc.cuh"
+#include "tune.cuh"
 #include "apply.cuh"
 #include "reduce.cuh"
 #include "pack.cuh"
@@ -738,12 +739,16 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size(), nit = (int)plan.items.size();
   // Tensor-core inner products: every instance's planar X copies, tensor maps and work lists,
   // made before anything is captured.
-  const TcMaps* d_tcmaps = nullptr;
-  const BTcInst* d_tcinst = nullptr;
-  const BTcPlanes* d_tcplanes = nullptr;
-  const int4* d_titems = nullptr;
-  const int4* d_pitems = nullptr;
-  int n_titems = 0, n_pitems = 0;
+  struct TcTables {
+    const TcMaps* maps = nullptr;
+    const BTcPlanes* planes = nullptr;
+    const BTcInst* inst = nullptr;
+    const int4* titems = nullptr;
+    const int4* pitems = nullptr;
+    int n_titems = 0, n_pitems = 0;
+  };
+  TcTables tct;
+  int tc_bn = kBatchTcBNs[0];
   if (tcin) {
     std::vector<size_t> poff(count);
     size_t ptot = 0;
@@ -752,53 +757,89 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       ptot += tc_batch_plane_bytes(ops[i]->n, ops[i]->s, ops[i]->K, o.precision);
     }
     char* planes = (char*)get("b_tc_planes", ptot);
-    std::vector<TcMaps> hmaps(count);
-    std::vector<BTcPlanes> hplanes(count);
-    std::vector<BTcInst> hinst(count);
-    std::vector<int4> titems, pitems;
-    for (int i = 0; i < count; ++i) {
-      const BInst& b = plan.inst[i];
-      tc_batch_instance(ops[i], o.precision, (const float2*)Xh + b.offS, planes + poff[i], &hplanes[i], &hmaps[i]);
-      hinst[i] = BTcInst{(float2*)Yh + b.offS, b.n, b.s, b.nyq};
-      for (int k = 0; k < b.K; ++k) {
-        for (int i0 = 0; i0 < b.n; i0 += 128)
-          for (int j0 = 0; j0 < b.s; j0 += kBatchTcBN) titems.push_back(make_int4(i, k, i0, j0));
-        for (int i0 = 0; i0 < b.n; i0 += 32)
-          for (int j0 = 0; j0 < b.s; j0 += 32) pitems.push_back(make_int4(i, k, i0, j0));
+    // One set of tables per candidate column tile: the tensor maps' B boxes and the tile work list
+    // depend on it, the planar X copies do not.
+    auto build_tables = [&](int bn) -> TcTables {
+      std::vector<TcMaps> hmaps(count);
+      std::vector<BTcPlanes> hplanes(count);
+      std::vector<BTcInst> hinst(count);
+      std::vector<int4> titems, pitems;
+      for (int i = 0; i < count; ++i) {
+        const BInst& b = plan.inst[i];
+        tc_batch_instance(ops[i], o.precision, (const float2*)Xh + b.offS, planes + poff[i], &hplanes[i], &hmaps[i],
+                          bn);
+        hinst[i] = BTcInst{(float2*)Yh + b.offS, b.n, b.s, b.nyq};
+        for (int k = 0; k < b.K; ++k) {
+          for (int i0 = 0; i0 < b.n; i0 += 128)
+            for (int j0 = 0; j0 < b.s; j0 += bn) titems.push_back(make_int4(i, k, i0, j0));
+          for (int i0 = 0; i0 < b.n; i0 += 32)
+            for (int j0 = 0; j0 < b.s; j0 += 32) pitems.push_back(make_int4(i, k, i0, j0));
+        }
       }
-    }
-    std::stable_sort(titems.begin(), titems.end(), [&](const int4& a, const int4& b) {
-      auto cost = [&](const int4& q) {
-        const BInst& x = plan.inst[q.x];
-        return ((q.y == 0 || q.y == x.nyq) ? 1.0 : 4.0) * (x.n + x.s);
-      };
-      return cost(a) > cost(b);
-    });
-    n_titems = (int)titems.size();
-    n_pitems = (int)pitems.size();
-    char* tab = (char*)get("b_tc_tables", sizeof(TcMaps) * count + sizeof(BTcPlanes) * count + sizeof(BTcInst) * count +
-                                              sizeof(int4) * (titems.size() + pitems.size()) + 1024);
-    TcMaps* m_ = (TcMaps*)tab;                                    // 2 KB each: 64-byte aligned tensor maps
-    BTcPlanes* p_ = (BTcPlanes*)(m_ + count);
-    BTcInst* in_ = (BTcInst*)(((uintptr_t)(p_ + count) + 15) & ~(uintptr_t)15);
-    int4* ti_ = (int4*)(((uintptr_t)(in_ + count) + 15) & ~(uintptr_t)15);
-    int4* pi_ = ti_ + titems.size();
-    TS_CUDA(cudaMemcpy(m_, hmaps.data(), sizeof(TcMaps) * count, cudaMemcpyHostToDevice));
-    TS_CUDA(cudaMemcpy(p_, hplanes.data(), sizeof(BTcPlanes) * count, cudaMemcpyHostToDevice));
-    TS_CUDA(cudaMemcpy(in_, hinst.data(), sizeof(BTcInst) * count, cudaMemcpyHostToDevice));
-    TS_CUDA(cudaMemcpy(ti_, titems.data(), sizeof(int4) * titems.size(), cudaMemcpyHostToDevice));
-    TS_CUDA(cudaMemcpy(pi_, pitems.data(), sizeof(int4) * pitems.size(), cudaMemcpyHostToDevice));
-    d_tcmaps = m_;
-    d_tcplanes = p_;
-    d_tcinst = in_;
-    d_titems = ti_;
-    d_pitems = pi_;
-    if (!ozaki) TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, user));
+      // largest tiles first: interior slices carry four real products, the DC and Nyquist ones one
+      std::stable_sort(titems.begin(), titems.end(), [&](const int4& a, const int4& b) {
+        auto cost = [&](const int4& q) {
+          const BInst& x = plan.inst[q.x];
+          return ((q.y == 0 || q.y == x.nyq) ? 1.0 : 4.0) * (x.n + x.s);
+        };
+        return cost(a) > cost(b);
+      });
+      const std::string name = "b_tc_tables_" + std::to_string(bn);
+      char* tab = (char*)get(name.c_str(), sizeof(TcMaps) * count + sizeof(BTcPlanes) * count +
+                                               sizeof(BTcInst) * count + sizeof(int4) * (titems.size() + pitems.size()) +
+                                               1024);
+      TcMaps* m_ = (TcMaps*)tab;                                  // 2 KB each: 64-byte aligned tensor maps
+      BTcPlanes* p_ = (BTcPlanes*)(m_ + count);
+      BTcInst* in_ = (BTcInst*)(((uintptr_t)(p_ + count) + 15) & ~(uintptr_t)15);
+      int4* ti_ = (int4*)(((uintptr_t)(in_ + count) + 15) & ~(uintptr_t)15);
+      int4* pi_ = ti_ + titems.size();
+      TS_CUDA(cudaMemcpy(m_, hmaps.data(), sizeof(TcMaps) * count, cudaMemcpyHostToDevice));
+      TS_CUDA(cudaMemcpy(p_, hplanes.data(), sizeof(BTcPlanes) * count, cudaMemcpyHostToDevice));
+      TS_CUDA(cudaMemcpy(in_, hinst.data(), sizeof(BTcInst) * count, cudaMemcpyHostToDevice));
+      TS_CUDA(cudaMemcpy(ti_, titems.data(), sizeof(int4) * titems.size(), cudaMemcpyHostToDevice));
+      TS_CUDA(cudaMemcpy(pi_, pitems.data(), sizeof(int4) * pitems.size(), cudaMemcpyHostToDevice));
+      TcTables t;
+      t.maps = m_;
+      t.planes = p_;
+      t.inst = in_;
+      t.titems = ti_;
+      t.pitems = pi_;
+      t.n_titems = (int)titems.size();
+      t.n_pitems = (int)pitems.size();
+      return t;
+    };
+    tc_batch_preload(o.precision);   // shared-memory limits of the product kernels, before any launch
+    std::vector<TcTables> cand_tables;
+    std::vector<int> cands;
+    int smax = 0;
+    for (int i = 0; i < count; ++i) smax = std::max(smax, plan.inst[i].s);
+    for (int bn : kBatchTcBNs)
+      if (bn == kBatchTcBNs[0] || bn / 2 < smax) {
+        cands.push_back(bn);
+        cand_tables.push_back(build_tables(bn));
+      }
+    // Pick the column tile by timing one product pass of the whole batch with every instance
+    // active (the activity flags are all set above); the choice is cached per batch shape.
+    std::string key = "btc:" + std::to_string(o.precision) + ":" + std::to_string(count);
+    for (int i = 0; i < count; ++i)
+      key += ":" + std::to_string(plan.inst[i].n) + "x" + std::to_string(plan.inst[i].s) + "x" +
+             std::to_string(plan.inst[i].K);
+    TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
+    tc_bn = tune_pick(
+        ctx, key, cands,
+        [&](int bn) {
+          const TcTables& t = cand_tables[std::find(cands.begin(), cands.end(), bn) - cands.begin()];
+          tc_batch_products(o.precision, bn, t.planes, t.pitems, t.n_pitems, t.maps, t.inst, d.act, t.titems,
+                            t.n_titems, tc_err, st);
+        },
+        st);
+    tct = cand_tables[std::find(cands.begin(), cands.end(), tc_bn) - cands.begin()];
+    TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
   }
   auto inner_products = [&](cudaStream_t s2) -> int {
     if (tcin) {
-      tc_batch_products(o.precision, d_tcplanes, d_pitems, n_pitems, d_tcmaps, d_tcinst, d.act, d_titems, n_titems,
-                        tc_err, s2);
+      tc_batch_products(o.precision, tc_bn, tct.planes, tct.pitems, tct.n_pitems, tct.maps, tct.inst, d.act,
+                        tct.titems, tct.n_titems, tc_err, s2);
       return 2;
     }
     if (mixed) k_b_gemm<float, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, (float2*)Xh, (float2*)Yh);
@@ -864,7 +905,6 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       if (!exec) {
         if (mixed) preload_cycle_kernels<float, float2>();
         else preload_cycle_kernels<double, double2>();
-        if (tcin) tc_batch_preload(o.precision);
         cudaGraph_t graph;
         CountSuppress no_count;   // the replays below count the recorded kernels
         TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));

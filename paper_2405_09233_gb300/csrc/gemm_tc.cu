@@ -30,6 +30,7 @@
 #include "internal.cuh"
 #include "tc.cuh"
 #include "tcgen05.cuh"
+#include "tune.cuh"
 #include "fft_reg.cuh"
 
 namespace ts {
@@ -603,33 +604,48 @@ void tc_apply(ts_ctx* ctx, ts_op* op, int precision, const float* X, float2* Yh,
   if (esz == 2) planar_dft<__nv_bfloat16>(X, w, n, s, p, t.ldn, t.lds, st);
   else planar_dft<float>(X, w, n, s, p, t.ldn, t.lds, st);
   tm.end(st);
-  TcMaps maps;
-  const int bn = s <= 64 ? 64 : (s <= 128 ? 128 : 256);
-  make_map(&maps.a_re, t.a_re, esz, t.ldn, n, n, K, kTileM);
-  make_map(&maps.a_im, t.a_im, esz, t.ldn, n, n, K, kTileM);
-  make_map(&maps.xc_re, w.xc_re, esz, t.ldn, n, s, K, bn);
-  make_map(&maps.xc_im, w.xc_im, esz, t.ldn, n, s, K, bn);
-  make_map(&maps.xr_re, w.xr_re, esz, t.lds, s, n, K, kTileM);
-  make_map(&maps.xr_im, w.xr_im, esz, t.lds, s, n, K, kTileM);
-  make_map(&maps.b_re, t.b_re, esz, t.lds, s, s, K, bn);
-  make_map(&maps.b_im, t.b_im, esz, t.lds, s, s, K, bn);
-  if (t.split) {
-    make_map(&maps.a_re_lo, t.a_re_lo, esz, t.ldn, n, n, K, kTileM);
-    make_map(&maps.a_im_lo, t.a_im_lo, esz, t.ldn, n, n, K, kTileM);
-    make_map(&maps.xc_re_lo, w.xc_re_lo, esz, t.ldn, n, s, K, bn);
-    make_map(&maps.xc_im_lo, w.xc_im_lo, esz, t.ldn, n, s, K, bn);
-    make_map(&maps.xr_re_lo, w.xr_re_lo, esz, t.lds, s, n, K, kTileM);
-    make_map(&maps.xr_im_lo, w.xr_im_lo, esz, t.lds, s, n, K, kTileM);
-    make_map(&maps.b_re_lo, t.b_re_lo, esz, t.lds, s, s, K, bn);
-    make_map(&maps.b_im_lo, t.b_im_lo, esz, t.lds, s, s, K, bn);
-  } else {
-    maps.a_re_lo = maps.a_re; maps.a_im_lo = maps.a_im; maps.xc_re_lo = maps.xc_re; maps.xc_im_lo = maps.xc_im;
-    maps.xr_re_lo = maps.xr_re; maps.xr_im_lo = maps.xr_im; maps.b_re_lo = maps.b_re; maps.b_im_lo = maps.b_im;
-  }
+  // The column tile BN (64, 128 or 256 output columns per CTA; tiles more than twice s are not
+  // tried) is chosen by the autotuner on the first application of this shape and precision.  The
+  // accumulation order of every output entry does not depend on BN, so neither does the result.
+  auto build = [&](int bn) {
+    TcMaps maps;
+    make_map(&maps.a_re, t.a_re, esz, t.ldn, n, n, K, kTileM);
+    make_map(&maps.a_im, t.a_im, esz, t.ldn, n, n, K, kTileM);
+    make_map(&maps.xc_re, w.xc_re, esz, t.ldn, n, s, K, bn);
+    make_map(&maps.xc_im, w.xc_im, esz, t.ldn, n, s, K, bn);
+    make_map(&maps.xr_re, w.xr_re, esz, t.lds, s, n, K, kTileM);
+    make_map(&maps.xr_im, w.xr_im, esz, t.lds, s, n, K, kTileM);
+    make_map(&maps.b_re, t.b_re, esz, t.lds, s, s, K, bn);
+    make_map(&maps.b_im, t.b_im, esz, t.lds, s, s, K, bn);
+    if (t.split) {
+      make_map(&maps.a_re_lo, t.a_re_lo, esz, t.ldn, n, n, K, kTileM);
+      make_map(&maps.a_im_lo, t.a_im_lo, esz, t.ldn, n, n, K, kTileM);
+      make_map(&maps.xc_re_lo, w.xc_re_lo, esz, t.ldn, n, s, K, bn);
+      make_map(&maps.xc_im_lo, w.xc_im_lo, esz, t.ldn, n, s, K, bn);
+      make_map(&maps.xr_re_lo, w.xr_re_lo, esz, t.lds, s, n, K, kTileM);
+      make_map(&maps.xr_im_lo, w.xr_im_lo, esz, t.lds, s, n, K, kTileM);
+      make_map(&maps.b_re_lo, t.b_re_lo, esz, t.lds, s, s, K, bn);
+      make_map(&maps.b_im_lo, t.b_im_lo, esz, t.lds, s, s, K, bn);
+    } else {
+      maps.a_re_lo = maps.a_re; maps.a_im_lo = maps.a_im; maps.xc_re_lo = maps.xc_re; maps.xc_im_lo = maps.xc_im;
+      maps.xr_re_lo = maps.xr_re; maps.xr_im_lo = maps.xr_im; maps.b_re_lo = maps.b_re; maps.b_im_lo = maps.b_im;
+    }
+    return maps;
+  };
   const int nyq = nyquist_index(p);
+  auto run = [&](int bn) {
+    const TcMaps maps = build(bn);
+    if (t.split) launch_by_bn<3>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
+    else launch_by_bn<1>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
+  };
+  std::vector<int> cands;
+  for (int c : {64, 128, 256})
+    if (c == 64 || c / 2 < s) cands.push_back(c);
+  const std::string key = "tc:" + std::to_string(n) + "x" + std::to_string(s) + "x" + std::to_string(K) + ":" +
+                          std::to_string(precision);
+  const int bn = tune_pick(ctx, key, cands, run, st);
   tm.begin(st, 2, gemm_flops_tc(n, s, K, nyq));
-  if (t.split) launch_by_bn<3>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
-  else launch_by_bn<1>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
+  run(bn);
   tm.end(st);
 }
 
@@ -639,24 +655,33 @@ void tc_apply(ts_ctx* ctx, ts_op* op, int precision, const float* X, float2* Yh,
 namespace {
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-template <typename OpT, int ESZ, int PARTS, bool SPLIT>
-void batch_preload_t() {
-  using Cfg = TcCfg<kBatchTcBN, ESZ>;
+template <typename OpT, int ESZ, int PARTS, bool SPLIT, int BN>
+void batch_preload_bn() {
+  using Cfg = TcCfg<BN, ESZ>;
   cudaFuncAttributes fa;
-  TS_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_b_planes<OpT, SPLIT>));
-  TS_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_b_tc<kBatchTcBN, ESZ, PARTS>));
-  TS_CUDA(cudaFuncSetAttribute(k_b_tc<kBatchTcBN, ESZ, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+  TS_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_b_tc<BN, ESZ, PARTS>));
+  TS_CUDA(cudaFuncSetAttribute(k_b_tc<BN, ESZ, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
 }
 
 template <typename OpT, int ESZ, int PARTS, bool SPLIT>
-void batch_products_t(const BTcPlanes* planes, const int4* pitems, int npitems, const TcMaps* maps,
+void batch_preload_t() {
+  cudaFuncAttributes fa;
+  TS_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_b_planes<OpT, SPLIT>));
+  batch_preload_bn<OpT, ESZ, PARTS, SPLIT, 64>();
+  batch_preload_bn<OpT, ESZ, PARTS, SPLIT, 128>();
+}
+
+template <typename OpT, int ESZ, int PARTS, bool SPLIT>
+void batch_products_t(int bn, const BTcPlanes* planes, const int4* pitems, int npitems, const TcMaps* maps,
                       const BTcInst* inst, const int* active, const int4* items, int nitems, int* err,
                       cudaStream_t st) {
-  using Cfg = TcCfg<kBatchTcBN, ESZ>;
   k_b_planes<OpT, SPLIT><<<npitems, dim3(32, 8), 0, st>>>(planes, active, pitems);
   count_launch();
   TS_CUDA(cudaGetLastError());
-  k_b_tc<kBatchTcBN, ESZ, PARTS><<<nitems, 192, Cfg::kSmem, st>>>(maps, inst, active, items, err);
+  if (bn == 128)
+    k_b_tc<128, ESZ, PARTS><<<nitems, 192, TcCfg<128, ESZ>::kSmem, st>>>(maps, inst, active, items, err);
+  else
+    k_b_tc<64, ESZ, PARTS><<<nitems, 192, TcCfg<64, ESZ>::kSmem, st>>>(maps, inst, active, items, err);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -670,7 +695,7 @@ size_t tc_batch_plane_bytes(int n, int s, int K, int precision) {
   return (split ? 4 : 2) * (nx + nr);
 }
 
-void tc_batch_instance(ts_op* op, int precision, const float2* Xh, void* base, BTcPlanes* pl, TcMaps* maps) {
+void tc_batch_instance(ts_op* op, int precision, const float2* Xh, void* base, BTcPlanes* pl, TcMaps* maps, int bn) {
   TS_REQUIRE(op->tc && op->tc_prec == precision, "tc_batch_instance: operator planes not prepared");
   const TcOperands& t = *op->tc;
   const int n = op->n, s = op->s, K = op->K, esz = t.esz;
@@ -689,7 +714,6 @@ void tc_batch_instance(ts_op* op, int precision, const float2* Xh, void* base, B
     pl->xr_im_lo = b; b += nr;
   }
   pl->n = n; pl->s = s; pl->ldn = t.ldn; pl->lds = t.lds; pl->nyq = nyquist_index(op->p);
-  const int bn = kBatchTcBN;
   make_map(&maps->a_re, t.a_re, esz, t.ldn, n, n, K, kTileM);
   make_map(&maps->a_im, t.a_im, esz, t.ldn, n, n, K, kTileM);
   make_map(&maps->xc_re, pl->xc_re, esz, t.ldn, n, s, K, bn);
@@ -720,15 +744,16 @@ void tc_batch_preload(int precision) {
   else batch_preload_t<float, 4, 3, true>();
 }
 
-void tc_batch_products(int precision, const BTcPlanes* planes, const int4* pitems, int npitems, const TcMaps* maps,
-                       const BTcInst* inst, const int* active, const int4* items, int nitems, int* err,
-                       cudaStream_t st) {
+void tc_batch_products(int precision, int bn, const BTcPlanes* planes, const int4* pitems, int npitems,
+                       const TcMaps* maps, const BTcInst* inst, const int* active, const int4* items, int nitems,
+                       int* err, cudaStream_t st) {
   if (precision == TS_MIXED_BF16)
-    batch_products_t<__nv_bfloat16, 2, 1, false>(planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
+    batch_products_t<__nv_bfloat16, 2, 1, false>(bn, planes, pitems, npitems, maps, inst, active, items, nitems, err,
+                                                 st);
   else if (precision == TS_MIXED_TF32)
-    batch_products_t<float, 4, 1, false>(planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
+    batch_products_t<float, 4, 1, false>(bn, planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
   else
-    batch_products_t<float, 4, 3, true>(planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
+    batch_products_t<float, 4, 3, true>(bn, planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
 }
 
 double gemm_flops_tc(int n, int s, int K, int nyq) {

@@ -60,18 +60,19 @@ struct BTcPlanes {
   void* xr_im_lo;
   int n, s, ldn, lds, nyq;
 };
-// Column tile of the batched kernel.
-constexpr int kBatchTcBN = 64;
+// Column tiles the batched kernel supports (chosen per batch by the autotuner).
+constexpr int kBatchTcBNs[2] = {64, 128};
 // Bytes of one instance's planar X copies (all planes) for `precision`.
 size_t tc_batch_plane_bytes(int n, int s, int K, int precision);
-// Fill `pl` (plane pointers carved from `base`) and `maps` for one instance of a batch.
-void tc_batch_instance(ts_op* op, int precision, const float2* Xh, void* base, BTcPlanes* pl, TcMaps* maps);
+// Fill `pl` (plane pointers carved from `base`) and `maps` (column tile bn) for one instance of a batch.
+void tc_batch_instance(ts_op* op, int precision, const float2* Xh, void* base, BTcPlanes* pl, TcMaps* maps, int bn);
 // Load the batched kernels and set their attributes (before any capture that records them).
 void tc_batch_preload(int precision);
-// Planar copies (planes work list) then the products (tiles work list) of the active instances.
-void tc_batch_products(int precision, const BTcPlanes* planes, const int4* pitems, int npitems, const TcMaps* maps,
-                       const BTcInst* inst, const int* active, const int4* items, int nitems, int* err,
-                       cudaStream_t st);
+// Planar copies (planes work list) then the products (tiles work list, column tile bn) of the
+// active instances.
+void tc_batch_products(int precision, int bn, const BTcPlanes* planes, const int4* pitems, int npitems,
+                       const TcMaps* maps, const BTcInst* inst, const int* active, const int4* items, int nitems,
+                       int* err, cudaStream_t st);
 
 void tc_prepare(ts_op* op, int precision, cudaStream_t st);
 // Yh (float2, K slices of column-major n x s) = A_k X_k - X_k B_k on the tensor cores, from the
