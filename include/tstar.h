@@ -242,6 +242,16 @@ ts_status ts_t_bartels_stewart(ts_ctx* ctx, const double* A, int n, const double
  * end of a buffer.  Synchronises the device.  A debugging and testing aid. */
 ts_status ts_workspace_check(ts_ctx* ctx);
 
+/* Launch shapes chosen by the autotuner (no counterpart in the paper: the column-tile width of the
+ * tcgen05 slice products, timed over its candidates on the first call of each shape and precision,
+ * then cached in the context; with the environment variable TSTAR_TUNE_CACHE naming a file, also
+ * read from and appended to that file, per device).  Writes the context's entries as
+ * "<key> <value>\n" lines, NUL-terminated, into `buf` (host memory of `cap` bytes; nothing is
+ * written if buf is NULL or cap is 0) and stores the bytes needed, terminator included, in
+ * *needed.  TS_ERR_ARG if ctx or needed is NULL; a short buffer is not an error (the text is cut
+ * and still NUL-terminated).  No device work. */
+ts_status ts_tune_entries(ts_ctx* ctx, char* buf, size_t cap, size_t* needed);
+
 /* Kernel statistics, for measurement.  Launch counts are process-wide (every libtstar kernel
  * launch on any context); kernel timings are per context and only collected while enabled,
  * by CUDA events recorded on the launching stream around each timed launch. */

@@ -87,6 +87,7 @@ _SIGNATURES = {
                               ctypes.POINTER(_i), _vp]),
     "ts_tstar_noalloc": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp]),
     "ts_workspace_check": (_i, [_vp]),
+    "ts_tune_entries": (_i, [_vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "ts_stats_enable": (_i, [_vp, _i]),
     "ts_stats_get": (_i, [_vp, ctypes.POINTER(Stats)]),
     "ts_stats_reset": (_i, [_vp]),
@@ -133,6 +134,12 @@ class Context:
             raise TstarError(st, "ts_create failed")
         self.device = device
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def close(self):
         if self._h:
             lib().ts_destroy(self._h)
@@ -152,6 +159,18 @@ class Context:
     def workspace_check(self):
         """Raise TstarError if any workspace buffer was written past its end."""
         self._check(lib().ts_workspace_check(self._h), "ts_workspace_check")
+
+    def tune_entries(self) -> dict:
+        """The autotuner's choices in this context, {key: value} (ts_tune_entries)."""
+        need = ctypes.c_size_t(0)
+        self._check(lib().ts_tune_entries(self._h, None, 0, ctypes.byref(need)), "ts_tune_entries")
+        buf = ctypes.create_string_buffer(need.value)
+        self._check(lib().ts_tune_entries(self._h, buf, need.value, ctypes.byref(need)), "ts_tune_entries")
+        out = {}
+        for line in buf.value.decode().splitlines():
+            k, v = line.rsplit(" ", 1)
+            out[k] = int(v)
+        return out
 
     # --- statistics ---------------------------------------------------------------------------
     def stats_enable(self, enable: bool = True):

@@ -2,6 +2,7 @@
 // ts_tstar (Definition 2.1 via Algorithm 1) and ts_sylv_apply (Eq. (2)).
 #include <cstring>
 #include <cstdio>
+#include <algorithm>
 #include "internal.cuh"
 #include "apply.cuh"
 #include "tc.cuh"
@@ -523,6 +524,21 @@ ts_status ts_workspace_check(ts_ctx* ctx) {
   if (!bad.empty()) {
     ctx->err = "workspace buffer written past its end: " + bad;
     return TS_ERR_CORRUPTION;
+  }
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
+ts_status ts_tune_entries(ts_ctx* ctx, char* buf, size_t cap, size_t* needed) {
+  if (!ctx || !needed) return TS_ERR_ARG;
+  TS_API_BEGIN
+  std::string text;
+  for (const auto& kv : ctx->tune) text += kv.first + " " + std::to_string(kv.second) + "\n";
+  *needed = text.size() + 1;
+  if (buf && cap > 0) {
+    const size_t m = std::min(cap - 1, text.size());
+    std::memcpy(buf, text.data(), m);
+    buf[m] = '\0';
   }
   return TS_OK;
   TS_API_END(ctx)

@@ -101,6 +101,7 @@ struct ts_ctx {
   cudaStream_t bstream = nullptr;  // private stream of the batched solver (graph capture)
   std::vector<cudaStream_t> side;  // side streams of the batched solver's parallel branches
   std::map<std::string, int> tune; // launch shapes chosen by the autotuner (tune.cuh), by problem key
+  bool tune_loaded = false;        // the on-disk tuning cache (TSTAR_TUNE_CACHE) has been read
   int f64_engine = 0;              // how the current call computes FP64 applications (ts_fp64_engine)
   int oz_digits = 6;               // digits per value of the emulated FP64 product
   ts::KernelTimer timer;

@@ -1,0 +1,117 @@
+"""The autotuner of the tcgen05 column tile: its choices are cached per context, persist through
+the TSTAR_TUNE_CACHE file, and do not change results (every output entry accumulates the same
+products in the same order whatever the tile width)."""
+import numpy as np
+import pytest
+
+from oracle import krylov as kr
+from paper_2405_09233_gb300 import inputs
+from tests.gpu_helpers import to_dev, from_dev
+
+pytestmark = pytest.mark.gpu
+
+PREC_CODE = {"mixed_tf32": 2, "mixed_bf16": 3, "mixed_tf32x3": 4}
+
+
+def _apply(ctx, shape, prec):
+    import torch
+    n, s, p = shape
+    pr = inputs.dense_problem(n, s, p, seed=11 + n)
+    X32 = inputs.random_tensor((n, s, p), seed=12).astype(np.float32)
+    op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
+    Y = from_dev(ctx.sylv_apply_lowp(op, torch.from_numpy(inputs.to_device_layout(X32)).cuda(), prec))
+    op.close()
+    return Y
+
+
+def _key(shape, prec):
+    n, s, p = shape
+    return f"tc:{n}x{s}x{p // 2 + 1}:{PREC_CODE[prec]}"
+
+
+def _lines(path):
+    return [ln for ln in path.read_text().splitlines() if ln.strip()] if path.exists() else []
+
+
+def test_choice_cached_and_persisted(tmp_path, monkeypatch):
+    from paper_2405_09233_gb300 import Context
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("TSTAR_TUNE_CACHE", str(cache))
+    shape, prec = (300, 200, 8), "mixed_bf16"
+    with Context(0) as ctx:
+        _apply(ctx, shape, prec)
+        ent = ctx.tune_entries()
+        assert ent[_key(shape, prec)] in (64, 128, 256)
+        lines = _lines(cache)
+        assert len(lines) == 1 and lines[0].split()[1:] == [_key(shape, prec), str(ent[_key(shape, prec)])]
+        _apply(ctx, shape, prec)                          # cached in the context: nothing retimed
+        assert len(_lines(cache)) == 1
+    with Context(0) as ctx:                               # a new context reads the file
+        _apply(ctx, shape, prec)
+        assert ctx.tune_entries()[_key(shape, prec)] == int(lines[0].split()[2])
+        assert len(_lines(cache)) == 1
+
+
+def _device_tag(tmp_path, monkeypatch):
+    from paper_2405_09233_gb300 import Context
+    probe = tmp_path / "probe.txt"
+    monkeypatch.setenv("TSTAR_TUNE_CACHE", str(probe))
+    with Context(0) as ctx:
+        _apply(ctx, (64, 200, 2), "mixed_bf16")
+    return _lines(probe)[0].split()[0]
+
+
+@pytest.mark.parametrize("prec", ["mixed_bf16", "mixed_tf32x3"])
+def test_tile_width_does_not_change_result(tmp_path, monkeypatch, prec):
+    """Force each candidate width through the cache file: the products agree bit for bit."""
+    from paper_2405_09233_gb300 import Context
+    tag = _device_tag(tmp_path, monkeypatch)
+    shape = (200, 300, 6)                                 # ragged in both tile directions
+    outs = {}
+    for bn in (64, 128, 256):
+        cache = tmp_path / f"forced_{bn}.txt"
+        cache.write_text(f"{tag} {_key(shape, prec)} {bn}\n")
+        monkeypatch.setenv("TSTAR_TUNE_CACHE", str(cache))
+        with Context(0) as ctx:
+            outs[bn] = _apply(ctx, shape, prec)
+            assert ctx.tune_entries()[_key(shape, prec)] == bn
+        assert len(_lines(cache)) == 1                    # nothing was tuned
+    assert np.isfinite(outs[64]).all()
+    for bn in (128, 256):
+        assert np.array_equal(outs[64].view(np.uint32), outs[bn].view(np.uint32)), bn
+
+
+def test_malformed_cache_lines_ignored(tmp_path, monkeypatch):
+    from paper_2405_09233_gb300 import Context
+    tag = _device_tag(tmp_path, monkeypatch)
+    shape, prec = (130, 70, 8), "mixed_tf32"
+    cache = tmp_path / "bad.txt"
+    cache.write_text("garbage\n\n"
+                     f"{tag} {_key(shape, prec)} notanumber\n"
+                     f"other_device {_key(shape, prec)} 64\n"
+                     f"{tag} {_key(shape, prec)} 96\n")       # not a candidate: tuned afresh
+    monkeypatch.setenv("TSTAR_TUNE_CACHE", str(cache))
+    with Context(0) as ctx:
+        _apply(ctx, shape, prec)
+        assert ctx.tune_entries()[_key(shape, prec)] in (64, 128)
+    assert _lines(cache)[-1].split()[:2] == [tag, _key(shape, prec)]
+
+
+def test_batched_tile_tuned(tmp_path, monkeypatch):
+    import torch
+    from paper_2405_09233_gb300 import Context
+    monkeypatch.setenv("TSTAR_TUNE_CACHE", str(tmp_path / "b.txt"))
+    shapes = [(96, 40, 4), (130, 150, 8), (64, 64, 2)]
+    with Context(0) as ctx:
+        ops, Cs, Xs = [], [], []
+        for i, (n, s, p) in enumerate(shapes):
+            pr = inputs.dense_problem(n, s, p, seed=40 + i)
+            ops.append(ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B)))
+            Cs.append(to_dev(kr.sylv_apply(pr.A, pr.B, pr.Xstar)))
+            Xs.append(torch.zeros((p, s, n), dtype=torch.float64, device="cuda"))
+        st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, precision="mixed_bf16", engine="ozaki")
+        assert st == 0 and all(x == 0 for x in sts)
+        btc = [v for k, v in ctx.tune_entries().items() if k.startswith("btc:")]
+        assert len(btc) == 1 and btc[0] in (64, 128)
+        for op in ops:
+            op.close()
