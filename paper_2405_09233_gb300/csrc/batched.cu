@@ -130,8 +130,7 @@ __global__ void __launch_bounds__(256) k_b_dot(BDev d, const T* __restrict__ x, 
     T a[4], c[4];
     ld4(x, p0 + q, a);
     ld4(y, p0 + q, c);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) acc += (double)a[t] * (double)c[t];
+    acc_pack(acc, a, c);   // an FP32 pack is summed in FP32 first (pack.cuh)
   }
   for (long long e = e0 + 4 * n4 + threadIdx.x; e < e1; e += blockDim.x) acc += (double)x[e] * (double)y[e];
   const double t = block_sum(acc);
@@ -176,9 +175,10 @@ __global__ void __launch_bounds__(256) k_b_mgs(BDev d, T* __restrict__ W, const 
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       w[t] = w[t] - hT * v[t];
-      acc += (double)(Vn ? o[t] : w[t]) * (double)w[t];
+      if (!Vn) o[t] = w[t];
     }
     st4(W, p0 + q, w);
+    acc_pack(acc, o, w);
   }
   for (long long e = e0 + 4 * n4 + threadIdx.x; e < e1; e += blockDim.x) {
     const T w = W[e] - hT * Vi[e];
@@ -206,17 +206,18 @@ __global__ void __launch_bounds__(256) k_b_axpy(BDev d, const T* __restrict__ V)
   const int i = d.nb_inst[blockIdx.x];
   if (!d.cyc[i]) return;
   const BInst& in = d.inst[i];
-  __shared__ double ys[256];
+  // an FP32 basis is combined in FP32 and added to X once (no per-term conversion, pack.cuh)
+  __shared__ T ys[256];
   StLayout L{d.m};
   const int k = (int)d.sc[16 * i + SC_K];
-  for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = d.state[i * d.stride + L.y() + q];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = (T)d.state[i * d.stride + L.y() + q];
   __syncthreads();
   const long long l0 = d.nb_off[blockIdx.x];
   const long long l1 = min(in.N, l0 + kChunk);
   for (long long l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
-    double acc = 0.0;
-    for (int q = 0; q < k; ++q) acc = fma(ys[q], (double)V[(long long)q * d.totN + in.offN + l], acc);
-    in.X[l] += acc;
+    T acc = 0;
+    for (int q = 0; q < k; ++q) acc = fma_t(ys[q], V[(long long)q * d.totN + in.offN + l], acc);
+    in.X[l] += (double)acc;
   }
 }
 

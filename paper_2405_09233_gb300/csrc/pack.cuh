@@ -21,4 +21,26 @@ __device__ __forceinline__ void st4(double* p, long long e, const double (&v)[4]
   reinterpret_cast<double2*>(p)[2 * e + 1] = make_double2(v[2], v[3]);
 }
 
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+// Dot products of packs.  An FP64 pack accumulates in FP64 term by term.  An FP32 pack sums its
+// products in FP32 (pack_dot) and the caller adds that sum to its FP64 accumulator once: GB300
+// executes FP64 arithmetic, and conversions between FP32 and FP64, at a small fraction of its FP32
+// rate, so a conversion and a DFMA per element left the FP32 streaming kernels bound by the FP64
+// pipe instead of by HBM.  The FP32 partial adds at most ~4u32 of the pack's absolute products,
+// the size of the rounding its FP32 operands already carry.
+__device__ __forceinline__ float pack_dot(const float (&a)[4], const float (&b)[4], float f = 0.f) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) f = fmaf(a[c], b[c], f);
+  return f;
+}
+__device__ __forceinline__ void acc_pack(double& acc, const float (&a)[4], const float (&b)[4]) {
+  acc += (double)pack_dot(a, b);
+}
+__device__ __forceinline__ void acc_pack(double& acc, const double (&a)[4], const double (&b)[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc += a[c] * b[c];
+}
+
 }  // namespace ts

@@ -3,12 +3,14 @@
 // (*) product of §3.1.  All are HBM-bound: grid-stride loops over packs of 4 elements (16- or
 // 32-byte loads, two packs in flight per thread) when N is a multiple of 4 and the tensors are
 // 16-byte aligned, scalar loops otherwise; a fixed grid of kRedBlocks blocks wherever a sum is
-// formed; FP64 accumulation whatever the storage type.
+// formed; FP64 accumulation across packs whatever the storage type (an FP32 pack sums its own few
+// products in FP32 first, see pack.cuh).
 //
 // Reductions never use atomics: each block writes one partial sum, and whoever needs the total
 // (the next MGS pass, the Givens kernel) adds the kRedBlocks partials in a fixed order.  The
 // results are therefore bitwise reproducible from run to run.
 #include <initializer_list>
+#include <type_traits>
 #include <cstdint>
 #include "internal.cuh"
 #include "reduce.cuh"
@@ -44,11 +46,13 @@ __global__ void __launch_bounds__(kRedThreads) k_dot4(const T* __restrict__ x, c
       ld4(x, e1, a1);
       ld4(y, e1, b1);
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc += (double)a0[c] * (double)b0[c];
-    if (two) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc += (double)a1[c] * (double)b1[c];
+    if constexpr (sizeof(T) == 4) {   // both packs summed in FP32, one FP64 add (pack.cuh)
+      float f = pack_dot(a0, b0);
+      if (two) f = pack_dot(a1, b1, f);
+      acc += (double)f;
+    } else {
+      acc_pack(acc, a0, b0);
+      if (two) acc_pack(acc, a1, b1);
     }
   }
   const double tot = block_sum(acc);
@@ -103,16 +107,24 @@ __global__ void __launch_bounds__(kRedThreads) k_mgs4(T* __restrict__ W, const T
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       w0[c] = w0[c] - hT * v0[c];
-      acc += (double)(Vn ? o0[c] : w0[c]) * (double)w0[c];
+      if (!Vn) o0[c] = w0[c];
     }
     st4(W, e, w0);
     if (two) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         w1[c] = w1[c] - hT * v1[c];
-        acc += (double)(Vn ? o1[c] : w1[c]) * (double)w1[c];
+        if (!Vn) o1[c] = w1[c];
       }
       st4(W, e1, w1);
+    }
+    if constexpr (sizeof(T) == 4) {   // both packs summed in FP32, one FP64 add (pack.cuh)
+      float f = pack_dot(o0, w0);
+      if (two) f = pack_dot(o1, w1, f);
+      acc += (double)f;
+    } else {
+      acc_pack(acc, o0, w0);
+      if (two) acc_pack(acc, o1, w1);
     }
   }
   const double tot = block_sum(acc);
@@ -131,12 +143,16 @@ template <typename T, typename U>
 __global__ void k_scale4(const T* __restrict__ x, U* __restrict__ y, long long N4, const double* __restrict__ s) {
   const double sc = *s;
   const long long stride = (long long)gridDim.x * blockDim.x;
+  const float scf = (float)sc;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N4; e += stride) {
     T a[4];
     U b[4];
     ld4(x, e, a);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) b[c] = (U)((double)a[c] * sc);
+    for (int c = 0; c < 4; ++c) {
+      if constexpr (sizeof(U) == 4) b[c] = (float)a[c] * scf;   // FP32 result: FP32 product
+      else b[c] = (U)((double)a[c] * sc);
+    }
     st4(y, e, b);
   }
 }
@@ -162,23 +178,30 @@ template <typename T, typename U>
 __global__ void k_multi_axpy4(U* __restrict__ X, const T* __restrict__ V, long long ldv, long long N4,
                               const double* __restrict__ y, int k, double alpha_scale,
                               const double* __restrict__ alpha_dev) {
-  __shared__ double ys[256];
+  // FP32 basis: the combination is formed in FP32 (coefficients rounded to FP32) and added to X
+  // once, so no element costs a conversion or a DFMA per basis vector (pack.cuh); an FP64 basis
+  // accumulates in FP64.
+  using Acc = typename std::conditional<sizeof(T) == 4, float, double>::type;
+  __shared__ Acc ys[256];
   const double alpha = alpha_scale * (alpha_dev ? *alpha_dev : 1.0);
-  for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) ys[i] = y[i] * alpha;
+  for (int i = threadIdx.x; i < k && i < 256; i += blockDim.x) ys[i] = (Acc)(y[i] * alpha);
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N4; e += stride) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    Acc acc[4] = {0, 0, 0, 0};
     for (int i = 0; i < k; ++i) {
       T v[4];
       ld4(V + (long long)i * ldv, e, v);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c] = fma(ys[i], (double)v[c], acc[c]);
+      for (int c = 0; c < 4; ++c) acc[c] = fma_t(ys[i], (Acc)v[c], acc[c]);
     }
     U x[4];
     ld4(X, e, x);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) x[c] = (U)((double)x[c] + acc[c]);
+    for (int c = 0; c < 4; ++c) {
+      if constexpr (sizeof(U) == 4) x[c] = x[c] + (float)acc[c];
+      else x[c] = (U)((double)x[c] + (double)acc[c]);
+    }
     st4(X, e, x);
   }
 }
