@@ -328,22 +328,26 @@ __global__ void k_oz_maxabs(const double2* __restrict__ Z, long long T, unsigned
   if (gate && *gate == 0) return;
   const int k = blockIdx.y;
   const double2* Zk = Z + (long long)k * T;
-  double m = 0.0;
+  // Non-negative doubles order like their bit patterns read as unsigned integers (and every
+  // non-finite pattern lies above that of +Inf), so the maximum is taken on integer ALUs: FP64
+  // compares would make this pass FP64-pipe bound on GB300.
+  constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+  unsigned long long m = 0;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < T; e += (long long)gridDim.x * blockDim.x) {
     const double2 v = Zk[e];
-    const double a = fabs(v.x), b = fabs(v.y);
-    if (!(a <= DBL_MAX) || !(b <= DBL_MAX)) m = __longlong_as_double(0x7ff0000000000000ll);
-    else m = fmax(m, fmax(a, b));
+    const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & kAbs;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & kAbs;
+    m = max(m, max(a, b));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  __shared__ double wm[32];
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ unsigned long long wm[32];
   if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, wm[w]);
-    atomicMax(out + k, (unsigned long long)__double_as_longlong(t));
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = max(t, wm[w]);
+    atomicMax(out + k, t >= kInf ? kInf : t);   // any non-finite entry reads as +Inf
   }
 }
 
