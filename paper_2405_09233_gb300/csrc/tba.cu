@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(256) k_gram(const C2* __restrict__ V, const C2
 #pragma unroll
         for (int y = 0; y < 4; ++y)
           if (a0 + x < s && b0 + y < s)
-            Pk[(a0 + x) + s * (b0 + y)] =
-                make_double2((double)T1[x][y] - (double)T3[x][y], (double)T1[x][y] + (double)T2[x][y]);
+            Pk[(a0 + x) + s * (b0 + y)] =   // combined in R, one conversion per part
+                make_double2((double)(T1[x][y] - T3[x][y]), (double)(T1[x][y] + T2[x][y]));
     }
     return;
   }
@@ -359,13 +359,37 @@ __global__ void __launch_bounds__(256) k_rows_mm(const Cin* In, Cout* Out, const
       for (int c = 0; c < kRowCols; ++c) {
         const int j = c0 + c;
         if (j < c1) {
-          double2 v = make_double2(alpha * (double)(T1[c] - T3[c]), alpha * (double)(T1[c] + T2[c]));
-          if (accumulate) {
-            const double2 o = widen(Out[ro + j]);
-            v.x += o.x;
-            v.y += o.y;
+          if constexpr (sizeof(R) == 4) {
+            // FP32 products: scale in FP32 and convert at most once, since GB300's FP64 and
+            // conversion rate would otherwise make this epilogue cost more than the s-term loop
+            const float al = (float)alpha;
+            const float vr = al * (T1[c] - T3[c]), vi = al * (T1[c] + T2[c]);
+            if constexpr (sizeof(Cout) == 8) {
+              float2 v = make_float2(vr, vi);
+              if (accumulate) {
+                const float2 o = Out[ro + j];
+                v.x += o.x;
+                v.y += o.y;
+              }
+              Out[ro + j] = v;
+            } else {
+              double2 v = make_double2((double)vr, (double)vi);
+              if (accumulate) {
+                const double2 o = widen(Out[ro + j]);
+                v.x += o.x;
+                v.y += o.y;
+              }
+              Out[ro + j] = to_c2(v, (Cout*)nullptr);
+            }
+          } else {
+            double2 v = make_double2(alpha * (double)(T1[c] - T3[c]), alpha * (double)(T1[c] + T2[c]));
+            if (accumulate) {
+              const double2 o = widen(Out[ro + j]);
+              v.x += o.x;
+              v.y += o.y;
+            }
+            Out[ro + j] = to_c2(v, (Cout*)nullptr);
           }
-          Out[ro + j] = to_c2(v, (Cout*)nullptr);
         }
       }
     }
