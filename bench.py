@@ -389,19 +389,25 @@ def main():
     # end to end through the C ABI with host buffers (copies inside the timed region)
     C_h = Cd.cpu().pin_memory()
     X_h = torch.zeros_like(C_h).pin_memory()
-    e2e_times = []
+    e2e_times, e2e_parts = [], []
     for _ in range(max(a.e2e_steps, 0)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         op = ctx.op_create_dense(A_h, B_h)
+        t1 = time.perf_counter()
         X_h.zero_()
         r = ctx.tgmres_solve(op, C_h, X_h, restart=m, tol=1e-10, precision=a.precision, engine=a.engine)
+        t2 = time.perf_counter()
         op.close()
-        e2e_times.append(time.perf_counter() - t0)
+        t3 = time.perf_counter()
+        e2e_times.append(t3 - t0)
+        e2e_parts.append((t1 - t0, t2 - t1, t3 - t2))
         assert r.status == 0, r
     e2e = {"value": unknowns * world / statistics.median(e2e_times) if e2e_times else None, "unit": UNIT,
            "h2d_bytes_per_step": 8 * (n * n * p + s * s * p + 2 * n * s * p),
            "d2h_bytes_per_step": 8 * n * s * p}
+    if e2e_parts:   # host-clock split of the last end-to-end step: operator setup, solve, release
+        e2e["split_ms"] = dict(zip(("op_create", "solve", "op_destroy"), (round(x * 1e3, 3) for x in e2e_parts[-1])))
 
     variants = {}
     primary = a.precision + ("" if a.engine == "dfma" else "@" + a.engine)

@@ -3,6 +3,7 @@
 #include <cstring>
 #include <cstdio>
 #include <algorithm>
+#include <mutex>
 #include "internal.cuh"
 #include "apply.cuh"
 #include "tc.cuh"
@@ -47,6 +48,54 @@ void Workspace::release_all() {
   for (auto& kv : bufs)
     if (kv.second.ptr) cudaFree(kv.second.ptr);
   bufs.clear();
+}
+
+namespace {
+struct OpPool {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;
+};
+std::mutex g_op_pool_mu;
+OpPool g_op_pool[64];
+
+OpPool& op_pool() {
+  int dev = 0;
+  TS_CUDA(cudaGetDevice(&dev));
+  TS_REQUIRE(dev >= 0 && dev < 64, "op_malloc: device index out of range");
+  std::lock_guard<std::mutex> lock(g_op_pool_mu);
+  OpPool& q = g_op_pool[dev];
+  if (!q.pool) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    TS_CUDA(cudaMemPoolCreate(&q.pool, &props));
+    unsigned long long keep = kOpPoolKeepBytes;
+    TS_CUDA(cudaMemPoolSetAttribute(q.pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    TS_CUDA(cudaStreamCreateWithFlags(&q.stream, cudaStreamNonBlocking));
+  }
+  return q;
+}
+}  // namespace
+
+void* op_malloc(size_t bytes) {
+  OpPool& q = op_pool();
+  void* p = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, q.pool, q.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(q.stream);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Error{TS_ERR_NOMEM, "operator buffer of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e)};
+  }
+  return p;
+}
+
+void op_free(void* p) {
+  if (!p) return;
+  OpPool& q = op_pool();
+  cudaDeviceSynchronize();
+  cudaFreeAsync(p, q.stream);
 }
 
 std::atomic<long long> g_launches{0};
@@ -168,8 +217,8 @@ void StagedOut::finish() {
 // Forward DFT of the operator tensors once (§8 setup: A_k, B_k for k <= p/2).
 static void op_prepare(ts_op* op, const double* A, const double* B, cudaStream_t st) {
   const int n = op->n, s = op->s, p = op->p, K = op->K;
-  TS_CUDA(cudaMalloc(&op->Ah, sizeof(double2) * (size_t)K * n * n));
-  TS_CUDA(cudaMalloc(&op->Bh, sizeof(double2) * (size_t)K * s * s));
+  op_alloc(op->Ah, sizeof(double2) * (size_t)K * n * n);
+  op_alloc(op->Bh, sizeof(double2) * (size_t)K * s * s);
   StagedIn a(op->ctx, "stage_A", A, (size_t)n * n * p, st);
   StagedIn b(op->ctx, "stage_B", B, (size_t)s * s * p, st);
   rfft_tube<double, double2>(a.dev, op->Ah, (long long)n * n, p, st);
@@ -361,10 +410,10 @@ ts_status ts_op_create_dense(ts_ctx* ctx, const double* A, int n, const double* 
 void ts_op_destroy(ts_op* op) {
   if (!op) return;
   if (op->ctx) cudaSetDevice(op->ctx->device);
-  cudaFree(op->Ah);
-  cudaFree(op->Bh);
-  cudaFree(op->Ah32);
-  cudaFree(op->Bh32);
+  op_free(op->Ah);
+  op_free(op->Bh);
+  op_free(op->Ah32);
+  op_free(op->Bh32);
   if (op->oz) {
     op->oz->release();
     delete op->oz;
@@ -377,9 +426,9 @@ void ts_op_destroy(ts_op* op) {
     op->sp->release();
     delete op->sp;
   }
-  cudaFree(op->Bh_row);
-  cudaFree(op->schurT);
-  cudaFree(op->schurQ);
+  op_free(op->Bh_row);
+  op_free(op->schurT);
+  op_free(op->schurQ);
   delete op;
 }
 
@@ -447,7 +496,7 @@ ts_status ts_op_create_csr(ts_ctx* ctx, int n, int p, const int* rowptr, const i
     op->s = s;
     op->p = p;
     op->K = num_slices(p);
-    TS_CUDA(cudaMalloc(&op->Bh, sizeof(double2) * (size_t)op->K * s * s));
+    op_alloc(op->Bh, sizeof(double2) * (size_t)op->K * s * s);
     StagedIn b(ctx, "stage_B", B, (size_t)s * s * p, st);
     rfft_tube<double, double2>(b.dev, op->Bh, (long long)s * s, p, st);
     op_prepare_csr(op, rowptr, col, val, st);

@@ -466,13 +466,13 @@ void split(const double2* src, long long sstride, int R, int C, int K, const int
 }  // namespace
 
 void OzOperands::release() {
-  cudaFree(a_re);
-  cudaFree(a_im);
-  cudaFree(b_re);
-  cudaFree(b_im);
-  cudaFree(b_nre);
-  cudaFree(Eop);
-  cudaFree(mx);
+  op_free(a_re);
+  op_free(a_im);
+  op_free(b_re);
+  op_free(b_im);
+  op_free(b_nre);
+  op_free(Eop);
+  op_free(mx);
   a_re = a_im = b_re = b_im = b_nre = nullptr;
   Eop = nullptr;
   mx = nullptr;
@@ -488,13 +488,13 @@ void oz_prepare(ts_op* op, int S, cudaStream_t st) {
   t->ldn = round_up(n, 64);
   t->lds = round_up(s, 64);
   const size_t na = (size_t)S * K * n * t->ldn * 2, nb = (size_t)S * K * s * t->lds * 2;
-  TS_CUDA(cudaMalloc(&t->a_re, na));
-  TS_CUDA(cudaMalloc(&t->a_im, na));
-  TS_CUDA(cudaMalloc(&t->b_re, nb));
-  TS_CUDA(cudaMalloc(&t->b_im, nb));
-  TS_CUDA(cudaMalloc(&t->b_nre, nb));
-  TS_CUDA(cudaMalloc(&t->Eop, sizeof(int) * K));
-  TS_CUDA(cudaMalloc(&t->mx, sizeof(unsigned long long) * K));
+  op_alloc(t->a_re, na);
+  op_alloc(t->a_im, na);
+  op_alloc(t->b_re, nb);
+  op_alloc(t->b_im, nb);
+  op_alloc(t->b_nre, nb);
+  op_alloc(t->Eop, sizeof(int) * K);
+  op_alloc(t->mx, sizeof(unsigned long long) * K);
   // A_k and B_k share one exponent per slice, so both products of Eq. (2) land on one fixed point.
   unsigned long long* mxb = t->mx;
   TS_CUDA(cudaMemsetAsync(mxb, 0, sizeof(unsigned long long) * K, st));

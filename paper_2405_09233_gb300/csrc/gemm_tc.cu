@@ -567,15 +567,15 @@ void tc_prepare(ts_op* op, int precision, cudaStream_t st) {
   t->ldn = round_up(op->n, 64);
   t->lds = round_up(op->s, 64);
   const size_t na = (size_t)op->K * op->n * t->ldn * esz, nb = (size_t)op->K * op->s * t->lds * esz;
-  TS_CUDA(cudaMalloc(&t->a_re, na));
-  TS_CUDA(cudaMalloc(&t->a_im, na));
-  TS_CUDA(cudaMalloc(&t->b_re, nb));
-  TS_CUDA(cudaMalloc(&t->b_im, nb));
+  op_alloc(t->a_re, na);
+  op_alloc(t->a_im, na);
+  op_alloc(t->b_re, nb);
+  op_alloc(t->b_im, nb);
   if (split) {
-    TS_CUDA(cudaMalloc(&t->a_re_lo, na));
-    TS_CUDA(cudaMalloc(&t->a_im_lo, na));
-    TS_CUDA(cudaMalloc(&t->b_re_lo, nb));
-    TS_CUDA(cudaMalloc(&t->b_im_lo, nb));
+    op_alloc(t->a_re_lo, na);
+    op_alloc(t->a_im_lo, na);
+    op_alloc(t->b_re_lo, nb);
+    op_alloc(t->b_im_lo, nb);
   }
   if (esz == 2) prepare_operator<__nv_bfloat16>(op, *t, st);
   else prepare_operator<float>(op, *t, st);
@@ -763,14 +763,14 @@ double gemm_flops_tc(int n, int s, int K, int nyq) {
 }
 
 void TcOperands::release() {
-  cudaFree(a_re);
-  cudaFree(a_im);
-  cudaFree(b_re);
-  cudaFree(b_im);
-  cudaFree(a_re_lo);
-  cudaFree(a_im_lo);
-  cudaFree(b_re_lo);
-  cudaFree(b_im_lo);
+  op_free(a_re);
+  op_free(a_im);
+  op_free(b_re);
+  op_free(b_im);
+  op_free(a_re_lo);
+  op_free(a_im_lo);
+  op_free(b_re_lo);
+  op_free(b_im_lo);
   a_re = a_im = b_re = b_im = nullptr;
   a_re_lo = a_im_lo = b_re_lo = b_im_lo = nullptr;
 }

@@ -47,6 +47,22 @@ struct Workspace {
 };
 
 // ----------------------------------------------------------------------------------------------
+// Operator buffers (Fourier slices, low-precision and digit planes, Schur factors, sparse pattern):
+// taken from a process-wide stream-ordered memory pool of the current device that keeps up to
+// kOpPoolKeepBytes of freed memory reserved, so creating and destroying operators of recurring
+// shapes does not map and unmap device memory every time.  op_malloc returns memory usable on
+// every stream (like cudaMalloc) and throws TS_ERR_NOMEM on failure; op_free synchronises the
+// device first (like cudaFree), so no pending kernel still reads the buffer; nullptr is ignored.
+// ----------------------------------------------------------------------------------------------
+constexpr unsigned long long kOpPoolKeepBytes = 16ull << 30;
+void* op_malloc(size_t bytes);
+void op_free(void* p);
+template <typename T>
+inline void op_alloc(T*& p, size_t bytes) {
+  p = static_cast<T*>(op_malloc(bytes));
+}
+
+// ----------------------------------------------------------------------------------------------
 // Reductions: a fixed grid so that the summation order (hence the result) is reproducible.
 // ----------------------------------------------------------------------------------------------
 constexpr int kRedBlocks = 608;   // 4 x 152 SMs

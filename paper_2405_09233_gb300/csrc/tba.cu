@@ -513,10 +513,10 @@ struct TbaWork {
 }  // namespace
 
 void SparseOp::release() {
-  cudaFree(rowptr);
-  cudaFree(col);
-  cudaFree(vals);
-  cudaFree(vals32);
+  op_free(rowptr);
+  op_free(col);
+  op_free(vals);
+  op_free(vals32);
   rowptr = col = nullptr;
   vals = nullptr;
   vals32 = nullptr;
@@ -525,8 +525,8 @@ void SparseOp::release() {
 void ensure_b_schur(ts_ctx* ctx, ts_op* op, cudaStream_t st) {
   if (op->schurT) return;
   const int s = op->s, K = op->K;
-  TS_CUDA(cudaMalloc(&op->schurT, sizeof(double2) * (size_t)K * s * s));
-  TS_CUDA(cudaMalloc(&op->schurQ, sizeof(double2) * (size_t)K * s * s));
+  op_alloc(op->schurT, sizeof(double2) * (size_t)K * s * s);
+  op_alloc(op->schurQ, sizeof(double2) * (size_t)K * s * s);
   TS_CUDA(cudaMemcpyAsync(op->schurT, op->Bh, sizeof(double2) * (size_t)K * s * s, cudaMemcpyDeviceToDevice, st));
   int* err = static_cast<int*>(ctx->ws.get("schur_err", sizeof(int)));
   TS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -535,8 +535,8 @@ void ensure_b_schur(ts_ctx* ctx, ts_op* op, cudaStream_t st) {
   TS_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TS_CUDA(cudaStreamSynchronize(st));
   if (e) {
-    cudaFree(op->schurT);
-    cudaFree(op->schurQ);
+    op_free(op->schurT);
+    op_free(op->schurQ);
     op->schurT = op->schurQ = nullptr;
     throw Error{TS_SINGULAR, "complex Schur iteration of B_k did not converge"};
   }
@@ -551,7 +551,7 @@ void rows_call_f32(ts_op* op, const float2* V, float2* Out, int n, int s, int K,
   if (op->sp) {
     SparseOp& sp = *op->sp;
     if (!sp.vals32) {
-      TS_CUDA(cudaMalloc(&sp.vals32, sizeof(float2) * (size_t)K * sp.nnz));
+      op_alloc(sp.vals32, sizeof(float2) * (size_t)K * sp.nnz);
       convert<double, float>(reinterpret_cast<const double*>(sp.vals), reinterpret_cast<float*>(sp.vals32),
                              2ll * K * sp.nnz, st);
     }
@@ -735,7 +735,7 @@ void from_rows(const double2* spec_rows, double* real, double2* tmp, int n, int 
 void ensure_brow(ts_op* op, cudaStream_t st) {
   if (op->Bh_row) return;
   const size_t b = sizeof(double2) * (size_t)op->K * op->s * op->s;
-  TS_CUDA(cudaMalloc(&op->Bh_row, b));
+  op_alloc(op->Bh_row, b);
   k_row_major_small<<<grid1d((long long)op->K * op->s * op->s), 256, 0, st>>>(op->Bh, op->Bh_row, op->s, op->K);
   count_launch();
   TS_CUDA(cudaGetLastError());
@@ -1037,9 +1037,9 @@ void op_prepare_csr(ts_op* op, const int* rowptr, const int* col, const double* 
   }
   op->sp = new SparseOp();
   op->sp->nnz = nnz;
-  TS_CUDA(cudaMalloc(&op->sp->rowptr, sizeof(int) * (n + 1)));
-  TS_CUDA(cudaMalloc(&op->sp->col, sizeof(int) * std::max(nnz, 1)));
-  TS_CUDA(cudaMalloc(&op->sp->vals, sizeof(double2) * (size_t)K * std::max(nnz, 1)));
+  op_alloc(op->sp->rowptr, sizeof(int) * (n + 1));
+  op_alloc(op->sp->col, sizeof(int) * std::max(nnz, 1));
+  op_alloc(op->sp->vals, sizeof(double2) * (size_t)K * std::max(nnz, 1));
   double* dval = (double*)op->ctx->ws.get("csr_stage_vals", sizeof(double) * (size_t)p * std::max(nnz, 1));
   TS_CUDA(cudaMemcpyAsync(op->sp->rowptr, urow.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
   if (nnz > 0) {
