@@ -86,16 +86,17 @@ TF32_OVER_BF16 = 1.1 / 2.25       # nominal dense tensor rates (PFLOP/s per GPU)
 FFMA_NOMINAL_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12   # 128 FP32 lanes/SM x 2 FLOP x 152 SMs x 2070 MHz
 
 
-def ozaki_roofline(flops_per_launch, avg_ms, sustained, share, digits=6):
+def ozaki_roofline(flops_per_launch, pair_flops_per_launch, avg_ms, sustained, share):
     """Emulated FP64 slice products: the tensor pipe executes S(S+1)/2 BF16 digit-pair products per
-    algorithmic FP64 product; achieved = those BF16 FLOPs / launch time (digit split included)."""
+    algorithmic FP64 product (S per launch: 6, or fewer for the early residuals of a mixed solve);
+    achieved = those BF16 FLOPs / launch time (digit split included)."""
     pk = peaks()
     peak = pk["bf16_sustained"] if sustained else pk["bf16_burst"]
-    pairs = digits * (digits + 1) // 2
-    achieved = pairs * flops_per_launch / (avg_ms * 1e-3) / 1e12
+    pairs = pair_flops_per_launch / max(flops_per_launch, 1e-30)
+    achieved = pair_flops_per_launch / (avg_ms * 1e-3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
-            "kernel": "k_oz_sylv (emulated FP64: %d BF16 digit-pair products on tcgen05)" % pairs,
+            "kernel": "k_oz_sylv (emulated FP64: %.1f BF16 digit-pair products per launch on tcgen05)" % pairs,
             "note": "peak: %s BF16 %s; FP64-equivalent rate %.2f TFLOP/s. Kernel share of the step: %.3f"
                     % (pk["source"], "sustained" if sustained else "burst",
                        flops_per_launch / (avg_ms * 1e-3) / 1e12, share)}
@@ -374,7 +375,8 @@ def main():
         roofline = gemm_roofline("fp64", "fp64", st.gemm_flops / max(st.gemm_launches, 1),
                                  st.gemm_ms / max(st.gemm_launches, 1), True, st.gemm_ms / step_ms_total)
     elif top == "oz":
-        roofline = ozaki_roofline(st.oz_flops / max(st.oz_launches, 1), st.oz_ms / max(st.oz_launches, 1),
+        roofline = ozaki_roofline(st.oz_flops / max(st.oz_launches, 1), st.oz_pair_flops / max(st.oz_launches, 1),
+                                  st.oz_ms / max(st.oz_launches, 1),
                                   True, st.oz_ms / step_ms_total)
     else:
         roofline = gemm_roofline("lowp", a.precision, st.lowp_flops / max(st.lowp_launches, 1),
@@ -714,7 +716,8 @@ def run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev):
     st = ctx.stats_get()
     ms = e0.elapsed_time(e1) / a.steps
     if a.precision == "fp64" and a.engine == "ozaki":
-        rf = ozaki_roofline(st.oz_flops / max(st.oz_launches, 1), st.oz_ms / max(st.oz_launches, 1), False,
+        rf = ozaki_roofline(st.oz_flops / max(st.oz_launches, 1), st.oz_pair_flops / max(st.oz_launches, 1),
+                                  st.oz_ms / max(st.oz_launches, 1), False,
                             st.oz_ms / (ms * a.steps))
     elif a.precision == "fp64":
         rf = gemm_roofline("fp64", "fp64", st.gemm_flops / max(st.gemm_launches, 1),

@@ -103,7 +103,14 @@ ts_status ts_sylv_apply(ts_ctx* ctx, const ts_op* op, const double* X, double* Y
 
 /* Y = M(X) as ts_sylv_apply, with the slice products on the emulated-FP64 tensor-core engine
  * (TS_ENGINE_OZAKI) and `digits` digits per value (3..8; 0 = 6).  Dense operators, p <= any.  The
- * first call with a digit count builds the operator's digit planes. */
+ * operator's digit planes are built on first use; an operator already holding more digits is used
+ * through its leading `digits` digits (an approximation as close as a `digits`-digit expansion,
+ * within 0.502 of the last kept digit's unit), a larger count rebuilds them.
+ *
+ * Mixed-precision solves on this engine with the default digit count (opts.ozaki_digits = 0) form
+ * each true residual with the fewest digits the next inner solve needs (at least 3), from the inner
+ * estimate of its norm, and form any residual that would end the solve again with all 6 digits; a
+ * residual that fails to halve turns this off for the rest of the solve. */
 ts_status ts_sylv_apply_ozaki(ts_ctx* ctx, const ts_op* op, int digits, const double* X, double* Y,
                               ts_stream stream);
 
@@ -272,6 +279,8 @@ typedef struct {
   long long tba_launches;  /* TBAS tubal Gram and block products (V^H W, W - V H), FP64 */
   double tba_ms;
   double tba_flops;        /* 8 n s^2 per complex slice product */
+  double oz_pair_flops;    /* BF16 FLOPs of the emulated products' digit pairs (S(S+1)/2 products per
+                              FP64 product, S the digits of each launch) */
 } ts_stats;
 
 /* Enable (1) or disable (0) per-kernel event timing on ctx. */

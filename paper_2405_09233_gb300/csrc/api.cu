@@ -156,6 +156,7 @@ void KernelTimer::reset() {
   collect();
   gemm_launches = fft_launches = lowp_launches = oz_launches = tba_launches = 0;
   gemm_ms = gemm_flops = fft_ms = fft_bytes = lowp_ms = lowp_flops = oz_ms = oz_flops = tba_ms = tba_flops = 0;
+  oz_pair_flops = 0;
 }
 
 void KernelTimer::destroy() {
@@ -240,7 +241,8 @@ void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mod
     return;
   }
   if (ctx->f64_engine == TS_ENGINE_OZAKI) {
-    apply_f64_oz(ctx, op, X, Y, mode, C, partials, ctx->oz_digits, st);
+    const int S = ctx->oz_step_digits > 0 && ctx->oz_step_digits < ctx->oz_digits ? ctx->oz_step_digits : ctx->oz_digits;
+    apply_f64_oz(ctx, op, X, Y, mode, C, partials, S, ctx->oz_digits, st);
     return;
   }
   double2* Xh = static_cast<double2*>(ctx->ws.get("apply_Xh", sizeof(double2) * (size_t)K * T));
@@ -469,7 +471,15 @@ ts_status ts_sylv_apply_ozaki(ts_ctx* ctx, const ts_op* op, int digits, const do
   const size_t N = (size_t)op->n * op->s * op->p;
   StagedIn x(ctx, "apply_inX", X, N, st);
   StagedOut y(ctx, "apply_outY", Y, N, false, st);
-  EngineScope scope(ctx, TS_ENGINE_OZAKI, digits == 0 ? 6 : digits);
+  // An operator already prepared with more digits is used through its leading `digits` digits.
+  const int S = digits == 0 ? 6 : digits;
+  const int S_op = op->oz && op->oz->S > S ? op->oz->S : S;
+  EngineScope scope(ctx, TS_ENGINE_OZAKI, S_op);
+  struct StepDigits {
+    ts_ctx* c;
+    ~StepDigits() { c->oz_step_digits = 0; }
+  } step{ctx};
+  ctx->oz_step_digits = S;
   apply_f64(ctx, op, x.dev, y.dev, IRFFT_STORE, nullptr, nullptr, st);
   y.finish();
   return TS_OK;
@@ -623,6 +633,7 @@ ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out) {
   out->tba_launches = t.tba_launches;
   out->tba_ms = t.tba_ms;
   out->tba_flops = t.tba_flops;
+  out->oz_pair_flops = t.oz_pair_flops;
   return TS_OK;
   TS_API_END(ctx)
 }

@@ -540,7 +540,7 @@ OzBufferSizes oz_buffer_sizes(int n, int s, int K, int S) {
 void oz_products(const ts_op* cop, const double2* Xh, double2* Yh, int S, const OzBuffers& b, const int* gate,
                  int* err, cudaStream_t st) {
   const OzOperands& t = *cop->oz;
-  TS_REQUIRE(t.S == S, "oz_products: operator digits not prepared");
+  TS_REQUIRE(S >= 1 && t.S >= S, "oz_products: operator digits not prepared");
   const int n = cop->n, s = cop->s, p = cop->p, K = cop->K;
   const long long T = (long long)n * s;
   TS_CUDA(cudaMemsetAsync(b.mx, 0, sizeof(unsigned long long) * K, st));
@@ -549,16 +549,17 @@ void oz_products(const ts_op* cop, const double2* Xh, double2* Yh, int S, const 
   split<false>(Xh, T, n, s, K, b.Ex, S, b.xc_re, b.xc_im, nullptr, b.xc_nim, t.ldn, (long long)s * t.ldn, st, gate);
   split<true>(Xh, T, n, s, K, b.Ex, S, b.xr_re, b.xr_im, nullptr, nullptr, t.lds, (long long)n * t.lds, st, gate);
   OzMaps maps;
-  make_map(&maps.a_re, t.a_re, 2, t.ldn, n, n, S * K, kOzM);
-  make_map(&maps.a_im, t.a_im, 2, t.ldn, n, n, S * K, kOzM);
+  // operator planes: all t.S digits exist (digit u of slice k is plane u K + k), the kernel reads u < S
+  make_map(&maps.a_re, t.a_re, 2, t.ldn, n, n, t.S * K, kOzM);
+  make_map(&maps.a_im, t.a_im, 2, t.ldn, n, n, t.S * K, kOzM);
   make_map(&maps.xc_nim, b.xc_nim, 2, t.ldn, n, s, S * K, kOzN);
   make_map(&maps.xc_re, b.xc_re, 2, t.ldn, n, s, S * K, kOzN);
   make_map(&maps.xc_im, b.xc_im, 2, t.ldn, n, s, S * K, kOzN);
   make_map(&maps.xr_re, b.xr_re, 2, t.lds, s, n, S * K, kOzM);
   make_map(&maps.xr_im, b.xr_im, 2, t.lds, s, n, S * K, kOzM);
-  make_map(&maps.b_re, t.b_re, 2, t.lds, s, s, S * K, kOzN);
-  make_map(&maps.b_im, t.b_im, 2, t.lds, s, s, S * K, kOzN);
-  make_map(&maps.b_nre, t.b_nre, 2, t.lds, s, s, S * K, kOzN);
+  make_map(&maps.b_re, t.b_re, 2, t.lds, s, s, t.S * K, kOzN);
+  make_map(&maps.b_im, t.b_im, 2, t.lds, s, s, t.S * K, kOzN);
+  make_map(&maps.b_nre, t.b_nre, 2, t.lds, s, s, t.S * K, kOzN);
   // Fixed point 2^(E_op + E_x - F): |partial sums| < 2 (n + s) 2^(E_op + E_x - 2) <= 2^(E_op + E_x + 62 - F).
   int lg = 0;
   while ((1ll << lg) < 2ll * (n + s)) ++lg;
@@ -570,9 +571,9 @@ void oz_products(const ts_op* cop, const double2* Xh, double2* Yh, int S, const 
 }
 
 void apply_f64_oz(ts_ctx* ctx, const ts_op* cop, const double* X, double* Y, int mode, const double* C,
-                  double* partials, int S, cudaStream_t st) {
+                  double* partials, int S, int S_op, cudaStream_t st) {
   ts_op* op = const_cast<ts_op*>(cop);   // the digit planes are cached on first use
-  oz_prepare(op, S, st);
+  oz_prepare(op, S_op, st);
   oz_preload();
   const int n = op->n, s = op->s, p = op->p, K = op->K;
   const long long T = (long long)n * s;
@@ -593,6 +594,7 @@ void apply_f64_oz(ts_ctx* ctx, const ts_op* cop, const double* X, double* Y, int
   rfft_tube<double, double2>(X, Xh, T, p, st);
   tm.end(st);
   tm.begin(st, 3, gemm_flops(n, s, n, s, K, nyquist_index(p)));
+  if (tm.enabled) tm.oz_pair_flops += oz_bf16_flops(n, s, K, nyquist_index(p), S);
   oz_products(op, Xh, Yh, S, b, nullptr, err, st);
   tm.end(st);
   tm.begin(st, 1, 16.0 * K * T + 8.0 * T * p * (mode == IRFFT_RESIDUAL ? 2 : 1));

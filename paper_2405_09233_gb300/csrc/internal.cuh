@@ -93,7 +93,7 @@ struct KernelTimer {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
   long long gemm_launches = 0, fft_launches = 0, lowp_launches = 0, oz_launches = 0;
   double gemm_ms = 0, gemm_flops = 0, fft_ms = 0, fft_bytes = 0, lowp_ms = 0, lowp_flops = 0;
-  double oz_ms = 0, oz_flops = 0;
+  double oz_ms = 0, oz_flops = 0, oz_pair_flops = 0;   // oz_pair_flops: added at launch time
   long long tba_launches = 0;
   double tba_ms = 0, tba_flops = 0;
   void begin(cudaStream_t st, int kind, double work);
@@ -120,6 +120,7 @@ struct ts_ctx {
   bool tune_loaded = false;        // the on-disk tuning cache (TSTAR_TUNE_CACHE) has been read
   int f64_engine = 0;              // how the current call computes FP64 applications (ts_fp64_engine)
   int oz_digits = 6;               // digits per value of the emulated FP64 product
+  int oz_step_digits = 0;          // fewer digits for the current application (0: oz_digits)
   ts::KernelTimer timer;
 };
 

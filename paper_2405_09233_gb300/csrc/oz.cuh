@@ -38,13 +38,16 @@ void oz_prepare(ts_op* op, int S, cudaStream_t st);
 // Loads the kernels and sets their attributes (call before any stream capture that records them).
 void oz_preload();
 // Yh_k = A_k Xh_k - Xh_k B_k for the K spectral slices of op (double2, column-major n x s each),
-// emulated FP64; op must be prepared with S digits.  gate (device, may be null): when *gate == 0
+// emulated FP64 with S digits per value; op must be prepared with at least S digits (the leading S
+// digits of a longer expansion approximate an entry as closely as an S-digit expansion, within
+// 0.502 of the last kept digit's unit).  gate (device, may be null): when *gate == 0
 // every kernel returns at once.  Captures into a CUDA graph (no allocation, no synchronisation).
 void oz_products(const ts_op* op, const double2* Xh, double2* Yh, int S, const OzBuffers& b, const int* gate,
                  int* err, cudaStream_t st);
-// Y = M(X) in FP64 through the emulated product (same contract as apply_f64).
+// Y = M(X) in FP64 through the emulated product (same contract as apply_f64), with S digits per
+// value; the operator's digit planes are prepared (once) with S_op >= S digits.
 void apply_f64_oz(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
-                  double* partials, int S, cudaStream_t st);
+                  double* partials, int S, int S_op, cudaStream_t st);
 // BF16 tensor FLOPs one emulated application executes (all kept digit pairs).
 double oz_bf16_flops(int n, int s, int K, int nyq, int S);
 

@@ -37,6 +37,18 @@ void apply_basis(ts_ctx* ctx, ts_op* op, int prec, const float* x, float* y, cud
   apply_low(ctx, op, prec, x, y, st);
 }
 
+// Digits for an emulated-FP64 residual that the next inner solve needs only to relative accuracy
+// ~inner_tol, when its norm is expected near rho ||C||.  An S-digit product of an output entry
+// carries n + s terms, each off by about 256^-S of its operands' largest entries, so its error is
+// taken as 10 (n + s) 256^-S ||C|| (a factor 10 for cancellation between C and M(X)); the fewest
+// S whose error stays below a tenth of inner_tol rho ||C|| is used, at least 3 and at most S_full.
+int progressive_digits(double rho, double inner_tol, int n, int s, int S_full) {
+  const double need = 0.1 * inner_tol * rho;
+  for (int S = 3; S < S_full; ++S)
+    if (10.0 * (n + s) * std::pow(256.0, -S) <= need) return S;
+  return S_full;
+}
+
 template <typename T>
 ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const ts_solve_opts& o,
                        ts_solve_info& info, cudaStream_t st, int method, int prec) {
@@ -62,6 +74,12 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
   int* tc_err = static_cast<int*>(ctx->ws.get("tc_err", sizeof(int) * 4));
   const bool ozaki = ctx->f64_engine == TS_ENGINE_OZAKI;
   if (mixed || ozaki) TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
+  // Progressive digits: mixed precision on the emulated engine with the default digit count.
+  bool progressive = mixed && ozaki && o.ozaki_digits == 0;
+  struct StepDigitsReset {   // an exception never leaves reduced digits behind in the context
+    ts_ctx* c;
+    ~StepDigitsReset() { c->oz_step_digits = 0; }
+  } step_digits_reset{ctx};
 
   int hist_len = 0, true_len = 0;
   auto push_hist = [&](double v) {
@@ -161,12 +179,26 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
     }
     ks_solve(state, m, k, method, st);
     multi_axpy<T, double>(X, V, N, N, ks_y(state, m), k, 1.0, nullptr, st);   // X = X0 + V_k (*) y
-    apply_f64(ctx, op, X, R, IRFFT_RESIDUAL, C, P2, st);                     // true residual
-    ++info.applies_fp64;
-    finalize_norm(P2, sc + 2, st);
-    TS_CUDA(cudaMemcpyAsync(hs, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    TS_CUDA(cudaStreamSynchronize(st));
-    res = hs[2];
+    // True residual.  With progressive digits it is first formed with the fewest digits its next
+    // use needs; a residual that would end the solve is formed again with every digit.
+    const double res_prev = res;
+    int S_step = progressive ? progressive_digits(std::max(last_est, o.tol * normC) / normC, inner_tol, op->n,
+                                                  op->s, ctx->oz_digits)
+                             : 0;
+    for (;;) {
+      ctx->oz_step_digits = S_step;
+      apply_f64(ctx, op, X, R, IRFFT_RESIDUAL, C, P2, st);
+      ctx->oz_step_digits = 0;
+      ++info.applies_fp64;
+      finalize_norm(P2, sc + 2, st);
+      TS_CUDA(cudaMemcpyAsync(hs, sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      TS_CUDA(cudaStreamSynchronize(st));
+      res = hs[2];
+      if (S_step == 0 || S_step >= ctx->oz_digits || !(res <= o.tol * normC)) break;
+      S_step = 0;
+    }
+    // a residual that did not at least halve: stop trusting reduced digits for this solve
+    if (S_step != 0 && !(res <= 0.5 * res_prev)) progressive = false;
     push_true(res);
     if (!std::isfinite(res)) {
       status = TS_ERR_NONFINITE;

@@ -84,6 +84,57 @@ def test_ozaki_digit_counts(ctx, digits):
     op.close()
 
 
+@pytest.mark.parametrize("digits", [3, 4, 5])
+def test_ozaki_leading_digits(ctx, digits):
+    """An operator prepared with 8 digits, applied through its leading 3..5: inside the same bound
+    as an expansion with that many digits, and bit-identical to a second call."""
+    n, s, p = 96, 40, 8
+    pr = inputs.dense_problem(n, s, p, seed=11)
+    X = inputs.random_tensor((n, s, p), seed=12)
+    op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
+    ctx.sylv_apply_ozaki(op, to_dev(X), digits=8)                 # digit planes built with 8 digits
+    Y = from_dev(ctx.sylv_apply_ozaki(op, to_dev(X), digits=digits))
+    ref = kr.sylv_apply(pr.A, pr.B, X)
+    bound = (fp64_product_bound(np.abs(pr.A), np.abs(X), tp.tprod, p + n)
+             + fp64_product_bound(np.abs(X), np.abs(pr.B), tp.tprod, p + s)
+             + ozaki_bound(pr.A, pr.B, X, digits))
+    err = np.abs(Y - ref)
+    assert np.all(err <= bound), (err / bound).max()
+    Y8 = from_dev(ctx.sylv_apply_ozaki(op, to_dev(X), digits=8))   # full digits again afterwards
+    assert np.all(np.abs(Y8 - ref) <= bound)
+    assert np.abs(Y8 - ref).max() < err.max() or digits >= 5
+    assert np.array_equal(Y, from_dev(ctx.sylv_apply_ozaki(op, to_dev(X), digits=digits)))
+    op.close()
+
+
+def test_mixed_ozaki_progressive_digits(ctx):
+    """BF16 inner solve, emulated residuals with progressive digits (default) and with 6 fixed
+    digits: both reach 1e-10 (oracle check), with the same number of outer steps within one, and a
+    later full-digit application is unaffected."""
+    n, s, p, m = 200, 130, 8, 20
+    pr = inputs.dense_problem(n, s, p, seed=21)
+    C = kr.sylv_apply(pr.A, pr.B, pr.Xstar)
+    op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
+    outs = {}
+    for digits in (0, 6):
+        Xd = to_dev(np.zeros_like(C))
+        res = ctx.tgmres_solve(op, to_dev(C), Xd, restart=m, tol=1e-10, precision="mixed_bf16", engine="ozaki",
+                               ozaki_digits=digits)
+        assert res.status == 0, res
+        X = from_dev(Xd)
+        assert tp.norm(C - kr.sylv_apply(pr.A, pr.B, X)) <= 1e-10 * tp.norm(C)
+        outs[digits] = res.info.outer
+    assert abs(outs[0] - outs[6]) <= 1, outs
+    Xr = inputs.random_tensor((n, s, p), seed=5)
+    Y = from_dev(ctx.sylv_apply_ozaki(op, to_dev(Xr)))
+    ref = kr.sylv_apply(pr.A, pr.B, Xr)
+    bound = (fp64_product_bound(np.abs(pr.A), np.abs(Xr), tp.tprod, p + n)
+             + fp64_product_bound(np.abs(Xr), np.abs(pr.B), tp.tprod, p + s)
+             + ozaki_bound(pr.A, pr.B, Xr, 6))
+    assert np.all(np.abs(Y - ref) <= bound)
+    op.close()
+
+
 def test_ozaki_scaled_operands(ctx):
     """Operands far from unit magnitude (A, B scaled by 2^40, X by 2^-70): the per-slice exponents
     absorb the scaling."""
