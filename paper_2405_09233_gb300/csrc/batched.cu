@@ -837,7 +837,27 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
     tct = cand_tables[std::find(cands.begin(), cands.end(), tc_bn) - cands.begin()];
     TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
   }
+  // Emulated-FP64 slice products of every instance (X -> Y, spectral FP64), each gated on the device
+  // by the instance's flag in `gate`: dealt largest first over the kOzBranches side streams, forked
+  // from and joined back to s2.
+  auto oz_all = [&](cudaStream_t s2, const double2* X, double2* Y, const int* gate) -> int {
+    // fork: every branch waits for the products' input; join: s2 waits for every branch
+    TS_CUDA(cudaEventRecord(fork_ev, s2));
+    for (int q = 0; q < kOzBranches; ++q) TS_CUDA(cudaStreamWaitEvent(ctx->side[q], fork_ev, 0));
+    for (int r = 0; r < count; ++r) {
+      const int i = order[r], q = r % kOzBranches;
+      oz_products(ops[i], X + plan.inst[i].offS, Y + plan.inst[i].offS, oz_digits, ozb[q], gate + i, tc_err,
+                  ctx->side[q]);
+    }
+    for (int q = 0; q < kOzBranches; ++q) {
+      TS_CUDA(cudaEventRecord(join_ev[q], ctx->side[q]));
+      TS_CUDA(cudaStreamWaitEvent(s2, join_ev[q], 0));
+    }
+    return 5 * count;
+  };
   auto inner_products = [&](cudaStream_t s2) -> int {
+    // FP64 solve on the emulated engine: the Arnoldi products too (gated by the inner-cycle flag)
+    if (!mixed && ozaki) return oz_all(s2, (const double2*)Xh, (double2*)Yh, d.act);
     if (tcin) {
       tc_batch_products(o.precision, tc_bn, tct.planes, tct.pitems, tct.n_pitems, tct.maps, tct.inst, d.act,
                         tct.titems, tct.n_titems, tc_err, s2);
@@ -856,19 +876,7 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       TS_CUDA(cudaGetLastError());
       return 1;
     }
-    // fork: every branch waits for the products' input; join: s2 waits for every branch
-    TS_CUDA(cudaEventRecord(fork_ev, s2));
-    for (int q = 0; q < kOzBranches; ++q) TS_CUDA(cudaStreamWaitEvent(ctx->side[q], fork_ev, 0));
-    for (int r = 0; r < count; ++r) {
-      const int i = order[r], q = r % kOzBranches;
-      oz_products(ops[i], Xh64 + plan.inst[i].offS, Yh64 + plan.inst[i].offS, oz_digits, ozb[q], d.cyc + i, tc_err,
-                  ctx->side[q]);
-    }
-    for (int q = 0; q < kOzBranches; ++q) {
-      TS_CUDA(cudaEventRecord(join_ev[q], ctx->side[q]));
-      TS_CUDA(cudaStreamWaitEvent(s2, join_ev[q], 0));
-    }
-    return 5 * count;
+    return oz_all(s2, Xh64, Yh64, d.cyc);
   };
   k_b_normC<<<nbs, 256, 0, st>>>(d, P0);
   k_b_finalize_norm<<<count, 256, 0, st>>>(d, P0, 0);

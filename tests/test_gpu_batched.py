@@ -109,8 +109,9 @@ def test_batched_repeated_calls_leave_operators_intact(ctx):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed_fp32"])
 def test_batched_ozaki_residuals(ctx, prec):
-    """The batch with its FP64 products on the emulated-FP64 engine: every instance reaches its
-    tolerance (checked by the oracle) and matches the DFMA-engine batch to 1e-8 relative."""
+    """The batch with its FP64 products on the emulated-FP64 engine (in an FP64 solve the Arnoldi
+    products as well as the residuals): every instance reaches its tolerance (checked by the oracle)
+    and matches the DFMA-engine batch to 1e-8 relative."""
     import torch
     probs, ops, Cs, Xs, Cn = make_batch(ctx, SHAPES, 400)
     st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=12, precision=prec, engine="ozaki")
