@@ -86,6 +86,17 @@ TF32_OVER_BF16 = 1.1 / 2.25       # nominal dense tensor rates (PFLOP/s per GPU)
 FFMA_NOMINAL_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12   # 128 FP32 lanes/SM x 2 FLOP x 152 SMs x 2070 MHz
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant kernels at the
+# n = s = 1024, p = 16 workload, from one ncu capture each (profiles/traffic_dense_n1024_s1024_p16.md);
+# a roofline object carries them only for that workload and, for the emulated product, only when every
+# launch used 6 digits.
+TRAFFIC_N1024 = {"k_gemm_slices<double>": 497799168 + 137544960, "k_oz_sylv/6": 1779147520 + 149931264}
+
+
+def traffic_for(kernel, workload):
+    return TRAFFIC_N1024.get(kernel) if workload == "dense_n1024_s1024_p16" else None
+
+
 def ozaki_roofline(flops_per_launch, pair_flops_per_launch, avg_ms, sustained, share):
     """Emulated FP64 slice products: the tensor pipe executes S(S+1)/2 BF16 digit-pair products per
     algorithmic FP64 product (S per launch: 6, or fewer for the early residuals of a mixed solve);
@@ -374,10 +385,13 @@ def main():
     if top == "fp64":
         roofline = gemm_roofline("fp64", "fp64", st.gemm_flops / max(st.gemm_launches, 1),
                                  st.gemm_ms / max(st.gemm_launches, 1), True, st.gemm_ms / step_ms_total)
+        roofline["traffic"] = traffic_for("k_gemm_slices<double>", a.workload)
     elif top == "oz":
         roofline = ozaki_roofline(st.oz_flops / max(st.oz_launches, 1), st.oz_pair_flops / max(st.oz_launches, 1),
                                   st.oz_ms / max(st.oz_launches, 1),
                                   True, st.oz_ms / step_ms_total)
+        if abs(st.oz_pair_flops - 21 * st.oz_flops) <= 1e-9 * st.oz_pair_flops:   # 6 digits in every launch
+            roofline["traffic"] = traffic_for("k_oz_sylv/6", a.workload)
     else:
         roofline = gemm_roofline("lowp", a.precision, st.lowp_flops / max(st.lowp_launches, 1),
                                  st.lowp_ms / max(st.lowp_launches, 1), True, st.lowp_ms / step_ms_total)
