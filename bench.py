@@ -45,8 +45,8 @@ def args_parse():
     ap.add_argument("--engine", choices=["dfma", "ozaki"], default="dfma",
                     help="how FP64 applications run: FP64 CUDA cores, or emulated on the BF16 tensor cores")
     ap.add_argument("--variants", default=None,
-                    help="comma list of extra precision[@engine] runs to time ('' = none; default: every "
-                         "precision and engine the workload supports)")
+                    help="comma list of extra precision[@engine] runs to time, 'tfom' for FP64 tFOM ('' = none; "
+                         "default: every method, precision and engine the workload supports)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
@@ -58,7 +58,7 @@ def args_parse():
     return ap.parse_args()
 
 
-DENSE_VARIANTS = "mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16,fp64@ozaki,mixed_tf32x3@ozaki,mixed_bf16@ozaki"
+DENSE_VARIANTS = "tfom,mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16,fp64@ozaki,tfom@ozaki,mixed_tf32x3@ozaki,mixed_bf16@ozaki"
 BATCHED_VARIANTS_DEFAULT_MARK = "<batched-default>"
 
 
@@ -344,7 +344,10 @@ def main():
     def step(precision, engine=a.engine):
         op = ctx.op_create_dense(Ad, Bd)
         X.zero_()
-        r = ctx.tgmres_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision, engine=engine)
+        if precision == "tfom":   # restarted tFOM(m), FP64 (variant)
+            r = ctx.tfom_solve(op, Cd, X, restart=m, tol=1e-10, engine=engine)
+        else:
+            r = ctx.tgmres_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision, engine=engine)
         op.close()
         return r
 
