@@ -91,11 +91,22 @@ void* op_malloc(size_t bytes) {
   return p;
 }
 
+thread_local int t_free_batch = 0;
+
+OpFreeBatch::OpFreeBatch() {
+  cudaDeviceSynchronize();
+  ++t_free_batch;
+}
+OpFreeBatch::~OpFreeBatch() { --t_free_batch; }
+
 void op_free(void* p) {
   if (!p) return;
-  OpPool& q = op_pool();
-  cudaDeviceSynchronize();
-  cudaFreeAsync(p, q.stream);
+  try {   // called from destructors and ts_op_destroy: never throws
+    OpPool& q = op_pool();
+    if (t_free_batch == 0) cudaDeviceSynchronize();
+    cudaFreeAsync(p, q.stream);
+  } catch (const Error&) {
+  }
 }
 
 std::atomic<long long> g_launches{0};
@@ -412,6 +423,7 @@ ts_status ts_op_create_dense(ts_ctx* ctx, const double* A, int n, const double* 
 void ts_op_destroy(ts_op* op) {
   if (!op) return;
   if (op->ctx) cudaSetDevice(op->ctx->device);
+  OpFreeBatch batch;   // one device synchronisation for all of the operator's buffers
   op_free(op->Ah);
   op_free(op->Bh);
   op_free(op->Ah32);

@@ -57,6 +57,12 @@ struct Workspace {
 constexpr unsigned long long kOpPoolKeepBytes = 16ull << 30;
 void* op_malloc(size_t bytes);
 void op_free(void* p);
+// While one of these lives on the calling thread, op_free skips its own device synchronisation:
+// the constructor synchronises the device once for a whole operator's buffers.
+struct OpFreeBatch {
+  OpFreeBatch();
+  ~OpFreeBatch();
+};
 template <typename T>
 inline void op_alloc(T*& p, size_t bytes) {
   p = static_cast<T*>(op_malloc(bytes));
