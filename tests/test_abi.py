@@ -33,11 +33,12 @@ def test_host_only_calls():
 
 
 def test_struct_layouts_match_header():
-    """The ctypes mirrors of ts_solve_opts / ts_solve_info have the header's field order and sizes."""
+    """The ctypes mirrors of ts_solve_opts / ts_solve_info / ts_stats / ts_instance have the header's
+    field order."""
     import re
     text = open(os.path.join(os.path.dirname(binding.LIB_PATH), "..", "include", "tstar.h")).read()
     for cls, tag in ((binding.SolveOpts, "ts_solve_opts"), (binding.SolveInfo, "ts_solve_info"),
-                     (binding.Stats, "ts_stats")):
+                     (binding.Stats, "ts_stats"), (binding.Instance, "ts_instance")):
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + tag + ";", text).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         names = []
