@@ -3,9 +3,21 @@
 Readings of the paper taken here:
   * Normalization1 (cited from Kilmer et al., not restated in the paper):
     v = u * a with u^T * u = e.  Per Fourier index k of the DFT along mode 3,
-    a_k = ||v_k||_2 and u_k = v_k / a_k; u and a are the inverse DFTs.  When
-    a_k <= 1e-14 * max_k a_k the slice is rank deficient: u_k = e_1 (first
-    unit vector), a_k = 0, which keeps u^T * u = e.
+    a_k = ||v_k||_2 and u_k = v_k / a_k; u and a are the inverse DFTs.  A
+    Fourier slice is numerically zero when a_k <= 1e-12 * ref, with ref the
+    largest a_k of v itself.  Then a_k = 0 and u_k = e_1 (first unit vector),
+    which keeps u^T * u = e.
+  * Inside Tubal-QR (Algorithm 6) Normalize is applied to a column after it
+    was orthogonalised against the previous ones.  There the scale ref is the
+    largest Fourier-slice norm of the column *before* orthogonalisation, so a
+    column that depends on the previous ones (whose orthogonalised remainder
+    is rounding noise) counts as rank deficient instead of having its noise
+    normalised.  The unit vector of a rank-deficient slice is then chosen
+    orthogonal to the previous columns of that slice, so that Q^T * Q = I as
+    Theorem 5.1 states: the first e_i (i = 1, 2, ...) whose component
+    orthogonal to them has squared norm >= 1/(2n), orthogonalised (twice)
+    and normalised.  Some e_i always qualifies: the squared norms of those
+    components sum to n - j >= 1 over the n unit vectors.
   * Algorithm 6's inner loop runs over i = 1..j-1 (the printed "i = 2..j-1"
     and the double normalisation of the first column are read as slips).
   * Tubal Block Arnoldi applies A, not M, in its loop (the paper's claim that
@@ -27,24 +39,53 @@ import numpy as np
 from .tproduct import dft3, idft3, tprod, ttranspose, norm
 from .schur import t_bartels_stewart
 
-NORMALIZE_TINY = 1e-14
+NORMALIZE_TINY = 1e-12
 BLOCK_BREAKDOWN_REL = 1e-13
 
 
-def normalize(v: np.ndarray):
-    """Normalization1: v (n x 1 x p) = u * a with u^T * u = e; returns (u, a)."""
+def fourier_norms(v: np.ndarray) -> np.ndarray:
+    """a_k = ||v_k||_2 for every Fourier index k of a lateral slice v (n x 1 x p)."""
+    return np.linalg.norm(dft3(v)[:, 0, :], axis=0)
+
+
+def completion_vector(P: np.ndarray) -> np.ndarray:
+    """A unit vector orthogonal to the orthonormal columns of P (n x j, complex, j < n): the first
+    e_i whose component orthogonal to them has squared norm >= 1/(2n), orthogonalised twice."""
+    n = P.shape[0]
+    for i in range(n):
+        z = np.zeros(n, dtype=complex)
+        z[i] = 1.0
+        for _ in range(2):
+            z = z - P @ (np.conj(P.T) @ z)
+        nz = np.linalg.norm(z)
+        if nz * nz >= 1.0 / (2 * n):
+            return z / nz
+    raise AssertionError("no unit vector has a component orthogonal to the previous columns")
+
+
+def normalize(v: np.ndarray, ref: Optional[float] = None, prev: Optional[np.ndarray] = None):
+    """Normalization1: v (n x 1 x p) = u * a with u^T * u = e; returns (u, a).
+
+    ref: the scale below which a Fourier slice counts as zero (times NORMALIZE_TINY); default the
+    largest a_k of v.  prev: the columns (n x j x p) that u must be orthogonal to in a rank-deficient
+    slice (Tubal-QR); default none, which gives u_k = e_1 there.
+    """
     n, _, p = v.shape
     vh = dft3(v)[:, 0, :]                     # n x p Fourier coefficients
     a = np.linalg.norm(vh, axis=0)            # a_k = ||v_k||_2
-    amax = a.max() if p else 0.0
+    if ref is None:
+        ref = a.max() if p else 0.0
+    prevh = dft3(prev) if prev is not None and prev.shape[1] > 0 else None
     uh = np.zeros_like(vh)
     ah = np.zeros(p, dtype=complex)
     for k in range(p):
-        if a[k] > NORMALIZE_TINY * amax:
+        if a[k] > NORMALIZE_TINY * ref:
             uh[:, k] = vh[:, k] / a[k]
             ah[k] = a[k]
-        else:
+        elif prevh is None:
             uh[0, k] = 1.0
+        else:
+            uh[:, k] = completion_vector(prevh[:, :, k])
     u = np.real(idft3(uh[:, None, :]))
     at = np.real(idft3(ah[None, None, :]))
     return u, at
@@ -57,12 +98,13 @@ def tubal_qr(Amat: np.ndarray):
     R = np.zeros((m, m, p))
     for j in range(m):
         W = Amat[:, j:j + 1, :].copy()
+        ref = fourier_norms(W).max()                # scale of the column before orthogonalisation
         for i in range(j):
             Qi = Q[:, i:i + 1, :]
             rij = tprod(ttranspose(Qi), W)          # tube V_i^T * W
             R[i:i + 1, j:j + 1, :] = rij
             W = W - tprod(Qi, rij)
-        q, a = normalize(W)
+        q, a = normalize(W, ref=ref, prev=Q[:, :j, :])
         Q[:, j:j + 1, :] = q
         R[j:j + 1, j:j + 1, :] = a
     return Q, R

@@ -148,3 +148,73 @@ def test_t_bartels_stewart_matches_fourier_solve(dims):
     assert imag < 1e-12
     np.testing.assert_allclose(X, pr.Xstar, atol=1e-12)
     np.testing.assert_allclose(X, fourier_solve(pr.A, pr.B, C), atol=1e-12)
+
+
+def deficient_block(n, p, seed):
+    """A random n x 4 x p block whose lateral slice 2 equals slice 0 and whose slice 3 is zero."""
+    Amat = inputs.random_tensor((n, 4, p), seed=seed)
+    Amat[:, 2, :] = Amat[:, 0, :]
+    Amat[:, 3, :] = 0.0
+    return Amat
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_tubal_qr_rank_deficient(p):
+    """Theorem 5.1 for a rank-deficient block: Q * R = A and Q^T * Q = I still hold, the dependent
+    and the zero column get an exactly zero diagonal tube in R, and the zero column an exactly zero
+    column of R."""
+    Amat = deficient_block(9, p, seed=20 + p)
+    Q, R = tb.tubal_qr(Amat)
+    np.testing.assert_allclose(tp.tprod(Q, R), Amat, atol=1e-13)
+    np.testing.assert_allclose(tp.tprod(tp.ttranspose(Q), Q), tp.identity(4, p), atol=1e-13)
+    assert np.all(R[2, 2, :] == 0.0) and np.all(R[3, 3, :] == 0.0)
+    assert np.all(R[:, 3, :] == 0.0)
+    for i in range(4):
+        for j in range(i):
+            assert np.abs(R[i, j, :]).max() == 0.0
+    if p == 1:   # the independent columns: thin QR with a positive diagonal
+        q, r = np.linalg.qr(Amat[:, :2, 0])
+        sgn = np.sign(np.diag(r))
+        np.testing.assert_allclose(Q[:, :2, 0], q * sgn, atol=1e-13)
+
+
+def test_tubal_qr_deficient_column_does_not_follow_rounding_noise():
+    """The dependent column's Q does not depend on the rounding noise its orthogonalisation leaves:
+    a copy of slice 0 and a copy scaled by (1 + 2^-52) give the same Q to rounding."""
+    Amat = deficient_block(11, 3, seed=7)
+    Q1, R1 = tb.tubal_qr(Amat)
+    A2 = Amat.copy()
+    A2[:, 2, :] = Amat[:, 0, :] * (1.0 + 2.0 ** -52)
+    Q2, R2 = tb.tubal_qr(A2)
+    np.testing.assert_allclose(Q2, Q1, atol=1e-14)
+    np.testing.assert_allclose(R2, R1, atol=1e-14)
+
+
+def test_completion_vector_skips_spanned_unit_vectors():
+    """When e_1 lies in the span of the previous columns the next qualifying e_i is taken."""
+    P = np.zeros((5, 2), dtype=complex)
+    P[0, 0] = 1.0                       # e_1 itself
+    P[1, 1] = 1j                        # a phase of e_2
+    z = tb.completion_vector(P)
+    np.testing.assert_allclose(z, np.eye(5)[2], atol=1e-15)
+
+
+@pytest.mark.parametrize("kind", ["equal", "zero"])
+def test_tba_and_tbas_with_rank_deficient_start(kind):
+    """Algorithm 7 from a rank-deficient R0 keeps Proposition 5.1's identities, and TBAS(m) (Algorithm 8)
+    solves the equation: a right-hand side whose lateral slice 2 equals slice 1, or whose slice 2 is zero."""
+    n, s, p, m = 20, 3, 4, 3
+    pr = inputs.dense_problem(n, s, p, seed=5)
+    C = inputs.random_tensor((n, s, p), seed=6)
+    if kind == "equal":
+        C[:, 1, :] = C[:, 0, :]
+    else:
+        C[:, 1, :] = 0.0
+    arn = tb.tba(lambda X: tp.tprod(pr.A, X), C, m)
+    Vm, Hm = arn.Vm(), arn.Hm()
+    np.testing.assert_allclose(tp.tprod(tp.ttranspose(Vm), Vm), tp.identity(m * s, p), atol=1e-12)
+    np.testing.assert_allclose(tp.tprod(tp.ttranspose(Vm), tp.tprod(pr.A, Vm)), Hm, atol=1e-12)
+    np.testing.assert_allclose(tp.tprod(arn.V[0], arn.H0), C, atol=1e-13)
+    r = tb.tbas(pr.A, pr.B, C, m=m, tol=1e-10)
+    assert r.status == "ok" and r.relres <= 1e-10
+    assert np.abs(r.X - fourier_solve(pr.A, pr.B, C)).max() < 1e-9
