@@ -196,8 +196,12 @@ typedef struct {
  * in lockstep: every phase of a restart cycle is one launch over all instances (block tables for
  * the streaming phases and the mode-3 DFTs, a cost-ordered (instance, slice, tile) work list for
  * the slice products), device-side masks retire converged instances, and one cycle is captured
- * as a CUDA graph and replayed.  opts->precision: TS_FP64, or TS_MIXED_FP32 (FP32 Arnoldi cycle,
- * FP64 residual and update; the cycle's inner tolerance is opts->inner_tol, default 1e-6).
+ * as a CUDA graph and replayed.  opts->precision: TS_FP64, or a mixed precision -- an FP32 Arnoldi
+ * cycle with FP64 residual and update, whose slice products run on FP32 CUDA cores
+ * (TS_MIXED_FP32) or on the tcgen05 tensor cores (TS_MIXED_TF32, TS_MIXED_BF16, TS_MIXED_TF32X3);
+ * the cycle's inner tolerance is opts->inner_tol (0: 1e-6 for FP32 and split TF32, 1e-3 TF32,
+ * 1e-2 BF16).  opts->fp64_engine picks the engine of every FP64 product (the residuals, and the
+ * whole cycle of a TS_FP64 batch): TS_ENGINE_DFMA or TS_ENGINE_OZAKI (opts->ozaki_digits).
  * opts->restart <= 128; dense operators with p <= 64.  infos / statuses (count entries each, may
  * be NULL) receive each instance's result; the call returns TS_OK when every instance reached its
  * tolerance, TS_NOT_CONVERGED (or TS_ERR_NONFINITE) otherwise.  Synchronous. */
@@ -205,21 +209,22 @@ ts_status ts_batched_solve(ts_ctx* ctx, int count, const ts_instance* insts, con
                            ts_solve_info* infos, int* statuses, ts_stream stream);
 
 /* ts_tstar without allocating: C = A*B exactly as ts_tstar computes it, for callers that cannot
- * allocate device memory at call time -- code recorded under CUDA stream capture (cudaMalloc
- * cannot be captured), latency-critical loops that must not risk an allocation's device-wide
- * synchronisation, and processes whose device memory is already claimed by another allocator.
- * The paper has no counterpart; this is a deployment variant of the T-product entry point.
+ * allocate device memory when they need a T-product: latency-critical loops that must not risk the
+ * device-wide synchronisation a cudaMalloc or cudaFree can cause, and processes whose device memory
+ * is already claimed by another allocator (a framework's caching pool), where a fresh cudaMalloc can
+ * fail.  The paper has no counterpart; this is a deployment variant of the T-product entry point.
  *
  * Scratch: a fixed array of TS_NOALLOC_MAX_COMPLEX complex doubles (32 MiB) in the library's own
  * device memory, present on every GPU that loads the library until the process exits.  The call
  * needs K*(n1*n2 + n2*m + n1*m) <= TS_NOALLOC_MAX_COMPLEX with K = p/2 + 1, else it returns
- * TS_ERR_ARG without doing anything.  A, B and C must be device pointers on the current device
- * (TS_ERR_ARG otherwise); no context is used and nothing is allocated or freed.
+ * TS_ERR_ARG without doing anything.  A, B and C must be device memory of the current device
+ * (TS_ERR_ARG for host memory or another device's memory); no context is used and nothing is
+ * allocated or freed (no cudaMalloc, cudaFree or allocating library routine).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All calls share the one
- * array and every call overwrites what it uses, so calls whose work overlaps on the GPU (other
- * streams, or other host threads) race and must be serialised by the caller.  Asynchronous on
- * `stream`. */
+ * that device current and caches it; make that first call before any stream capture.  All calls
+ * share the one array and every call overwrites what it uses (nothing has to start at zero), so
+ * calls whose work overlaps on the GPU (other streams, or other host threads) race and must be
+ * serialised by the caller.  Asynchronous on `stream`. */
 #define TS_NOALLOC_MAX_COMPLEX (2LL * 1024 * 1024)
 ts_status ts_tstar_noalloc(const double* A, int n1, int n2, const double* B, int m, int p, double* C,
                            ts_stream stream);

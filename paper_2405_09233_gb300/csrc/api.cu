@@ -193,7 +193,28 @@ bool is_device_ptr(const void* p) {
     (void)cudaGetLastError();
     return false;
   }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return false;
+  int dev = -1;
+  TS_CUDA(cudaGetDevice(&dev));
+  if (attr.device != dev) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "pointer %p is memory of device %d, but the call runs on device %d", p,
+                  attr.device, dev);
+    throw Error{TS_ERR_ARG, buf};
+  }
+  return true;
+}
+
+void set_max_dynamic_smem(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;   // (kernel, device) -> bytes already allowed
+  int dev = 0;
+  TS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  int& have = done[{func, dev}];
+  if (have >= bytes) return;
+  TS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  have = bytes;
 }
 
 StagedIn::StagedIn(ts_ctx* ctx, const std::string& name, const double* p, size_t count, cudaStream_t st) {
@@ -508,9 +529,9 @@ ts_status ts_op_create_csr(ts_ctx* ctx, int n, int p, const int* rowptr, const i
     TS_REQUIRE(rowptr && col && val && B, "ts_op_create_csr: null pointer");
     TS_REQUIRE(n >= 1 && s >= 1 && p >= 1, "ts_op_create_csr: sizes must be >= 1");
     TS_REQUIRE(flags == 0, "ts_op_create_csr: flags must be 0");
+    TS_CUDA(cudaSetDevice(ctx->device));
     TS_REQUIRE(!is_device_ptr(rowptr) && !is_device_ptr(col) && !is_device_ptr(val),
                "ts_op_create_csr: the CSR arrays must be host memory");
-    TS_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     op = new ts_op();
     op->ctx = ctx;
@@ -570,9 +591,9 @@ ts_status ts_sylv_apply_lowp(ts_ctx* ctx, const ts_op* op, int precision, const 
   TS_REQUIRE(precision == TS_MIXED_FP32 || precision == TS_MIXED_TF32 || precision == TS_MIXED_BF16 ||
                  precision == TS_MIXED_TF32X3,
              "ts_sylv_apply_lowp: precision must be a mixed precision");
+  TS_CUDA(cudaSetDevice(ctx->device));
   TS_REQUIRE(is_device_ptr(X) && is_device_ptr(Y), "ts_sylv_apply_lowp: X and Y must be device memory");
   if (op->sp) throw Error{TS_ERR_UNSUPPORTED, "ts_sylv_apply_lowp: sparse operators run in FP64 only"};
-  TS_CUDA(cudaSetDevice(ctx->device));
   apply_low(ctx, const_cast<ts_op*>(op), precision, X, Y, reinterpret_cast<cudaStream_t>(stream));
   return TS_OK;
   TS_API_END(ctx)

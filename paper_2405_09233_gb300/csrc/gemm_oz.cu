@@ -130,10 +130,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* smem = smem_raw + (base - raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStage);
-  // bars: full[kOzStages], empty[kOzStages], acc[2], free[2]; then the TMEM address slot
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kOzStages + 4);
+  // bars: full[kOzStages], empty[kOzStages], acc[2], free[2], done; then the TMEM address slot
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kOzStages + 5);
   const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + kOzStages);
   const uint32_t bar_acc = smem_u32(bars + 2 * kOzStages), bar_free = smem_u32(bars + 2 * kOzStages + 2);
+  const uint32_t bar_done = smem_u32(bars + 2 * kOzStages + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j0 = blockIdx.x * kOzN, i0 = blockIdx.y * kOzM, k = blockIdx.z;
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       mbar_init(bar_acc + 8 * b, 1);
       mbar_init(bar_free + 8 * b, 8);   // one arrival per epilogue warp
     }
+    mbar_init(bar_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 9) {
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
   if (warp == 8) {
     if (lane == 0) {
-      int it = 0;
+      int it = 0, issued = 0;   // stages visited / stages whose loads were issued
       bool ok = true;
       const int U = seq.units();
       for (int q = 0; q < U && ok; ++q) {
@@ -196,8 +198,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             tma_load_3d(sQ, &maps.b_im, l0, j0, pb, full);
             tma_load_3d(sR, &maps.b_nre, l0, j0, pb, full);
           }
+          issued = it + 1;
         }
       }
+      // Every stage this warp loaded lands before the CTA exits, also when an error stopped the MMA
+      // warp from consuming it: bounded waits on the last kOzStages loads (immediate when all were used).
+      for (int i = issued > kOzStages ? issued - kOzStages : 0; i < issued; ++i)
+        mbar_wait(bar_full + 8 * (i % kOzStages), (uint32_t)(i / kOzStages) & 1u, err, 15);
     }
   } else if (warp == 9) {
     if (lane == 0) {
@@ -258,6 +265,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           mma_commit(bar_empty + 8 * slot);
         }
         if (ok) mma_commit(bar_acc + 8 * b);
+      }
+      if (!ok) {   // after an error the MMAs already issued still complete before TMEM is freed
+        mma_commit(bar_done);
+        mbar_wait(bar_done, 0u, err, 16);
       }
     }
   } else {
@@ -522,11 +533,7 @@ void oz_preload() {
     cudaFuncAttributes fa;
     TS_CUDA(cudaFuncGetAttributes(&fa, f));
   }
-  static bool attr_set = false;
-  if (!attr_set) {
-    TS_CUDA(cudaFuncSetAttribute(k_oz_sylv, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem));
-    attr_set = true;
-  }
+  set_max_dynamic_smem((const void*)k_oz_sylv, kOzSmem);
 }
 
 OzBufferSizes oz_buffer_sizes(int n, int s, int K, int S) {

@@ -24,6 +24,7 @@
 // Stages are recycled through full/empty mbarriers; tcgen05.commit arrives on "empty" when the
 // MMAs reading a stage have completed.  Every wait is bounded: on expiry the kernel records an
 // error code, skips the rest of its work, still frees its TMEM and returns.
+#include <cstdlib>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -61,7 +62,8 @@ struct TcCfg {
 // n x s float2 matrices.  `maps` may live in kernel parameter space or in global memory.
 template <int BN, int ESZ, int PARTS>
 __device__ __forceinline__ void tc_sylv_tile(const TcMaps& maps, float2* __restrict__ Y, int n, int s, int nyq,
-                                             int k, int i0, int j0, int* err) {
+                                             int k, int i0, int j0, int* err, int stall,
+                                             unsigned long long wait_ns) {
   using Cfg = TcCfg<BN, ESZ>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -98,10 +100,12 @@ __device__ __forceinline__ void tc_sylv_tile(const TcMaps& maps, float2* __restr
 
   if (warp == 4) {
     if (lane == 0) {
+      int issued = 0;   // stages whose loads were issued
       for (int it = 0; it < iters; ++it) {
         const int slot = it % Cfg::kStages;
         const uint32_t phase = (uint32_t)(it / Cfg::kStages) & 1u;
-        if (!mbar_wait(bar_empty + 8 * slot, phase ^ 1u, err, 1)) break;
+        if (!mbar_wait(bar_empty + 8 * slot, phase ^ 1u, err, 1, wait_ns)) break;
+        if (stall) continue;   // test aid: arm no stage, so the MMA warp's wait expires
         const uint32_t full = bar_full + 8 * slot;
         mbar_expect_tx(full, Cfg::kStage);
         const uint32_t sA = base + slot * Cfg::kStage;
@@ -121,7 +125,12 @@ __device__ __forceinline__ void tc_sylv_tile(const TcMaps& maps, float2* __restr
           tma_load_3d(sB, blo ? &maps.b_re_lo : &maps.b_re, l0, j0, k, full);
           tma_load_3d(sBi, blo ? &maps.b_im_lo : &maps.b_im, l0, j0, k, full);
         }
+        issued = it + 1;
       }
+      // Every stage this warp loaded lands before the CTA exits, also when an error stopped the MMA
+      // warp from consuming it: bounded waits on the last kStages loads (immediate when all were used).
+      for (int it = issued > Cfg::kStages ? issued - Cfg::kStages : 0; it < issued; ++it)
+        mbar_wait(bar_full + 8 * (it % Cfg::kStages), (uint32_t)(it / Cfg::kStages) & 1u, err, 4, wait_ns);
     }
   } else if (warp == 5) {
     if (lane == 0) {
@@ -133,7 +142,7 @@ __device__ __forceinline__ void tc_sylv_tile(const TcMaps& maps, float2* __restr
       for (int it = 0; it < iters && ok; ++it) {
         const int slot = it % Cfg::kStages;
         const uint32_t phase = (uint32_t)(it / Cfg::kStages) & 1u;
-        if (!mbar_wait(bar_full + 8 * slot, phase, err, 2)) {
+        if (!mbar_wait(bar_full + 8 * slot, phase, err, 2, wait_ns)) {
           ok = false;
           break;
         }
@@ -165,10 +174,12 @@ __device__ __forceinline__ void tc_sylv_tile(const TcMaps& maps, float2* __restr
         mma_commit(bar_empty + 8 * slot);
       }
       mma_commit(bar_acc);
+      // after an error the MMAs already issued still complete before TMEM is freed
+      if (!ok) mbar_wait(bar_acc, 0u, err, 5, wait_ns);
     }
   } else {
     // Epilogue: warp w reads TMEM lanes 32w..32w+31 (= output rows i0 + 32w + lane).
-    const bool ok = mbar_wait(bar_acc, 0u, err, 3);
+    const bool ok = mbar_wait(bar_acc, 0u, err, 3, wait_ns);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
       const int row = i0 + warp * 32 + lane;
@@ -204,8 +215,10 @@ __device__ __forceinline__ void tc_sylv_tile(const TcMaps& maps, float2* __restr
 
 template <int BN, int ESZ, int PARTS>
 __global__ void __launch_bounds__(192, 1)
-    k_tc_sylv(const __grid_constant__ TcMaps maps, float2* __restrict__ Y, int n, int s, int nyq, int* err) {
-  tc_sylv_tile<BN, ESZ, PARTS>(maps, Y, n, s, nyq, blockIdx.z, blockIdx.y * kTileM, blockIdx.x * BN, err);
+    k_tc_sylv(const __grid_constant__ TcMaps maps, float2* __restrict__ Y, int n, int s, int nyq, int* err, int stall,
+              unsigned long long wait_ns) {
+  tc_sylv_tile<BN, ESZ, PARTS>(maps, Y, n, s, nyq, blockIdx.z, blockIdx.y * kTileM, blockIdx.x * BN, err, stall,
+                               wait_ns);
 }
 
 template <typename OpT> __device__ __forceinline__ OpT to_op(float v);
@@ -230,7 +243,7 @@ __global__ void __launch_bounds__(192, 1)
   const int4 it = items[blockIdx.x];
   if (!active[it.x]) return;   // instance not in the current inner cycle (uniform over the CTA)
   const BTcInst& b = inst[it.x];
-  tc_sylv_tile<BN, ESZ, PARTS>(maps[it.x], b.Y, b.n, b.s, b.nyq, it.y, it.z, it.w, err);
+  tc_sylv_tile<BN, ESZ, PARTS>(maps[it.x], b.Y, b.n, b.s, b.nyq, it.y, it.z, it.w, err, 0, kWaitNs);
 }
 
 // Planar copies of the FP32 spectra of a batch: per (instance, slice, 32 x 32 tile) work item,
@@ -446,15 +459,12 @@ __global__ void k_transpose_planes(const OpT* __restrict__ cre, const OpT* __res
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 template <int BN, int ESZ, int PARTS>
-void launch_tc(const TcMaps& maps, float2* Y, int n, int s, int K, int nyq, int* err, cudaStream_t st) {
+void launch_tc(const TcMaps& maps, float2* Y, int n, int s, int K, int nyq, int* err, int stall,
+               unsigned long long wait_ns, cudaStream_t st) {
   using Cfg = TcCfg<BN, ESZ>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    TS_CUDA(cudaFuncSetAttribute(k_tc_sylv<BN, ESZ, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
-    attr_set = true;
-  }
+  set_max_dynamic_smem((const void*)k_tc_sylv<BN, ESZ, PARTS>, Cfg::kSmem);
   dim3 grid((s + BN - 1) / BN, (n + kTileM - 1) / kTileM, K);
-  k_tc_sylv<BN, ESZ, PARTS><<<grid, 192, Cfg::kSmem, st>>>(maps, Y, n, s, nyq, err);
+  k_tc_sylv<BN, ESZ, PARTS><<<grid, 192, Cfg::kSmem, st>>>(maps, Y, n, s, nyq, err, stall, wait_ns);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -509,15 +519,15 @@ void planar_dft(const float* X, TcWork& w, int n, int s, int p, int ldn, int lds
 
 template <int PARTS>
 void launch_by_bn(int esz, int bn, const TcMaps& maps, float2* Yh, int n, int s, int K, int nyq, int* err,
-                  cudaStream_t st) {
+                  int stall, unsigned long long wait_ns, cudaStream_t st) {
   if (esz == 2) {
-    if (bn == 64) launch_tc<64, 2, PARTS>(maps, Yh, n, s, K, nyq, err, st);
-    else if (bn == 128) launch_tc<128, 2, PARTS>(maps, Yh, n, s, K, nyq, err, st);
-    else launch_tc<256, 2, PARTS>(maps, Yh, n, s, K, nyq, err, st);
+    if (bn == 64) launch_tc<64, 2, PARTS>(maps, Yh, n, s, K, nyq, err, stall, wait_ns, st);
+    else if (bn == 128) launch_tc<128, 2, PARTS>(maps, Yh, n, s, K, nyq, err, stall, wait_ns, st);
+    else launch_tc<256, 2, PARTS>(maps, Yh, n, s, K, nyq, err, stall, wait_ns, st);
   } else {
-    if (bn == 64) launch_tc<64, 4, PARTS>(maps, Yh, n, s, K, nyq, err, st);
-    else if (bn == 128) launch_tc<128, 4, PARTS>(maps, Yh, n, s, K, nyq, err, st);
-    else launch_tc<256, 4, PARTS>(maps, Yh, n, s, K, nyq, err, st);
+    if (bn == 64) launch_tc<64, 4, PARTS>(maps, Yh, n, s, K, nyq, err, stall, wait_ns, st);
+    else if (bn == 128) launch_tc<128, 4, PARTS>(maps, Yh, n, s, K, nyq, err, stall, wait_ns, st);
+    else launch_tc<256, 4, PARTS>(maps, Yh, n, s, K, nyq, err, stall, wait_ns, st);
   }
 }
 
@@ -633,10 +643,17 @@ void tc_apply(ts_ctx* ctx, ts_op* op, int precision, const float* X, float2* Yh,
     return maps;
   };
   const int nyq = nyquist_index(p);
+  // Test aid for the failure path: with TSTAR_TEST_STALL_TMA=1 in the environment the TMA producer
+  // arms no stage, so the MMA warp's bounded wait expires (after 50 ms instead of the usual limit),
+  // the kernel records the error, frees its tensor memory and returns; the caller then sees
+  // TS_ERR_TIMEOUT.  Read on every application, so a test can turn it on and off around one call.
+  const char* stall_env = std::getenv("TSTAR_TEST_STALL_TMA");
+  const int stall = stall_env && stall_env[0] == '1';
+  const unsigned long long wait_ns = stall ? 50000000ull : kWaitNs;
   auto run = [&](int bn) {
     const TcMaps maps = build(bn);
-    if (t.split) launch_by_bn<3>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
-    else launch_by_bn<1>(esz, bn, maps, Yh, n, s, K, nyq, err, st);
+    if (t.split) launch_by_bn<3>(esz, bn, maps, Yh, n, s, K, nyq, err, stall, wait_ns, st);
+    else launch_by_bn<1>(esz, bn, maps, Yh, n, s, K, nyq, err, stall, wait_ns, st);
   };
   std::vector<int> cands;
   for (int c : {64, 128, 256})
@@ -660,7 +677,7 @@ void batch_preload_bn() {
   using Cfg = TcCfg<BN, ESZ>;
   cudaFuncAttributes fa;
   TS_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_b_tc<BN, ESZ, PARTS>));
-  TS_CUDA(cudaFuncSetAttribute(k_b_tc<BN, ESZ, PARTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+  set_max_dynamic_smem((const void*)k_b_tc<BN, ESZ, PARTS>, Cfg::kSmem);
 }
 
 template <typename OpT, int ESZ, int PARTS, bool SPLIT>

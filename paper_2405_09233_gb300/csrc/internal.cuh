@@ -151,8 +151,12 @@ namespace ts {
 inline int nyquist_index(int p) { return (p % 2 == 0 && p > 1) ? p / 2 : -1; }
 inline int num_slices(int p) { return p / 2 + 1; }
 
-// Memory-kind helpers (host or device pointer).
+// Memory-kind helper: true for device (or managed) memory of the current device, false for host
+// memory; throws TS_ERR_ARG for memory of another device, which a kernel here must not be given.
 bool is_device_ptr(const void* p);
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device (once per kernel and
+// device; thread-safe).
+void set_max_dynamic_smem(const void* func, int bytes);
 
 // ---------------- FFT along mode 3 (fft_tube.cu) ----------------
 // Forward: out[k*T + e] = sum_{t<p} in[t*T + e] exp(-2 pi i k t / p), k < K = p/2+1.

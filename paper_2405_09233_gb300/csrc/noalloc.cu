@@ -1,17 +1,17 @@
 // ts_tstar_noalloc: the T-product C = A*B with no memory allocation at call time.
 //
-// Some callers cannot allocate device memory when they need a T-product: code that records
-// work under CUDA stream capture (cudaMalloc is not a capturable operation and breaks the
-// capture), latency-critical serving loops that must not hit an allocation (cudaMalloc and
-// cudaFree can synchronise the device), and hosts whose device memory is already claimed by
-// another allocator (a framework's caching pool) so that a fresh cudaMalloc can fail.  For them
-// this entry point keeps its scratch -- the Fourier slices of A, B and C -- in a fixed-size
-// array in the library's own device memory, loaded with the library and held by every GPU that
-// loads it until the process exits.  It calls no cudaMalloc, cudaFree or allocating routine.
+// Some callers cannot allocate device memory when they need a T-product: latency-critical serving
+// loops that must not hit an allocation (cudaMalloc and cudaFree can synchronise the whole device),
+// and hosts whose device memory is already claimed by another allocator (a framework's caching
+// pool), so that a fresh cudaMalloc can fail.  For them this entry point keeps its scratch -- the
+// Fourier slices of A, B and C -- in a fixed-size array in the library's own device memory, loaded
+// with the library and held by every GPU that loads it until the process exits.  It calls no
+// cudaMalloc, cudaFree or allocating routine.
 //
 // Host code cannot pass the array's name to a kernel: in host code that name is a host-side
 // stand-in, not a device address.  The device address is looked up once per device with
-// cudaGetSymbolAddress (on the first call made while that device is current) and cached.
+// cudaGetSymbolAddress (on the first call made while that device is current, so that first call
+// belongs before any stream capture) and cached.
 #include <mutex>
 #include "internal.cuh"
 

@@ -365,24 +365,36 @@ __global__ void k_small_gemm(const double2* __restrict__ A, long long sA, int ld
 }
 
 // Cholesky G = R^H R of a Hermitian positive definite s x s matrix per slice (one warp each).
-// R is written upper triangular (zeros below).  err bit 4 on a non-positive pivot.
-__global__ void k_cholesky(const double2* __restrict__ Gall, double2* __restrict__ Rall, int s, int* err,
-                           int* fail_slice) {
+// R is written upper triangular (zeros below).  A pivot d_j (the squared norm of column j's part
+// orthogonal to the previous columns, when G is a Gram matrix) fails when it is not above
+// max(rel * g_jj, tiny2 * max_k g_jj(k)), the second maximum taken over the Grams of all K slices;
+// rel = tiny2 = 0 asks for d_j > 0 only.  A failed slice stops early (R partly written), sets
+// fail_slice[slice] = 1 (each slice's entry is reset to 0 first) and err bit 4 (err may be NULL).
+__global__ void k_cholesky(const double2* __restrict__ Gall, double2* __restrict__ Rall, int s, int K, double rel,
+                           double tiny2, int* err, int* fail_slice) {
   const double2* G = Gall + (long long)blockIdx.x * s * s;
   double2* R = Rall + (long long)blockIdx.x * s * s;
   const int lane = threadIdx.x & 31;
+  if (fail_slice && lane == 0) fail_slice[blockIdx.x] = 0;
   for (int e = lane; e < s * s; e += 32) R[e] = make_double2(0.0, 0.0);
   __syncwarp();
   for (int j = 0; j < s; ++j) {
     // r_jj = sqrt(g_jj - sum_{i<j} |r_ij|^2)
-    double d = G[j + (long long)s * j].x;
+    const double gjj = G[j + (long long)s * j].x;
+    double d = gjj;
     for (int i = 0; i < j; ++i) {
       const double2 r = R[i + (long long)s * j];
       d -= r.x * r.x + r.y * r.y;
     }
-    if (!(d > 0.0)) {
+    double floor_d = rel * gjj;
+    if (tiny2 > 0.0) {
+      double ref2 = 0.0;
+      for (int q = 0; q < K; ++q) ref2 = fmax(ref2, Gall[(long long)q * s * s + j + (long long)s * j].x);
+      floor_d = fmax(floor_d, tiny2 * ref2);
+    }
+    if (!(d > floor_d)) {
       if (lane == 0) {
-        atomicOr(err, 4);
+        if (err) atomicOr(err, 4);
         if (fail_slice) fail_slice[blockIdx.x] = 1;
       }
       return;
@@ -436,8 +448,9 @@ void small_gemm(const double2* A, long long sA, int lda, const double2* B, long 
   TS_CUDA(cudaGetLastError());
 }
 
-void cholesky_small(const double2* G, double2* R, int s, int K, int* err, int* fail_slice, cudaStream_t st) {
-  k_cholesky<<<K, 32, 0, st>>>(G, R, s, err, fail_slice);
+void cholesky_small(const double2* G, double2* R, int s, int K, double rel, double tiny2, int* err, int* fail_slice,
+                    cudaStream_t st) {
+  k_cholesky<<<K, 32, 0, st>>>(G, R, s, K, rel, tiny2, err, fail_slice);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }

@@ -164,6 +164,13 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
       scale_dev<T, T>(W, basis_ptr(V, N, j + 1), N, ks_est(state, m) + 1, st);  // V_{j+1} = W / h
     }
     ++info.cycles;
+    // An expired tensor-core wait makes this cycle's products meaningless, whatever they produced:
+    // checked before the flags those products may have set.
+    if ((mixed && prec != TS_MIXED_FP32) || ozaki) {
+      int e = 0;
+      TS_CUDA(cudaMemcpy(&e, tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (e != 0) throw Error{TS_ERR_TIMEOUT, "tensor-core kernel wait expired (code " + std::to_string(e) + ")"};
+    }
     if ((int)flags & 2) {
       status = TS_SINGULAR;
       break;
@@ -171,11 +178,6 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
     if ((int)flags & 4) {
       status = TS_ERR_NONFINITE;
       break;
-    }
-    if ((mixed && prec != TS_MIXED_FP32) || ozaki) {
-      int e = 0;
-      TS_CUDA(cudaMemcpy(&e, tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-      if (e != 0) throw Error{TS_ERR_TIMEOUT, "tensor-core kernel wait expired (code " + std::to_string(e) + ")"};
     }
     ks_solve(state, m, k, method, st);
     multi_axpy<T, double>(X, V, N, N, ks_y(state, m), k, 1.0, nullptr, st);   // X = X0 + V_k (*) y

@@ -4,9 +4,11 @@
 // Everything runs in the Fourier domain (Eq. (5)): the T-product decouples into K = p/2 + 1
 // independent complex slices, the T-transpose becomes the conjugate transpose of each slice, and
 // a tube becomes one complex number per slice.  So, slice by slice:
-//   * Tubal-QR (Algorithm 6) of an n x s block is the thin QR with a positive real diagonal --
-//     unique, whatever algorithm computes it.  It is computed by CholeskyQR2 (Gram matrix, small
-//     Cholesky, triangular multiply, twice), which keeps the work in GEMM-shaped passes.
+//   * Tubal-QR (Algorithm 6) of a full-rank n x s block is the thin QR with a positive real
+//     diagonal -- unique, whatever algorithm computes it.  It is computed by CholeskyQR2 (Gram
+//     matrix, small Cholesky, triangular multiply, twice), which keeps the work in GEMM-shaped
+//     passes; slices of a (nearly) rank-deficient block run Algorithm 6's Gram-Schmidt with the
+//     Normalize tie-break instead.
 //   * The block MGS step H_ij = V_i^H W, W -= V_i H_ij is a tall-skinny Gram and an update.
 //   * The projected equation H_m Y - Y B = C1 (Eq. (46)) is solved per slice by Hessenberg-Schur
 //     (small_complex.cu) and X += V_m Y.
@@ -413,6 +415,113 @@ __global__ void k_triinv(const double2* __restrict__ Rall, double2* __restrict__
   }
 }
 
+// Algorithm 6 with Normalization1 on the Fourier slices whose first Cholesky pivot showed a (nearly)
+// rank-deficient block (fail[k] = 1; other slices return at once): modified Gram-Schmidt over the s
+// columns of W_k (row-major n x s, in place -> Q_k), r_ij = q_i^H w_j, w_j -= q_i r_ij, then
+// a = ||w_j||.  Column j counts as zero in this slice when a <= tiny * ref_j, ref_j the largest norm of
+// column j over all K slices before orthogonalisation (the square root of max_k G_k(j, j), G the Gram
+// of the original block); then r_jj = 0 and q_j is the first unit vector e_i whose component
+// orthogonal to q_0..q_{j-1} has squared norm >= 1/(2n), orthogonalised twice (classical
+// Gram-Schmidt) and normalised.  Writes R_k (upper triangular, column-major) to R and the identity to
+// Rinv, so the CholeskyQR2 steps that follow leave the slice as it is.  One CTA per slice; rows are
+// strided over the threads (each thread only reads back the rows it wrote, so the block reductions
+// are the only synchronisation needed).  A fallback for rare blocks: columns are read with stride s.
+template <typename C2>
+__global__ void __launch_bounds__(256) k_tubal_mgs(C2* __restrict__ W, const double2* __restrict__ G,
+                                                   const int* __restrict__ fail, double2* __restrict__ R,
+                                                   double2* __restrict__ Rinv, int n, int s, int K, double tiny) {
+  const int k = blockIdx.x;
+  if (!fail[k]) return;
+  __shared__ double2 coef[kMaxS];
+  const long long ns = (long long)n * s;
+  C2* Wk = W + k * ns;
+  double2* Rk = R + (long long)k * s * s;
+  double2* Ik = Rinv + (long long)k * s * s;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    Rk[e] = make_double2(0.0, 0.0);
+    Ik[e] = make_double2(e % s == e / s ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  auto ld = [&](int r, int c) { return widen(Wk[(long long)r * s + c]); };
+  auto st = [&](int r, int c, double2 v) { Wk[(long long)r * s + c] = to_c2(v, (C2*)nullptr); };
+  for (int j = 0; j < s; ++j) {
+    double ref2 = 0.0;
+    for (int q = 0; q < K; ++q) ref2 = fmax(ref2, G[(long long)q * s * s + j + (long long)s * j].x);
+    for (int i = 0; i < j; ++i) {                       // r_ij = q_i^H w_j; w_j -= q_i r_ij
+      double re = 0.0, im = 0.0;
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const double2 q = ld(r, i), w = ld(r, j);
+        re += q.x * w.x + q.y * w.y;
+        im += q.x * w.y - q.y * w.x;
+      }
+      re = block_sum(re);
+      im = block_sum(im);
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const double2 q = ld(r, i), w = ld(r, j);
+        st(r, j, make_double2(w.x - (q.x * re - q.y * im), w.y - (q.x * im + q.y * re)));
+      }
+      if (threadIdx.x == 0) Rk[i + (long long)s * j] = make_double2(re, im);
+    }
+    double a2 = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const double2 w = ld(r, j);
+      a2 += w.x * w.x + w.y * w.y;
+    }
+    const double a = sqrt(block_sum(a2));
+    if (a > tiny * sqrt(ref2)) {                        // Normalize: q_j = w_j / a, r_jj = a
+      const double inv = 1.0 / a;
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const double2 w = ld(r, j);
+        st(r, j, make_double2(w.x * inv, w.y * inv));
+      }
+      if (threadIdx.x == 0) Rk[j + (long long)s * j] = make_double2(a, 0.0);
+      continue;
+    }
+    // rank-deficient slice of column j: r_jj = 0 (already), q_j = a unit vector orthogonal to q_<j
+    for (int e = 0; e < n; ++e) {
+      for (int r = threadIdx.x; r < n; r += blockDim.x) st(r, j, make_double2(r == e ? 1.0 : 0.0, 0.0));
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i < j; ++i) {                   // c_i = q_i^H z for every i first (classical)
+          double re = 0.0, im = 0.0;
+          for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            const double2 q = ld(r, i), z = ld(r, j);
+            re += q.x * z.x + q.y * z.y;
+            im += q.x * z.y - q.y * z.x;
+          }
+          re = block_sum(re);
+          im = block_sum(im);
+          if (threadIdx.x == 0) coef[i] = make_double2(re, im);
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+          double2 z = ld(r, j);
+          for (int i = 0; i < j; ++i) {
+            const double2 q = ld(r, i), c = coef[i];
+            z.x -= q.x * c.x - q.y * c.y;
+            z.y -= q.x * c.y + q.y * c.x;
+          }
+          st(r, j, z);
+        }
+        __syncthreads();                                // coef is rewritten by the next pass
+      }
+      double z2 = 0.0;
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const double2 z = ld(r, j);
+        z2 += z.x * z.x + z.y * z.y;
+      }
+      z2 = block_sum(z2);
+      if (z2 >= 0.5 / n) {
+        const double inv = 1.0 / sqrt(z2);
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+          const double2 z = ld(r, j);
+          st(r, j, make_double2(z.x * inv, z.y * inv));
+        }
+        break;
+      }
+    }
+  }
+}
+
 // Column-major spectral [k][j][i] <-> row-major [k][i][j], 32 x 32 tiles.
 __global__ void k_spec_transpose(const double2* __restrict__ in, double2* __restrict__ out, int rows, int cols) {
   // in: K x (cols x rows) with rows fastest; out: K x (rows x cols) with cols fastest
@@ -507,6 +616,7 @@ struct TbaWork {
   double* P;                // kRedBlocks partials
   double* sc;               // scalars
   int* err;                 // error bits
+  int* fail;                // K flags: slices whose Tubal-QR took the Gram-Schmidt fallback
   KernelTimer* tm;          // per-kernel timing (kind 4: tubal Gram and block products)
 };
 
@@ -633,12 +743,7 @@ void rows_mm(const Cin* In, Cout* Out, const double2* M, long long sM, int ldm, 
   const int rows_per_block = 256 / tpr;
   const int gx = std::max(1, std::min((n + rows_per_block - 1) / rows_per_block, 4 * 152 * 4 / K));
   const size_t smem = sizeof(R) * 3 * (size_t)s * s;
-  static bool attr = false;
-  if (!attr) {
-    TS_CUDA(cudaFuncSetAttribute(k_rows_mm<Cin, Cout>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(R) * 3 * kMaxS * kMaxS)));
-    attr = true;
-  }
+  set_max_dynamic_smem((const void*)k_rows_mm<Cin, Cout>, (int)(sizeof(R) * 3 * kMaxS * kMaxS));
   k_rows_mm<Cin, Cout><<<dim3(gx, K), 256, smem, st>>>(In, Out, M, sM, ldm, n, s, alpha, accumulate ? 1 : 0);
   count_launch();
   TS_CUDA(cudaGetLastError());
@@ -673,19 +778,31 @@ void triinv(const double2* R, double2* X, int s, int K, cudaStream_t st) {
   TS_CUDA(cudaGetLastError());
 }
 
-// Tubal-QR of the block W (in place -> Q) by CholeskyQR2; R written to Rout (column-major, ldr).
-// Returns false on a failed Cholesky (rank-deficient block).
+// Tubal-QR of the block W (in place -> Q); R written to Rout (column-major, ldr).  Per Fourier slice
+// the QR with a positive real diagonal is unique for a full-rank block, and CholeskyQR2 computes it
+// in GEMM-shaped passes: G = W^H W, G = R1^H R1, W <- W R1^-1, again with R2, R = R2 R1.  A slice
+// whose first Cholesky pivot says that a column is (nearly) dependent on the previous ones -- its
+// orthogonal part below 1e-6 of its norm in FP64 (1e-3 in FP32), or its norm below the rank-deficiency
+// scale of Normalization1 -- takes Algorithm 6 itself instead (k_tubal_mgs: Gram-Schmidt with the
+// Normalize tie-break), whose Q the second CholeskyQR pass then only re-orthogonalises to rounding.
+// Returns false when the second Cholesky fails (not expected after either first pass).
 template <typename C2>
 bool tubal_qr(const TbaWork& w, C2* W, double2* Rout, long long sR, int ldr, cudaStream_t st) {
   const int s = w.s, K = w.K;
   const long long ss = (long long)s * s;
+  constexpr bool f64 = sizeof(C2) == 16;
+  const double tiny = f64 ? 1e-12 : 1e-4;      // Normalization1: a slice is zero below tiny * ref_j
+  const double rel = f64 ? 1e-12 : 1e-6;       // CholeskyQR is trusted for orthogonal parts above sqrt(rel)
   TS_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   gram(w, W, W, w.G, ss, s, st);
-  cholesky_small(w.G, w.R1, s, K, w.err, nullptr, st);
+  cholesky_small(w.G, w.R1, s, K, rel, tiny * tiny, nullptr, w.fail, st);
   triinv(w.R1, w.Rinv, s, K, st);
+  k_tubal_mgs<C2><<<K, 256, 0, st>>>(W, w.G, w.fail, w.R1, w.Rinv, w.n, s, K, tiny);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
   rows_mm_timed(w, W, W, w.Rinv, ss, s, 1.0, false, st);
   gram(w, W, W, w.G, ss, s, st);
-  cholesky_small(w.G, w.R2, s, K, w.err, nullptr, st);
+  cholesky_small(w.G, w.R2, s, K, 0.0, 0.0, w.err, nullptr, st);
   triinv(w.R2, w.Rinv, s, K, st);
   rows_mm_timed(w, W, W, w.Rinv, ss, s, 1.0, false, st);
   small_gemm(w.R2, ss, s, w.R1, ss, s, false, Rout, sR, ldr, s, s, s, K, false, st);   // R = R2 R1
@@ -772,6 +889,7 @@ TbaWork tba_work(ts_ctx* ctx, const ts_op* op, int m) {
   w.P = (double*)get("tba_P", sizeof(double) * kRedBlocks);
   w.sc = (double*)get("tba_sc", sizeof(double) * 16);
   w.err = (int*)get("tba_err", sizeof(int) * 4);
+  w.fail = (int*)get("tba_fail", sizeof(int) * (size_t)K);
   w.tm = &ctx->timer;
   return w;
 }

@@ -23,7 +23,9 @@ void hs_solve(const double2* LU, const int* piv, const double2* G, const double2
               int K, cudaStream_t st);
 void small_gemm(const double2* A, long long sA, int lda, const double2* B, long long sB, int ldb, bool transB, double2* C,
                 long long sC, int ldc, int M, int L, int Ncol, int K, bool accumulate, cudaStream_t st);
-void cholesky_small(const double2* G, double2* R, int s, int K, int* err, int* fail_slice, cudaStream_t st);
+// Per-slice Cholesky G = R^H R with the pivot test of k_cholesky (rel, tiny2; 0, 0 for d > 0 only).
+void cholesky_small(const double2* G, double2* R, int s, int K, double rel, double tiny2, int* err, int* fail_slice,
+                    cudaStream_t st);
 
 // Schur factors of the operator's B_k (computed on first use and cached in the operator).
 void ensure_b_schur(ts_ctx* ctx, ts_op* op, cudaStream_t st);

@@ -10,7 +10,9 @@
 namespace ts {
 namespace tcg {
 
-constexpr long long kWaitLimit = 1ll << 26;  // polls (with nanosleep backoff) before giving up
+// Every mbarrier wait is bounded by elapsed time (the %globaltimer nanosecond clock): a stage of a
+// healthy pipeline completes in microseconds, so a wait that lasts kWaitNs means a stalled pipeline.
+constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -34,11 +36,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; returns false (and records `code`) when the limit expires.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-  for (long long i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: returns false (and records `code` in *err unless an earlier code is there) when
+// the phase has not completed within limit_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code,
+                                          unsigned long long limit_ns = kWaitNs) {
+  for (int i = 0; i < 64; ++i)
     if (mbar_try(bar, parity)) return true;
-    if (i > 64) __nanosleep(128);
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    __nanosleep(128);
+    if (globaltimer_ns() - t0 > limit_ns) break;
   }
   atomicCAS(err, 0, code);
   return false;

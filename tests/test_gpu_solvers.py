@@ -134,3 +134,24 @@ def test_errors_are_reported(ctx):
         ctx.tgmres_solve(op, Cn, torch.zeros_like(C), restart=5)
     assert e.value.status == -4                            # TS_ERR_NONFINITE
     op.close()
+
+
+@pytest.mark.parametrize("method", ["gmres", "fom"])
+def test_breakdown_gives_exact_solution(ctx, method):
+    """Algorithm 2's breakdown h_{j+1,j} = 0 on the GPU: M = 4 I (A^(1) = 3 I, B^(1) = -I), so C spans an
+    invariant subspace, the Arnoldi process stops after one step and X = C / 4 exactly (as the oracle)."""
+    import torch
+    n, s, p = 4, 3, 2
+    A = np.zeros((n, n, p)); A[:, :, 0] = 3.0 * np.eye(n)
+    B = np.zeros((s, s, p)); B[:, :, 0] = -np.eye(s)
+    C = inputs.random_tensor((n, s, p), seed=1)
+    ref = kr.restarted_solve(method, A, B, C, m=5, tol=1e-10)
+    assert ref.iters == 1 and ref.status == "ok"
+    op = ctx.op_create_dense(to_dev(A), to_dev(B))
+    Xd = torch.zeros((p, s, n), dtype=torch.float64, device="cuda")
+    fn = ctx.tgmres_solve if method == "gmres" else ctx.tfom_solve
+    res = fn(op, to_dev(C), Xd, restart=5, tol=1e-10)
+    assert res.status == 0 and res.info.iters == 1 and res.info.cycles == 1, res
+    np.testing.assert_allclose(from_dev(Xd), C / 4.0, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(from_dev(Xd), ref.X, rtol=0, atol=1e-15)
+    op.close()

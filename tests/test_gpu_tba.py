@@ -184,3 +184,68 @@ def test_tbas_mixed_fp32_sparse_lap128(ctx, s):
     assert float(torch.max(torch.abs(Xd - Xs))) < 1e-8
     op.close()
 
+
+
+def deficient_rhs(n, s, p, kind, seed):
+    """A random right-hand side whose lateral slice 1 repeats slice 0 ("equal") or is zero ("zero")."""
+    C = inputs.random_tensor((n, s, p), seed=seed)
+    C[:, 1, :] = C[:, 0, :] if kind == "equal" else 0.0
+    return C
+
+
+@pytest.mark.parametrize("kind", ["equal", "zero"])
+@pytest.mark.parametrize("case", [(20, 3, 4, 3), (40, 4, 5, 4), (33, 6, 8, 3)], ids=lambda c: "n%d_s%d_p%d_m%d" % c)
+def test_tbas_rank_deficient_start_dense(ctx, case, kind):
+    """R0 = C with a repeated or zero lateral slice: Tubal-QR's first block is rank deficient in every
+    Fourier slice, the GPU takes Algorithm 6 with the Normalize tie-break there (not CholeskyQR2),
+    and TBAS(m) follows the oracle's residual histories and solution."""
+    import torch
+    n, s, p, m = case
+    pr = inputs.dense_problem(n, s, p, seed=5)
+    C = deficient_rhs(n, s, p, kind, seed=6)
+    ref = tb.tbas(pr.A, pr.B, C, m=m, tol=1e-10)
+    op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
+    Xd = torch.zeros((p, s, n), dtype=torch.float64, device="cuda")
+    res = ctx.tba_solve(op, to_dev(C), Xd, restart=m, tol=1e-10)
+    X = from_dev(Xd)
+    assert res.status == 0 and ref.status == "ok", (res, ref.status)
+    assert len(res.true_history) == len(ref.true_res)
+    np.testing.assert_allclose(res.true_history, ref.true_res, rtol=0, atol=1e-10 * ref.normC)
+    np.testing.assert_allclose(res.history, ref.history, rtol=0, atol=1e-10 * ref.normC)
+    np.testing.assert_allclose(X, ref.X, rtol=0, atol=1e-9 * np.abs(ref.X).max())
+    op.close()
+
+
+@pytest.mark.parametrize("kind", ["equal", "zero"])
+def test_tbas_rank_deficient_start_sparse(ctx, kind):
+    import torch
+    grid, s, p, m = 6, 3, 3, 5
+    prob = inputs.sparse_problem(grid=grid, s=s, p=p, seed=5)
+    slices = scipy_slices(prob)
+    applyA = lambda Z: tb.tprod_sparse(slices, Z)  # noqa: E731
+    rowptr, col, val = csr_arrays(prob)
+    op = ctx.op_create_csr(prob.n, p, rowptr, col, val, to_dev(prob.B))
+    C = deficient_rhs(prob.n, s, p, kind, seed=8)
+    ref = tb.tbas(None, prob.B, C, m=m, tol=1e-10, applyA=applyA)
+    Xd = torch.zeros((p, s, prob.n), dtype=torch.float64, device="cuda")
+    res = ctx.tba_solve(op, to_dev(C), Xd, restart=m, tol=1e-10)
+    assert res.status == 0 and ref.status == "ok", (res, ref.status)
+    assert len(res.true_history) == len(ref.true_res)
+    np.testing.assert_allclose(res.true_history, ref.true_res, rtol=0, atol=1e-10 * ref.normC)
+    np.testing.assert_allclose(res.history, ref.history, rtol=0, atol=1e-10 * ref.normC)
+    np.testing.assert_allclose(from_dev(Xd), ref.X, rtol=0, atol=1e-9 * np.abs(ref.X).max())
+    op.close()
+
+
+def test_tbas_mixed_rank_deficient_start_converges(ctx):
+    """The FP32 inner cycle of mixed-precision TBAS takes the same fallback and still reaches 1e-10."""
+    import torch
+    n, s, p, m = 40, 4, 5, 4
+    pr = inputs.dense_problem(n, s, p, seed=5)
+    C = deficient_rhs(n, s, p, "zero", seed=6)
+    op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
+    Xd = torch.zeros((p, s, n), dtype=torch.float64, device="cuda")
+    res = ctx.tba_solve(op, to_dev(C), Xd, restart=m, tol=1e-10, precision="mixed_fp32")
+    assert res.status == 0, res
+    assert tp.norm(C - kr.sylv_apply(pr.A, pr.B, from_dev(Xd))) <= 1e-10 * tp.norm(C)
+    op.close()
