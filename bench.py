@@ -5,14 +5,17 @@ of 1e-10, on GB300.
 One step = one complete solve of A*X - X*B = C from X0 = 0 through the C ABI (operator setup
 ts_op_create_dense included), with the inputs resident in HBM.  The default workload is the
 dense 1024 x 1024 x 16 family (A^(1) = tridiag(-1,4,-1) + 0.1 G/sqrt(n), ...; X* ~ U(-1,1),
-C = M(X*)) solved by FP64 tGMRES(30).  Every rank solves its own instance (weak scaling, no
-collective on the data path).
+C = M(X*)) solved by FP64 tGMRES(30) on the FP64 CUDA cores.  Every rank solves its own instance
+(weak scaling, no collective on the data path).
 
 The JSON line also carries: `e2e` (the same metric with host buffers, copies inside the timed
-region), `roofline` for the dominant kernel (the per-slice GEMM, timed by CUDA events inside
-the library over the timed region), `cpu_baseline` (the CPU oracle on this host's cores, on a
-bounded sample), `clocks` sampled during the timed region, `gpu_launches`, and `variants`
-(mixed precision on the same workload).
+region, median of --e2e-steps), `roofline` for the dominant kernel (timed by CUDA events inside
+the library over the timed region), `cpu_baseline` (one complete solve of the CPU oracle on this
+host's cores), `clocks` sampled during the timed region, `gpu_launches`, `variants` (the other
+methods, precisions and FP64 engines on the same workload, each the median of --reps timed solves
+and certified by the FP64 CUDA-core operator) and `comparisons` (the mixed-precision and batched
+forms against FP64 tGMRES on both FP64 engines, for the dense 1024 x 1024 x 16, the dense
+4096 x 256 x 32 and the 256-instance batched workloads).
 """
 from __future__ import annotations
 
@@ -30,10 +33,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "STE unknowns/s at rel. residual 1e-10: mixed/batched vs FP64 tGMRES, 1 GB300"
 UNIT = "unknowns/s"
-FP64_NOMINAL_TFLOPS = 4 * 152 * 2.070e9 / 1e12   # 4 FP64 FLOP/clk/SM x 152 SMs x 2070 MHz
+NOMINAL_SMS = 152           # GB300, used only when no device can be queried
+NOMINAL_SM_MHZ = 2070.0
 
 
-def args_parse():
+def args_parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -47,19 +51,24 @@ def args_parse():
     ap.add_argument("--variants", default=None,
                     help="comma list of extra precision[@engine] runs to time, 'tfom' for FP64 tFOM ('' = none; "
                          "default: every method, precision and engine the workload supports)")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=3, help="timed solves per variant / comparison entry (median)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparisons", action="store_true",
+                    help="skip the cross-workload comparison of the mixed/batched forms with FP64 tGMRES")
     ap.add_argument("--mode", choices=["solve", "apply"], default="solve",
                     help="solve: full solves (the benchmark); apply: operator applications only (kernel runs)")
     ap.add_argument("--count", type=int, default=None, help="instances of the batched workload (default 256)")
     ap.add_argument("--n", type=int)
     ap.add_argument("--s", type=int)
     ap.add_argument("--p", type=int)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
-DENSE_VARIANTS = "tfom,mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16,fp64@ozaki,tfom@ozaki,mixed_tf32x3@ozaki,mixed_bf16@ozaki"
-BATCHED_VARIANTS_DEFAULT_MARK = "<batched-default>"
+DENSE_VARIANTS = ("tfom,mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16,fp64@ozaki,tfom@ozaki,mixed_tf32x3@ozaki,"
+                  "mixed_bf16@ozaki")
+BATCHED_VARIANTS = "fp64,mixed_fp32,fp64@ozaki,mixed_fp32@ozaki,mixed_tf32x3@ozaki,mixed_bf16@ozaki"
+DENSE_WORKLOADS = ("dense_n24_s24_p4", "dense_n1024_s1024_p16", "dense_n4096_s256_p32_g0.3")
 
 
 def workload_cfg(a):
@@ -71,25 +80,57 @@ def workload_cfg(a):
     return cfg
 
 
+# ------------------------------------------------------------------------------------------------
+# roofline arithmetic
+# ------------------------------------------------------------------------------------------------
 def peaks():
     """Roofline denominators: MEASURED_PEAKS.json when present, else the recipe's fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         d = json.load(open(path))
         return {"hbm_gbs": d["hbm_gbs"], "bf16_burst": d["bf16_tflops"], "bf16_sustained": d["bf16_tflops_sustained"],
-                "source": "measured"}
+                "sm_max_mhz": d.get("sm_max_mhz", NOMINAL_SM_MHZ), "source": "measured"}
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_burst": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
+        return {"hbm_gbs": 6800.0, "bf16_burst": 1900.0, "bf16_sustained": 1700.0, "sm_max_mhz": NOMINAL_SM_MHZ,
+                "source": "fallback"}
+
+
+def device_sms(dev=None) -> int:
+    """SM count of the device (the nominal 152 when no device can be queried)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(dev if dev is not None else 0).multi_processor_count)
+    except Exception:
+        pass
+    return NOMINAL_SMS
+
+
+def fp64_peak_tflops(sms: int, mhz: float) -> float:
+    """FP64 CUDA-core peak derived from unit counts and clock: 2 DFMA (4 FLOP) per clock per SM."""
+    return 4.0 * sms * mhz * 1e6 / 1e12
+
+
+def ffma_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 CUDA-core peak: 128 FP32 lanes per SM, 2 FLOP per FMA."""
+    return 2.0 * 128 * sms * mhz * 1e6 / 1e12
 
 
 TF32_OVER_BF16 = 1.1 / 2.25       # nominal dense tensor rates (PFLOP/s per GPU)
-FFMA_NOMINAL_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12   # 128 FP32 lanes/SM x 2 FLOP x 152 SMs x 2070 MHz
+
+
+def slice_flops(n, s, p, per_complex):
+    """FLOPs of one application's slice products Y_k = A_k X_k - X_k B_k over the K = p/2 + 1 Fourier
+    slices, at `per_complex` FLOPs per complex multiply-add (8 conventional, 6 for the three-multiply
+    form) and 2 per real one (slices 0 and p/2)."""
+    K = p // 2 + 1
+    nreal = 1 + (1 if p % 2 == 0 and p > 1 else 0)
+    return n * s * (n + s) * (per_complex * (K - nreal) + 2 * nreal)
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant kernels at the
-# n = s = 1024, p = 16 workload, from one ncu capture each (profiles/traffic_dense_n1024_s1024_p16.md);
-# a roofline object carries them only for that workload and, for the emulated product, only when every
-# launch used 6 digits.
+# n = s = 1024, p = 16 workload, from one ncu capture each of the kernels as they stand; a roofline object
+# carries them only for that workload and, for the emulated product, only when every launch used 6 digits.
 TRAFFIC_N1024 = {"k_gemm_slices<double>": 497799168 + 137544960, "k_oz_sylv/6": 1779147520 + 149931264}
 
 
@@ -108,27 +149,37 @@ def ozaki_roofline(flops_per_launch, pair_flops_per_launch, avg_ms, sustained, s
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
             "kernel": "k_oz_sylv (emulated FP64: %.1f BF16 digit-pair products per launch on tcgen05)" % pairs,
-            "note": "peak: %s BF16 %s; FP64-equivalent rate %.2f TFLOP/s. Kernel share of the step: %.3f"
+            "note": "peak: %s BF16 %s (of measured); FP64-equivalent rate %.2f TFLOP/s (8 FLOP per complex "
+                    "multiply-add). Kernel share of the step: %.3f"
                     % (pk["source"], "sustained" if sustained else "burst",
                        flops_per_launch / (avg_ms * 1e-3) / 1e12, share)}
 
 
-def gemm_roofline(kind, precision, flops_per_launch, avg_ms, sustained, share):
-    """Roofline object for the dominant slice-GEMM kernel."""
+def fp64_gemm_roofline(executed_per_launch, conventional_per_launch, avg_ms, share, sms, mhz, dgemm_tflops=None):
+    """The FP64 CUDA-core slice GEMM.  It implements the three-multiplication (Gauss) complex product,
+    whose FLOP count is 6 per complex multiply-add (3 DFMA) and 2 per real one: achieved = that count
+    / launch time, against the FP64 peak derived from the device's SM count and maximum clock."""
+    peak = fp64_peak_tflops(sms, mhz)
+    achieved = executed_per_launch / (avg_ms * 1e-3) / 1e12
+    conv = conventional_per_launch / (avg_ms * 1e-3) / 1e12
+    note = (f"FLOPs of the 3-multiply complex product the kernel implements (6 per complex multiply-add, 2 per "
+            f"real); the conventional 8-FLOP count gives {conv:.3f} TFLOP/s. peak derived: 2 DFMA/clk/SM x "
+            f"{sms} SMs x {mhz:.0f} MHz. Kernel share of the step: {share:.3f}")
+    if dgemm_tflops:
+        note += f". cuBLAS DGEMM (8192^3, torch) in this run: {dgemm_tflops:.3f} TFLOP/s"
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_gemm_slices<double> (FP64 DFMA, 3-multiply complex)", "note": note}
+
+
+def lowp_gemm_roofline(precision, flops_per_launch, avg_ms, sustained, share, sms, mhz):
+    """The low-precision slice products: FP32 CUDA cores, or tcgen05 with TF32 / BF16 / split-TF32 inputs."""
     achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
     pk = peaks()
-    if kind == "fp64":
-        return {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
-                "kernel": "k_gemm_slices<double> (FP64 DFMA, 3-multiply complex)",
-                "note": ("peak derived: 4 FP64 FLOP/clk/SM x 152 SMs x 2070 MHz (nominal). Algorithmic FLOPs count 8 "
-                         "per complex multiply-add; the kernel executes 6 (Gauss), so frac can reach 1.33. "
-                         f"Kernel share of the step: {share:.3f}")}
     if precision == "mixed_fp32":
-        return {"bound": "alu", "achieved": achieved, "peak": FFMA_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FFMA_NOMINAL_TFLOPS, "traffic": None,
-                "kernel": "k_gemm_slices<float> (FP32 FFMA, 3-multiply complex)",
-                "note": f"peak derived: 2 FLOP x 128 lanes/SM x 152 SMs x 2070 MHz. Kernel share: {share:.3f}"}
+        peak = ffma_peak_tflops(sms, mhz)
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_gemm_slices<float> (FP32 FFMA)",
+                "note": f"peak derived: 2 FLOP x 128 lanes/SM x {sms} SMs x {mhz:.0f} MHz. Kernel share: {share:.3f}"}
     bf = pk["bf16_sustained"] if sustained else pk["bf16_burst"]
     tf32 = precision in ("mixed_tf32", "mixed_tf32x3")
     parts = 3 if precision == "mixed_tf32x3" else 1
@@ -136,10 +187,39 @@ def gemm_roofline(kind, precision, flops_per_launch, avg_ms, sustained, share):
     name = {"mixed_tf32": "TF32", "mixed_bf16": "BF16", "mixed_tf32x3": "split TF32 x3"}[precision]
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "kernel": f"k_tc_sylv ({name} tcgen05)",
-            "note": (f"peak: {pk['source']} BF16 {'sustained' if sustained else 'burst'}"
+            "note": (f"peak: {pk['source']} BF16 {'sustained' if sustained else 'burst'} (of measured)"
                      + (" x nominal TF32/BF16 ratio 0.489" if tf32 else "")
                      + (" / 3 products (split TF32)" if parts == 3 else "")
-                     + f". Kernel share of the step: {share:.3f}")}
+                     + f"; 8 FLOP per complex multiply-add. Kernel share of the step: {share:.3f}")}
+
+
+def stats_rooflines(st, n, s, p, total_ms, sustained, precision, sms, mhz, workload, dgemm=None, exec_ratio=None):
+    """Roofline objects of every slice-product class the library timed; the first is the dominant one.
+    exec_ratio (batched workloads): executed / conventional FLOPs of the FP64 products over the batch."""
+    out = []
+    batched = exec_ratio is not None
+    if st.gemm_launches:
+        if batched:
+            conv = st.gemm_flops / st.gemm_launches
+            executed = conv * exec_ratio
+        else:
+            conv, executed = slice_flops(n, s, p, 8), slice_flops(n, s, p, 6)
+        r = fp64_gemm_roofline(executed, conv, st.gemm_ms / st.gemm_launches, st.gemm_ms / total_ms, sms, mhz, dgemm)
+        if not batched:
+            r["traffic"] = traffic_for("k_gemm_slices<double>", workload)
+        out.append((st.gemm_ms, r))
+    if st.oz_launches:
+        r = ozaki_roofline(st.oz_flops / st.oz_launches, st.oz_pair_flops / st.oz_launches,
+                           st.oz_ms / st.oz_launches, sustained, st.oz_ms / total_ms)
+        if not batched and abs(st.oz_pair_flops - 21 * st.oz_flops) <= 1e-9 * st.oz_pair_flops:
+            r["traffic"] = traffic_for("k_oz_sylv/6", workload)
+        out.append((st.oz_ms, r))
+    if st.lowp_launches and precision != "fp64":
+        r = lowp_gemm_roofline(precision, st.lowp_flops / st.lowp_launches, st.lowp_ms / st.lowp_launches,
+                               sustained, st.lowp_ms / total_ms, sms, mhz)
+        out.append((st.lowp_ms, r))
+    out.sort(key=lambda t: -t[0])
+    return [r for _, r in out]
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -168,6 +248,28 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def blas_threads():
+    """Threads numpy's BLAS uses (threadpoolctl when importable, else the host's core count)."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads") for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def speedups(entries, base_names, fast_names):
+    """value(fast) / value(base) for every pair present without error."""
+    out = {}
+    for f in fast_names:
+        for b in base_names:
+            if f in entries and b in entries and "value" in entries[f] and "value" in entries[b]:
+                out[f"{f} / {b}"] = entries[f]["value"] / entries[b]["value"]
+    return out
 
 
 # ------------------------------------------------------------------------------------------------
@@ -226,92 +328,341 @@ class ClockSampler:
                 "power_w_median": statistics.median(power) if power else None}
 
 
+def measure_dgemm_tflops(dev):
+    """cuBLAS FP64 GEMM rate (torch.matmul, 8192^3, best of 3): a measured reference for the FP64 roof."""
+    try:
+        import torch
+        a = torch.randn(8192, 8192, dtype=torch.float64, device=dev)
+        b = torch.randn(8192, 8192, dtype=torch.float64, device=dev)
+        torch.matmul(a, b)
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b
+        torch.cuda.empty_cache()
+        return 2 * 8192 ** 3 / (best * 1e-3) / 1e12
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------------------------------------------
-# the CPU oracle on a bounded sample (rank 0, N = 1)
+# the CPU oracle (rank 0, N = 1)
 # ------------------------------------------------------------------------------------------------
-def oracle_apply_sample(wl_cfg, seed, n_applies=2):
-    """Time n_applies oracle applications of M (Definition 2.1 route) at the full workload size."""
-    import numpy as np
+def oracle_dense_inputs(wl_cfg, seed):
+    """The workload's inputs with C = M(X*) formed by the oracle (never by the CUDA path)."""
     from paper_2405_09233_gb300 import inputs
     from oracle import krylov
     pr = inputs.dense_problem(wl_cfg["n"], wl_cfg["s"], wl_cfg["p"], seed=seed, scale=wl_cfg["scale"])
-    X = pr.Xstar
-    times = []
-    for _ in range(n_applies):
-        t0 = time.perf_counter()
-        Y = krylov.sylv_apply(pr.A, pr.B, X)
-        times.append(time.perf_counter() - t0)
-        X = Y / np.linalg.norm(Y)
-    return min(times)
+    return pr, krylov.sylv_apply(pr.A, pr.B, pr.Xstar)
 
 
-def oracle_applies_needed(wl_cfg, seed):
-    """Operator applications the oracle's own tGMRES needs on the same family at n = s = 128
-    (the spectrum of this family, hence the iteration count, does not depend on n)."""
+def oracle_full_solve(pr, C, restart):
+    """One complete oracle tGMRES(m) solve (Algorithm 3 over the bcirc definition), timed."""
+    from oracle import krylov
+    t0 = time.perf_counter()
+    r = krylov.tgmres(pr.A, pr.B, C, m=restart, tol=1e-10)
+    return time.perf_counter() - t0, r
+
+
+def cpu_baseline_dense(wl_cfg, seed):
+    n, s, p = wl_cfg["n"], wl_cfg["s"], wl_cfg["p"]
+    pr, C = oracle_dense_inputs(wl_cfg, seed)
+    t, r = oracle_full_solve(pr, C, wl_cfg["restart"])
+    return {"value": n * s * p / t, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": (f"one complete oracle tGMRES({wl_cfg['restart']}) solve at n={n}, s={s}, p={p} (timed solve, "
+                       f"MGS included; numpy FP64, T-product by the bcirc block-row definition): {t:.1f} s, "
+                       f"{r.iters} inner steps in {r.cycles} cycles, status {r.status}, true rel. residual "
+                       f"{r.relres:.2e}")}
+
+
+def cpu_baseline_batched(specs, budget_s=20.0):
+    """Complete oracle tGMRES(20) solves of the batch's instances in their order, until ~budget_s."""
     from paper_2405_09233_gb300 import inputs
     from oracle import krylov
-    pr = inputs.dense_problem(128, 128, wl_cfg["p"], seed=seed, scale=wl_cfg["scale"])
-    C = krylov.sylv_apply(pr.A, pr.B, pr.Xstar)
-    r = krylov.tgmres(pr.A, pr.B, C, m=wl_cfg["restart"], tol=1e-10)
-    return r.iters + r.cycles + 1, r
+    solved, t_tot, unknowns = 0, 0.0, 0
+    for sp in specs:
+        pr = inputs.dense_problem(sp.n, sp.s, sp.p, seed=sp.seed)
+        C = krylov.sylv_apply(pr.A, pr.B, pr.Xstar)
+        t0 = time.perf_counter()
+        krylov.tgmres(pr.A, pr.B, C, m=20, tol=1e-10)
+        t_tot += time.perf_counter() - t0
+        unknowns += sp.n * sp.s * sp.p
+        solved += 1
+        if t_tot >= budget_s:
+            break
+    return {"value": unknowns / t_tot, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": (f"complete oracle tGMRES(20) solves (FP64, bcirc definition) of the batch's first {solved} "
+                       f"instances in their order ({unknowns} unknowns, {t_tot:.1f} s)")}
 
 
-def cpu_baseline(wl_cfg, seed):
-    import numpy as np
-    n, s, p = wl_cfg["n"], wl_cfg["s"], wl_cfg["p"]
-    t_apply = oracle_apply_sample(wl_cfg, seed)
-    applies, r = oracle_applies_needed(wl_cfg, seed)
-    t_solve = t_apply * applies
-    cores = os.cpu_count()
-    return {"value": n * s * p / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"oracle M(X) (bcirc block-row definition, numpy FP64, {cores} host threads) timed at "
-                       f"n={n}, s={s}, p={p}: {t_apply:.2f} s/apply; x {applies} applies (the oracle tGMRES("
-                       f"{wl_cfg['restart']}) iteration count + residuals at n=s=128, same family); "
-                       f"MGS cost (<1%) not included")}
+def cpu_baseline_tbas(prob, m):
+    import scipy.sparse as sp
+    from oracle import tubal
+    slices = [sp.csr_matrix((sl.val, sl.col, sl.rowptr), shape=(prob.n, prob.n)) for sl in prob.slices]
+    applyA = lambda Z: tubal.tprod_sparse(slices, Z)  # noqa: E731
+    from oracle import tproduct
+    C = applyA(prob.Xstar) - tproduct.tprod(prob.Xstar, prob.B)
+    t0 = time.perf_counter()
+    r = tubal.tbas(None, prob.B, C, m=m, tol=1e-10, applyA=applyA)
+    t = time.perf_counter() - t0
+    return {"value": prob.n * prob.B.shape[0] * prob.p / t, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": (f"one complete oracle TBAS({m}) solve at n={prob.n}, s={prob.B.shape[0]}, p={prob.p} (timed "
+                       f"solve; sparse frontal slices, bcirc block-row T-products): {t:.1f} s, {r.cycles} cycles, "
+                       f"status {r.status}")}
 
 
-# ------------------------------------------------------------------------------------------------
 def run_reference(a):
+    """The reference arm: the oracle on this host's cores, on the default workload's config.
+
+    A complete oracle tGMRES(30) solve is timed once first (calibration).  Each warm-up and timed step
+    is then a bounded sample of the same solve: one inner step of the oracle's Algorithm 2 at the full
+    size (one M(X) by the bcirc definition, the MGS pass, the norm), about 1/S of the complete solve's
+    time, S = T(complete solve) / T(sample) from the calibration.  ms_per_step is the sample's own
+    time; value = unknowns / (median step x S)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import numpy as np
     from paper_2405_09233_gb300 import inputs
+    from oracle import krylov
+    if a.workload not in ("dense_n1024_s1024_p16", "dense_n24_s24_p4"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the dense workloads only"}))
+        return
     cfg = inputs.WORKLOADS[a.workload]
-    n, s, p = cfg["n"], cfg["s"], cfg["p"]
-    applies, _ = oracle_applies_needed(cfg, 1)
+    n, s, p, m = cfg["n"], cfg["s"], cfg["p"], cfg["restart"]
+    pr, C = oracle_dense_inputs(cfg, 1)
+    apply = lambda X: krylov.sylv_apply(pr.A, pr.B, X)  # noqa: E731
+    V = C / np.linalg.norm(C)
+
+    def sample():
+        t0 = time.perf_counter()
+        krylov.tarnoldi(apply, V, 1)
+        return time.perf_counter() - t0
+
+    t_full, r = oracle_full_solve(pr, C, m)
+    t_cal = sample()
+    S = t_full / t_cal
     for _ in range(a.warmup):
-        oracle_apply_sample(cfg, 1, n_applies=1)
-    ts = []
-    for _ in range(a.steps):
-        ts.append(oracle_apply_sample(cfg, 1, n_applies=1))
-    t_step = statistics.mean(ts)
-    value = n * s * p / (t_step * applies)
-    cores = os.cpu_count()
+        sample()
+    ts = [sample() for _ in range(a.steps)]
+    t_step = statistics.median(ts)
+    value = n * s * p / (t_step * S)
+    cores = blas_threads()
+    desc = (f"calibration: one complete oracle tGMRES({m}) solve ({t_full:.1f} s, {r.iters} inner steps, "
+            f"{r.cycles} cycles, status {r.status}) = {S:.1f} samples of {t_cal:.2f} s; each step = one inner step "
+            f"of the oracle's Algorithm 2 at full size (M(X) by the bcirc definition, MGS pass, norm); "
+            f"value = unknowns / (median step x {S:.1f})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_step * applies * 1e3,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * statistics.mean(ts),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": a.workload, "n": n, "s": s, "p": p,
-                                            "restart": cfg["restart"], "tol": 1e-10},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step = one oracle M(X) at full size ({t_step:.2f} s); "
-                                       f"solve time = step x {applies} applies (oracle tGMRES count at n=s=128)"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": {"workload": a.workload, "n": n, "s": s, "p": p, "restart": m, "tol": 1e-10},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "oracle_complete_solve_s": t_full}
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------------
+# dense and batched measurement helpers
+# ------------------------------------------------------------------------------------------------
+class DenseSetup:
+    """Device-resident inputs of one dense workload instance; C = M(X*) by the library's FP64 operator."""
+
+    def __init__(self, ctx, wl, seed, dev, n=None, s=None, p=None, pinned=False):
+        import torch
+        from paper_2405_09233_gb300 import inputs
+        cfg = dict(inputs.WORKLOADS[wl])
+        for key, v in (("n", n), ("s", s), ("p", p)):
+            if v is not None:
+                cfg[key] = v
+        self.cfg, self.wl = cfg, wl
+        self.n, self.s, self.p, self.m = cfg["n"], cfg["s"], cfg["p"], cfg["restart"]
+        pr = inputs.dense_problem(self.n, self.s, self.p, seed=seed, scale=cfg["scale"])
+        A_h = torch.from_numpy(inputs.to_device_layout(pr.A))
+        B_h = torch.from_numpy(inputs.to_device_layout(pr.B))
+        Xs_h = torch.from_numpy(inputs.to_device_layout(pr.Xstar))
+        if pinned:
+            A_h, B_h, Xs_h = A_h.pin_memory(), B_h.pin_memory(), Xs_h.pin_memory()
+        self.A_h, self.B_h = A_h, B_h
+        self.Ad, self.Bd, self.Xs = A_h.to(dev), B_h.to(dev), Xs_h.to(dev)
+        del pr
+        self.ctx = ctx
+        self.op_cert = ctx.op_create_dense(self.Ad, self.Bd)     # the FP64 CUDA-core operator (certificates)
+        self.Cd = ctx.sylv_apply(self.op_cert, self.Xs)
+        self.normC = float(torch.linalg.norm(self.Cd))
+        self.X = torch.zeros_like(self.Cd)
+        self.unknowns = self.n * self.s * self.p
+        torch.cuda.synchronize()
+
+    def solve(self, name):
+        """One step: operator setup + solve from X0 = 0 ("tfom" = FP64 tFOM; "prec@engine")."""
+        prec, _, eng = name.partition("@")
+        eng = eng or "dfma"
+        op = self.ctx.op_create_dense(self.Ad, self.Bd)
+        self.X.zero_()
+        if prec == "tfom":
+            r = self.ctx.tfom_solve(op, self.Cd, self.X, restart=self.m, tol=1e-10, engine=eng)
+        else:
+            r = self.ctx.tgmres_solve(op, self.Cd, self.X, restart=self.m, tol=1e-10, precision=prec, engine=eng)
+        op.close()
+        return r
+
+    def certify(self):
+        """||C - M(X)|| / ||C|| with the FP64 CUDA-core operator (outside any timed region)."""
+        import torch
+        R = self.Cd - self.ctx.sylv_apply(self.op_cert, self.X)
+        return float(torch.linalg.norm(R)) / self.normC
+
+    def err_xstar(self):
+        import torch
+        return float(torch.max(torch.abs(self.X - self.Xs)) / torch.max(torch.abs(self.Xs)))
+
+    def close(self):
+        self.op_cert.close()
+
+
+def timed_median(fn, reps, warm):
+    """warm untimed calls, then reps calls each timed with CUDA events; returns (median ms, list, last result)."""
+    import torch
+    r = None
+    for _ in range(warm):
+        r = fn()
+    ms = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms), ms, r
+
+
+def dense_entry(setup, name, reps, warm=1, world=1):
+    """Median of reps timed solves of one method / precision / engine, with its FP64 certificate."""
+    try:
+        med, ms, r = timed_median(lambda: setup.solve(name), reps, warm)
+        return {"value": setup.unknowns * world / (med / 1e3), "ms_per_step": med, "ms_all": ms,
+                "status": r.status_name, "relres_true": r.info.relres_true, "relres_fp64_dfma": setup.certify(),
+                "outer": r.info.outer, "inner_iters": r.info.iters, "applies_fp64": r.info.applies_fp64,
+                "applies_low": r.info.applies_low, "err_vs_xstar": setup.err_xstar()}
+    except Exception as e:  # report, do not hide
+        return {"error": str(e)}
+
+
+class BatchedSetup:
+    """The batched workload: `count` dense-family instances (n log-uniform in [64, 1024], s uniform in
+    [16, 128], p in {4, 8, 16}), device-resident; C_i = M_i(X*_i) by the library's FP64 operator."""
+
+    def __init__(self, ctx, count, seed, dev, pinned=False):
+        import torch
+        from paper_2405_09233_gb300 import inputs
+        self.ctx, self.count = ctx, count
+        self.specs = inputs.batched_specs(count, seed=seed)
+        self.host = []
+        for sp in self.specs:
+            pr = inputs.dense_problem(sp.n, sp.s, sp.p, seed=sp.seed)
+            t = (torch.from_numpy(inputs.to_device_layout(pr.A)), torch.from_numpy(inputs.to_device_layout(pr.B)),
+                 torch.from_numpy(inputs.to_device_layout(pr.Xstar)))
+            self.host.append(tuple(x.pin_memory() for x in t) if pinned else t)
+        self.dev_in = [(A.to(dev), B.to(dev), X.to(dev)) for A, B, X in self.host]
+        self.ops_cert = [ctx.op_create_dense(A, B) for A, B, _ in self.dev_in]
+        self.Cs = [ctx.sylv_apply(op, Xst) for op, (_, _, Xst) in zip(self.ops_cert, self.dev_in)]
+        self.normC = [float(torch.linalg.norm(C)) for C in self.Cs]
+        self.Xs = [torch.zeros_like(C) for C in self.Cs]
+        self.unknowns = sum(sp.n * sp.s * sp.p for sp in self.specs)
+        torch.cuda.synchronize()
+
+    def solve(self, name):
+        prec, _, eng = name.partition("@")
+        ops = [self.ctx.op_create_dense(A, B) for A, B, _ in self.dev_in]
+        for X in self.Xs:
+            X.zero_()
+        st, infos, _ = self.ctx.batched_solve(ops, self.Cs, self.Xs, restart=20, tol=1e-10, precision=prec,
+                                              engine=eng or "dfma")
+        for op in ops:
+            op.close()
+        return st, infos
+
+    def certify(self):
+        import torch
+        return max(float(torch.linalg.norm(C - self.ctx.sylv_apply(op, X))) / nc
+                   for op, C, X, nc in zip(self.ops_cert, self.Cs, self.Xs, self.normC))
+
+    def err_xstar(self):
+        import torch
+        return max(float(torch.max(torch.abs(X - Xst))) for X, (_, _, Xst) in zip(self.Xs, self.dev_in))
+
+    def close(self):
+        for op in self.ops_cert:
+            op.close()
+
+
+def batched_entry(setup, name, reps, warm=1, world=1):
+    try:
+        med, ms, (st, infos) = timed_median(lambda: setup.solve(name), reps, warm)
+        return {"value": setup.unknowns * world / (med / 1e3), "ms_per_step": med, "ms_all": ms, "status": st,
+                "max_relres_true": max(i.relres_true for i in infos), "max_relres_fp64_dfma": setup.certify(),
+                "max_err_vs_xstar": setup.err_xstar(), "max_outer": max(i.outer for i in infos)}
+    except Exception as e:  # report, do not hide
+        return {"error": str(e)}
+
+
+def run_comparisons(ctx, dev, reps, dense1=None, dense1_entries=None):
+    """The metric's comparison: the mixed-precision and batched forms against FP64 tGMRES on both FP64
+    engines (CUDA cores and the emulated tensor-core product), each entry the median of `reps` timed solves
+    and certified by the FP64 CUDA-core operator."""
+    import torch
+    out = {}
+    fp64s = ["fp64", "fp64@ozaki"]
+    fast = ["mixed_bf16@ozaki", "mixed_tf32x3@ozaki"]
+    if dense1 is not None and dense1_entries is not None:
+        out["dense_n1024_s1024_p16"] = {"entries": dense1_entries,
+                                        "speedup": speedups(dense1_entries, fp64s, fast)}
+    try:
+        d2 = DenseSetup(ctx, "dense_n4096_s256_p32_g0.3", 1, dev)
+        ent = {"fp64": dense_entry(d2, "fp64", 1, warm=0)}
+        for nm in ("fp64@ozaki", "mixed_tf32x3@ozaki", "mixed_bf16@ozaki"):
+            ent[nm] = dense_entry(d2, nm, reps)
+        out["dense_n4096_s256_p32_g0.3"] = {"entries": ent, "speedup": speedups(ent, fp64s, fast)}
+        d2.close()
+        del d2
+        torch.cuda.empty_cache()
+    except Exception as e:  # report, do not hide
+        out["dense_n4096_s256_p32_g0.3"] = {"error": str(e)}
+    try:
+        b = BatchedSetup(ctx, 256, 4, dev)
+        ent = {nm: batched_entry(b, nm, reps) for nm in ("fp64", "fp64@ozaki", "mixed_bf16@ozaki",
+                                                          "mixed_tf32x3@ozaki")}
+        out["batched_256"] = {"entries": ent, "speedup": speedups(ent, fp64s, fast)}
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+    except Exception as e:  # report, do not hide
+        out["batched_256"] = {"error": str(e)}
+    return out
+
+
+# ------------------------------------------------------------------------------------------------
 def main():
     a = args_parse()
     if a.variants is None:
-        a.variants = BATCHED_VARIANTS_DEFAULT_MARK if a.workload == "batched_256" else DENSE_VARIANTS
+        a.variants = BATCHED_VARIANTS if a.workload == "batched_256" else DENSE_VARIANTS
     if a.precision is None:
         a.precision = ("fp64" if a.workload in ("dense_n24_s24_p4", "dense_n1024_s1024_p16", "sparse_lap128_s32_p8")
                        else "mixed_fp32")
     if a.impl == "reference":
         run_reference(a)
         return
-    import numpy as np
     import torch
-    from paper_2405_09233_gb300 import Context, inputs
+    from paper_2405_09233_gb300 import Context
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -324,35 +675,18 @@ def main():
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    cfg = workload_cfg(a)
-    n, s, p, m = cfg["n"], cfg["s"], cfg["p"], cfg["restart"]
-    seed = rank_seed(rank)
-    pr = inputs.dense_problem(n, s, p, seed=seed, scale=cfg["scale"])
-    A_h = torch.from_numpy(inputs.to_device_layout(pr.A)).pin_memory()
-    B_h = torch.from_numpy(inputs.to_device_layout(pr.B)).pin_memory()
-    Xs_h = torch.from_numpy(inputs.to_device_layout(pr.Xstar)).pin_memory()
-    Ad, Bd, Xs = A_h.to(dev), B_h.to(dev), Xs_h.to(dev)
     ctx = Context(local)
-    op0 = ctx.op_create_dense(Ad, Bd)
-    Cd = ctx.sylv_apply(op0, Xs)              # manufactured right-hand side C = M(X*)
-    op0.close()
-    X = torch.zeros_like(Cd)
-    torch.cuda.synchronize()
     if a.mode == "apply":
-        return run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev)
-
-    def step(precision, engine=a.engine):
-        op = ctx.op_create_dense(Ad, Bd)
-        X.zero_()
-        if precision == "tfom":   # restarted tFOM(m), FP64 (variant)
-            r = ctx.tfom_solve(op, Cd, X, restart=m, tol=1e-10, engine=engine)
-        else:
-            r = ctx.tgmres_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision, engine=engine)
-        op.close()
-        return r
+        cfg = workload_cfg(a)
+        su = DenseSetup(ctx, a.workload, rank_seed(rank), dev, a.n, a.s, a.p)
+        su.close()
+        return run_apply_mode(a, ctx, su.Ad, su.Bd, su.Xs, cfg, world, dev)
+    su = DenseSetup(ctx, a.workload, rank_seed(rank), dev, a.n, a.s, a.p, pinned=True)
+    n, s, p, m = su.n, su.s, su.p, su.m
+    primary = a.precision + ("" if a.engine == "dfma" else "@" + a.engine)
 
     for _ in range(a.warmup):
-        r = step(a.precision)
+        r = su.solve(primary)
     assert r.status == 0, r
 
     def barrier():
@@ -367,7 +701,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     ev0.record()
-    results = [step(a.precision) for _ in range(a.steps)]
+    results = [su.solve(primary) for _ in range(a.steps)]
     ev1.record()
     torch.cuda.synchronize()
     barrier()
@@ -377,27 +711,15 @@ def main():
     ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dev)
     last = results[-1]
     assert all(r.status == 0 for r in results), results
-    relres = last.info.relres_true
-    err_xstar = float(torch.max(torch.abs(X - Xs)) / torch.max(torch.abs(Xs)))
-    unknowns = n * s * p
-    value = job_throughput(unknowns, world, ms)
+    relres_cert = su.certify()
+    err_xstar = su.err_xstar()
+    value = job_throughput(su.unknowns, world, ms)
 
-    # dominant kernel: whichever slice-GEMM class (FP64 DFMA, emulated FP64, low precision) took most time
-    step_ms_total = ms * a.steps
-    top = max(("fp64", st.gemm_ms), ("oz", st.oz_ms), ("lowp", st.lowp_ms), key=lambda t: t[1])[0]
-    if top == "fp64":
-        roofline = gemm_roofline("fp64", "fp64", st.gemm_flops / max(st.gemm_launches, 1),
-                                 st.gemm_ms / max(st.gemm_launches, 1), True, st.gemm_ms / step_ms_total)
-        roofline["traffic"] = traffic_for("k_gemm_slices<double>", a.workload)
-    elif top == "oz":
-        roofline = ozaki_roofline(st.oz_flops / max(st.oz_launches, 1), st.oz_pair_flops / max(st.oz_launches, 1),
-                                  st.oz_ms / max(st.oz_launches, 1),
-                                  True, st.oz_ms / step_ms_total)
-        if abs(st.oz_pair_flops - 21 * st.oz_flops) <= 1e-9 * st.oz_pair_flops:   # 6 digits in every launch
-            roofline["traffic"] = traffic_for("k_oz_sylv/6", a.workload)
-    else:
-        roofline = gemm_roofline("lowp", a.precision, st.lowp_flops / max(st.lowp_launches, 1),
-                                 st.lowp_ms / max(st.lowp_launches, 1), True, st.lowp_ms / step_ms_total)
+    sms = device_sms(dev)
+    mhz = clk.get("sm_max_mhz") or peaks()["sm_max_mhz"]
+    dgemm = measure_dgemm_tflops(dev) if rank == 0 and st.gemm_launches else None
+    rooflines = stats_rooflines(st, n, s, p, ms * a.steps, True, a.precision, sms, mhz, a.workload, dgemm)
+    roofline = rooflines[0] if rooflines else None
     kernel_times = {"fp64_gemm_ms": st.gemm_ms / a.steps, "ozaki_gemm_ms": st.oz_ms / a.steps,
                     "lowp_gemm_ms": st.lowp_ms / a.steps,
                     "fft_ms": st.fft_ms / a.steps, "fp64_gemm_launches": st.gemm_launches // a.steps,
@@ -406,13 +728,13 @@ def main():
                     "fft_gbs": st.fft_bytes / max(st.fft_ms, 1e-9) / 1e6}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
-    C_h = Cd.cpu().pin_memory()
+    C_h = su.Cd.cpu().pin_memory()
     X_h = torch.zeros_like(C_h).pin_memory()
     e2e_times, e2e_parts = [], []
     for _ in range(max(a.e2e_steps, 0)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        op = ctx.op_create_dense(A_h, B_h)
+        op = ctx.op_create_dense(su.A_h, su.B_h)
         t1 = time.perf_counter()
         X_h.zero_()
         r = ctx.tgmres_solve(op, C_h, X_h, restart=m, tol=1e-10, precision=a.precision, engine=a.engine)
@@ -422,63 +744,47 @@ def main():
         e2e_times.append(t3 - t0)
         e2e_parts.append((t1 - t0, t2 - t1, t3 - t2))
         assert r.status == 0, r
-    e2e = {"value": unknowns * world / statistics.median(e2e_times) if e2e_times else None, "unit": UNIT,
+    e2e = {"value": su.unknowns * world / statistics.median(e2e_times) if e2e_times else None, "unit": UNIT,
            "h2d_bytes_per_step": 8 * (n * n * p + s * s * p + 2 * n * s * p),
-           "d2h_bytes_per_step": 8 * n * s * p}
-    if e2e_parts:   # host-clock split of the last end-to-end step: operator setup, solve, release
-        e2e["split_ms"] = dict(zip(("op_create", "solve", "op_destroy"), (round(x * 1e3, 3) for x in e2e_parts[-1])))
+           "d2h_bytes_per_step": 8 * n * s * p, "steps": len(e2e_times), "statistic": "median"}
+    if e2e_parts:   # host-clock split of the median end-to-end step: operator setup, solve, release
+        mid = sorted(range(len(e2e_times)), key=lambda i: e2e_times[i])[len(e2e_times) // 2]
+        e2e["split_ms"] = dict(zip(("op_create", "solve", "op_destroy"), (round(x * 1e3, 3) for x in e2e_parts[mid])))
 
     variants = {}
-    primary = a.precision + ("" if a.engine == "dfma" else "@" + a.engine)
     for name in [v for v in a.variants.split(",") if v and v != primary]:
-        prec, _, eng = name.partition("@")
-        eng = eng or "dfma"
-        try:
-            step(prec, eng)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            rv = step(prec, eng)
-            e1.record()
-            torch.cuda.synchronize()
-            tv = e0.elapsed_time(e1)
-            variants[name] = {"value": unknowns * world / (tv / 1e3), "ms_per_step": tv,
-                              "status": rv.status_name, "relres_true": rv.info.relres_true,
-                              "outer": rv.info.outer, "inner_iters": rv.info.iters,
-                              "applies_fp64": rv.info.applies_fp64, "applies_low": rv.info.applies_low,
-                              "err_vs_xstar": float(torch.max(torch.abs(X - Xs)) / torch.max(torch.abs(Xs)))}
-        except Exception as e:  # report, do not hide
-            variants[name] = {"error": str(e)}
+        variants[name] = dense_entry(su, name, a.reps, warm=1, world=world)
 
-    if n * s * p <= 1 << 16:
+    if su.unknowns <= 1 << 16:
         # small problems are launch-latency bound: also time the graph-replayed form (the batched
         # solver on this single instance: one CUDA graph per restart cycle, no per-step host sync)
         try:
-            ops1 = [ctx.op_create_dense(Ad, Bd)]
-            for _ in range(3):
-                X.zero_()
-                ctx.batched_solve(ops1, [Cd], [X], restart=m, tol=1e-10, precision=a.precision)
-            torch.cuda.synchronize()
-            reps = 20
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
-                X.zero_()
-                stb, infb, _ = ctx.batched_solve(ops1, [Cd], [X], restart=m, tol=1e-10, precision=a.precision)
-            e1.record()
-            torch.cuda.synchronize()
-            tb = e0.elapsed_time(e1) / reps
-            variants["graph_replay"] = {"value": unknowns * world / (tb / 1e3), "ms_per_step": tb, "status": stb,
+            ops1 = [ctx.op_create_dense(su.Ad, su.Bd)]
+
+            def one():
+                su.X.zero_()
+                return ctx.batched_solve(ops1, [su.Cd], [su.X], restart=m, tol=1e-10, precision=a.precision)
+            med, _, (stb, infb, _) = timed_median(one, 20, 3)
+            variants["graph_replay"] = {"value": su.unknowns * world / (med / 1e3), "ms_per_step": med, "status": stb,
                                         "inner_iters": infb[0].iters, "relres_true": infb[0].relres_true,
-                                        "us_per_inner_step": 1e3 * tb / max(infb[0].iters, 1)}
+                                        "us_per_inner_step": 1e3 * med / max(infb[0].iters, 1)}
             ops1[0].close()
         except Exception as e:  # report, do not hide
             variants["graph_replay"] = {"error": str(e)}
         variants["us_per_inner_step"] = 1e3 * ms / max(last.info.iters, 1)
 
+    comparisons = None
+    if rank == 0 and world == 1 and not a.no_comparisons and a.workload == "dense_n1024_s1024_p16":
+        d1 = {primary: {"value": value, "ms_per_step": ms, "relres_fp64_dfma": relres_cert, "status": "ok"}}
+        for nm in ("fp64@ozaki", "mixed_bf16@ozaki", "mixed_tf32x3@ozaki"):
+            if nm in variants:
+                d1[nm] = variants[nm]
+        comparisons = run_comparisons(ctx, dev, a.reps, su, d1)
+
     cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu_baseline and a.workload == "dense_n1024_s1024_p16":
-        cpu = cpu_baseline(cfg, seed)
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and a.workload in ("dense_n1024_s1024_p16",
+                                                                                "dense_n24_s24_p4"):
+        cpu = cpu_baseline_dense(su.cfg, rank_seed(rank))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -490,11 +796,13 @@ def main():
                            "l2": "inputs larger than L2 "
                            "(A-hat 151 MB, Krylov basis 4.2 GB at n=s=1024, p=16)",
                            "iters": last.info.iters, "cycles": last.info.cycles,
-                           "applies_fp64": last.info.applies_fp64, "relres_true": relres,
-                           "err_vs_xstar": err_xstar},
-                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-                "gpu_launches": int(st.launches), "kernels_per_step": kernel_times, "variants": variants}
+                           "applies_fp64": last.info.applies_fp64, "relres_true": last.info.relres_true,
+                           "relres_fp64_dfma": relres_cert, "err_vs_xstar": err_xstar, "sms": sms},
+                "e2e": e2e, "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": int(st.launches), "kernels_per_step": kernel_times, "variants": variants,
+                "comparisons": comparisons}
         print(json.dumps(line), flush=True)
+    su.close()
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -504,101 +812,83 @@ def run_batched(a, rank, world, local, dev):
     """The batched workload: 256 instances (n log-uniform in [64, 1024], s uniform in [16, 128],
     p in {4, 8, 16}), one step = one ts_batched_solve of all of them (operator setup included)."""
     import torch
-    from paper_2405_09233_gb300 import Context, inputs
-    count = a.count if a.count else inputs.WORKLOADS["batched_256"]["count"]
-    specs = inputs.batched_specs(count, seed=4 + rank)
+    from paper_2405_09233_gb300 import Context
+    count = a.count if a.count else 256
     ctx = Context(local)
-    host = []
-    for sp in specs:
-        pr = inputs.dense_problem(sp.n, sp.s, sp.p, seed=sp.seed)
-        host.append((torch.from_numpy(inputs.to_device_layout(pr.A)).pin_memory(),
-                     torch.from_numpy(inputs.to_device_layout(pr.B)).pin_memory(),
-                     torch.from_numpy(inputs.to_device_layout(pr.Xstar)).pin_memory()))
-    dev_in = [(A.to(dev), B.to(dev), X.to(dev)) for A, B, X in host]
-    Cs = []
-    for A, B, Xst in dev_in:
-        op = ctx.op_create_dense(A, B)
-        Cs.append(ctx.sylv_apply(op, Xst))
-        op.close()
-    Xs = [torch.zeros_like(C) for C in Cs]
-    unknowns = sum(sp.n * sp.s * sp.p for sp in specs)
+    b = BatchedSetup(ctx, count, 4 + rank, dev, pinned=True)
     prec = a.precision
-
-    def step(precision, engine=a.engine):
-        ops = [ctx.op_create_dense(A, B) for A, B, _ in dev_in]
-        for X in Xs:
-            X.zero_()
-        st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, tol=1e-10, precision=precision, engine=engine)
-        for op in ops:
-            op.close()
-        return st, infos
-
+    primary = prec + ("" if a.engine == "dfma" else "@" + a.engine)
     for _ in range(a.warmup):
-        st, infos = step(prec)
+        st, infos = b.solve(primary)
     assert st == 0
     ctx.stats_reset()
+    ctx.stats_enable(True)
     clocks = ClockSampler(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(a.steps):
-        st, infos = step(prec)
+        st, infos = b.solve(primary)
     e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    ctx.stats_enable(False)
     stt = ctx.stats_get()
     ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+    assert st == 0, st
     relres = max(i.relres_true for i in infos)
-    err = max(float(torch.max(torch.abs(X - Xst))) for X, (_, _, Xst) in zip(Xs, dev_in))
+    cert = b.certify()
+    err = b.err_xstar()
+    sms = device_sms(dev)
+    mhz = clk.get("sm_max_mhz") or peaks()["sm_max_mhz"]
+    ratio = (sum(slice_flops(sp.n, sp.s, sp.p, 6) for sp in b.specs)
+             / sum(slice_flops(sp.n, sp.s, sp.p, 8) for sp in b.specs))
+    rooflines = stats_rooflines(stt, 0, 0, 0, ms * a.steps, True, prec, sms, mhz, "batched_256", exec_ratio=ratio)
+    for r in rooflines:
+        r["note"] += ("; batched: every phase of the captured cycle is timed by events recorded in the graph, "
+                      "its work counted for the instances active in that phase (masked instances' CTAs exit early "
+                      "and still count in the time)")
     # end to end: operators and right-hand sides from pinned host memory, solutions back to host
-    C_h = [C.cpu().pin_memory() for C in Cs]
-    X_h = [torch.zeros_like(C) for C in C_h]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ops = [ctx.op_create_dense(A, B) for A, B, _ in host]
-    Cd = [C.to(dev, non_blocking=True) for C in C_h]
-    Xd = [torch.zeros_like(C) for C in Cd]
-    st2, _, _ = ctx.batched_solve(ops, Cd, Xd, restart=20, tol=1e-10, precision=prec, engine=a.engine)
-    for Xh_, Xd_ in zip(X_h, Xd):
-        Xh_.copy_(Xd_)
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    for op in ops:
-        op.close()
-    h2d = sum(8 * (A.numel() + B.numel() + C.numel()) for (A, B, _), C in zip(host, C_h))
+    C_h = [C.cpu().pin_memory() for C in b.Cs]
+    X_h = [torch.zeros_like(C).pin_memory() for C in C_h]
+    t_e2e = []
+    for _ in range(max(a.e2e_steps, 1)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ops = [ctx.op_create_dense(A, B) for A, B, _ in b.host]
+        Cd = [C.to(dev, non_blocking=True) for C in C_h]
+        Xd = [torch.zeros_like(C) for C in Cd]
+        st2, _, _ = ctx.batched_solve(ops, Cd, Xd, restart=20, tol=1e-10, precision=prec, engine=a.engine)
+        for Xh_, Xd_ in zip(X_h, Xd):
+            Xh_.copy_(Xd_, non_blocking=True)
+        torch.cuda.synchronize()
+        t_e2e.append(time.perf_counter() - t0)
+        for op in ops:
+            op.close()
+        assert st2 == 0, st2
+    h2d = sum(8 * (A.numel() + B.numel() + C.numel()) for (A, B, _), C in zip(b.host, C_h))
     d2h = sum(8 * X.numel() for X in X_h)
     variants = {}
-    primary = prec + ("" if a.engine == "dfma" else "@" + a.engine)
-    names = a.variants.split(",") if a.variants else []
-    if a.variants == BATCHED_VARIANTS_DEFAULT_MARK:
-        names = ["fp64", "mixed_fp32", "fp64@ozaki", "mixed_fp32@ozaki", "mixed_tf32x3@ozaki", "mixed_bf16@ozaki"]
-    for name in [v for v in names if v and v != primary]:
-        vp, _, ve = name.partition("@")
-        try:
-            torch.cuda.synchronize()
-            f0 = time.perf_counter()
-            stf, infof = step(vp, ve or "dfma")
-            torch.cuda.synchronize()
-            variants[name] = {"value": unknowns * world / (time.perf_counter() - f0), "status": stf,
-                              "max_relres_true": max(i.relres_true for i in infof),
-                              "max_err_vs_xstar": max(float(torch.max(torch.abs(X - Xst)))
-                                                      for X, (_, _, Xst) in zip(Xs, dev_in))}
-        except Exception as e:  # report, do not hide
-            variants[name] = {"error": str(e)}
+    for name in [v for v in (a.variants or "").split(",") if v and v != primary]:
+        variants[name] = batched_entry(b, name, a.reps, warm=1, world=world)
+    cpu = cpu_baseline_batched(b.specs) if rank == 0 and world == 1 and not a.no_cpu_baseline else None
     if rank == 0:
-        line = {"metric": METRIC, "value": unknowns * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        line = {"metric": METRIC, "value": b.unknowns * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64" if prec != "fp64" else "f64", "data": "synthetic",
                 "config": {"workload": "batched_256" if count == 256 else "batched_%d" % count, "instances": count,
-                           "unknowns": unknowns, "restart": 20,
+                           "unknowns": b.unknowns, "restart": 20,
                            "tol": 1e-10, "precision": prec, "fp64_engine": a.engine, "method": "batched tGMRES",
-                           "max_relres_true": relres, "max_err_vs_xstar": err,
-                           "l2": "inputs larger than L2 (5 GB basis)"},
-                "e2e": {"value": unknowns * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
+                           "max_relres_true": relres, "max_relres_fp64_dfma": cert, "max_err_vs_xstar": err,
+                           "l2": "inputs larger than L2 (5 GB basis)", "sms": sms},
+                "e2e": {"value": b.unknowns * world / statistics.median(t_e2e), "unit": UNIT,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": len(t_e2e),
+                        "statistic": "median"},
+                "roofline": rooflines[0] if rooflines else None, "rooflines": rooflines, "cpu_baseline": cpu,
                 "clocks": clk, "gpu_launches": int(stt.launches), "variants": variants}
         print(json.dumps(line), flush=True)
+    b.close()
     ctx.close()
 
 
@@ -623,11 +913,12 @@ def run_tbas(a, rank, world, local, dev):
     cols = np.concatenate(cols)
     vals = np.concatenate(vals)
     ctx = Context(local)
-    Bd = torch.from_numpy(inputs.to_device_layout(prob.B)).to(dev)
+    B_h = torch.from_numpy(inputs.to_device_layout(prob.B)).pin_memory()
+    Bd = B_h.to(dev)
     Xs = torch.from_numpy(inputs.to_device_layout(prob.Xstar)).to(dev)
     op0 = ctx.op_create_csr(n, p, rowptr, cols, vals, Bd)
     Cd = ctx.sylv_apply(op0, Xs)
-    op0.close()
+    normC = float(torch.linalg.norm(Cd))
     X = torch.zeros_like(Cd)
     m = 10
 
@@ -637,6 +928,9 @@ def run_tbas(a, rank, world, local, dev):
         r = ctx.tba_solve(op, Cd, X, restart=m, tol=1e-10, precision=precision)
         op.close()
         return r
+
+    def certify():
+        return float(torch.linalg.norm(Cd - ctx.sylv_apply(op0, X))) / normC
 
     for _ in range(a.warmup):
         r = step()
@@ -656,32 +950,62 @@ def run_tbas(a, rank, world, local, dev):
     ctx.stats_enable(False)
     stt = ctx.stats_get()
     ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+    cert = certify()
     unknowns = n * s_blk * p
-    blk_ms = stt.tba_ms / max(stt.tba_launches, 1)
-    blk_tf = stt.tba_flops / max(stt.tba_launches, 1) / (blk_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": blk_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": blk_tf / FP64_NOMINAL_TFLOPS, "traffic": None,
-                "kernel": "k_gram / k_rows_mm (TBAS tubal Gram and block update, FP64 complex, n x s blocks)",
-                "note": ("peak derived: 4 FP64 FLOP/clk/SM x 152 SMs x 2070 MHz (nominal); 8 n s^2 FLOP per slice "
-                         "product. Share of the step: %.3f (timed with events around each product, which adds "
-                         "event overhead)" % (stt.tba_ms / (ms * a.steps)))}
+    sms = device_sms(dev)
+    mhz = clk.get("sm_max_mhz") or peaks()["sm_max_mhz"]
+    peak64 = fp64_peak_tflops(sms, mhz)
+    rooflines = []
+    if stt.tba_launches:
+        blk_ms = stt.tba_ms / stt.tba_launches
+        blk_tf = stt.tba_flops / stt.tba_launches / (blk_ms * 1e-3) / 1e12 * 0.75   # 3-multiply form executed
+        rooflines.append((stt.tba_ms, {
+            "bound": "alu", "achieved": blk_tf, "peak": peak64, "unit": "TFLOP/s", "frac": blk_tf / peak64,
+            "traffic": None,
+            "kernel": "k_gram / k_rows_mm (TBAS tubal Gram and block update, FP64 complex, n x s blocks)",
+            "note": ("FLOPs of the 3-multiply complex form the kernels implement (6 n s^2 per slice product); peak "
+                     "derived: 2 DFMA/clk/SM x %d SMs x %.0f MHz. Share of the step: %.3f (timed with events around "
+                     "each product)" % (sms, mhz, stt.tba_ms / (ms * a.steps)))}))
+    if stt.spmm_launches:
+        sp_ms = stt.spmm_ms / stt.spmm_launches
+        sp_tf = stt.spmm_flops / stt.spmm_launches / (sp_ms * 1e-3) / 1e12
+        sp_gbs = stt.spmm_bytes / stt.spmm_launches / (sp_ms * 1e-3) / 1e9
+        rooflines.append((stt.spmm_ms, {
+            "bound": "alu", "achieved": sp_tf, "peak": peak64, "unit": "TFLOP/s", "frac": sp_tf / peak64,
+            "traffic": None,
+            "kernel": "k_sylv_rows (complex CSR SpMM over the union pattern, all Fourier slices)",
+            "algorithmic_gbs": sp_gbs, "hbm_frac": sp_gbs / peaks()["hbm_gbs"],
+            "note": ("FLOPs executed: 8 per stored complex value and block column; peak derived: 2 DFMA/clk/SM x %d "
+                     "SMs x %.0f MHz. Algorithmic bytes (values, pattern, V once, W once) / time = %.0f GB/s = %.3f of "
+                     "measured HBM. Share of the step: %.3f" % (sms, mhz, sp_gbs, sp_gbs / peaks()["hbm_gbs"],
+                                                                stt.spmm_ms / (ms * a.steps)))}))
+    rooflines.sort(key=lambda t: -t[0])
+    rooflines = [r for _, r in rooflines]
+    # end to end: B, C and X in host memory (the CSR arrays are host arrays by contract)
+    C_h = Cd.cpu().pin_memory()
+    X_h = torch.zeros_like(C_h).pin_memory()
+    t_e2e = []
+    for _ in range(max(a.e2e_steps, 1)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op = ctx.op_create_csr(n, p, rowptr, cols, vals, B_h)
+        X_h.zero_()
+        r2 = ctx.tba_solve(op, C_h, X_h, restart=m, tol=1e-10, precision=a.precision)
+        op.close()
+        t_e2e.append(time.perf_counter() - t0)
+        assert r2.status == 0, r2
+    h2d = 4 * (rowptr.size + cols.size) + 8 * (vals.size + B_h.numel() + 2 * C_h.numel())
     variants = {}
     other = "mixed_fp32" if a.precision == "fp64" else "fp64"
     if a.variants != "":
         try:
-            step(other)
-            torch.cuda.synchronize()
-            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            v0.record()
-            rv = step(other)
-            v1.record()
-            torch.cuda.synchronize()
-            tv = v0.elapsed_time(v1)
-            variants[other] = {"value": unknowns * world / (tv / 1e3), "ms_per_step": tv, "status": rv.status_name,
-                               "cycles": rv.info.cycles, "relres_true": rv.info.relres_true,
-                               "err_vs_xstar": float(torch.max(torch.abs(X - Xs)))}
+            med, msl, rv = timed_median(lambda: step(other), a.reps, 1)
+            variants[other] = {"value": unknowns * world / (med / 1e3), "ms_per_step": med, "ms_all": msl,
+                               "status": rv.status_name, "cycles": rv.info.cycles, "relres_true": rv.info.relres_true,
+                               "relres_fp64_dfma": certify(), "err_vs_xstar": float(torch.max(torch.abs(X - Xs)))}
         except Exception as e:  # report, do not hide
             variants[other] = {"error": str(e)}
+    cpu = cpu_baseline_tbas(prob, m) if rank == 0 and world == 1 and not a.no_cpu_baseline else None
     if rank == 0:
         line = {"metric": METRIC, "value": job_throughput(unknowns, world, ms), "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -690,10 +1014,14 @@ def run_tbas(a, rank, world, local, dev):
                 "config": {"workload": "sparse_lap128_s32_p8", "n": n, "s": s_blk, "p": p, "restart": m,
                            "precision": a.precision,
                            "tol": 1e-10, "method": "TBAS", "cycles": r.info.cycles, "block_steps": r.info.iters,
-                           "relres_true": r.info.relres_true,
-                           "err_vs_xstar": float(torch.max(torch.abs(X - Xs)))},
-                "roofline": roofline, "clocks": clk, "gpu_launches": int(stt.launches), "variants": variants}
+                           "relres_true": r.info.relres_true, "relres_fp64_dfma": cert,
+                           "err_vs_xstar": float(torch.max(torch.abs(X - Xs))), "sms": sms},
+                "e2e": {"value": unknowns * world / statistics.median(t_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": 8 * X_h.numel(), "steps": len(t_e2e), "statistic": "median"},
+                "roofline": rooflines[0] if rooflines else None, "rooflines": rooflines, "cpu_baseline": cpu,
+                "clocks": clk, "gpu_launches": int(stt.launches), "variants": variants}
         print(json.dumps(line), flush=True)
+    op0.close()
     ctx.close()
 
 
@@ -732,21 +1060,15 @@ def run_apply_mode(a, ctx, Ad, Bd, Xs, cfg, world, dev):
     ctx.stats_enable(False)
     st = ctx.stats_get()
     ms = e0.elapsed_time(e1) / a.steps
-    if a.precision == "fp64" and a.engine == "ozaki":
-        rf = ozaki_roofline(st.oz_flops / max(st.oz_launches, 1), st.oz_pair_flops / max(st.oz_launches, 1),
-                                  st.oz_ms / max(st.oz_launches, 1), False,
-                            st.oz_ms / (ms * a.steps))
-    elif a.precision == "fp64":
-        rf = gemm_roofline("fp64", "fp64", st.gemm_flops / max(st.gemm_launches, 1),
-                           st.gemm_ms / max(st.gemm_launches, 1), False, st.gemm_ms / (ms * a.steps))
-    else:
-        rf = gemm_roofline("lowp", a.precision, st.lowp_flops / max(st.lowp_launches, 1),
-                           st.lowp_ms / max(st.lowp_launches, 1), False, st.lowp_ms / (ms * a.steps))
+    sms = device_sms(dev)
+    mhz = clk.get("sm_max_mhz") or peaks()["sm_max_mhz"]
+    rfs = stats_rooflines(st, n, s, p, ms * a.steps, False, a.precision, sms, mhz, a.workload)
     line = {"mode": "apply", "metric": "operator applications (unknowns/s)", "value": n * s * p / (ms / 1e3),
             "unit": "unknowns/s", "ms_per_step": ms, "steps": a.steps, "warmup": a.warmup,
             "config": {"workload": a.workload, "n": n, "s": s, "p": p, "precision": a.precision,
                        "fp64_engine": a.engine},
-            "roofline": rf, "fft_gbs": st.fft_bytes / max(st.fft_ms, 1e-9) / 1e6,
+            "roofline": rfs[0] if rfs else None, "rooflines": rfs,
+            "fft_gbs": st.fft_bytes / max(st.fft_ms, 1e-9) / 1e6,
             "fft_ms_per_step": st.fft_ms / a.steps, "clocks": clk, "gpu_launches": int(st.launches)}
     print(json.dumps(line), flush=True)
     op.close()

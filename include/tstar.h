@@ -286,6 +286,11 @@ typedef struct {
   double tba_flops;        /* 8 n s^2 per complex slice product */
   double oz_pair_flops;    /* BF16 FLOPs of the emulated products' digit pairs (S(S+1)/2 products per
                               FP64 product, S the digits of each launch) */
+  long long spmm_launches; /* sparse products A_k V of TBAS (Algorithm 7 step 3(a)), FP64 or FP32 */
+  double spmm_ms;
+  double spmm_flops;       /* FLOPs the kernel executes: 8 per stored complex value and block column */
+  double spmm_bytes;       /* algorithmic bytes: values, column indices, row pointers, V read and W
+                              written once */
 } ts_stats;
 
 /* Enable (1) or disable (0) per-kernel event timing on ctx. */

@@ -53,7 +53,9 @@ class Stats(ctypes.Structure):
                 ("lowp_flops", ctypes.c_double), ("fft_launches", ctypes.c_longlong), ("fft_ms", ctypes.c_double),
                 ("fft_bytes", ctypes.c_double), ("oz_launches", ctypes.c_longlong), ("oz_ms", ctypes.c_double),
                 ("oz_flops", ctypes.c_double), ("tba_launches", ctypes.c_longlong), ("tba_ms", ctypes.c_double),
-                ("tba_flops", ctypes.c_double), ("oz_pair_flops", ctypes.c_double)]
+                ("tba_flops", ctypes.c_double), ("oz_pair_flops", ctypes.c_double),
+                ("spmm_launches", ctypes.c_longlong), ("spmm_ms", ctypes.c_double), ("spmm_flops", ctypes.c_double),
+                ("spmm_bytes", ctypes.c_double)]
 
 
 class TstarError(RuntimeError):

@@ -112,7 +112,7 @@ void op_free(void* p) {
 std::atomic<long long> g_launches{0};
 thread_local int g_count_suppress = 0;
 
-void KernelTimer::begin(cudaStream_t st, int kind, double work) {
+void KernelTimer::begin(cudaStream_t st, int kind, double work, double work2) {
   if (!enabled) return;
   if (pool.empty()) {
     cudaEvent_t a, b;
@@ -123,7 +123,7 @@ void KernelTimer::begin(cudaStream_t st, int kind, double work) {
   auto ev = pool.back();
   pool.pop_back();
   TS_CUDA(cudaEventRecord(ev.first, st));
-  done.push_back(TimedRegion{ev.first, ev.second, kind, work});
+  done.push_back(TimedRegion{ev.first, ev.second, kind, work, work2});
 }
 
 void KernelTimer::end(cudaStream_t st) {
@@ -153,6 +153,11 @@ void KernelTimer::collect() {
       ++tba_launches;
       tba_ms += ms;
       tba_flops += r.work;
+    } else if (r.kind == 5) {
+      ++spmm_launches;
+      spmm_ms += ms;
+      spmm_flops += r.work;
+      spmm_bytes += r.work2;
     } else {
       ++fft_launches;
       fft_ms += ms;
@@ -165,8 +170,9 @@ void KernelTimer::collect() {
 
 void KernelTimer::reset() {
   collect();
-  gemm_launches = fft_launches = lowp_launches = oz_launches = tba_launches = 0;
+  gemm_launches = fft_launches = lowp_launches = oz_launches = tba_launches = spmm_launches = 0;
   gemm_ms = gemm_flops = fft_ms = fft_bytes = lowp_ms = lowp_flops = oz_ms = oz_flops = tba_ms = tba_flops = 0;
+  spmm_ms = spmm_flops = spmm_bytes = 0;
   oz_pair_flops = 0;
 }
 
@@ -667,6 +673,10 @@ ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out) {
   out->tba_ms = t.tba_ms;
   out->tba_flops = t.tba_flops;
   out->oz_pair_flops = t.oz_pair_flops;
+  out->spmm_launches = t.spmm_launches;
+  out->spmm_ms = t.spmm_ms;
+  out->spmm_flops = t.spmm_flops;
+  out->spmm_bytes = t.spmm_bytes;
   return TS_OK;
   TS_API_END(ctx)
 }

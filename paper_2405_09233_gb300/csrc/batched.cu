@@ -501,10 +501,12 @@ struct BatchPlan {
 // `residual_products(st)` issues the FP64 slice products of the true residual (Xh64 -> Yh64) and
 // returns how many kernels it launched.
 // `inner_products(st)` issues the inner operator's slice products (Xh -> Yh) likewise.
+// ev (may be null): 2m + 2 events recorded as graph nodes around the inner products of step j
+// (ev[2j], ev[2j+1]) and around the residual products (ev[2m], ev[2m+1]), for the statistics.
 template <typename T, typename Real2, typename InnerProducts, typename ResidualProducts>
 int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Real2* Yh, double* R, double2* Xh64,
                  double2* Yh64, double* P0, double* P1, double* Pt, const InnerProducts& inner_products,
-                 const ResidualProducts& residual_products, cudaStream_t st) {
+                 const ResidualProducts& residual_products, const cudaEvent_t* ev, cudaStream_t st) {
   using Real = T;
   const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size();
   const int count = d.count, m = d.m;
@@ -515,7 +517,9 @@ int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Re
   kernels += 2;
   for (int j = 0; j < m; ++j) {
     k_b_rfft<Real, Real2, 0, 0><<<ntb, kTubes, 0, st>>>(d, basis(V, d.totN, j), Xh);
+    if (ev) TS_CUDA(cudaEventRecordWithFlags(ev[2 * j], st, cudaEventRecordExternal));
     kernels += inner_products(st);
+    if (ev) TS_CUDA(cudaEventRecordWithFlags(ev[2 * j + 1], st, cudaEventRecordExternal));
     k_b_irfft<Real, Real2, 0><<<ntb, kTubes, 0, st>>>(d, Yh, W, nullptr);
     k_b_dot<T><<<nbs, 256, 0, st>>>(d, basis(V, d.totN, 0), W, Pp[0]);
     for (int i = 0; i <= j; ++i)
@@ -529,7 +533,9 @@ int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Re
   k_b_axpy<T><<<nbs, 256, 0, st>>>(d, V);
   // true residual R = C - M(X) in FP64
   k_b_rfft<double, double2, 1, 1><<<ntb, kTubes, 0, st>>>(d, nullptr, Xh64);
+  if (ev) TS_CUDA(cudaEventRecordWithFlags(ev[2 * m], st, cudaEventRecordExternal));
   kernels += residual_products(st);
+  if (ev) TS_CUDA(cudaEventRecordWithFlags(ev[2 * m + 1], st, cudaEventRecordExternal));
   k_b_irfft<double, double2, 1><<<ntb, kTubes, 0, st>>>(d, Yh64, R, Pt);
   k_b_finalize_norm<<<count, 256, 0, st>>>(d, Pt, 1);
   kernels += 5;
@@ -894,10 +900,83 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   int max_cycles = mixed ? (o.max_outer > 0 ? o.max_outer : 50) : o.max_restarts;
   int launched = 0;
   ts_status overall = TS_OK;
+  // Statistics (while enabled): events recorded inside the cycle graph time the inner products of each
+  // step and the residual products; after each replay the host adds their durations, and the
+  // algorithmic work of the instances that took part (inner steps from each instance's iteration
+  // count, residuals from its cycle flag), to the context's timer.
+  std::vector<cudaEvent_t> tev;
+  struct TevGuard {
+    std::vector<cudaEvent_t>& e;
+    ~TevGuard() {
+      for (auto x : e) cudaEventDestroy(x);
+    }
+  } tev_guard{tev};
+  if (ctx->timer.enabled) {
+    tev.resize(2 * m + 2);
+    for (auto& e : tev) TS_CUDA(cudaEventCreate(&e));
+  }
+  std::vector<double> iters_prev(count, 0.0), inst_flops(count), inst_pairs(count);
+  for (int i = 0; i < count; ++i) {
+    const ts_op* op = ops[i];
+    inst_flops[i] = gemm_flops(op->n, op->s, op->n, op->s, op->K, nyquist_index(op->p));
+    inst_pairs[i] = ozaki ? oz_bf16_flops(op->n, op->s, op->K, nyquist_index(op->p), oz_digits) : 0.0;
+  }
+  std::vector<int> in_cycle(count, 0);
+  auto collect_phase_times = [&]() {
+    KernelTimer& tm = ctx->timer;
+    double inner_ms = 0.0, res_ms = 0.0, inner_work = 0.0, res_work = 0.0, inner_pairs = 0.0, res_pairs = 0.0;
+    for (int j = 0; j < m; ++j) {
+      float x = 0.f;
+      TS_CUDA(cudaEventElapsedTime(&x, tev[2 * j], tev[2 * j + 1]));
+      inner_ms += x;
+    }
+    float x = 0.f;
+    TS_CUDA(cudaEventElapsedTime(&x, tev[2 * m], tev[2 * m + 1]));
+    res_ms = x;
+    for (int i = 0; i < count; ++i) {
+      const double steps = hsc[16 * i + SC_ITERS] - iters_prev[i];
+      iters_prev[i] = hsc[16 * i + SC_ITERS];
+      inner_work += steps * inst_flops[i];
+      inner_pairs += steps * inst_pairs[i];
+      if (in_cycle[i]) {
+        res_work += inst_flops[i];
+        res_pairs += inst_pairs[i];
+      }
+    }
+    // inner products: low precision (kind 2), or FP64 on the emulated (3) or DFMA (0) engine
+    if (mixed) {
+      tm.lowp_launches += m;
+      tm.lowp_ms += inner_ms;
+      tm.lowp_flops += inner_work;
+    } else if (ozaki) {
+      tm.oz_launches += m;
+      tm.oz_ms += inner_ms;
+      tm.oz_flops += inner_work;
+      tm.oz_pair_flops += inner_pairs;
+    } else {
+      tm.gemm_launches += m;
+      tm.gemm_ms += inner_ms;
+      tm.gemm_flops += inner_work;
+    }
+    if (ozaki) {
+      tm.oz_launches += 1;
+      tm.oz_ms += res_ms;
+      tm.oz_flops += res_work;
+      tm.oz_pair_flops += res_pairs;
+    } else {
+      tm.gemm_launches += 1;
+      tm.gemm_ms += res_ms;
+      tm.gemm_flops += res_work;
+    }
+  };
   try {
     for (int cycle = 0; cycle <= max_cycles; ++cycle) {
       TS_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(double) * 16 * count, cudaMemcpyDeviceToHost, st));
       TS_CUDA(cudaStreamSynchronize(st));
+      if (cycle == 0)
+        for (int i = 0; i < count; ++i) iters_prev[i] = hsc[16 * i + SC_ITERS];
+      else if (!tev.empty())
+        collect_phase_times();
       int remaining = 0;
       for (int i = 0; i < count; ++i) {
         done[i] = hsc[16 * i + SC_DONE] != 0.0 || hsc[16 * i + SC_FLAGS] != 0.0;
@@ -907,6 +986,7 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       for (int i = 0; i < count; ++i) {
         hflags[i] = done[i] ? 0 : 1;
         hflags[count + i] = hflags[i];
+        in_cycle[i] = hflags[i];
         if (!done[i]) ++cycles[i];
       }
       TS_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice, st));
@@ -919,10 +999,12 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
         TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         if (mixed)
           graph_kernels = record_cycle<float, float2>(d, plan, (float*)V, (float*)W, (float2*)Xh, (float2*)Yh, R, Xh64,
-                                                      Yh64, P0, P1, Pt, inner_products, residual_products, st);
+                                                      Yh64, P0, P1, Pt, inner_products, residual_products,
+                                                      tev.empty() ? nullptr : tev.data(), st);
         else
           graph_kernels = record_cycle<double, double2>(d, plan, (double*)V, (double*)W, (double2*)Xh, (double2*)Yh, R,
-                                                        Xh64, Yh64, P0, P1, Pt, inner_products, residual_products, st);
+                                                        Xh64, Yh64, P0, P1, Pt, inner_products, residual_products,
+                                                        tev.empty() ? nullptr : tev.data(), st);
         TS_CUDA(cudaStreamEndCapture(st, &graph));
         TS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
         TS_CUDA(cudaGraphDestroy(graph));

@@ -90,8 +90,10 @@ struct CountSuppress {
 // Event timing of selected kernels while a context has statistics enabled.
 struct TimedRegion {
   cudaEvent_t a, b;
-  int kind;        // 0 = FP64 GEMM, 1 = FFT, 2 = low-precision GEMM, 3 = emulated FP64 GEMM, 4 = TBAS block products
-  double work;     // algorithmic FLOPs (GEMM) or bytes (FFT)
+  int kind;        // 0 = FP64 GEMM, 1 = FFT, 2 = low-precision GEMM, 3 = emulated FP64 GEMM, 4 = TBAS block products,
+                   // 5 = sparse A_k V products (TBAS)
+  double work;     // algorithmic FLOPs (GEMM, sparse products) or bytes (FFT)
+  double work2;    // sparse products: algorithmic bytes
 };
 struct KernelTimer {
   bool enabled = false;
@@ -102,7 +104,9 @@ struct KernelTimer {
   double oz_ms = 0, oz_flops = 0, oz_pair_flops = 0;   // oz_pair_flops: added at launch time
   long long tba_launches = 0;
   double tba_ms = 0, tba_flops = 0;
-  void begin(cudaStream_t st, int kind, double work);
+  long long spmm_launches = 0;
+  double spmm_ms = 0, spmm_flops = 0, spmm_bytes = 0;
+  void begin(cudaStream_t st, int kind, double work, double work2 = 0.0);
   void end(cudaStream_t st);
   void collect();  // synchronise the recorded events and accumulate
   void reset();

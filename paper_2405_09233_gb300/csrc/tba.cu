@@ -941,6 +941,14 @@ ts_status tbas_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const t
   const bool low = o.precision == TS_MIXED_FP32;
   float2* V32 = low ? (float2*)ctx->ws.get("tba_V32", sizeof(float2) * (size_t)blk * (m + 1)) : nullptr;
   const double breakdown_rel = low ? 1e-6 : 1e-13;
+  // Work of one A V_j product over all K slices: the kernel forms 8 FLOPs per stored complex value
+  // and block column (dense A: n^2 values per slice); algorithmically it reads the values, the
+  // pattern and V once and writes W once.
+  const double a_vals = op->sp ? (double)op->sp->nnz : (double)n * n;
+  const double spmm_flops = 8.0 * a_vals * s * K;
+  auto spmm_bytes = [&](size_t c2) {
+    return (double)K * a_vals * c2 + (op->sp ? 4.0 * (a_vals + n + 1) : 0.0) + 2.0 * (double)K * n * s * c2;
+  };
   for (int cycle = 0; cycle < o.max_restarts; ++cycle) {
     const int N = m * s;
     int mm = m;
@@ -958,6 +966,7 @@ ts_status tbas_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const t
       for (int j = 0; j < m; ++j) {
         C2* Vj = V + (long long)j * blk;
         C2* Wb = V + (long long)(j + 1) * blk;
+        w.tm->begin(st, 5, spmm_flops, spmm_bytes(sizeof(C2)));
         if constexpr (sizeof(C2) == 16) {
           rows_call(0, op, Vj, nullptr, Wb, nullptr, n, s, K, p, st);          // W = A * V_j (A, not M)
           ++info.applies_fp64;
@@ -965,6 +974,7 @@ ts_status tbas_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const t
           rows_call_f32(op, Vj, Wb, n, s, K, p, st);
           ++info.applies_low;
         }
+        w.tm->end(st);
         for (int i = 0; i <= j; ++i) {                                          // block MGS
           C2* Vi = V + (long long)i * blk;
           double2* Hij = w.Hm + (long long)i * s + (long long)N * j * s;       // block (i, j) of H_m

@@ -23,6 +23,11 @@ families stand in for it):
   B^(1) = -4 I + 0.1 G'/sqrt(s) and B^(k>=2) = 0.1 G'/sqrt(s).
 * batched family: many dense-family instances with n log-uniform in
   [64, 1024], s uniform in [16, 128], p drawn from {4, 8, 16}.
+* convection-diffusion family (the paper's §6 example, with the viscosity mu
+  given explicitly and a seeded right-hand side): A^(i) = mu/h1^2 tridiag(-1, 2, -1)
+  + a_i/(4 h1) T_n and B^(i) = mu/h2^2 tridiag(-1, 2, -1) + b_i/(4 h2) T_s, with
+  T the banded matrix of 3 on the diagonal, -5 above it, 1 two above it and 1 below
+  it, a_i = i, b_i = p + i, h1 = 1/(n+1), h2 = 1/(s+1); C entries i.i.d. U(0, 1).
 """
 from __future__ import annotations
 
@@ -201,3 +206,39 @@ WORKLOADS = {
     "sparse_lap128_s32_p8": dict(grid=128, s=32, p=8),
     "batched_256": dict(count=256),
 }
+
+
+def convection_band(n: int) -> np.ndarray:
+    """The banded n x n matrix of the paper's convection term: 1 below the diagonal, 3 on it, -5 above it
+    and 1 two above it."""
+    T = np.zeros((n, n))
+    i = np.arange(n)
+    T[i, i] = 3.0
+    T[i[1:], i[:-1]] = 1.0
+    T[i[:-1], i[1:]] = -5.0
+    T[i[:-2], i[2:]] = 1.0
+    return T
+
+
+@dataclasses.dataclass
+class ConvDiffProblem:
+    A: np.ndarray          # n x n x p
+    B: np.ndarray          # s x s x p
+    C: np.ndarray          # n x s x p, entries U(0, 1)
+    mu: float
+    seed: int
+
+
+def convdiff_problem(n: int, s: int, p: int, mu: float, seed: int) -> ConvDiffProblem:
+    """The convection-diffusion family of the paper's §6 example (frontal slices i = 1..p)."""
+    h1, h2 = 1.0 / (n + 1), 1.0 / (s + 1)
+    A = np.empty((n, n, p), order="F")
+    B = np.empty((s, s, p), order="F")
+    Ln, Ls = tridiag(n, -1.0, 2.0, -1.0), tridiag(s, -1.0, 2.0, -1.0)
+    Tn, Ts = convection_band(n), convection_band(s)
+    for i in range(1, p + 1):
+        A[:, :, i - 1] = (mu / h1 ** 2) * Ln + (i / (4 * h1)) * Tn
+        B[:, :, i - 1] = (mu / h2 ** 2) * Ls + ((p + i) / (4 * h2)) * Ts
+    rng = np.random.default_rng(seed)
+    C = np.asfortranarray(rng.uniform(0.0, 1.0, size=(n, s, p)))
+    return ConvDiffProblem(A, B, C, mu, seed)
