@@ -181,22 +181,27 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             break;
           }
           const uint32_t full = bar_full + 8 * slot;
-          mbar_expect_tx(full, kOzStage);
+          // a real slice (k = 0 or p/2) uses the real A tile and one B block (Q = Xr, or P = Br) only
+          mbar_expect_tx(full, real ? kOzTileA + kOzTileB : kOzStage);
           const uint32_t sA = base + slot * kOzStage;
           const uint32_t sAi = sA + kOzTileA, sP = sA + 2 * kOzTileA, sQ = sP + kOzTileB, sR = sQ + kOzTileB;
           const int l0 = (lb0 + t) * kOzKB;
           if (ax) {
             tma_load_3d(sA, &maps.a_re, l0, i0, pa, full);
-            tma_load_3d(sAi, &maps.a_im, l0, i0, pa, full);
-            tma_load_3d(sP, &maps.xc_nim, l0, j0, pb, full);   // [P; Q; R] = [-Xi; Xr; Xi]
-            tma_load_3d(sQ, &maps.xc_re, l0, j0, pb, full);
-            tma_load_3d(sR, &maps.xc_im, l0, j0, pb, full);
+            tma_load_3d(sQ, &maps.xc_re, l0, j0, pb, full);    // [P; Q; R] = [-Xi; Xr; Xi]
+            if (!real) {
+              tma_load_3d(sAi, &maps.a_im, l0, i0, pa, full);
+              tma_load_3d(sP, &maps.xc_nim, l0, j0, pb, full);
+              tma_load_3d(sR, &maps.xc_im, l0, j0, pb, full);
+            }
           } else {
             tma_load_3d(sA, &maps.xr_re, l0, i0, pa, full);
-            tma_load_3d(sAi, &maps.xr_im, l0, i0, pa, full);
             tma_load_3d(sP, &maps.b_re, l0, j0, pb, full);     // [P; Q; R] = [Br; Bi; -Br]
-            tma_load_3d(sQ, &maps.b_im, l0, j0, pb, full);
-            tma_load_3d(sR, &maps.b_nre, l0, j0, pb, full);
+            if (!real) {
+              tma_load_3d(sAi, &maps.xr_im, l0, i0, pa, full);
+              tma_load_3d(sQ, &maps.b_im, l0, j0, pb, full);
+              tma_load_3d(sR, &maps.b_nre, l0, j0, pb, full);
+            }
           }
           issued = it + 1;
         }
@@ -499,13 +504,13 @@ void oz_prepare(ts_op* op, int S, cudaStream_t st) {
   t->ldn = round_up(n, 64);
   t->lds = round_up(s, 64);
   const size_t na = (size_t)S * K * n * t->ldn * 2, nb = (size_t)S * K * s * t->lds * 2;
-  op_alloc(t->a_re, na);
-  op_alloc(t->a_im, na);
-  op_alloc(t->b_re, nb);
-  op_alloc(t->b_im, nb);
-  op_alloc(t->b_nre, nb);
-  op_alloc(t->Eop, sizeof(int) * K);
-  op_alloc(t->mx, sizeof(unsigned long long) * K);
+  op_alloc_on(t->a_re, na, st);
+  op_alloc_on(t->a_im, na, st);
+  op_alloc_on(t->b_re, nb, st);
+  op_alloc_on(t->b_im, nb, st);
+  op_alloc_on(t->b_nre, nb, st);
+  op_alloc_on(t->Eop, sizeof(int) * K, st);
+  op_alloc_on(t->mx, sizeof(unsigned long long) * K, st);
   // A_k and B_k share one exponent per slice, so both products of Eq. (2) land on one fixed point.
   unsigned long long* mxb = t->mx;
   TS_CUDA(cudaMemsetAsync(mxb, 0, sizeof(unsigned long long) * K, st));

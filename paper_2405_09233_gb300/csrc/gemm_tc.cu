@@ -107,7 +107,8 @@ __device__ __forceinline__ void tc_sylv_tile(const TcMaps& maps, float2* __restr
         if (!mbar_wait(bar_empty + 8 * slot, phase ^ 1u, err, 1, wait_ns)) break;
         if (stall) continue;   // test aid: arm no stage, so the MMA warp's wait expires
         const uint32_t full = bar_full + 8 * slot;
-        mbar_expect_tx(full, Cfg::kStage);
+        // a real slice (k = 0 or p/2) multiplies the real planes only, so only those are loaded
+        mbar_expect_tx(full, real ? Cfg::kTileA + Cfg::kTileB : Cfg::kStage);
         const uint32_t sA = base + slot * Cfg::kStage;
         const uint32_t sAi = sA + Cfg::kTileA, sB = sA + 2 * Cfg::kTileA, sBi = sB + Cfg::kTileB;
         const int blk = it / PARTS, part = it % PARTS;
@@ -115,15 +116,19 @@ __device__ __forceinline__ void tc_sylv_tile(const TcMaps& maps, float2* __restr
         if (blk < it1) {
           const int l0 = blk * Cfg::kElemsK;
           tma_load_3d(sA, alo ? &maps.a_re_lo : &maps.a_re, l0, i0, k, full);
-          tma_load_3d(sAi, alo ? &maps.a_im_lo : &maps.a_im, l0, i0, k, full);
           tma_load_3d(sB, blo ? &maps.xc_re_lo : &maps.xc_re, l0, j0, k, full);
-          tma_load_3d(sBi, blo ? &maps.xc_im_lo : &maps.xc_im, l0, j0, k, full);
+          if (!real) {
+            tma_load_3d(sAi, alo ? &maps.a_im_lo : &maps.a_im, l0, i0, k, full);
+            tma_load_3d(sBi, blo ? &maps.xc_im_lo : &maps.xc_im, l0, j0, k, full);
+          }
         } else {
           const int l0 = (blk - it1) * Cfg::kElemsK;
           tma_load_3d(sA, alo ? &maps.xr_re_lo : &maps.xr_re, l0, i0, k, full);
-          tma_load_3d(sAi, alo ? &maps.xr_im_lo : &maps.xr_im, l0, i0, k, full);
           tma_load_3d(sB, blo ? &maps.b_re_lo : &maps.b_re, l0, j0, k, full);
-          tma_load_3d(sBi, blo ? &maps.b_im_lo : &maps.b_im, l0, j0, k, full);
+          if (!real) {
+            tma_load_3d(sAi, alo ? &maps.xr_im_lo : &maps.xr_im, l0, i0, k, full);
+            tma_load_3d(sBi, blo ? &maps.b_im_lo : &maps.b_im, l0, j0, k, full);
+          }
         }
         issued = it + 1;
       }
@@ -577,15 +582,15 @@ void tc_prepare(ts_op* op, int precision, cudaStream_t st) {
   t->ldn = round_up(op->n, 64);
   t->lds = round_up(op->s, 64);
   const size_t na = (size_t)op->K * op->n * t->ldn * esz, nb = (size_t)op->K * op->s * t->lds * esz;
-  op_alloc(t->a_re, na);
-  op_alloc(t->a_im, na);
-  op_alloc(t->b_re, nb);
-  op_alloc(t->b_im, nb);
+  op_alloc_on(t->a_re, na, st);
+  op_alloc_on(t->a_im, na, st);
+  op_alloc_on(t->b_re, nb, st);
+  op_alloc_on(t->b_im, nb, st);
   if (split) {
-    op_alloc(t->a_re_lo, na);
-    op_alloc(t->a_im_lo, na);
-    op_alloc(t->b_re_lo, nb);
-    op_alloc(t->b_im_lo, nb);
+    op_alloc_on(t->a_re_lo, na, st);
+    op_alloc_on(t->a_im_lo, na, st);
+    op_alloc_on(t->b_re_lo, nb, st);
+    op_alloc_on(t->b_im_lo, nb, st);
   }
   if (esz == 2) prepare_operator<__nv_bfloat16>(op, *t, st);
   else prepare_operator<float>(op, *t, st);
