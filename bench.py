@@ -581,14 +581,24 @@ class BatchedSetup:
         torch.cuda.synchronize()
 
     def solve(self, name):
+        """One step: create the batch's operators, solve them together, release the operators.  The host
+        time of each part of the last call is kept in self.split_ms."""
+        import torch
         prec, _, eng = name.partition("@")
+        t0 = time.perf_counter()
         ops = [self.ctx.op_create_dense(A, B) for A, B, _ in self.dev_in]
         for X in self.Xs:
             X.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         st, infos, _ = self.ctx.batched_solve(ops, self.Cs, self.Xs, restart=20, tol=1e-10, precision=prec,
                                               engine=eng or "dfma")
+        t2 = time.perf_counter()
         for op in ops:
             op.close()
+        t3 = time.perf_counter()
+        self.split_ms = {"op_create": 1e3 * (t1 - t0), "solve": 1e3 * (t2 - t1), "op_destroy": 1e3 * (t3 - t2),
+                         "solve_device_ms": infos[0].ms_total if infos else None}
         return st, infos
 
     def certify(self):
@@ -610,7 +620,8 @@ def batched_entry(setup, name, reps, warm=1, world=1):
         med, ms, (st, infos) = timed_median(lambda: setup.solve(name), reps, warm)
         return {"value": setup.unknowns * world / (med / 1e3), "ms_per_step": med, "ms_all": ms, "status": st,
                 "max_relres_true": max(i.relres_true for i in infos), "max_relres_fp64_dfma": setup.certify(),
-                "max_err_vs_xstar": setup.err_xstar(), "max_outer": max(i.outer for i in infos)}
+                "max_err_vs_xstar": setup.err_xstar(), "max_outer": max(i.outer for i in infos),
+                "split_ms_last": setup.split_ms}
     except Exception as e:  # report, do not hide
         return {"error": str(e)}
 
@@ -693,8 +704,11 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    # Small problems run their restart cycles as CUDA graphs, which per-kernel event timing would turn
+    # off: they are timed with statistics off, and the kernel split comes from one extra solve.
+    small = su.unknowns <= 1 << 20
     ctx.stats_reset()
-    ctx.stats_enable(True)
+    ctx.stats_enable(not small)
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -709,6 +723,20 @@ def main():
     ctx.stats_enable(False)
     st = ctx.stats_get()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dev)
+    launches = int(st.launches)
+    host_split = {"graph_build_ms_per_step": st.graph_build_ms / a.steps}
+    kernel_steps, kernel_ms = a.steps, ms * a.steps
+    if small:
+        ctx.stats_reset()
+        ctx.stats_enable(True)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record()
+        su.solve(primary)
+        k1.record()
+        torch.cuda.synchronize()
+        ctx.stats_enable(False)
+        st = ctx.stats_get()
+        kernel_steps, kernel_ms = 1, k0.elapsed_time(k1)
     last = results[-1]
     assert all(r.status == 0 for r in results), results
     relres_cert = su.certify()
@@ -718,14 +746,18 @@ def main():
     sms = device_sms(dev)
     mhz = clk.get("sm_max_mhz") or peaks()["sm_max_mhz"]
     dgemm = measure_dgemm_tflops(dev) if rank == 0 and st.gemm_launches else None
-    rooflines = stats_rooflines(st, n, s, p, ms * a.steps, True, a.precision, sms, mhz, a.workload, dgemm)
+    rooflines = stats_rooflines(st, n, s, p, kernel_ms, True, a.precision, sms, mhz, a.workload, dgemm)
+    if small:
+        for r in rooflines:
+            r["note"] += ("; latency-bound workload: a roofline fraction says little here (the kernel split is "
+                          "from one extra solve with per-kernel event timing, which runs the cycle step by step)")
     roofline = rooflines[0] if rooflines else None
-    kernel_times = {"fp64_gemm_ms": st.gemm_ms / a.steps, "ozaki_gemm_ms": st.oz_ms / a.steps,
-                    "lowp_gemm_ms": st.lowp_ms / a.steps,
-                    "fft_ms": st.fft_ms / a.steps, "fp64_gemm_launches": st.gemm_launches // a.steps,
-                    "ozaki_gemm_launches": st.oz_launches // a.steps,
-                    "lowp_gemm_launches": st.lowp_launches // a.steps,
-                    "fft_gbs": st.fft_bytes / max(st.fft_ms, 1e-9) / 1e6}
+    kernel_times = {"fp64_gemm_ms": st.gemm_ms / kernel_steps, "ozaki_gemm_ms": st.oz_ms / kernel_steps,
+                    "lowp_gemm_ms": st.lowp_ms / kernel_steps,
+                    "fft_ms": st.fft_ms / kernel_steps, "fp64_gemm_launches": st.gemm_launches // kernel_steps,
+                    "ozaki_gemm_launches": st.oz_launches // kernel_steps,
+                    "lowp_gemm_launches": st.lowp_launches // kernel_steps,
+                    "fft_gbs": st.fft_bytes / max(st.fft_ms, 1e-9) / 1e6, "from_steps": kernel_steps}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     C_h = su.Cd.cpu().pin_memory()
@@ -799,8 +831,8 @@ def main():
                            "applies_fp64": last.info.applies_fp64, "relres_true": last.info.relres_true,
                            "relres_fp64_dfma": relres_cert, "err_vs_xstar": err_xstar, "sms": sms},
                 "e2e": e2e, "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu, "clocks": clk,
-                "gpu_launches": int(st.launches), "kernels_per_step": kernel_times, "variants": variants,
-                "comparisons": comparisons}
+                "gpu_launches": launches, "kernels_per_step": kernel_times, "host_split": host_split,
+                "variants": variants, "comparisons": comparisons}
         print(json.dumps(line), flush=True)
     su.close()
     ctx.close()
@@ -821,8 +853,10 @@ def run_batched(a, rank, world, local, dev):
     for _ in range(a.warmup):
         st, infos = b.solve(primary)
     assert st == 0
+    # Timed with statistics off: per-phase event timing needs the flat cycle graph, while the timed
+    # steps run the nested one (a cycle stops as soon as no instance iterates).  The phase split
+    # comes from one extra instrumented step.
     ctx.stats_reset()
-    ctx.stats_enable(True)
     clocks = ClockSampler(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -833,9 +867,19 @@ def run_batched(a, rank, world, local, dev):
     e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    sth = ctx.stats_get()                       # host phases and launches of the timed steps
+    step_split = dict(b.split_ms)
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+    ctx.stats_reset()
+    ctx.stats_enable(True)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record()
+    b.solve(primary)
+    k1.record()
+    torch.cuda.synchronize()
     ctx.stats_enable(False)
     stt = ctx.stats_get()
-    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
+    instrumented_ms = k0.elapsed_time(k1)
     assert st == 0, st
     relres = max(i.relres_true for i in infos)
     cert = b.certify()
@@ -844,11 +888,12 @@ def run_batched(a, rank, world, local, dev):
     mhz = clk.get("sm_max_mhz") or peaks()["sm_max_mhz"]
     ratio = (sum(slice_flops(sp.n, sp.s, sp.p, 6) for sp in b.specs)
              / sum(slice_flops(sp.n, sp.s, sp.p, 8) for sp in b.specs))
-    rooflines = stats_rooflines(stt, 0, 0, 0, ms * a.steps, True, prec, sms, mhz, "batched_256", exec_ratio=ratio)
+    rooflines = stats_rooflines(stt, 0, 0, 0, instrumented_ms, True, prec, sms, mhz, "batched_256", exec_ratio=ratio)
     for r in rooflines:
-        r["note"] += ("; batched: every phase of the captured cycle is timed by events recorded in the graph, "
-                      "its work counted for the instances active in that phase (masked instances' CTAs exit early "
-                      "and still count in the time)")
+        r["note"] += ("; batched: from one extra step whose flat cycle graph times every product phase with events "
+                      "recorded in the graph, its work counted for the instances active in that phase (masked "
+                      "instances' CTAs exit early and still count in the time); that step took %.1f ms"
+                      % instrumented_ms)
     # end to end: operators and right-hand sides from pinned host memory, solutions back to host
     C_h = [C.cpu().pin_memory() for C in b.Cs]
     X_h = [torch.zeros_like(C).pin_memory() for C in C_h]
@@ -886,7 +931,11 @@ def run_batched(a, rank, world, local, dev):
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": len(t_e2e),
                         "statistic": "median"},
                 "roofline": rooflines[0] if rooflines else None, "rooflines": rooflines, "cpu_baseline": cpu,
-                "clocks": clk, "gpu_launches": int(stt.launches), "variants": variants}
+                "clocks": clk, "gpu_launches": int(sth.launches), "split_ms_last_step": step_split,
+                "host_split_per_step": {"setup_ms": sth.host_setup_ms / a.steps,
+                                        "graph_build_ms": sth.graph_build_ms / a.steps,
+                                        "cycles_ms": sth.host_cycles_ms / a.steps},
+                "variants": variants}
         print(json.dumps(line), flush=True)
     b.close()
     ctx.close()

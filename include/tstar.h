@@ -16,8 +16,9 @@
  *   workspace.  The caller owns every pointer it passes; the library never
  *   frees caller memory.  Pointers must stay valid until the call returns.
  * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
- *   ts_tstar and ts_sylv_apply with device pointers are asynchronous on that
- *   stream; every other call returns after its work on the stream completed.
+ *   ts_tstar, ts_sylv_apply and ts_op_create_dense with device pointers are
+ *   asynchronous on that stream; every other call returns after its work on
+ *   the stream completed.
  * Errors.  Every call returns a ts_status; nothing throws, exits or aborts.
  *   ts_last_error(ctx) describes the last failure on that context.
  * Threads.  A ts_ctx (and the ts_op objects made from it) must be used by one
@@ -81,7 +82,10 @@ ts_status ts_tstar(ts_ctx* ctx, const double* A, int n1, int n2, const double* B
  * and B (s x s x p): computes and keeps the Fourier slices A_k, B_k for
  * k = 0..floor(p/2) (FP64; lower-precision copies are made on first use by a
  * mixed-precision solve).  `flags` is reserved (pass 0).  *op is owned by the
- * caller and freed with ts_op_destroy before ts_destroy(ctx). */
+ * caller and freed with ts_op_destroy before ts_destroy(ctx).  With A and B in
+ * device memory the preparation is asynchronous on `stream`: the operator may
+ * be used on that stream at once, on another stream once `stream` has been
+ * synchronised (host inputs are staged and the call returns after the work). */
 ts_status ts_op_create_dense(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p,
                              unsigned flags, ts_op** op, ts_stream stream);
 /* Prepare M(X) = A*X - X*B with a sparse A given by its p frontal slices in CSR form (host
@@ -92,7 +96,9 @@ ts_status ts_op_create_dense(ts_ctx* ctx, const double* A, int n, const double* 
  * in FP64 (ts_sylv_apply, ts_tgmres_solve, ts_tfom_solve, ts_tba_solve); s <= 64. */
 ts_status ts_op_create_csr(ts_ctx* ctx, int n, int p, const int* rowptr, const int* col, const double* val,
                            const double* B, int s, unsigned flags, ts_op** op, ts_stream stream);
-/* Free an operator.  NULL is ignored. */
+/* Free an operator.  NULL is ignored.  Its device buffers return to the library's operator pool
+ * once work that may still read them is known to have finished (they are collected and released
+ * together after one device synchronisation, at the latest when the context is destroyed). */
 void ts_op_destroy(ts_op* op);
 /* Sizes of a prepared operator (any output pointer may be NULL). */
 ts_status ts_op_shape(const ts_op* op, int* n, int* s, int* p);
@@ -291,6 +297,12 @@ typedef struct {
   double spmm_flops;       /* FLOPs the kernel executes: 8 per stored complex value and block column */
   double spmm_bytes;       /* algorithmic bytes: values, column indices, row pointers, V read and W
                               written once */
+  double host_setup_ms;    /* host clock (always collected): batched solves' preparation before the
+                              first residual (operator copies, work lists, tensor maps, tuning) */
+  double graph_build_ms;   /* capture and instantiation of restart-cycle graphs (batched and small
+                              single-instance solves) */
+  double host_cycles_ms;   /* batched solves: the restart cycles (graph replays and the host's look at
+                              each cycle's residuals) */
 } ts_stats;
 
 /* Enable (1) or disable (0) per-kernel event timing on ctx. */

@@ -55,7 +55,8 @@ class Stats(ctypes.Structure):
                 ("oz_flops", ctypes.c_double), ("tba_launches", ctypes.c_longlong), ("tba_ms", ctypes.c_double),
                 ("tba_flops", ctypes.c_double), ("oz_pair_flops", ctypes.c_double),
                 ("spmm_launches", ctypes.c_longlong), ("spmm_ms", ctypes.c_double), ("spmm_flops", ctypes.c_double),
-                ("spmm_bytes", ctypes.c_double)]
+                ("spmm_bytes", ctypes.c_double), ("host_setup_ms", ctypes.c_double),
+                ("graph_build_ms", ctypes.c_double), ("host_cycles_ms", ctypes.c_double)]
 
 
 class TstarError(RuntimeError):

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <mutex>
+#include <unordered_map>
 #include "internal.cuh"
 #include "apply.cuh"
 #include "tc.cuh"
@@ -54,15 +55,26 @@ namespace {
 struct OpPool {
   cudaMemPool_t pool = nullptr;
   cudaStream_t stream = nullptr;
+  // Released buffers wait here until kOpFreeDeferBytes have gathered (or an allocation fails, or a
+  // context is destroyed): then one device synchronisation covers them all, instead of one per
+  // buffer.  Until then they stay reserved, so nothing can reuse memory a kernel may still read.
+  std::unordered_map<void*, size_t> sizes;
+  std::vector<void*> pending;
+  size_t pending_bytes = 0;
 };
+constexpr size_t kOpFreeDeferBytes = 2ull << 30;
 std::mutex g_op_pool_mu;
 OpPool g_op_pool[64];
 
-OpPool& op_pool() {
+int current_device_checked() {
   int dev = 0;
   TS_CUDA(cudaGetDevice(&dev));
   TS_REQUIRE(dev >= 0 && dev < 64, "op_malloc: device index out of range");
-  std::lock_guard<std::mutex> lock(g_op_pool_mu);
+  return dev;
+}
+
+// the pool of device `dev`; the caller holds g_op_pool_mu
+OpPool& op_pool_locked(int dev) {
   OpPool& q = g_op_pool[dev];
   if (!q.pool) {
     cudaMemPoolProps props = {};
@@ -77,34 +89,66 @@ OpPool& op_pool() {
   }
   return q;
 }
-}  // namespace
 
-void* op_malloc(size_t bytes) {
-  OpPool& q = op_pool();
+// Free every pending buffer of the pool after one device synchronisation (caller holds the lock).
+void flush_pending_locked(OpPool& q) {
+  if (q.pending.empty()) return;
+  cudaDeviceSynchronize();
+  for (void* p : q.pending) {
+    cudaFreeAsync(p, q.stream);
+    q.sizes.erase(p);
+  }
+  q.pending.clear();
+  q.pending_bytes = 0;
+}
+
+// Allocate from the pool on `st` (or on the pool's own stream, synchronised, when st_given is false);
+// on failure, free what is pending and try once more.
+void* op_alloc_bytes(size_t bytes, bool st_given, cudaStream_t st) {
+  const int dev = current_device_checked();
+  std::lock_guard<std::mutex> lock(g_op_pool_mu);
+  OpPool& q = op_pool_locked(dev);
+  if (!bytes) bytes = 16;
   void* p = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, q.pool, q.stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(q.stream);
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, q.pool, st_given ? st : q.stream);
+  if (e != cudaSuccess && !q.pending.empty()) {
+    (void)cudaGetLastError();
+    flush_pending_locked(q);
+    e = cudaMallocFromPoolAsync(&p, bytes, q.pool, st_given ? st : q.stream);
+  }
+  if (e == cudaSuccess && !st_given) e = cudaStreamSynchronize(q.stream);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     throw Error{TS_ERR_NOMEM, "operator buffer of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e)};
   }
+  q.sizes[p] = bytes;
   return p;
 }
+}  // namespace
 
-thread_local int t_free_batch = 0;
+void* op_malloc(size_t bytes) { return op_alloc_bytes(bytes, false, nullptr); }
 
-OpFreeBatch::OpFreeBatch() {
-  cudaDeviceSynchronize();
-  ++t_free_batch;
-}
-OpFreeBatch::~OpFreeBatch() { --t_free_batch; }
+void* op_malloc_on(size_t bytes, cudaStream_t st) { return op_alloc_bytes(bytes, true, st); }
 
 void op_free(void* p) {
   if (!p) return;
   try {   // called from destructors and ts_op_destroy: never throws
-    OpPool& q = op_pool();
-    if (t_free_batch == 0) cudaDeviceSynchronize();
-    cudaFreeAsync(p, q.stream);
+    const int dev = current_device_checked();
+    std::lock_guard<std::mutex> lock(g_op_pool_mu);
+    OpPool& q = op_pool_locked(dev);
+    auto it = q.sizes.find(p);
+    q.pending.push_back(p);
+    q.pending_bytes += it != q.sizes.end() ? it->second : 0;
+    if (q.pending_bytes >= kOpFreeDeferBytes) flush_pending_locked(q);
+  } catch (const Error&) {
+  }
+}
+
+void op_free_flush() {
+  try {
+    const int dev = current_device_checked();
+    std::lock_guard<std::mutex> lock(g_op_pool_mu);
+    if (g_op_pool[dev].pool) flush_pending_locked(g_op_pool[dev]);
   } catch (const Error&) {
   }
 }
@@ -173,6 +217,7 @@ void KernelTimer::reset() {
   gemm_launches = fft_launches = lowp_launches = oz_launches = tba_launches = spmm_launches = 0;
   gemm_ms = gemm_flops = fft_ms = fft_bytes = lowp_ms = lowp_flops = oz_ms = oz_flops = tba_ms = tba_flops = 0;
   spmm_ms = spmm_flops = spmm_bytes = 0;
+  host_setup_ms = graph_build_ms = host_cycles_ms = 0;
   oz_pair_flops = 0;
 }
 
@@ -256,13 +301,14 @@ void StagedOut::finish() {
 // Forward DFT of the operator tensors once (§8 setup: A_k, B_k for k <= p/2).
 static void op_prepare(ts_op* op, const double* A, const double* B, cudaStream_t st) {
   const int n = op->n, s = op->s, p = op->p, K = op->K;
-  op_alloc(op->Ah, sizeof(double2) * (size_t)K * n * n);
-  op_alloc(op->Bh, sizeof(double2) * (size_t)K * s * s);
+  op_alloc_on(op->Ah, sizeof(double2) * (size_t)K * n * n, st);
+  op_alloc_on(op->Bh, sizeof(double2) * (size_t)K * s * s, st);
   StagedIn a(op->ctx, "stage_A", A, (size_t)n * n * p, st);
   StagedIn b(op->ctx, "stage_B", B, (size_t)s * s * p, st);
   rfft_tube<double, double2>(a.dev, op->Ah, (long long)n * n, p, st);
   rfft_tube<double, double2>(b.dev, op->Bh, (long long)s * s, p, st);
-  TS_CUDA(cudaStreamSynchronize(st));  // the staging buffers may be reused right after
+  // host inputs went through the context's staging buffers, which the next call may reuse
+  if (a.staged || b.staged) TS_CUDA(cudaStreamSynchronize(st));
 }
 
 void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
@@ -352,7 +398,7 @@ ts_status ts_create(ts_ctx** out, int device) {
     ctx->device = device;
     TS_CUDA(cudaSetDevice(device));
     TS_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
-    TS_CUDA(cudaMallocHost(&ctx->host_scalars, 256 * sizeof(double)));
+    TS_CUDA(cudaMallocHost(&ctx->host_scalars, 1024 * sizeof(double)));
     TS_CUDA(cudaEventCreate(&ctx->ev0));
     TS_CUDA(cudaEventCreate(&ctx->ev1));
     *out = ctx;
@@ -372,6 +418,7 @@ ts_status ts_create(ts_ctx** out, int device) {
 void ts_destroy(ts_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  op_free_flush();   // operator buffers released meanwhile go back to the pool
   ctx->ws.release_all();
   ctx->timer.destroy();
   if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
@@ -450,7 +497,6 @@ ts_status ts_op_create_dense(ts_ctx* ctx, const double* A, int n, const double* 
 void ts_op_destroy(ts_op* op) {
   if (!op) return;
   if (op->ctx) cudaSetDevice(op->ctx->device);
-  OpFreeBatch batch;   // one device synchronisation for all of the operator's buffers
   op_free(op->Ah);
   op_free(op->Bh);
   op_free(op->Ah32);
@@ -677,6 +723,9 @@ ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out) {
   out->spmm_ms = t.spmm_ms;
   out->spmm_flops = t.spmm_flops;
   out->spmm_bytes = t.spmm_bytes;
+  out->host_setup_ms = t.host_setup_ms;
+  out->graph_build_ms = t.graph_build_ms;
+  out->host_cycles_ms = t.host_cycles_ms;
   return TS_OK;
   TS_API_END(ctx)
 }

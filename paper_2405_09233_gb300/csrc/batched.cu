@@ -15,9 +15,11 @@
 // captured once as a CUDA graph and replayed; the host only reads the per-instance residuals at
 // the end of each cycle.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <numeric>
 #include <vector>
+#include <type_traits>
 #include <string>
 #include "internal.cuh"
 #include "oz.cuh"
@@ -28,6 +30,7 @@
 #include "pack.cuh"
 #include "fft_reg.cuh"
 #include "gemm_tile.cuh"
+#include "cycle_graph.cuh"
 
 namespace ts {
 
@@ -474,6 +477,14 @@ __global__ void k_b_solve_y(BDev d) {
   }
 }
 
+// Ends a nested cycle graph after the current step when no instance is still iterating.
+__global__ void k_b_any_active(BDev d, cudaGraphConditionalHandle next) {
+  int any = 0;
+  for (int i = threadIdx.x; i < d.count; i += blockDim.x) any |= d.act[i];
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0 && !any) cudaGraphSetConditional(next, 0);
+}
+
 // --- host orchestration -----------------------------------------------------------------------------
 // Kernels are loaded lazily on first launch, and loading is not allowed while a stream is being
 // captured; every kernel of the captured cycle is therefore loaded (cudaFuncGetAttributes) first.
@@ -485,7 +496,7 @@ void preload_cycle_kernels() {
       (const void*)k_b_gemm<T, 0>, (const void*)k_b_irfft<T, Real2, 0>, (const void*)k_b_dot<T>,
       (const void*)k_b_mgs<T>, (const void*)k_b_givens, (const void*)k_b_scale_W<T>, (const void*)k_b_solve_y,
       (const void*)k_b_axpy<T>, (const void*)k_b_rfft<double, double2, 1, 1>, (const void*)k_b_gemm<double, 1>,
-      (const void*)k_b_irfft<double, double2, 1>, (const void*)k_b_finalize_norm};
+      (const void*)k_b_irfft<double, double2, 1>, (const void*)k_b_finalize_norm, (const void*)k_b_any_active};
   for (const void* f : fns) TS_CUDA(cudaFuncGetAttributes(&fa, f));
 }
 
@@ -497,25 +508,44 @@ struct BatchPlan {
   long long totN = 0, totS = 0;
 };
 
-// Records one restart cycle on `st`; returns the number of kernels it launched.
-// `residual_products(st)` issues the FP64 slice products of the true residual (Xh64 -> Yh64) and
-// returns how many kernels it launched.
-// `inner_products(st)` issues the inner operator's slice products (Xh -> Yh) likewise.
-// ev (may be null): 2m + 2 events recorded as graph nodes around the inner products of step j
-// (ev[2j], ev[2j+1]) and around the residual products (ev[2m], ev[2m+1]), for the statistics.
+// The pieces of one restart cycle, each recorded on `st` and returning the kernels it launched:
+// the prologue (Givens state reset, V_1 = R / ||R||), inner step j (DFT, inner slice products,
+// inverse DFT, MGS sweep, Givens update, V_{j+1}; with a conditional handle of step j + 1 it also ends
+// a nested cycle graph once no instance is iterating), and the epilogue (y, X += V y, the FP64 true
+// residual).  `residual_products(st)` issues the FP64 slice products of the residual (Xh64 -> Yh64)
+// and `inner_products(st)` the inner operator's (Xh -> Yh); both return their kernel counts.
+// ev (may be null; flat graphs only): 2m + 2 events recorded as graph nodes around the inner products
+// of step j (ev[2j], ev[2j+1]) and around the residual products (ev[2m], ev[2m+1]), for the statistics.
 template <typename T, typename Real2, typename InnerProducts, typename ResidualProducts>
-int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Real2* Yh, double* R, double2* Xh64,
-                 double2* Yh64, double* P0, double* P1, double* Pt, const InnerProducts& inner_products,
-                 const ResidualProducts& residual_products, const cudaEvent_t* ev, cudaStream_t st) {
-  using Real = T;
-  const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size();
-  const int count = d.count, m = d.m;
-  double* Pp[2] = {P0, P1};
-  int kernels = 0;
-  k_b_ks_init<<<count, 256, 0, st>>>(d);
-  k_b_scale_R<T><<<nbs, 256, 0, st>>>(d, R, basis(V, d.totN, 0));
-  kernels += 2;
-  for (int j = 0; j < m; ++j) {
+struct CycleRecorder {
+  const BDev& d;
+  const BatchPlan& plan;
+  T* V;
+  T* W;
+  Real2* Xh;
+  Real2* Yh;
+  double* R;
+  double2* Xh64;
+  double2* Yh64;
+  double* P0;
+  double* P1;
+  double* Pt;
+  const InnerProducts& inner_products;
+  const ResidualProducts& residual_products;
+  const cudaEvent_t* ev;
+
+  int prologue(cudaStream_t st) const {
+    const int nbs = (int)plan.nb_inst.size();
+    k_b_ks_init<<<d.count, 256, 0, st>>>(d);
+    k_b_scale_R<T><<<nbs, 256, 0, st>>>(d, R, basis(V, d.totN, 0));
+    TS_CUDA(cudaGetLastError());
+    return 2;
+  }
+  int step(int j, cudaGraphConditionalHandle next, cudaStream_t st) const {
+    using Real = T;
+    const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size();
+    double* Pp[2] = {P0, P1};
+    int kernels = 0;
     k_b_rfft<Real, Real2, 0, 0><<<ntb, kTubes, 0, st>>>(d, basis(V, d.totN, j), Xh);
     if (ev) TS_CUDA(cudaEventRecordWithFlags(ev[2 * j], st, cudaEventRecordExternal));
     kernels += inner_products(st);
@@ -525,29 +555,44 @@ int record_cycle(const BDev& d, const BatchPlan& plan, T* V, T* W, Real2* Xh, Re
     for (int i = 0; i <= j; ++i)
       k_b_mgs<T><<<nbs, 256, 0, st>>>(d, W, basis(V, d.totN, i), i < j ? basis(V, d.totN, i + 1) : nullptr,
                                       Pp[i & 1], Pp[(i + 1) & 1], i, j);
-    k_b_givens<<<count, 256, 0, st>>>(d, Pp[(j + 1) & 1], j);
+    k_b_givens<<<d.count, 256, 0, st>>>(d, Pp[(j + 1) & 1], j);
     k_b_scale_W<T><<<nbs, 256, 0, st>>>(d, W, basis(V, d.totN, j + 1));
     kernels += 5 + j + 1;
+    if (next) {
+      k_b_any_active<<<1, 256, 0, st>>>(d, next);
+      ++kernels;
+    }
+    TS_CUDA(cudaGetLastError());
+    return kernels;
   }
-  k_b_solve_y<<<count, 32, 0, st>>>(d);
-  k_b_axpy<T><<<nbs, 256, 0, st>>>(d, V);
-  // true residual R = C - M(X) in FP64
-  k_b_rfft<double, double2, 1, 1><<<ntb, kTubes, 0, st>>>(d, nullptr, Xh64);
-  if (ev) TS_CUDA(cudaEventRecordWithFlags(ev[2 * m], st, cudaEventRecordExternal));
-  kernels += residual_products(st);
-  if (ev) TS_CUDA(cudaEventRecordWithFlags(ev[2 * m + 1], st, cudaEventRecordExternal));
-  k_b_irfft<double, double2, 1><<<ntb, kTubes, 0, st>>>(d, Yh64, R, Pt);
-  k_b_finalize_norm<<<count, 256, 0, st>>>(d, Pt, 1);
-  kernels += 5;
-  TS_CUDA(cudaGetLastError());
-  return kernels;
-}
+  int epilogue(cudaStream_t st) const {
+    const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size();
+    const int m = d.m;
+    int kernels = 0;
+    k_b_solve_y<<<d.count, 32, 0, st>>>(d);
+    k_b_axpy<T><<<nbs, 256, 0, st>>>(d, V);
+    // true residual R = C - M(X) in FP64
+    k_b_rfft<double, double2, 1, 1><<<ntb, kTubes, 0, st>>>(d, nullptr, Xh64);
+    if (ev) TS_CUDA(cudaEventRecordWithFlags(ev[2 * m], st, cudaEventRecordExternal));
+    kernels += residual_products(st);
+    if (ev) TS_CUDA(cudaEventRecordWithFlags(ev[2 * m + 1], st, cudaEventRecordExternal));
+    k_b_irfft<double, double2, 1><<<ntb, kTubes, 0, st>>>(d, Yh64, R, Pt);
+    k_b_finalize_norm<<<d.count, 256, 0, st>>>(d, Pt, 1);
+    kernels += 5;
+    TS_CUDA(cudaGetLastError());
+    return kernels;
+  }
+};
 
 }  // namespace
 
 ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const ts_solve_opts* opts,
                         ts_solve_info* infos, int* statuses, ts_stream stream) {
   TS_REQUIRE(count >= 1 && insts && opts, "ts_batched_solve: bad arguments");
+  const auto host_t0 = std::chrono::steady_clock::now();
+  auto host_ms_since = [](std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+  };
   const ts_solve_opts& o = *opts;
   TS_REQUIRE(o.restart >= 1 && o.restart <= 128, "ts_batched_solve: restart must be in 1..128");
   TS_REQUIRE(o.tol > 0.0, "ts_batched_solve: tol must be positive");
@@ -816,21 +861,32 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       return t;
     };
     tc_batch_preload(o.precision);   // shared-memory limits of the product kernels, before any launch
+    // Pick the column tile by timing one product pass of the whole batch with every instance
+    // active (the activity flags are all set above); the choice is cached per batch shape, and once
+    // it exists only its tables are built.
+    std::string key = "btc:" + std::to_string(o.precision) + ":" + std::to_string(count);
+    for (int i = 0; i < count; ++i)
+      key += ":" + std::to_string(plan.inst[i].n) + "x" + std::to_string(plan.inst[i].s) + "x" +
+             std::to_string(plan.inst[i].K);
+    if (!ctx->tune_loaded) tune_load(ctx);
+    const auto tuned = ctx->tune.find(key);
     std::vector<TcTables> cand_tables;
     std::vector<int> cands;
     int smax = 0;
     for (int i = 0; i < count; ++i) smax = std::max(smax, plan.inst[i].s);
     for (int bn : kBatchTcBNs)
-      if (bn == kBatchTcBNs[0] || bn / 2 < smax) {
+      if ((bn == kBatchTcBNs[0] || bn / 2 < smax) && (tuned == ctx->tune.end() || tuned->second == bn)) {
         cands.push_back(bn);
         cand_tables.push_back(build_tables(bn));
       }
-    // Pick the column tile by timing one product pass of the whole batch with every instance
-    // active (the activity flags are all set above); the choice is cached per batch shape.
-    std::string key = "btc:" + std::to_string(o.precision) + ":" + std::to_string(count);
-    for (int i = 0; i < count; ++i)
-      key += ":" + std::to_string(plan.inst[i].n) + "x" + std::to_string(plan.inst[i].s) + "x" +
-             std::to_string(plan.inst[i].K);
+    if (cands.empty()) {   // a cached choice this batch cannot use: tune again
+      ctx->tune.erase(key);
+      for (int bn : kBatchTcBNs)
+        if (bn == kBatchTcBNs[0] || bn / 2 < smax) {
+          cands.push_back(bn);
+          cand_tables.push_back(build_tables(bn));
+        }
+    }
     TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
     tc_bn = tune_pick(
         ctx, key, cands,
@@ -884,6 +940,8 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
     }
     return oz_all(s2, Xh64, Yh64, d.cyc);
   };
+  ctx->timer.host_setup_ms += host_ms_since(host_t0);
+  const auto cycles_t0 = std::chrono::steady_clock::now();
   k_b_normC<<<nbs, 256, 0, st>>>(d, P0);
   k_b_finalize_norm<<<count, 256, 0, st>>>(d, P0, 0);
   k_b_rfft<double, double2, 1, 1><<<ntb, kTubes, 0, st>>>(d, nullptr, Xh64);
@@ -896,7 +954,9 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   std::vector<double> hsc(16 * count);
   std::vector<int> done(count, 0), cycles(count, 0);
   cudaGraphExec_t exec = nullptr;
-  int graph_kernels = 0;
+  long long cycle_fixed_kernels = 0;          // prologue and epilogue of a cycle graph
+  std::vector<long long> cycle_step_kernels;  // kernels of each inner step
+  bool nested_graph = false;
   int max_cycles = mixed ? (o.max_outer > 0 ? o.max_outer : 50) : o.max_restarts;
   int launched = 0;
   ts_status overall = TS_OK;
@@ -973,6 +1033,18 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
     for (int cycle = 0; cycle <= max_cycles; ++cycle) {
       TS_CUDA(cudaMemcpyAsync(hsc.data(), sc, sizeof(double) * 16 * count, cudaMemcpyDeviceToHost, st));
       TS_CUDA(cudaStreamSynchronize(st));
+      if (cycle > 0) {
+        // kernels of the replay just done: a nested graph ran as many steps as its busiest instance
+        int steps_run = m;
+        if (nested_graph) {
+          steps_run = 0;
+          for (int i = 0; i < count; ++i)
+            if (in_cycle[i]) steps_run = std::max(steps_run, (int)hsc[16 * i + SC_K]);
+        }
+        long long ran = cycle_fixed_kernels;
+        for (int j = 0; j < steps_run && j < (int)cycle_step_kernels.size(); ++j) ran += cycle_step_kernels[j];
+        count_launch(ran);
+      }
       if (cycle == 0)
         for (int i = 0; i < count; ++i) iters_prev[i] = hsc[16 * i + SC_ITERS];
       else if (!tev.empty())
@@ -992,25 +1064,53 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       TS_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice, st));
       TS_CUDA(cudaStreamSynchronize(st));
       if (!exec) {
+        const auto build_t0 = std::chrono::steady_clock::now();
         if (mixed) preload_cycle_kernels<float, float2>();
         else preload_cycle_kernels<double, double2>();
-        cudaGraph_t graph;
         CountSuppress no_count;   // the replays below count the recorded kernels
-        TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        if (mixed)
-          graph_kernels = record_cycle<float, float2>(d, plan, (float*)V, (float*)W, (float2*)Xh, (float2*)Yh, R, Xh64,
-                                                      Yh64, P0, P1, Pt, inner_products, residual_products,
-                                                      tev.empty() ? nullptr : tev.data(), st);
-        else
-          graph_kernels = record_cycle<double, double2>(d, plan, (double*)V, (double*)W, (double2*)Xh, (double2*)Yh, R,
-                                                        Xh64, Yh64, P0, P1, Pt, inner_products, residual_products,
-                                                        tev.empty() ? nullptr : tev.data(), st);
-        TS_CUDA(cudaStreamEndCapture(st, &graph));
-        TS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-        TS_CUDA(cudaGraphDestroy(graph));
+        auto build = [&](auto* Vt, auto* Xht) -> cudaGraph_t {
+          using TT = std::remove_pointer_t<decltype(Vt)>;
+          using R2 = std::remove_pointer_t<decltype(Xht)>;
+          const CycleRecorder<TT, R2, decltype(inner_products), decltype(residual_products)> rec{
+              d, plan, Vt, (TT*)W, Xht, (R2*)Yh, R, Xh64, Yh64, P0, P1, Pt, inner_products, residual_products,
+              tev.empty() ? nullptr : tev.data()};
+          if (tev.empty()) {
+            // statistics off: nested conditional steps, so a cycle stops once no instance iterates
+            NestedCycleCounts cnt;
+            cudaGraph_t g = build_nested_cycle(
+                m, st, [&](cudaStream_t q) { return rec.prologue(q); },
+                [&](int j, cudaGraphConditionalHandle next, cudaStream_t q) { return rec.step(j, next, q); },
+                [&](cudaStream_t q) { return rec.epilogue(q); }, cnt);
+            cycle_fixed_kernels = cnt.prologue + cnt.epilogue;
+            cycle_step_kernels = cnt.steps;
+            return g;
+          }
+          // statistics on: one flat graph (event records are not allowed inside conditional bodies)
+          cudaGraph_t g;
+          TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+          try {
+            long long k = rec.prologue(st);
+            cycle_step_kernels.clear();
+            for (int j = 0; j < m; ++j) cycle_step_kernels.push_back(rec.step(j, 0, st));
+            k += rec.epilogue(st);
+            cycle_fixed_kernels = k;
+          } catch (...) {
+            cudaGraph_t dropped = nullptr;
+            cudaStreamEndCapture(st, &dropped);
+            if (dropped) cudaGraphDestroy(dropped);
+            throw;
+          }
+          TS_CUDA(cudaStreamEndCapture(st, &g));
+          return g;
+        };
+        cudaGraph_t graph = mixed ? build((float*)V, (float2*)Xh) : build((double*)V, (double2*)Xh);
+        nested_graph = tev.empty();
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        TS_CUDA(ie);
+        ctx->timer.graph_build_ms += host_ms_since(build_t0);
       }
       TS_CUDA(cudaGraphLaunch(exec, st));
-      count_launch(graph_kernels);
       ++launched;
     }
   } catch (...) {
@@ -1021,6 +1121,7 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   }
   TS_CUDA(cudaEventRecord(t1, st));
   TS_CUDA(cudaEventSynchronize(t1));
+  ctx->timer.host_cycles_ms += host_ms_since(cycles_t0);
   float ms = 0.f;
   TS_CUDA(cudaEventElapsedTime(&ms, t0, t1));
   if (exec) TS_CUDA(cudaGraphExecDestroy(exec));

@@ -16,31 +16,41 @@
 namespace ts {
 namespace {
 
-constexpr int BM = kGemmBM, BN = kGemmBN, NT = kGemmNT;
+template <typename Real, int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__(kGemmNT, 1) k_gemm_slices(GemmArgs<typename CplxOf<Real>::T> a) {
+  gemm_tile<Real, BM, BN, TM, TN>(a, blockIdx.z, blockIdx.x * BM, blockIdx.y * BN);
+}
 
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  TS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return 152;
+  if (!cached[dev]) TS_CUDA(cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev));
+  return cached[dev];
+}
+
+// Output tile: the largest of 64, 32, 16 whose grid still covers every SM (a product of a few large
+// tiles would leave most of the FP64 pipes idle); 16 when even that does not.
 template <typename Real>
-__global__ void __launch_bounds__(NT, 1) k_gemm_slices(GemmArgs<typename CplxOf<Real>::T> a) {
-  gemm_tile<Real>(a, blockIdx.z, blockIdx.x * BM, blockIdx.y * BN);
+void launch_slices(const GemmArgs<typename CplxOf<Real>::T>& a, cudaStream_t st) {
+  if (a.M <= 0 || a.N <= 0 || a.K <= 0) return;
+  const long long sms = sm_count();
+  auto ctas = [&](int t) { return (long long)a.K * ((a.M + t - 1) / t) * ((a.N + t - 1) / t); };
+  const int tile = ctas(64) >= sms ? 64 : (ctas(32) >= sms ? 32 : 16);
+  dim3 grid((a.M + tile - 1) / tile, (a.N + tile - 1) / tile, a.K);
+  TS_REQUIRE(grid.y <= 65535 && grid.z <= 65535, "slice GEMM grid too large");
+  if (tile == 64) k_gemm_slices<Real, 64, 64, 4, 4><<<grid, kGemmNT, 0, st>>>(a);
+  else if (tile == 32) k_gemm_slices<Real, 32, 32, 2, 2><<<grid, kGemmNT, 0, st>>>(a);
+  else k_gemm_slices<Real, 16, 16, 1, 1><<<grid, kGemmNT, 0, st>>>(a);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
 }
 
 }  // namespace
 
-void zgemm_slices_f64(const ZGemmArgs& a, cudaStream_t st) {
-  if (a.M <= 0 || a.N <= 0 || a.K <= 0) return;
-  dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN, a.K);
-  TS_REQUIRE(grid.y <= 65535 && grid.z <= 65535, "slice GEMM grid too large");
-  k_gemm_slices<double><<<grid, NT, 0, st>>>(a);
-  count_launch();
-  TS_CUDA(cudaGetLastError());
-}
+void zgemm_slices_f64(const ZGemmArgs& a, cudaStream_t st) { launch_slices<double>(a, st); }
 
-void cgemm_slices_f32(const CGemmArgs& a, cudaStream_t st) {
-  if (a.M <= 0 || a.N <= 0 || a.K <= 0) return;
-  dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN, a.K);
-  TS_REQUIRE(grid.y <= 65535 && grid.z <= 65535, "slice GEMM grid too large");
-  k_gemm_slices<float><<<grid, NT, 0, st>>>(a);
-  count_launch();
-  TS_CUDA(cudaGetLastError());
-}
+void cgemm_slices_f32(const CGemmArgs& a, cudaStream_t st) { launch_slices<float>(a, st); }
 
 }  // namespace ts

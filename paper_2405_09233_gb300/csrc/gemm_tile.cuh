@@ -1,5 +1,9 @@
-// One 64 x 64 output tile of the fused per-slice complex product (see gemm_simt.cu), shared by
-// the grid-mapped kernel and the work-list kernel of the batched solver.
+// One BM x BN output tile of the fused per-slice complex product (see gemm_simt.cu), shared by
+// the grid-mapped kernel and the work-list kernel of the batched solver.  NT = (BM/TM)(BN/TN)
+// threads, each owning TM x TN outputs.  64 x 64 tiles (4 x 4 per thread) reuse every shared
+// operand four times; 32 x 32 and 16 x 16 tiles spread a small product over more SMs, which is what
+// counts on GB300, whose FP64 pipe issues 2 DFMA per clock per SM: a lone 64 x 64 tile needs ~47 us
+// per 16-deep reduction step however small the problem.
 #pragma once
 #include "internal.cuh"
 
@@ -12,23 +16,24 @@ template <> struct CplxOf<double> { using T = double2; };
 template <> struct CplxOf<float> { using T = float2; };
 
 // Y_k(i0.., j0..) = A1_k B1_k + sgn2 A2_k B2_k for one tile; slices k == 0 and k == nyq are real.
-template <typename Real>
+template <typename Real, int BM = kGemmBM, int BN = kGemmBN, int TM = 4, int TN = 4>
 __device__ __forceinline__ void gemm_tile(const GemmArgs<typename CplxOf<Real>::T>& a, int k, int i0, int j0) {
-  constexpr int BM = kGemmBM, BN = kGemmBN, BK = kGemmBK, NT = kGemmNT;
+  constexpr int BK = kGemmBK, TX = BN / TN, NT = (BM / TM) * TX;
+  static_assert(NT == kGemmNT && (BM * BK) % NT == 0 && (BN * BK) % NT == 0, "tile shape");
   using Cplx = typename CplxOf<Real>::T;
   const bool real = (k == 0) || (k == a.nyq);
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
 
   __shared__ Real sA[3][BK][BM];
   __shared__ Real sB[3][BK][BN];
 
-  Real acc[3][4][4];
+  Real acc[3][TM][TN];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < TM; ++q)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[c][q][r] = Real(0);
+      for (int r = 0; r < TN; ++r) acc[c][q][r] = Real(0);
 
   for (int phase = 0; phase < 2; ++phase) {
     const int L = phase == 0 ? a.L1 : a.L2;
@@ -73,33 +78,33 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs<typename CplxOf<Real>::
       if (real) {
 #pragma unroll 4
         for (int c = 0; c < BK; ++c) {
-          Real ar[4], br[4];
+          Real ar[TM], br[TN];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) ar[q] = sA[0][c][ty * 4 + q];
+          for (int q = 0; q < TM; ++q) ar[q] = sA[0][c][ty * TM + q];
 #pragma unroll
-          for (int r = 0; r < 4; ++r) br[r] = sB[0][c][tx * 4 + r];
+          for (int r = 0; r < TN; ++r) br[r] = sB[0][c][tx * TN + r];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < TM; ++q)
 #pragma unroll
-            for (int r = 0; r < 4; ++r) acc[0][q][r] = fma(ar[q], br[r], acc[0][q][r]);
+            for (int r = 0; r < TN; ++r) acc[0][q][r] = fma(ar[q], br[r], acc[0][q][r]);
         }
       } else {
 #pragma unroll 2
         for (int c = 0; c < BK; ++c) {
-          Real av[3][4], bv[3][4];
+          Real av[3][TM], bv[3][TN];
 #pragma unroll
           for (int z = 0; z < 3; ++z) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) av[z][q] = sA[z][c][ty * 4 + q];
+            for (int q = 0; q < TM; ++q) av[z][q] = sA[z][c][ty * TM + q];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) bv[z][r] = sB[z][c][tx * 4 + r];
+            for (int r = 0; r < TN; ++r) bv[z][r] = sB[z][c][tx * TN + r];
           }
 #pragma unroll
           for (int z = 0; z < 3; ++z)
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < TM; ++q)
 #pragma unroll
-              for (int r = 0; r < 4; ++r) acc[z][q][r] = fma(av[z][q], bv[z][r], acc[z][q][r]);
+              for (int r = 0; r < TN; ++r) acc[z][q][r] = fma(av[z][q], bv[z][r], acc[z][q][r]);
         }
       }
       __syncthreads();
@@ -108,12 +113,12 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs<typename CplxOf<Real>::
 
   Cplx* Y = a.Y + a.sY * k;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int j = j0 + tx * 4 + r;
+  for (int r = 0; r < TN; ++r) {
+    const int j = j0 + tx * TN + r;
     if (j >= a.N) continue;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = i0 + ty * 4 + q;
+    for (int q = 0; q < TM; ++q) {
+      const int i = i0 + ty * TM + q;
       if (i >= a.M) continue;
       Cplx v;
       if (real) {

@@ -51,21 +51,25 @@ struct Workspace {
 // taken from a process-wide stream-ordered memory pool of the current device that keeps up to
 // kOpPoolKeepBytes of freed memory reserved, so creating and destroying operators of recurring
 // shapes does not map and unmap device memory every time.  op_malloc returns memory usable on
-// every stream (like cudaMalloc) and throws TS_ERR_NOMEM on failure; op_free synchronises the
-// device first (like cudaFree), so no pending kernel still reads the buffer; nullptr is ignored.
+// every stream (like cudaMalloc) and throws TS_ERR_NOMEM on failure.  op_free defers the release:
+// buffers are kept (unusable by anyone) until 2 GiB of them have gathered, an allocation fails or
+// a context is destroyed, and are then returned together after one device synchronisation, so that
+// no pending kernel can still read them; nullptr is ignored.
 // ----------------------------------------------------------------------------------------------
 constexpr unsigned long long kOpPoolKeepBytes = 16ull << 30;
 void* op_malloc(size_t bytes);
 void op_free(void* p);
-// While one of these lives on the calling thread, op_free skips its own device synchronisation:
-// the constructor synchronises the device once for a whole operator's buffers.
-struct OpFreeBatch {
-  OpFreeBatch();
-  ~OpFreeBatch();
-};
+void op_free_flush();   // return every deferred buffer of the current device's pool now
 template <typename T>
 inline void op_alloc(T*& p, size_t bytes) {
   p = static_cast<T*>(op_malloc(bytes));
+}
+// Stream-ordered form: the buffer is usable on `st` (and on work ordered after it) without any host
+// synchronisation; for buffers that a call prepares on `st` and that are only used after it.
+void* op_malloc_on(size_t bytes, cudaStream_t st);
+template <typename T>
+inline void op_alloc_on(T*& p, size_t bytes, cudaStream_t st) {
+  p = static_cast<T*>(op_malloc_on(bytes, st));
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -106,6 +110,7 @@ struct KernelTimer {
   double tba_ms = 0, tba_flops = 0;
   long long spmm_launches = 0;
   double spmm_ms = 0, spmm_flops = 0, spmm_bytes = 0;
+  double host_setup_ms = 0, graph_build_ms = 0, host_cycles_ms = 0;   // host clock, always collected
   void begin(cudaStream_t st, int kind, double work, double work2 = 0.0);
   void end(cudaStream_t st);
   void collect();  // synchronise the recorded events and accumulate
@@ -122,7 +127,7 @@ struct ts_ctx {
   int num_sms = 0;
   std::string err;
   ts::Workspace ws;
-  double* host_scalars = nullptr;  // pinned, 256 doubles, for small device->host reads
+  double* host_scalars = nullptr;  // pinned, 1024 doubles, for small host<->device transfers
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t bstream = nullptr;  // private stream of the batched solver (graph capture)
   std::vector<cudaStream_t> side;  // side streams of the batched solver's parallel branches
@@ -216,14 +221,19 @@ struct KrylovState;  // device-resident, see small.cu
 size_t krylov_state_bytes(int m);
 void ks_init(void* state, int m, const double* beta_and_inv, cudaStream_t st);
 // GMRES (method 0) / FOM (method 1) step j: consumes column j of H (rows 0..j written by MGS) and
-// ||W|| from Pnorm partials; writes the estimate and 1/h_{j+1,j} into the state.
-void ks_step(void* state, int m, int j, int method, const double* Pnorm, cudaStream_t st);
+// ||W|| from Pnorm partials; writes the estimate and 1/h_{j+1,j} into the state.  Inside a
+// graph-captured cycle, `handle` is the conditional handle of step j + 1, which it sets to 0 when the
+// cycle stops after this step (breakdown, bad step, estimate <= stop[0] or <= stop[1]).
+void ks_step(void* state, int m, int j, int method, const double* Pnorm, cudaStream_t st,
+             cudaGraphConditionalHandle handle = 0, const double* stop = nullptr);
 // Solve for y over the first k columns; result in the state's y array.
 void ks_solve(void* state, int m, int k, int method, cudaStream_t st);
 // Device addresses inside the state block.
 double* ks_H(void* state, int m);          // column-major (m+1) x m, H[i + (m+1)*j]
 double* ks_y(void* state, int m);
-double* ks_est(void* state, int m);        // [0] = estimate, [1] = 1/h_{j+1,j}, [2] = h_{j+1,j}, [3] = flags
+double* ks_est(void* state, int m);        // [0] = estimate, [1] = 1/h_{j+1,j}, [2] = h_{j+1,j}, [3] = flags,
+                                           // [4] = steps taken in the cycle
+double* ks_hist(void* state, int m);       // the estimate of every step of the cycle (m entries)
 double* ks_beta(void* state, int m);       // [0] = beta, [1] = 1/beta
 
 }  // namespace ts

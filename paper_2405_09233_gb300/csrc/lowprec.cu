@@ -9,8 +9,8 @@ namespace ts {
 void ensure_f32_operator(ts_op* op, cudaStream_t st) {
   if (op->Ah32) return;
   const size_t na = (size_t)op->K * op->n * op->n, nb = (size_t)op->K * op->s * op->s;
-  op_alloc(op->Ah32, sizeof(float2) * na);
-  op_alloc(op->Bh32, sizeof(float2) * nb);
+  op_alloc_on(op->Ah32, sizeof(float2) * na, st);
+  op_alloc_on(op->Bh32, sizeof(float2) * nb, st);
   convert<double, float>(reinterpret_cast<const double*>(op->Ah), reinterpret_cast<float*>(op->Ah32),
                          (long long)(2 * na), st);
   convert<double, float>(reinterpret_cast<const double*>(op->Bh), reinterpret_cast<float*>(op->Bh32),

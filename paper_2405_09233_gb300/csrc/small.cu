@@ -25,7 +25,8 @@ struct Layout {
   __host__ __device__ size_t est() const { return y() + m; }
   __host__ __device__ size_t beta() const { return est() + 8; }
   __host__ __device__ size_t lu() const { return beta() + 8; }
-  __host__ __device__ size_t total() const { return lu() + (size_t)m * m + m; }
+  __host__ __device__ size_t hist() const { return lu() + (size_t)m * m + m; }
+  __host__ __device__ size_t total() const { return hist() + m; }
 };
 
 constexpr double kBreakdownRel = 1e-14;
@@ -47,8 +48,13 @@ __global__ void k_ks_init(double* st, int m, const double* beta_in) {
 }
 
 // est[0] = estimate, est[1] = 1/h_{j+1,j}, est[2] = h_{j+1,j}, est[3] = flags (1 breakdown,
-// 2 singular, 4 non-finite).
-__global__ void k_ks_step(double* st, int m, int j, int method, const double* Pnorm) {
+// 2 singular, 4 non-finite), est[4] = steps taken in this cycle (j + 1), est[8 + j] = estimate of
+// step j.  In a graph-captured cycle, `handle` is the conditional handle of step j + 1 (0 for the
+// last step) and the kernel decides whether the cycle goes on: it sets that handle to 0 on breakdown,
+// a bad step, an estimate <= stop[0] (the tolerance times ||C||) or <= stop[1] (the inner tolerance
+// of mixed precision, or -1).
+__global__ void k_ks_step(double* st, int m, int j, int method, const double* Pnorm,
+                          cudaGraphConditionalHandle handle, const double* stop) {
   Layout L{m};
   const double hn = sqrt(finalize_partials(Pnorm));
   if (threadIdx.x != 0) return;
@@ -132,6 +138,12 @@ __global__ void k_ks_step(double* st, int m, int j, int method, const double* Pn
   st[L.est() + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
   st[L.est() + 2] = hn;
   st[L.est() + 3] = flags;
+  st[L.est() + 4] = j + 1;
+  st[L.hist() + j] = est;
+  if (handle) {
+    const bool go = flags == 0.0 && !(est <= stop[0]) && !(est <= stop[1]);
+    if (!go) cudaGraphSetConditional(handle, 0);
+  }
 }
 
 // tGMRES: back substitution R_k y = g_k.  tFOM: y is already the solution of the last step.
@@ -163,8 +175,11 @@ void ks_init(void* state, int m, const double* beta_and_inv, cudaStream_t st) {
   TS_CUDA(cudaGetLastError());
 }
 
-void ks_step(void* state, int m, int j, int method, const double* Pnorm, cudaStream_t st) {
-  k_ks_step<<<1, 256, 0, st>>>(static_cast<double*>(state), m, j, method, Pnorm);
+double* ks_hist(void* s, int m) { return static_cast<double*>(s) + Layout{m}.hist(); }
+
+void ks_step(void* state, int m, int j, int method, const double* Pnorm, cudaStream_t st,
+             cudaGraphConditionalHandle handle, const double* stop) {
+  k_ks_step<<<1, 256, 0, st>>>(static_cast<double*>(state), m, j, method, Pnorm, handle, stop);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }

@@ -5,20 +5,51 @@
 //             (Algorithm 2); h_{j+1,j} = ||W||; Givens (tGMRES) or Hessenberg LU (tFOM) on the
 //             device gives the residual estimate; stop early when it reaches the tolerance;
 //             V_{j+1} = W / h_{j+1,j}.  Then y, X += V_k (*) y, and the true residual.
-// The host reads 4 doubles per inner step (estimate, 1/h, h, flags) to decide whether to stop.
+// The host reads 4 doubles per inner step (estimate, 1/h, h, flags) to decide whether to stop --
+// except for small problems, which are bound by launch latency and by that look at every step:
+// from their second cycle on, a restart cycle runs as one CUDA graph in which step j is the body of a
+// conditional (IF)
+// node (step j + 1's node nested inside it) and the step's Givens / Hessenberg kernel switches the
+// remaining steps off on the device, so the host looks once per cycle.  Both forms run the same
+// kernels in the same order, so they give identical results.
 //
 // Mixed precision: the Arnoldi cycle (basis, W, operator) runs in FP32 storage with a FP32 or
 // tensor-core operator, while R = C - M(X), the small problem, and X += ||R|| (V (*) y) stay in
 // FP64.  Every cycle is thus one step of iterative refinement with an inner tGMRES whose own
 // stopping tolerance is inner_tol relative to ||R||; only the residual needs an FP64 apply.
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <memory>
 #include <vector>
 #include "internal.cuh"
 #include "apply.cuh"
+#include "cycle_graph.cuh"
 
 namespace ts {
 
 namespace {
+
+// Problems of at most this many unknowns run their restart cycles, from the second one on, as CUDA
+// graphs (unless the environment sets TSTAR_NO_GRAPH_CYCLE=1, or statistics are being collected:
+// event timing is not allowed inside the conditional bodies).
+constexpr long long kGraphCycleMaxN = 1ll << 20;
+
+// One restart cycle (Algorithm 2 up to m steps) as an executable graph: a prologue (Givens state
+// reset, V_1 = R / ||R||), then m conditional (IF) nodes, node j holding inner step j and, nested at
+// its end, node j + 1; the kernels of each part are counted once while captured, so replays can be
+// counted as the steps they ran.
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  long long prologue_kernels = 0;
+  std::vector<long long> step_kernels;
+  ~CycleGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
 
 struct Result {
   ts_status status = TS_NOT_CONVERGED;
@@ -135,33 +166,124 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
   }
   if (res <= o.tol * normC) return finish(TS_OK);
 
+  // Inner step j of a cycle: W = M(V_j), the MGS sweep (fused with the next dot), the Givens /
+  // Hessenberg update (which, inside a graph, also decides whether the cycle goes on), and
+  // V_{j+1} = W / h_{j+1,j} when `scale_next` (the graph always forms it; unused after the last step).
+  double* stop_dev = sc + 8;   // [tol ||C||, inner threshold or -1] for the graph's stopping test
+  auto inner_step = [&](int j, cudaGraphConditionalHandle handle, bool scale_next, cudaStream_t q) {
+    apply_basis(ctx, op, prec, basis_ptr(V, N, j), W, q);         // W = M(V_j)
+    dot_partials<T>(basis_ptr(V, N, 0), W, N, Pp[0], q);
+    for (int i = 0; i <= j; ++i) {                                  // MGS sweep, fused with the next dot
+      const T* Vn = i < j ? basis_ptr(V, N, i + 1) : nullptr;
+      mgs_pass<T>(W, basis_ptr(V, N, i), Vn, N, Pp[i & 1], ks_H(state, m) + i + (size_t)(m + 1) * j,
+                  Pp[(i + 1) & 1], q);
+    }
+    ks_step(state, m, j, method, Pp[(j + 1) & 1], q, handle, stop_dev);
+    if (scale_next) scale_dev<T, T>(W, basis_ptr(V, N, j + 1), N, ks_est(state, m) + 1, q);   // V_{j+1}
+  };
+  const char* no_graph = std::getenv("TSTAR_NO_GRAPH_CYCLE");
+  const bool graph_allowed = !ctx->timer.enabled && N <= kGraphCycleMaxN && !(no_graph && no_graph[0] == '1');
+  std::unique_ptr<CycleGraph> cg;
+  // Built when a second cycle starts: a one-cycle solve would not earn the graph back, and by then every
+  // workspace buffer, operator copy and tuning choice a step needs exists (nothing may allocate or
+  // tune inside a capture).
+  auto build_cycle_graph = [&]() {
+    // captured on and replayed from the context's private stream (a capture cannot start on the
+    // legacy default stream), ordered after the caller's stream by an event
+    if (!ctx->bstream) TS_CUDA(cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking));
+    TS_CUDA(cudaStreamSynchronize(st));
+    cg.reset(new CycleGraph());
+    const cudaStream_t gst = ctx->bstream;
+    const long long launches0 = g_launches.load();
+    const auto build_t0 = std::chrono::steady_clock::now();
+    try {
+      auto counted = [&](auto&& record) {   // kernels a piece records, from the launch counter
+        const long long c0 = g_launches.load();
+        record();
+        return g_launches.load() - c0;
+      };
+      NestedCycleCounts cnt;
+      cg->graph = build_nested_cycle(
+          m, gst,
+          [&](cudaStream_t q) {
+            return counted([&] {
+              ks_init(state, m, sc + 2, q);
+              scale_dev<double, T>(R, basis_ptr(V, N, 0), N, sc + 3, q);   // V_1 = R / ||R||
+            });
+          },
+          [&](int j, cudaGraphConditionalHandle next, cudaStream_t q) {
+            return counted([&] { inner_step(j, next, j + 1 < m, q); });
+          },
+          [&](cudaStream_t) { return 0ll; }, cnt);
+      cg->prologue_kernels = cnt.prologue;
+      cg->step_kernels = cnt.steps;
+      const auto inst_t0 = std::chrono::steady_clock::now();
+      TS_CUDA(cudaGraphInstantiate(&cg->exec, cg->graph, 0));
+      const char* dbg = std::getenv("TSTAR_DEBUG_GRAPH");
+      if (dbg && dbg[0] == '1')
+        std::fprintf(stderr, "tstar: cycle graph of %d steps: capture %.3f ms, instantiate %.3f ms\n", m,
+                     std::chrono::duration<double, std::milli>(inst_t0 - build_t0).count(),
+                     std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - inst_t0).count());
+    } catch (const Error& e) {
+      // not capturable here (the apply path of this precision did something a capture forbids):
+      // keep the per-step form (TSTAR_DEBUG_GRAPH=1 reports why on stderr)
+      const char* dbg = std::getenv("TSTAR_DEBUG_GRAPH");
+      if (dbg && dbg[0] == '1') std::fprintf(stderr, "tstar: restart-cycle graph not used: %s\n", e.msg.c_str());
+      cg.reset();
+    }
+    g_launches.fetch_sub(g_launches.load() - launches0);   // captured launches did not run
+    ctx->timer.graph_build_ms +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - build_t0).count();
+  };
+
   for (int cycle = 0; cycle < max_cycles; ++cycle) {
-    ks_init(state, m, sc + 2, st);
-    scale_dev<double, T>(R, basis_ptr(V, N, 0), N, sc + 3, st);  // V_1 = R / ||R||
     int k = 0;
     double flags = 0.0;
-    for (int j = 0; j < m; ++j) {
-      apply_basis(ctx, op, prec, basis_ptr(V, N, j), W, st);        // W = M(V_j)
-      if (mixed) ++info.applies_low; else ++info.applies_fp64;
-      dot_partials<T>(basis_ptr(V, N, 0), W, N, Pp[0], st);
-      for (int i = 0; i <= j; ++i) {                                  // MGS sweep, fused with the next dot
-        const T* Vn = i < j ? basis_ptr(V, N, i + 1) : nullptr;
-        mgs_pass<T>(W, basis_ptr(V, N, i), Vn, N, Pp[i & 1], ks_H(state, m) + i + (size_t)(m + 1) * j,
-                    Pp[(i + 1) & 1], st);
+    if (cycle == 1 && graph_allowed) build_cycle_graph();
+    if (cg) {
+      double* hstop = hs + 64;
+      hstop[0] = o.tol * normC;
+      hstop[1] = mixed ? inner_tol * res : -1.0;
+      const cudaStream_t gst = ctx->bstream;
+      TS_CUDA(cudaEventRecord(ctx->ev1, st));                  // the cycle follows the caller's stream
+      TS_CUDA(cudaStreamWaitEvent(gst, ctx->ev1, 0));
+      TS_CUDA(cudaMemcpyAsync(stop_dev, hstop, 2 * sizeof(double), cudaMemcpyHostToDevice, gst));
+      TS_CUDA(cudaGraphLaunch(cg->exec, gst));
+      double* hest = hs + 96;
+      double* hhist = hs + 256;
+      TS_CUDA(cudaMemcpyAsync(hest, ks_est(state, m), 8 * sizeof(double), cudaMemcpyDeviceToHost, gst));
+      TS_CUDA(cudaMemcpyAsync(hhist, ks_hist(state, m), m * sizeof(double), cudaMemcpyDeviceToHost, gst));
+      TS_CUDA(cudaStreamSynchronize(gst));                     // later work on the caller's stream follows it
+      k = (int)hest[4];
+      flags = hest[3];
+      long long ran = cg->prologue_kernels;
+      for (int j = 0; j < k; ++j) {
+        ran += cg->step_kernels[j];
+        push_hist(hhist[j]);
       }
-      ks_step(state, m, j, method, Pp[(j + 1) & 1], st);
-      TS_CUDA(cudaMemcpyAsync(hs + 8, ks_est(state, m), 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      TS_CUDA(cudaStreamSynchronize(st));
-      const double est = hs[8];
-      flags = hs[11];
-      k = j + 1;
-      ++info.iters;
-      last_est = est;
-      push_hist(est);
-      const bool broke = ((int)flags & 1) != 0;
-      const bool bad = ((int)flags & 6) != 0;
-      if (bad || broke || est <= o.tol * normC || (mixed && est <= inner_tol * res)) break;
-      scale_dev<T, T>(W, basis_ptr(V, N, j + 1), N, ks_est(state, m) + 1, st);  // V_{j+1} = W / h
+      count_launch(ran);
+      info.iters += k;
+      if (mixed) info.applies_low += k; else info.applies_fp64 += k;
+      last_est = k > 0 ? hhist[k - 1] : last_est;
+    } else {
+      ks_init(state, m, sc + 2, st);
+      scale_dev<double, T>(R, basis_ptr(V, N, 0), N, sc + 3, st);  // V_1 = R / ||R||
+      for (int j = 0; j < m; ++j) {
+        inner_step(j, 0, false, st);
+        if (mixed) ++info.applies_low; else ++info.applies_fp64;
+        TS_CUDA(cudaMemcpyAsync(hs + 8, ks_est(state, m), 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TS_CUDA(cudaStreamSynchronize(st));
+        const double est = hs[8];
+        flags = hs[11];
+        k = j + 1;
+        ++info.iters;
+        last_est = est;
+        push_hist(est);
+        const bool broke = ((int)flags & 1) != 0;
+        const bool bad = ((int)flags & 6) != 0;
+        if (bad || broke || est <= o.tol * normC || (mixed && est <= inner_tol * res)) break;
+        scale_dev<T, T>(W, basis_ptr(V, N, j + 1), N, ks_est(state, m) + 1, st);  // V_{j+1} = W / h
+      }
     }
     ++info.cycles;
     // An expired tensor-core wait makes this cycle's products meaningless, whatever they produced:

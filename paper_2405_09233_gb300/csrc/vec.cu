@@ -8,7 +8,10 @@
 //
 // Reductions never use atomics: each block writes one partial sum, and whoever needs the total
 // (the next MGS pass, the Givens kernel) adds the kRedBlocks partials in a fixed order.  The
-// results are therefore bitwise reproducible from run to run.
+// results are therefore bitwise reproducible from run to run.  A short vector is reduced by fewer
+// blocks (red_blocks: one per 2048 elements, at most kRedBlocks), whose first block zeroes the
+// rest of the partial array, so consumers still add kRedBlocks entries: a small solve does not pay
+// for 608 mostly idle blocks in each of its dozen reductions per step.
 #include <initializer_list>
 #include <type_traits>
 #include <cstdint>
@@ -19,9 +22,16 @@
 namespace ts {
 namespace {
 
+// Block 0 zeroes the partial sums that no block of this (shortened) grid writes.
+__device__ __forceinline__ void zero_unused_partials(double* __restrict__ partials) {
+  if (blockIdx.x == 0)
+    for (int b = gridDim.x + threadIdx.x; b < kRedBlocks; b += blockDim.x) partials[b] = 0.0;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const T* __restrict__ x, const T* __restrict__ y,
                                                      long long N, double* __restrict__ partials) {
+  zero_unused_partials(partials);
   double acc = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += stride)
@@ -34,6 +44,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(const T* __restrict__ x, co
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_dot4(const T* __restrict__ x, const T* __restrict__ y,
                                                       long long N4, double* __restrict__ partials) {
+  zero_unused_partials(partials);
   double acc = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < N4; e += 2 * stride) {
@@ -68,6 +79,7 @@ __global__ void __launch_bounds__(kRedThreads) k_mgs(T* __restrict__ W, const T*
                                                      double* __restrict__ Pout) {
   const double h = finalize_partials(Pin);
   if (blockIdx.x == 0 && threadIdx.x == 0) *h_out = h;
+  zero_unused_partials(Pout);
   const T hT = (T)h;
   double acc = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -89,6 +101,7 @@ __global__ void __launch_bounds__(kRedThreads) k_mgs4(T* __restrict__ W, const T
                                                       double* __restrict__ Pout) {
   const double h = finalize_partials(Pin);
   if (blockIdx.x == 0 && threadIdx.x == 0) *h_out = h;
+  zero_unused_partials(Pout);
   const T hT = (T)h;
   double acc = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -236,6 +249,12 @@ bool packable(long long N, std::initializer_list<const void*> ptrs) {
   return true;
 }
 
+// Blocks of a reduction over N elements: one per 2048 (a thread takes two packs of 4 per pass).
+int red_blocks(long long N) {
+  const long long b = (N + 2047) / 2048;
+  return (int)(b < 1 ? 1 : (b > kRedBlocks ? kRedBlocks : b));
+}
+
 int grid_for(long long N) {
   long long b = (N + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -246,8 +265,8 @@ int grid_for(long long N) {
 
 template <typename T>
 void dot_partials(const T* x, const T* y, long long N, double* partials, cudaStream_t st) {
-  if (packable(N, {x, y})) k_dot4<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, y, N / 4, partials);
-  else k_dot<T><<<kRedBlocks, kRedThreads, 0, st>>>(x, y, N, partials);
+  if (packable(N, {x, y})) k_dot4<T><<<red_blocks(N), kRedThreads, 0, st>>>(x, y, N / 4, partials);
+  else k_dot<T><<<red_blocks(N), kRedThreads, 0, st>>>(x, y, N, partials);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -255,8 +274,10 @@ void dot_partials(const T* x, const T* y, long long N, double* partials, cudaStr
 template <typename T>
 void mgs_pass(T* W, const T* Vi, const T* Vnext, long long N, const double* Pin, double* h_out, double* Pout,
               cudaStream_t st) {
-  if (packable(N, {W, Vi, Vnext})) k_mgs4<T><<<kRedBlocks, kRedThreads, 0, st>>>(W, Vi, Vnext, N / 4, Pin, h_out, Pout);
-  else k_mgs<T><<<kRedBlocks, kRedThreads, 0, st>>>(W, Vi, Vnext, N, Pin, h_out, Pout);
+  if (packable(N, {W, Vi, Vnext}))
+    k_mgs4<T><<<red_blocks(N), kRedThreads, 0, st>>>(W, Vi, Vnext, N / 4, Pin, h_out, Pout);
+  else
+    k_mgs<T><<<red_blocks(N), kRedThreads, 0, st>>>(W, Vi, Vnext, N, Pin, h_out, Pout);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
