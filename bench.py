@@ -65,8 +65,8 @@ def args_parse(argv=None):
     return ap.parse_args(argv)
 
 
-DENSE_VARIANTS = ("tfom,mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16,fp64@ozaki,tfom@ozaki,mixed_tf32x3@ozaki,"
-                  "mixed_bf16@ozaki")
+DENSE_VARIANTS = ("tfom,fp64+spectral,mixed_fp32,mixed_tf32x3,mixed_tf32,mixed_bf16,fp64@ozaki,fp64@ozaki+spectral,"
+                  "tfom@ozaki,mixed_tf32x3@ozaki,mixed_bf16@ozaki")
 BATCHED_VARIANTS = "fp64,mixed_fp32,fp64@ozaki,mixed_fp32@ozaki,mixed_tf32x3@ozaki,mixed_bf16@ozaki"
 DENSE_WORKLOADS = ("dense_n24_s24_p4", "dense_n1024_s1024_p16", "dense_n4096_s256_p32_g0.3")
 
@@ -501,15 +501,20 @@ class DenseSetup:
         torch.cuda.synchronize()
 
     def solve(self, name):
-        """One step: operator setup + solve from X0 = 0 ("tfom" = FP64 tFOM; "prec@engine")."""
-        prec, _, eng = name.partition("@")
+        """One step: operator setup + solve from X0 = 0.  name = method-or-precision[@engine][+spectral]:
+        "tfom" = FP64 tFOM, else a tGMRES precision; "+spectral" keeps the FP64 Krylov basis in the
+        Fourier domain."""
+        base, _, flag = name.partition("+")
+        prec, _, eng = base.partition("@")
         eng = eng or "dfma"
+        spectral = flag == "spectral"
         op = self.ctx.op_create_dense(self.Ad, self.Bd)
         self.X.zero_()
         if prec == "tfom":
-            r = self.ctx.tfom_solve(op, self.Cd, self.X, restart=self.m, tol=1e-10, engine=eng)
+            r = self.ctx.tfom_solve(op, self.Cd, self.X, restart=self.m, tol=1e-10, engine=eng, spectral=spectral)
         else:
-            r = self.ctx.tgmres_solve(op, self.Cd, self.X, restart=self.m, tol=1e-10, precision=prec, engine=eng)
+            r = self.ctx.tgmres_solve(op, self.Cd, self.X, restart=self.m, tol=1e-10, precision=prec, engine=eng,
+                                      spectral=spectral)
         op.close()
         return r
 
@@ -632,7 +637,7 @@ def run_comparisons(ctx, dev, reps, dense1=None, dense1_entries=None):
     and certified by the FP64 CUDA-core operator."""
     import torch
     out = {}
-    fp64s = ["fp64", "fp64@ozaki"]
+    fp64s = ["fp64", "fp64@ozaki", "fp64@ozaki+spectral"]
     fast = ["mixed_bf16@ozaki", "mixed_tf32x3@ozaki"]
     if dense1 is not None and dense1_entries is not None:
         out["dense_n1024_s1024_p16"] = {"entries": dense1_entries,
@@ -640,7 +645,7 @@ def run_comparisons(ctx, dev, reps, dense1=None, dense1_entries=None):
     try:
         d2 = DenseSetup(ctx, "dense_n4096_s256_p32_g0.3", 1, dev)
         ent = {"fp64": dense_entry(d2, "fp64", 1, warm=0)}
-        for nm in ("fp64@ozaki", "mixed_tf32x3@ozaki", "mixed_bf16@ozaki"):
+        for nm in ("fp64@ozaki", "fp64@ozaki+spectral", "mixed_tf32x3@ozaki", "mixed_bf16@ozaki"):
             ent[nm] = dense_entry(d2, nm, reps)
         out["dense_n4096_s256_p32_g0.3"] = {"entries": ent, "speedup": speedups(ent, fp64s, fast)}
         d2.close()
@@ -808,7 +813,7 @@ def main():
     comparisons = None
     if rank == 0 and world == 1 and not a.no_comparisons and a.workload == "dense_n1024_s1024_p16":
         d1 = {primary: {"value": value, "ms_per_step": ms, "relres_fp64_dfma": relres_cert, "status": "ok"}}
-        for nm in ("fp64@ozaki", "mixed_bf16@ozaki", "mixed_tf32x3@ozaki"):
+        for nm in ("fp64@ozaki", "fp64@ozaki+spectral", "mixed_bf16@ozaki", "mixed_tf32x3@ozaki"):
             if nm in variants:
                 d1[nm] = variants[nm]
         comparisons = run_comparisons(ctx, dev, a.reps, su, d1)

@@ -152,6 +152,13 @@ typedef struct {
   int fp64_engine;       /* ts_fp64_engine of every FP64 application (the whole FP64 solve, or the true
                             residuals of mixed precision); dense operators of ts_tgmres/ts_tfom only */
   int ozaki_digits;      /* TS_ENGINE_OZAKI: digits per value, 3..8 (0 = 6) */
+  int spectral_basis;    /* TS_FP64 tGMRES / tFOM with a dense operator: 1 keeps the Krylov basis in the
+                            Fourier domain (the K = p/2 + 1 slices of each basis tensor, slice k scaled by
+                            sqrt(w_k / p), w_k = 1 for k = 0 and p/2, else 2, so that the Euclidean inner
+                            product of the scaled slices is the tensor inner product of Definition 2.3 by
+                            Parseval); every inner step then applies M slice by slice without the two
+                            mode-3 DFTs, which only the residuals and the solution update still need.  The
+                            same iterates as 0 (the default, real-space basis) up to rounding. */
 } ts_solve_opts;
 
 typedef struct {

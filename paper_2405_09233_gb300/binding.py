@@ -32,7 +32,7 @@ class SolveOpts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int),
                 ("true_history", ctypes.POINTER(ctypes.c_double)), ("true_history_cap", ctypes.c_int),
-                ("fp64_engine", ctypes.c_int), ("ozaki_digits", ctypes.c_int)]
+                ("fp64_engine", ctypes.c_int), ("ozaki_digits", ctypes.c_int), ("spectral_basis", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -260,7 +260,7 @@ class Context:
         return Y
 
     def _solve(self, fn, name, op, C, X, restart, tol, max_restarts, precision, inner_tol, max_outer,
-               history_cap, engine="dfma", ozaki_digits=0):
+               history_cap, engine="dfma", ozaki_digits=0, spectral=False):
         opts = SolveOpts()
         lib().ts_solve_opts_default(ctypes.byref(opts))
         opts.restart, opts.tol, opts.max_restarts = restart, tol, max_restarts
@@ -268,6 +268,7 @@ class Context:
         opts.inner_tol, opts.max_outer = inner_tol, max_outer
         opts.fp64_engine = ENGINES[engine] if isinstance(engine, str) else int(engine)
         opts.ozaki_digits = ozaki_digits
+        opts.spectral_basis = 1 if spectral else 0
         hist = np.zeros(history_cap)
         thist = np.zeros(history_cap)
         opts.history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -281,11 +282,12 @@ class Context:
                            thist[:min(info.true_history_len, history_cap)].copy())
 
     def tgmres_solve(self, op, C, X, restart=20, tol=1e-10, max_restarts=200, precision="fp64",
-                     inner_tol=0.0, max_outer=0, history_cap=4096, engine="dfma", ozaki_digits=0):
+                     inner_tol=0.0, max_outer=0, history_cap=4096, engine="dfma", ozaki_digits=0, spectral=False):
         """Restarted tGMRES(m); X holds X0 on entry and the solution on return.  engine selects how
-        FP64 applications are computed ("dfma" or "ozaki")."""
+        FP64 applications are computed ("dfma" or "ozaki"); spectral=True keeps an FP64 Krylov basis in
+        the Fourier domain."""
         return self._solve(lib().ts_tgmres_solve, "ts_tgmres_solve", op, C, X, restart, tol, max_restarts,
-                           precision, inner_tol, max_outer, history_cap, engine, ozaki_digits)
+                           precision, inner_tol, max_outer, history_cap, engine, ozaki_digits, spectral)
 
     def tba_solve(self, op, C, X, restart=10, tol=1e-10, max_restarts=100, history_cap=4096, precision="fp64"):
         """Restarted TBAS(m); X holds X0 on entry and the solution on return.  precision "fp64", or
@@ -318,10 +320,10 @@ class Context:
         return st, list(infos), list(sts)
 
     def tfom_solve(self, op, C, X, restart=20, tol=1e-10, max_restarts=200, history_cap=4096, engine="dfma",
-                   ozaki_digits=0):
-        """Restarted tFOM(m) (FP64)."""
+                   ozaki_digits=0, spectral=False):
+        """Restarted tFOM(m) (FP64); spectral=True keeps the Krylov basis in the Fourier domain."""
         return self._solve(lib().ts_tfom_solve, "ts_tfom_solve", op, C, X, restart, tol, max_restarts,
-                           "fp64", 0.0, 0, history_cap, engine, ozaki_digits)
+                           "fp64", 0.0, 0, history_cap, engine, ozaki_digits, spectral)
 
 
 class Operator:

@@ -350,6 +350,28 @@ void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mod
   tm.end(st);
 }
 
+void apply_f64_spectral(ts_ctx* ctx, const ts_op* op, const double2* Xh, double2* Yh, cudaStream_t st) {
+  TS_REQUIRE(!op->sp, "spectral Krylov basis: dense operators only");
+  if (ctx->f64_engine == TS_ENGINE_OZAKI) {
+    const int S = ctx->oz_step_digits > 0 && ctx->oz_step_digits < ctx->oz_digits ? ctx->oz_step_digits : ctx->oz_digits;
+    oz_apply_spectral(ctx, op, Xh, Yh, S, ctx->oz_digits, st);
+    return;
+  }
+  const int n = op->n, s = op->s, p = op->p, K = op->K;
+  const long long T = (long long)n * s;
+  ZGemmArgs g{};
+  g.A1 = op->Ah; g.sA1 = (long long)n * n; g.lda1 = n;
+  g.B1 = Xh;     g.sB1 = T;                g.ldb1 = n; g.L1 = n;
+  g.A2 = Xh;     g.sA2 = T;                g.lda2 = n;
+  g.B2 = op->Bh; g.sB2 = (long long)s * s; g.ldb2 = s; g.L2 = s;
+  g.Y = Yh; g.sY = T; g.ldy = n;
+  g.M = n; g.N = s; g.K = K; g.nyq = nyquist_index(p); g.sgn2 = -1.0;
+  KernelTimer& tm = ctx->timer;
+  tm.begin(st, 0, gemm_flops(n, s, n, s, K, g.nyq));
+  zgemm_slices_f64(g, st);
+  tm.end(st);
+}
+
 }  // namespace ts
 
 using namespace ts;

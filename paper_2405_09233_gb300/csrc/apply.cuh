@@ -43,6 +43,10 @@ struct EngineScope {
 void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
                double* partials, cudaStream_t st);
 
+// Yh = A_k Xh_k - Xh_k B_k slice by slice on spectral tensors (K slices of n x s, column-major), on the
+// context's FP64 engine: the operator of the spectral Krylov basis (no mode-3 DFTs).
+void apply_f64_spectral(ts_ctx* ctx, const ts_op* op, const double2* Xh, double2* Yh, cudaStream_t st);
+
 // Algorithmic FLOPs of one fused slice-GEMM launch (8 per complex, 2 per real multiply-add).
 double gemm_flops(int M, int N, int L1, int L2, int K, int nyq);
 

@@ -302,6 +302,33 @@ void irfft_tube(const Cplx* in, Real* out, long long T, int p, int mode, const R
   TS_CUDA(cudaGetLastError());
 }
 
+namespace {
+// Scaled half spectrum of the spectral Krylov basis: out_k = in_k * sqrt(w_k / p) (or its inverse),
+// times *alpha when given; the imaginary parts of the real slices (k = 0 and p/2) are set to zero.
+__global__ void k_spec_weight(const double2* in, double2* out, long long T, int p,
+                              int inverse, const double* __restrict__ alpha) {
+  const int K = p / 2 + 1;
+  const double a = alpha ? *alpha : 1.0;
+  const long long tot = (long long)K * T;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / T);
+    const bool real = k == 0 || (p % 2 == 0 && k == p / 2);
+    const double w = real ? 1.0 : 2.0;
+    const double f = a * (inverse ? sqrt(p / w) : sqrt(w / p));
+    const double2 v = in[e];
+    out[e] = make_double2(v.x * f, real ? 0.0 : v.y * f);
+  }
+}
+}  // namespace
+
+void spec_weight(const double2* in, double2* out, long long T, int p, bool inverse, const double* alpha,
+                 cudaStream_t st) {
+  k_spec_weight<<<stream_grid((long long)(p / 2 + 1) * T), 256, 0, st>>>(in, out, T, p, inverse ? 1 : 0, alpha);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
 template void rfft_tube<double, double2>(const double*, double2*, long long, int, cudaStream_t);
 template void rfft_tube<float, float2>(const float*, float2*, long long, int, cudaStream_t);
 template void irfft_tube<double, double2>(const double2*, double*, long long, int, int, const double*, double*,

@@ -582,6 +582,30 @@ void oz_products(const ts_op* cop, const double2* Xh, double2* Yh, int S, const 
   TS_CUDA(cudaGetLastError());
 }
 
+// The emulated products on spectral tensors: Yh = A_k Xh_k - Xh_k B_k (workspace digit planes of Xh).
+void oz_apply_spectral(ts_ctx* ctx, const ts_op* cop, const double2* Xh, double2* Yh, int S, int S_op,
+                       cudaStream_t st) {
+  ts_op* op = const_cast<ts_op*>(cop);   // the digit planes are cached on first use
+  oz_prepare(op, S_op, st);
+  oz_preload();
+  const int n = op->n, s = op->s, p = op->p, K = op->K;
+  const OzBufferSizes z = oz_buffer_sizes(n, s, K, S);
+  OzBuffers b;
+  b.xc_re = ctx->ws.get("oz_xc_re", z.xc);
+  b.xc_im = ctx->ws.get("oz_xc_im", z.xc);
+  b.xc_nim = ctx->ws.get("oz_xc_nim", z.xc);
+  b.xr_re = ctx->ws.get("oz_xr_re", z.xr);
+  b.xr_im = ctx->ws.get("oz_xr_im", z.xr);
+  b.mx = static_cast<unsigned long long*>(ctx->ws.get("oz_mx", sizeof(unsigned long long) * K));
+  b.Ex = static_cast<int*>(ctx->ws.get("oz_Ex", sizeof(int) * K));
+  int* err = static_cast<int*>(ctx->ws.get("tc_err", sizeof(int) * 4));
+  KernelTimer& tm = ctx->timer;
+  tm.begin(st, 3, gemm_flops(n, s, n, s, K, nyquist_index(p)));
+  if (tm.enabled) tm.oz_pair_flops += oz_bf16_flops(n, s, K, nyquist_index(p), S);
+  oz_products(op, Xh, Yh, S, b, nullptr, err, st);
+  tm.end(st);
+}
+
 void apply_f64_oz(ts_ctx* ctx, const ts_op* cop, const double* X, double* Y, int mode, const double* C,
                   double* partials, int S, int S_op, cudaStream_t st) {
   ts_op* op = const_cast<ts_op*>(cop);   // the digit planes are cached on first use

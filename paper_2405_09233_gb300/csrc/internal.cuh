@@ -178,6 +178,12 @@ template <typename Real, typename Cplx>
 void irfft_tube(const Cplx* in, Real* out, long long T, int p, int mode, const Real* C,
                 double* partials, cudaStream_t st);
 
+// Spectral Krylov basis: out_k = alpha * sqrt(w_k / p) * in_k (inverse: sqrt(p / w_k)) over K = p/2+1
+// slices of T entries, w_k = 1 for k = 0 and p/2, else 2; real slices get zero imaginary parts.
+// alpha is a device scalar (nullptr: 1).  in and out may alias.
+void spec_weight(const double2* in, double2* out, long long T, int p, bool inverse, const double* alpha,
+                 cudaStream_t st);
+
 // ---------------- per-slice complex GEMM on CUDA cores, FP64 / FP32 (gemm_simt.cu) ----------------
 // Y_k = A1_k B1_k + sgn2 * A2_k B2_k for k < K (phase 2 skipped when L2 == 0);
 // slices k == 0 and k == nyq are treated as real (imaginary parts ignored, result imag = 0).

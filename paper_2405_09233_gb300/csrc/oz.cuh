@@ -48,6 +48,9 @@ void oz_products(const ts_op* op, const double2* Xh, double2* Yh, int S, const O
 // value; the operator's digit planes are prepared (once) with S_op >= S digits.
 void apply_f64_oz(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
                   double* partials, int S, int S_op, cudaStream_t st);
+// The emulated products alone on spectral tensors (the spectral Krylov basis): Yh = A_k Xh_k - Xh_k B_k.
+void oz_apply_spectral(ts_ctx* ctx, const ts_op* op, const double2* Xh, double2* Yh, int S, int S_op,
+                       cudaStream_t st);
 // BF16 tensor FLOPs one emulated application executes (all kept digit pairs).
 double oz_bf16_flops(int n, int s, int K, int nyq, int S);
 

@@ -93,13 +93,22 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
       (prec == TS_MIXED_FP32 || prec == TS_MIXED_TF32X3) ? 1e-6 : (prec == TS_MIXED_TF32 ? 1e-3 : 1e-2);
   const double inner_tol = mixed ? (o.inner_tol > 0 ? o.inner_tol : inner_default) : 0.0;
 
-  T* V = static_cast<T*>(ctx->ws.get("krylov_V", sizeof(T) * (size_t)(m + 1) * N));
-  T* W = static_cast<T*>(ctx->ws.get("krylov_W", sizeof(T) * (size_t)N));
+  // Spectral basis (FP64, dense operators): basis tensors are the K scaled Fourier slices, 2 K n s
+  // doubles each, on which the tensor inner product is the Euclidean one (Parseval).
+  const bool spectral = sizeof(T) == 8 && o.spectral_basis != 0;
+  const long long Ts = (long long)op->n * op->s;
+  const long long Nb = spectral ? 2ll * op->K * Ts : N;      // length of a basis vector, in T
+  T* V = static_cast<T*>(ctx->ws.get("krylov_V", sizeof(T) * (size_t)(m + 1) * Nb));
+  T* W = static_cast<T*>(ctx->ws.get("krylov_W", sizeof(T) * (size_t)Nb));
+  double2* Rh = spectral ? static_cast<double2*>(ctx->ws.get("krylov_Rh", sizeof(double2) * (size_t)op->K * Ts))
+                         : nullptr;
   double* R = static_cast<double*>(ctx->ws.get("krylov_R", sizeof(double) * (size_t)N));
   double* P = static_cast<double*>(ctx->ws.get("krylov_P", sizeof(double) * 3 * kRedBlocks));
   double* Pp[2] = {P, P + kRedBlocks};
   double* P2 = P + 2 * kRedBlocks;
   double* sc = static_cast<double*>(ctx->ws.get("krylov_scalars", sizeof(double) * 64));
+  ctx->host_scalars[13] = 1.0;
+  TS_CUDA(cudaMemcpyAsync(sc + 12, ctx->host_scalars + 13, sizeof(double), cudaMemcpyHostToDevice, st));
   void* state = ctx->ws.get("krylov_state", krylov_state_bytes(m));
   double* hs = ctx->host_scalars;
   int* tc_err = static_cast<int*>(ctx->ws.get("tc_err", sizeof(int) * 4));
@@ -171,15 +180,34 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
   // V_{j+1} = W / h_{j+1,j} when `scale_next` (the graph always forms it; unused after the last step).
   double* stop_dev = sc + 8;   // [tol ||C||, inner threshold or -1] for the graph's stopping test
   auto inner_step = [&](int j, cudaGraphConditionalHandle handle, bool scale_next, cudaStream_t q) {
-    apply_basis(ctx, op, prec, basis_ptr(V, N, j), W, q);         // W = M(V_j)
-    dot_partials<T>(basis_ptr(V, N, 0), W, N, Pp[0], q);
+    if constexpr (sizeof(T) == 8) {
+      if (spectral)   // W = M(V_j) slice by slice: the scaling commutes with the per-slice operator
+        apply_f64_spectral(ctx, op, reinterpret_cast<const double2*>(basis_ptr(V, Nb, j)),
+                           reinterpret_cast<double2*>(W), q);
+      else
+        apply_basis(ctx, op, prec, basis_ptr(V, Nb, j), W, q);     // W = M(V_j)
+    } else {
+      apply_basis(ctx, op, prec, basis_ptr(V, Nb, j), W, q);
+    }
+    dot_partials<T>(basis_ptr(V, Nb, 0), W, Nb, Pp[0], q);
     for (int i = 0; i <= j; ++i) {                                  // MGS sweep, fused with the next dot
-      const T* Vn = i < j ? basis_ptr(V, N, i + 1) : nullptr;
-      mgs_pass<T>(W, basis_ptr(V, N, i), Vn, N, Pp[i & 1], ks_H(state, m) + i + (size_t)(m + 1) * j,
+      const T* Vn = i < j ? basis_ptr(V, Nb, i + 1) : nullptr;
+      mgs_pass<T>(W, basis_ptr(V, Nb, i), Vn, Nb, Pp[i & 1], ks_H(state, m) + i + (size_t)(m + 1) * j,
                   Pp[(i + 1) & 1], q);
     }
     ks_step(state, m, j, method, Pp[(j + 1) & 1], q, handle, stop_dev);
-    if (scale_next) scale_dev<T, T>(W, basis_ptr(V, N, j + 1), N, ks_est(state, m) + 1, q);   // V_{j+1}
+    if (scale_next) scale_dev<T, T>(W, basis_ptr(V, Nb, j + 1), Nb, ks_est(state, m) + 1, q);   // V_{j+1}
+  };
+  // V_1 = R / ||R|| (in the spectral basis: the scaled Fourier slices of R, over ||R||)
+  auto init_v1 = [&](cudaStream_t q) {
+    if constexpr (sizeof(T) == 8) {
+      if (spectral) {
+        rfft_tube<double, double2>(R, Rh, Ts, op->p, q);
+        spec_weight(Rh, reinterpret_cast<double2*>(basis_ptr(V, Nb, 0)), Ts, op->p, false, sc + 3, q);
+        return;
+      }
+    }
+    scale_dev<double, T>(R, basis_ptr(V, Nb, 0), N, sc + 3, q);
   };
   const char* no_graph = std::getenv("TSTAR_NO_GRAPH_CYCLE");
   const bool graph_allowed = !ctx->timer.enabled && N <= kGraphCycleMaxN && !(no_graph && no_graph[0] == '1');
@@ -208,7 +236,7 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
           [&](cudaStream_t q) {
             return counted([&] {
               ks_init(state, m, sc + 2, q);
-              scale_dev<double, T>(R, basis_ptr(V, N, 0), N, sc + 3, q);   // V_1 = R / ||R||
+              init_v1(q);
             });
           },
           [&](int j, cudaGraphConditionalHandle next, cudaStream_t q) {
@@ -267,7 +295,7 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
       last_est = k > 0 ? hhist[k - 1] : last_est;
     } else {
       ks_init(state, m, sc + 2, st);
-      scale_dev<double, T>(R, basis_ptr(V, N, 0), N, sc + 3, st);  // V_1 = R / ||R||
+      init_v1(st);
       for (int j = 0; j < m; ++j) {
         inner_step(j, 0, false, st);
         if (mixed) ++info.applies_low; else ++info.applies_fp64;
@@ -282,7 +310,7 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
         const bool broke = ((int)flags & 1) != 0;
         const bool bad = ((int)flags & 6) != 0;
         if (bad || broke || est <= o.tol * normC || (mixed && est <= inner_tol * res)) break;
-        scale_dev<T, T>(W, basis_ptr(V, N, j + 1), N, ks_est(state, m) + 1, st);  // V_{j+1} = W / h
+        scale_dev<T, T>(W, basis_ptr(V, Nb, j + 1), Nb, ks_est(state, m) + 1, st);  // V_{j+1} = W / h
       }
     }
     ++info.cycles;
@@ -302,7 +330,19 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
       break;
     }
     ks_solve(state, m, k, method, st);
-    multi_axpy<T, double>(X, V, N, N, ks_y(state, m), k, 1.0, nullptr, st);   // X = X0 + V_k (*) y
+    if (spectral) {
+      // X += V_k (*) y: combine the spectral basis, undo the slice scaling, back to real space
+      double2* D = Rh;
+      double* Dr = static_cast<double*>(ctx->ws.get("krylov_Dr", sizeof(double) * (size_t)N));
+      fill_zero(D, sizeof(double2) * (size_t)op->K * Ts, st);
+      multi_axpy<double, double>(reinterpret_cast<double*>(D), reinterpret_cast<const double*>(V), Nb, Nb,
+                                 ks_y(state, m), k, 1.0, nullptr, st);
+      spec_weight(D, D, Ts, op->p, true, nullptr, st);
+      irfft_tube<double, double2>(D, Dr, Ts, op->p, IRFFT_STORE, nullptr, nullptr, st);
+      multi_axpy<double, double>(X, Dr, N, N, sc + 12, 1, 1.0, nullptr, st);   // sc[12] = 1
+    } else {
+      multi_axpy<T, double>(X, V, N, N, ks_y(state, m), k, 1.0, nullptr, st);   // X = X0 + V_k (*) y
+    }
     // True residual.  With progressive digits it is first formed with the fewest digits its next
     // use needs; a residual that would end the solve is formed again with every digit.
     const double res_prev = res;
@@ -360,6 +400,9 @@ ts_status solve_entry(ts_ctx* ctx, const ts_op* cop, const double* C, double* X,
   TS_REQUIRE(o.ozaki_digits == 0 || (o.ozaki_digits >= 3 && o.ozaki_digits <= 8), "solve: ozaki_digits must be 3..8");
   if (op->sp && o.fp64_engine != TS_ENGINE_DFMA)
     throw Error{TS_ERR_UNSUPPORTED, "the emulated FP64 engine takes dense operators only"};
+  TS_REQUIRE(o.spectral_basis == 0 || o.spectral_basis == 1, "solve: spectral_basis must be 0 or 1");
+  if (o.spectral_basis && (o.precision != TS_FP64 || op->sp))
+    throw Error{TS_ERR_UNSUPPORTED, "the spectral Krylov basis is for FP64 solves with dense operators"};
   EngineScope scope(ctx, o.fp64_engine, o.ozaki_digits == 0 ? 6 : o.ozaki_digits);
   TS_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -186,16 +186,18 @@ CASES = [(24, 24, 4, 20, 0), (24, 24, 4, 5, 0), (37, 5, 7, 8, 3), (16, 9, 1, 10,
 
 @pytest.mark.parametrize("method", ["gmres", "fom"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "n%d_s%d_p%d_m%d" % c[:4])
-def test_ozaki_solve_history_parity(ctx, method, case):
+@pytest.mark.parametrize("spectral", [False, True], ids=["real_basis", "spectral_basis"])
+def test_ozaki_solve_history_parity(ctx, method, case, spectral):
     """tGMRES / tFOM with every FP64 application on the emulated engine: the residual history
-    matches the oracle's to 1e-10 ||C|| at every inner step, as the DFMA engine's does."""
+    matches the oracle's to 1e-10 ||C|| at every inner step, as the DFMA engine's does, with the
+    Krylov basis in real space or in the Fourier domain."""
     n, s, p, m, seed = case
     pr = inputs.dense_problem(n, s, p, seed=seed)
     C = kr.sylv_apply(pr.A, pr.B, pr.Xstar)
     op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
     Xd = to_dev(np.zeros_like(C))
     fn = ctx.tgmres_solve if method == "gmres" else ctx.tfom_solve
-    res = fn(op, to_dev(C), Xd, restart=m, tol=1e-10, engine="ozaki")
+    res = fn(op, to_dev(C), Xd, restart=m, tol=1e-10, engine="ozaki", spectral=spectral)
     X = from_dev(Xd)
     ref = kr.restarted_solve(method, pr.A, pr.B, C, m=m, tol=1e-10)
     assert res.status == 0 and ref.status == "ok"

@@ -62,6 +62,36 @@ def test_fp64_history_parity(ctx, method, case):
     assert res.info.iters == ref.iters and res.info.cycles == ref.cycles
 
 
+@pytest.mark.parametrize("method", ["gmres", "fom"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "n%d_s%d_p%d_m%d" % c[:4])
+def test_fp64_spectral_basis_history_parity(ctx, method, case):
+    """The Krylov basis kept in the Fourier domain (scaled half spectrum, Parseval inner product): the
+    same iterates as the real-space basis, so the oracle's residual histories, cycles and solution."""
+    n, s, p, m, seed = case
+    pr = inputs.dense_problem(n, s, p, seed=seed)
+    C, X, res = run(ctx, method, pr, m, spectral=True)
+    ref = kr.restarted_solve(method, pr.A, pr.B, C, m=m, tol=1e-10)
+    assert res.status == 0 and ref.status == "ok"
+    assert len(res.history) == len(ref.history), (len(res.history), len(ref.history))
+    np.testing.assert_allclose(res.history, ref.history, rtol=0, atol=1e-10 * ref.normC)
+    np.testing.assert_allclose(res.true_history, ref.true_res, rtol=0, atol=1e-10 * ref.normC)
+    assert tp.norm(C - kr.sylv_apply(pr.A, pr.B, X)) <= 1e-10 * tp.norm(C)
+    assert np.abs(X - ref.X).max() <= 1e-8 * np.abs(ref.X).max()
+    assert res.info.iters == ref.iters and res.info.cycles == ref.cycles
+
+
+def test_spectral_basis_rejected_where_unsupported(ctx):
+    import torch
+    from paper_2405_09233_gb300 import TstarError
+    pr = inputs.dense_problem(8, 4, 3, seed=1)
+    op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
+    C = to_dev(inputs.random_tensor((8, 4, 3), seed=2))
+    with pytest.raises(TstarError) as e:
+        ctx.tgmres_solve(op, C, torch.zeros_like(C), restart=5, precision="mixed_fp32", spectral=True)
+    assert e.value.status == -6                            # TS_ERR_UNSUPPORTED
+    op.close()
+
+
 def test_fp64_deterministic_and_resumable(ctx):
     """Fixed-order reductions: two runs are bitwise equal, and stopping after two cycles then
     resuming from the returned X (the restart state of Algorithm 3) reproduces the full run."""
