@@ -131,7 +131,7 @@ def slice_flops(n, s, p, per_complex):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant kernels at the
 # n = s = 1024, p = 16 workload, from one ncu capture each of the kernels as they stand; a roofline object
 # carries them only for that workload and, for the emulated product, only when every launch used 6 digits.
-TRAFFIC_N1024 = {"k_gemm_slices<double>": 497799168 + 137544960, "k_oz_sylv/6": 1779147520 + 149931264}
+TRAFFIC_N1024 = {"k_gemm_slices<double>": 502828800 + 137370112, "k_oz_sylv/6": 1566623488 + 140020736}
 
 
 def traffic_for(kernel, workload):
@@ -703,7 +703,7 @@ def main():
 
     for _ in range(a.warmup):
         r = su.solve(primary)
-    assert r.status == 0, r
+        assert r.status == 0, r
 
     def barrier():
         if world > 1:
@@ -857,7 +857,7 @@ def run_batched(a, rank, world, local, dev):
     primary = prec + ("" if a.engine == "dfma" else "@" + a.engine)
     for _ in range(a.warmup):
         st, infos = b.solve(primary)
-    assert st == 0
+        assert st == 0, st
     # Timed with statistics off: per-phase event timing needs the flat cycle graph, while the timed
     # steps run the nested one (a cycle stops as soon as no instance iterates).  The phase split
     # comes from one extra instrumented step.
@@ -988,7 +988,7 @@ def run_tbas(a, rank, world, local, dev):
 
     for _ in range(a.warmup):
         r = step()
-    assert r.status == 0, r
+        assert r.status == 0, r
     ctx.stats_reset()
     ctx.stats_enable(True)
     clocks = ClockSampler(local)

@@ -11,8 +11,8 @@ import bench
 
 
 def test_traffic_only_for_the_captured_workload():
-    assert bench.traffic_for("k_gemm_slices<double>", "dense_n1024_s1024_p16") == 497799168 + 137544960
-    assert bench.traffic_for("k_oz_sylv/6", "dense_n1024_s1024_p16") == 1779147520 + 149931264
+    assert bench.traffic_for("k_gemm_slices<double>", "dense_n1024_s1024_p16") == 502828800 + 137370112
+    assert bench.traffic_for("k_oz_sylv/6", "dense_n1024_s1024_p16") == 1566623488 + 140020736
     assert bench.traffic_for("k_gemm_slices<double>", "dense_n4096_s256_p32_g0.3") is None
     assert bench.traffic_for("k_tc_sylv", "dense_n1024_s1024_p16") is None
 
