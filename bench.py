@@ -793,8 +793,20 @@ def main():
         variants[name] = dense_entry(su, name, a.reps, warm=1, world=world)
 
     if su.unknowns <= 1 << 16:
-        # small problems are launch-latency bound: also time the graph-replayed form (the batched
-        # solver on this single instance: one CUDA graph per restart cycle, no per-step host sync)
+        # Small problems are latency bound.  The default path launches a cycle's steps ahead behind a
+        # device gate (no host round trip per step); also time the same solve with one host round trip
+        # per step, and the batched solver on this single instance (one CUDA graph per restart cycle).
+        variants["us_per_inner_step"] = 1e3 * ms / max(last.info.iters, 1)
+        try:
+            os.environ["TSTAR_NO_LAUNCH_AHEAD"] = "1"
+            med, _, r1 = timed_median(lambda: su.solve(a.precision), 20, 3)
+            variants["host_round_trip_per_step"] = {
+                "ms_per_step": med, "status": r1.status, "inner_iters": r1.info.iters,
+                "us_per_inner_step": 1e3 * med / max(r1.info.iters, 1)}
+        except Exception as e:  # report, do not hide
+            variants["host_round_trip_per_step"] = {"error": str(e)}
+        finally:
+            os.environ.pop("TSTAR_NO_LAUNCH_AHEAD", None)
         try:
             ops1 = [ctx.op_create_dense(su.Ad, su.Bd)]
 
@@ -802,13 +814,13 @@ def main():
                 su.X.zero_()
                 return ctx.batched_solve(ops1, [su.Cd], [su.X], restart=m, tol=1e-10, precision=a.precision)
             med, _, (stb, infb, _) = timed_median(one, 20, 3)
-            variants["graph_replay"] = {"value": su.unknowns * world / (med / 1e3), "ms_per_step": med, "status": stb,
-                                        "inner_iters": infb[0].iters, "relres_true": infb[0].relres_true,
-                                        "us_per_inner_step": 1e3 * med / max(infb[0].iters, 1)}
+            variants["batched_solver_one_instance"] = {
+                "value": su.unknowns * world / (med / 1e3), "ms_per_step": med, "status": stb,
+                "inner_iters": infb[0].iters, "relres_true": infb[0].relres_true,
+                "us_per_inner_step": 1e3 * med / max(infb[0].iters, 1)}
             ops1[0].close()
         except Exception as e:  # report, do not hide
-            variants["graph_replay"] = {"error": str(e)}
-        variants["us_per_inner_step"] = 1e3 * ms / max(last.info.iters, 1)
+            variants["batched_solver_one_instance"] = {"error": str(e)}
 
     comparisons = None
     if rank == 0 and world == 1 and not a.no_comparisons and a.workload == "dense_n1024_s1024_p16":

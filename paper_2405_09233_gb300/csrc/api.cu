@@ -312,9 +312,10 @@ static void op_prepare(ts_op* op, const double* A, const double* B, cudaStream_t
 }
 
 void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
-               double* partials, cudaStream_t st) {
+               double* partials, cudaStream_t st, const int* gate) {
   const int n = op->n, s = op->s, p = op->p, K = op->K;
   const long long T = (long long)n * s;
+  TS_REQUIRE(!gate || (!op->sp && ctx->f64_engine != TS_ENGINE_OZAKI), "apply_f64: gate on an ungated path");
   if (op->sp) {
     // Sparse A: SpMM path; the residual epilogue becomes a subtraction and a fixed-order norm.
     apply_sparse_f64(ctx, op, X, Y, st);
@@ -333,7 +334,7 @@ void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mod
   double2* Yh = static_cast<double2*>(ctx->ws.get("apply_Yh", sizeof(double2) * (size_t)K * T));
   KernelTimer& tm = ctx->timer;
   tm.begin(st, 1, 8.0 * T * p + 16.0 * K * T);
-  rfft_tube<double, double2>(X, Xh, T, p, st);
+  rfft_tube<double, double2>(X, Xh, T, p, st, gate);
   tm.end(st);
   ZGemmArgs g{};
   g.A1 = op->Ah; g.sA1 = (long long)n * n; g.lda1 = n;
@@ -342,11 +343,12 @@ void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mod
   g.B2 = op->Bh; g.sB2 = (long long)s * s; g.ldb2 = s; g.L2 = s;
   g.Y = Yh; g.sY = T; g.ldy = n;
   g.M = n; g.N = s; g.K = K; g.nyq = nyquist_index(p); g.sgn2 = -1.0;
+  g.gate = gate;
   tm.begin(st, 0, gemm_flops(n, s, n, s, K, g.nyq));
   zgemm_slices_f64(g, st);
   tm.end(st);
   tm.begin(st, 1, 16.0 * K * T + 8.0 * T * p * (mode == IRFFT_RESIDUAL ? 2 : 1));
-  irfft_tube<double, double2>(Yh, Y, T, p, mode, C, partials, st);
+  irfft_tube<double, double2>(Yh, Y, T, p, mode, C, partials, st, gate);
   tm.end(st);
 }
 

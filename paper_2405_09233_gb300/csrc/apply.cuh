@@ -39,9 +39,10 @@ struct EngineScope {
 };
 
 // Y = M(X) in FP64 (rfft -> fused per-slice GEMMs -> irfft).  mode IRFFT_RESIDUAL writes
-// Y = C - M(X) and the kRedBlocks partial sums of Y^2 to `partials`.
+// Y = C - M(X) and the kRedBlocks partial sums of Y^2 to `partials`.  gate (device, may be null; dense
+// operators on the DFMA engine only): when *gate == 0 the three kernels return at once.
 void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
-               double* partials, cudaStream_t st);
+               double* partials, cudaStream_t st, const int* gate = nullptr);
 
 // Yh = A_k Xh_k - Xh_k B_k slice by slice on spectral tensors (K slices of n x s, column-major), on the
 // context's FP64 engine: the operator of the spectral Krylov basis (no mode-3 DFTs).

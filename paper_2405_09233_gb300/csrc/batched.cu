@@ -345,7 +345,9 @@ __global__ void __launch_bounds__(kTubes) k_b_irfft(BDev d, const Cplx* __restri
 }
 
 // --- per-slice products over the work list ---------------------------------------------------------
-template <typename Real, int MASK>
+// TINY: every instance has n, s <= kTinyL and the items are 8 x 4 tiles for kTinyThreads (gemm_tiny_tile);
+// otherwise 64 x 64 tiles for kGemmNT threads.
+template <typename Real, int MASK, int TINY>
 __global__ void __launch_bounds__(kGemmNT, 1) k_b_gemm(BDev d, const int4* __restrict__ items,
                                                        const typename CplxOf<Real>::T* __restrict__ Xh,
                                                        typename CplxOf<Real>::T* __restrict__ Yh) {
@@ -371,7 +373,8 @@ __global__ void __launch_bounds__(kGemmNT, 1) k_b_gemm(BDev d, const int4* __res
   a.B2 = Bh; a.sB2 = (long long)in.s * in.s; a.ldb2 = in.s; a.L2 = in.s;
   a.Y = Yh + in.offS; a.sY = T; a.ldy = in.n;
   a.M = in.n; a.N = in.s; a.K = in.K; a.nyq = in.nyq; a.sgn2 = -1.0;
-  gemm_tile<Real>(a, it.y, it.z, it.w);
+  if constexpr (TINY) gemm_tiny_tile<Real>(a, it.y, it.z, it.w);
+  else gemm_tile<Real>(a, it.y, it.z, it.w);
 }
 
 // --- small per-instance kernels ---------------------------------------------------------------------
@@ -493,9 +496,11 @@ void preload_cycle_kernels() {
   cudaFuncAttributes fa;
   const void* fns[] = {
       (const void*)k_b_ks_init, (const void*)k_b_scale_R<T>, (const void*)k_b_rfft<T, Real2, 0, 0>,
-      (const void*)k_b_gemm<T, 0>, (const void*)k_b_irfft<T, Real2, 0>, (const void*)k_b_dot<T>,
+      (const void*)k_b_gemm<T, 0, 0>, (const void*)k_b_gemm<T, 0, 1>, (const void*)k_b_irfft<T, Real2, 0>,
+      (const void*)k_b_dot<T>,
       (const void*)k_b_mgs<T>, (const void*)k_b_givens, (const void*)k_b_scale_W<T>, (const void*)k_b_solve_y,
-      (const void*)k_b_axpy<T>, (const void*)k_b_rfft<double, double2, 1, 1>, (const void*)k_b_gemm<double, 1>,
+      (const void*)k_b_axpy<T>, (const void*)k_b_rfft<double, double2, 1, 1>, (const void*)k_b_gemm<double, 1, 0>,
+      (const void*)k_b_gemm<double, 1, 1>,
       (const void*)k_b_irfft<double, double2, 1>, (const void*)k_b_finalize_norm, (const void*)k_b_any_active};
   for (const void* f : fns) TS_CUDA(cudaFuncGetAttributes(&fa, f));
 }
@@ -505,6 +510,7 @@ struct BatchPlan {
   std::vector<int> nb_inst, tb_inst;
   std::vector<long long> nb_off, tb_off;
   std::vector<int4> items;
+  bool tiny = false;   // items are 8 x 4 tiles (gemm_tiny_tile) instead of 64 x 64
   long long totN = 0, totS = 0;
 };
 
@@ -651,9 +657,17 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
       plan.tb_off.push_back(t);
     }
     b.tb1 = (int)plan.tb_inst.size();
+  }
+  // CUDA-core slice products: warp-sized 8 x 4 tiles when every instance is tiny (a 64 x 64 tile
+  // of a 24 x 24 product issues 10x the FP64 work it needs), else 64 x 64 tiles.
+  plan.tiny = true;
+  for (const BInst& b : plan.inst) plan.tiny = plan.tiny && b.n <= kTinyL && b.s <= kTinyL;
+  const int tbm = plan.tiny ? kTinyBM : kGemmBM, tbn = plan.tiny ? kTinyBN : kGemmBN;
+  for (int i = 0; i < count; ++i) {
+    const BInst& b = plan.inst[i];
     for (int k = 0; k < b.K; ++k)
-      for (int i0 = 0; i0 < b.n; i0 += kGemmBM)
-        for (int j0 = 0; j0 < b.s; j0 += kGemmBN) plan.items.push_back(make_int4(i, k, i0, j0));
+      for (int i0 = 0; i0 < b.n; i0 += tbm)
+        for (int j0 = 0; j0 < b.s; j0 += tbn) plan.items.push_back(make_int4(i, k, i0, j0));
   }
   plan.totN = (plan.totN + 3) / 4 * 4;   // every basis vector V + j totN starts 16-byte aligned
   // Largest tiles first (reduction length n + s; real slices are a quarter of the work).
@@ -925,8 +939,13 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
                         tct.titems, tct.n_titems, tc_err, s2);
       return 2;
     }
-    if (mixed) k_b_gemm<float, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, (float2*)Xh, (float2*)Yh);
-    else k_b_gemm<double, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, (double2*)Xh, (double2*)Yh);
+    if (mixed) {
+      if (plan.tiny) k_b_gemm<float, 0, 1><<<nit, kTinyThreads, 0, s2>>>(d, d_items, (float2*)Xh, (float2*)Yh);
+      else k_b_gemm<float, 0, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, (float2*)Xh, (float2*)Yh);
+    } else {
+      if (plan.tiny) k_b_gemm<double, 0, 1><<<nit, kTinyThreads, 0, s2>>>(d, d_items, (double2*)Xh, (double2*)Yh);
+      else k_b_gemm<double, 0, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, (double2*)Xh, (double2*)Yh);
+    }
     TS_CUDA(cudaGetLastError());
     return 1;
   };
@@ -934,7 +953,8 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   // one emulated-FP64 product per instance (each gated by the instance's cycle flag).
   auto residual_products = [&](cudaStream_t s2) -> int {
     if (!ozaki) {
-      k_b_gemm<double, 1><<<nit, kGemmNT, 0, s2>>>(d, d_items, Xh64, Yh64);
+      if (plan.tiny) k_b_gemm<double, 1, 1><<<nit, kTinyThreads, 0, s2>>>(d, d_items, Xh64, Yh64);
+      else k_b_gemm<double, 1, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, Xh64, Yh64);
       TS_CUDA(cudaGetLastError());
       return 1;
     }

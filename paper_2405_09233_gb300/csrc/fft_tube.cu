@@ -31,7 +31,8 @@ __device__ __forceinline__ void load_twiddles(Real* c, Real* s, int p) {
 
 template <typename Real, typename Cplx, int PMAX>
 __global__ void __launch_bounds__(256) k_rfft(const Real* __restrict__ in, Cplx* __restrict__ out,
-                                              long long T, int p) {
+                                              long long T, int p, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;   // a cycle that already ended (launched ahead)
   __shared__ Real tc[PMAX], tsn[PMAX];
   load_twiddles(tc, tsn, p);
   const int K = p / 2 + 1;
@@ -65,7 +66,9 @@ __global__ void __launch_bounds__(256) k_rfft(const Real* __restrict__ in, Cplx*
 
 // Power-of-two p: register radix-2 FFT (fft_reg.cuh), P compile-time.
 template <typename Real, typename Cplx, int P>
-__global__ void __launch_bounds__(256) k_rfft_pow2(const Real* __restrict__ in, Cplx* __restrict__ out, long long T) {
+__global__ void __launch_bounds__(256) k_rfft_pow2(const Real* __restrict__ in, Cplx* __restrict__ out, long long T,
+                                                   const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;   // a cycle that already ended (launched ahead)
   __shared__ Real tc[P], tsn[P];
   load_twiddles(tc, tsn, P);
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < T;
@@ -83,7 +86,9 @@ __global__ void __launch_bounds__(256) k_rfft_pow2(const Real* __restrict__ in, 
 
 template <typename Real, typename Cplx, int P, int MODE>
 __global__ void __launch_bounds__(256) k_irfft_pow2(const Cplx* __restrict__ in, Real* __restrict__ out, long long T,
-                                                    const Real* __restrict__ C, double* __restrict__ partials) {
+                                                    const Real* __restrict__ C, double* __restrict__ partials,
+                                                    const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;   // a cycle that already ended (launched ahead)
   __shared__ Real tc[P], tsn[P];
   load_twiddles(tc, tsn, P);
   const Real invp = Real(1) / Real(P);
@@ -115,7 +120,8 @@ __global__ void __launch_bounds__(256) k_irfft_pow2(const Cplx* __restrict__ in,
 // Any p: samples re-read from memory for every k (L1/L2 hits after the first).
 template <typename Real, typename Cplx>
 __global__ void __launch_bounds__(256) k_rfft_any(const Real* __restrict__ in, Cplx* __restrict__ out,
-                                                  long long T, int p) {
+                                                  long long T, int p, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;   // a cycle that already ended (launched ahead)
   extern __shared__ unsigned char smem_raw[];
   Real* tc = reinterpret_cast<Real*>(smem_raw);
   Real* tsn = tc + p;
@@ -145,7 +151,8 @@ __global__ void __launch_bounds__(256) k_rfft_any(const Real* __restrict__ in, C
 template <typename Real, typename Cplx, int PMAX, int MODE>
 __global__ void __launch_bounds__(256) k_irfft(const Cplx* __restrict__ in, Real* __restrict__ out,
                                                long long T, int p, const Real* __restrict__ C,
-                                               double* __restrict__ partials) {
+                                               double* __restrict__ partials, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;   // a cycle that already ended (launched ahead)
   __shared__ Real tc[PMAX], tsn[PMAX];
   load_twiddles(tc, tsn, p);
   const int K = p / 2 + 1;
@@ -200,7 +207,8 @@ __global__ void __launch_bounds__(256) k_irfft(const Cplx* __restrict__ in, Real
 template <typename Real, typename Cplx, int MODE>
 __global__ void __launch_bounds__(256) k_irfft_any(const Cplx* __restrict__ in, Real* __restrict__ out,
                                                    long long T, int p, const Real* __restrict__ C,
-                                                   double* __restrict__ partials) {
+                                                   double* __restrict__ partials, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;   // a cycle that already ended (launched ahead)
   extern __shared__ unsigned char smem_raw[];
   Real* tc = reinterpret_cast<Real*>(smem_raw);
   Real* tsn = tc + p;
@@ -246,41 +254,41 @@ int stream_grid(long long T) {
 }  // namespace
 
 template <typename Real, typename Cplx>
-void rfft_tube(const Real* in, Cplx* out, long long T, int p, cudaStream_t st) {
+void rfft_tube(const Real* in, Cplx* out, long long T, int p, cudaStream_t st, const int* gate) {
   const int g = stream_grid(T);
-  if (p == 2) k_rfft_pow2<Real, Cplx, 2><<<g, 256, 0, st>>>(in, out, T);
-  else if (p == 4) k_rfft_pow2<Real, Cplx, 4><<<g, 256, 0, st>>>(in, out, T);
-  else if (p == 8) k_rfft_pow2<Real, Cplx, 8><<<g, 256, 0, st>>>(in, out, T);
-  else if (p == 16) k_rfft_pow2<Real, Cplx, 16><<<g, 256, 0, st>>>(in, out, T);
-  else if (p == 32) k_rfft_pow2<Real, Cplx, 32><<<g, 256, 0, st>>>(in, out, T);
-  else if (p <= 2) k_rfft<Real, Cplx, 2><<<g, 256, 0, st>>>(in, out, T, p);
-  else if (p <= 4) k_rfft<Real, Cplx, 4><<<g, 256, 0, st>>>(in, out, T, p);
-  else if (p <= 8) k_rfft<Real, Cplx, 8><<<g, 256, 0, st>>>(in, out, T, p);
-  else if (p <= 16) k_rfft<Real, Cplx, 16><<<g, 256, 0, st>>>(in, out, T, p);
-  else if (p <= 32) k_rfft<Real, Cplx, 32><<<g, 256, 0, st>>>(in, out, T, p);
-  else k_rfft_any<Real, Cplx><<<g, 256, 2 * p * sizeof(Real), st>>>(in, out, T, p);
+  if (p == 2) k_rfft_pow2<Real, Cplx, 2><<<g, 256, 0, st>>>(in, out, T, gate);
+  else if (p == 4) k_rfft_pow2<Real, Cplx, 4><<<g, 256, 0, st>>>(in, out, T, gate);
+  else if (p == 8) k_rfft_pow2<Real, Cplx, 8><<<g, 256, 0, st>>>(in, out, T, gate);
+  else if (p == 16) k_rfft_pow2<Real, Cplx, 16><<<g, 256, 0, st>>>(in, out, T, gate);
+  else if (p == 32) k_rfft_pow2<Real, Cplx, 32><<<g, 256, 0, st>>>(in, out, T, gate);
+  else if (p <= 2) k_rfft<Real, Cplx, 2><<<g, 256, 0, st>>>(in, out, T, p, gate);
+  else if (p <= 4) k_rfft<Real, Cplx, 4><<<g, 256, 0, st>>>(in, out, T, p, gate);
+  else if (p <= 8) k_rfft<Real, Cplx, 8><<<g, 256, 0, st>>>(in, out, T, p, gate);
+  else if (p <= 16) k_rfft<Real, Cplx, 16><<<g, 256, 0, st>>>(in, out, T, p, gate);
+  else if (p <= 32) k_rfft<Real, Cplx, 32><<<g, 256, 0, st>>>(in, out, T, p, gate);
+  else k_rfft_any<Real, Cplx><<<g, 256, 2 * p * sizeof(Real), st>>>(in, out, T, p, gate);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
 
 template <typename Real, typename Cplx>
 void irfft_tube(const Cplx* in, Real* out, long long T, int p, int mode, const Real* C,
-                double* partials, cudaStream_t st) {
+                double* partials, cudaStream_t st, const int* gate) {
   // The residual epilogue writes one partial per block: it runs on exactly kRedBlocks blocks.
   const int g = mode == IRFFT_RESIDUAL ? kRedBlocks : stream_grid(T);
 #define TS_IRFFT(PM)                                                                            \
   do {                                                                                          \
     if (mode == IRFFT_RESIDUAL)                                                                 \
-      k_irfft<Real, Cplx, PM, IRFFT_RESIDUAL><<<g, 256, 0, st>>>(in, out, T, p, C, partials);   \
+      k_irfft<Real, Cplx, PM, IRFFT_RESIDUAL><<<g, 256, 0, st>>>(in, out, T, p, C, partials, gate);   \
     else                                                                                        \
-      k_irfft<Real, Cplx, PM, IRFFT_STORE><<<g, 256, 0, st>>>(in, out, T, p, C, partials);      \
+      k_irfft<Real, Cplx, PM, IRFFT_STORE><<<g, 256, 0, st>>>(in, out, T, p, C, partials, gate);      \
   } while (0)
 #define TS_IRFFT_POW2(PP)                                                                        \
   do {                                                                                           \
     if (mode == IRFFT_RESIDUAL)                                                                  \
-      k_irfft_pow2<Real, Cplx, PP, IRFFT_RESIDUAL><<<g, 256, 0, st>>>(in, out, T, C, partials);  \
+      k_irfft_pow2<Real, Cplx, PP, IRFFT_RESIDUAL><<<g, 256, 0, st>>>(in, out, T, C, partials, gate);  \
     else                                                                                         \
-      k_irfft_pow2<Real, Cplx, PP, IRFFT_STORE><<<g, 256, 0, st>>>(in, out, T, C, partials);     \
+      k_irfft_pow2<Real, Cplx, PP, IRFFT_STORE><<<g, 256, 0, st>>>(in, out, T, C, partials, gate);     \
   } while (0)
   if (p == 2) TS_IRFFT_POW2(2);
   else if (p == 4) TS_IRFFT_POW2(4);
@@ -293,9 +301,9 @@ void irfft_tube(const Cplx* in, Real* out, long long T, int p, int mode, const R
   else if (p <= 16) TS_IRFFT(16);
   else if (p <= 32) TS_IRFFT(32);
   else if (mode == IRFFT_RESIDUAL)
-    k_irfft_any<Real, Cplx, IRFFT_RESIDUAL><<<g, 256, 2 * p * sizeof(Real), st>>>(in, out, T, p, C, partials);
+    k_irfft_any<Real, Cplx, IRFFT_RESIDUAL><<<g, 256, 2 * p * sizeof(Real), st>>>(in, out, T, p, C, partials, gate);
   else
-    k_irfft_any<Real, Cplx, IRFFT_STORE><<<g, 256, 2 * p * sizeof(Real), st>>>(in, out, T, p, C, partials);
+    k_irfft_any<Real, Cplx, IRFFT_STORE><<<g, 256, 2 * p * sizeof(Real), st>>>(in, out, T, p, C, partials, gate);
 #undef TS_IRFFT
 #undef TS_IRFFT_POW2
   count_launch();
@@ -329,11 +337,11 @@ void spec_weight(const double2* in, double2* out, long long T, int p, bool inver
   TS_CUDA(cudaGetLastError());
 }
 
-template void rfft_tube<double, double2>(const double*, double2*, long long, int, cudaStream_t);
-template void rfft_tube<float, float2>(const float*, float2*, long long, int, cudaStream_t);
+template void rfft_tube<double, double2>(const double*, double2*, long long, int, cudaStream_t, const int*);
+template void rfft_tube<float, float2>(const float*, float2*, long long, int, cudaStream_t, const int*);
 template void irfft_tube<double, double2>(const double2*, double*, long long, int, int, const double*, double*,
-                                          cudaStream_t);
+                                          cudaStream_t, const int*);
 template void irfft_tube<float, float2>(const float2*, float*, long long, int, int, const float*, double*,
-                                        cudaStream_t);
+                                        cudaStream_t, const int*);
 
 }  // namespace ts

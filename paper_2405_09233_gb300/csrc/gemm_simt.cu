@@ -21,6 +21,11 @@ __global__ void __launch_bounds__(kGemmNT, 1) k_gemm_slices(GemmArgs<typename Cp
   gemm_tile<Real, BM, BN, TM, TN>(a, blockIdx.z, blockIdx.x * BM, blockIdx.y * BN);
 }
 
+template <typename Real>
+__global__ void __launch_bounds__(kTinyThreads) k_gemm_tiny(GemmArgs<typename CplxOf<Real>::T> a) {
+  gemm_tiny_tile<Real>(a, blockIdx.z, blockIdx.x * kTinyBM, blockIdx.y * kTinyBN);
+}
+
 int sm_count() {
   static int cached[64] = {0};
   int dev = 0;
@@ -30,11 +35,19 @@ int sm_count() {
   return cached[dev];
 }
 
-// Output tile: the largest of 64, 32, 16 whose grid still covers every SM (a product of a few large
+// Otherwise the output tile is the largest of 64, 32, 16 whose grid still covers every SM (a product of a few large
 // tiles would leave most of the FP64 pipes idle); 16 when even that does not.
 template <typename Real>
 void launch_slices(const GemmArgs<typename CplxOf<Real>::T>& a, cudaStream_t st) {
   if (a.M <= 0 || a.N <= 0 || a.K <= 0) return;
+  if (a.L1 <= kTinyL && a.L2 <= kTinyL) {
+    dim3 grid((a.M + kTinyBM - 1) / kTinyBM, (a.N + kTinyBN - 1) / kTinyBN, a.K);
+    TS_REQUIRE(grid.y <= 65535 && grid.z <= 65535, "slice GEMM grid too large");
+    k_gemm_tiny<Real><<<grid, kTinyThreads, 0, st>>>(a);
+    count_launch();
+    TS_CUDA(cudaGetLastError());
+    return;
+  }
   const long long sms = sm_count();
   auto ctas = [&](int t) { return (long long)a.K * ((a.M + t - 1) / t) * ((a.N + t - 1) / t); };
   const int tile = ctas(64) >= sms ? 64 : (ctas(32) >= sms ? 32 : 16);

@@ -169,14 +169,16 @@ void set_max_dynamic_smem(const void* func, int bytes);
 
 // ---------------- FFT along mode 3 (fft_tube.cu) ----------------
 // Forward: out[k*T + e] = sum_{t<p} in[t*T + e] exp(-2 pi i k t / p), k < K = p/2+1.
+// gate (device, may be null) in this and the inverse: when *gate == 0 the kernel returns at once
+// (a launched-ahead step of a restart cycle that has already ended).
 template <typename Real, typename Cplx>
-void rfft_tube(const Real* in, Cplx* out, long long T, int p, cudaStream_t st);
+void rfft_tube(const Real* in, Cplx* out, long long T, int p, cudaStream_t st, const int* gate = nullptr);
 // Inverse: out[t*T + e] = (1/p) sum over the full Hermitian spectrum; mode selects the epilogue.
 enum IrfftMode { IRFFT_STORE = 0, IRFFT_RESIDUAL = 1 };
 // IRFFT_STORE: out = y.  IRFFT_RESIDUAL: out = C - y and partials[b] = block sums of out^2.
 template <typename Real, typename Cplx>
 void irfft_tube(const Cplx* in, Real* out, long long T, int p, int mode, const Real* C,
-                double* partials, cudaStream_t st);
+                double* partials, cudaStream_t st, const int* gate = nullptr);
 
 // Spectral Krylov basis: out_k = alpha * sqrt(w_k / p) * in_k (inverse: sqrt(p / w_k)) over K = p/2+1
 // slices of T entries, w_k = 1 for k = 0 and p/2, else 2; real slices get zero imaginary parts.
@@ -196,6 +198,7 @@ struct GemmArgs {
   Cplx* Y; long long sY; int ldy;
   int M, N, K, nyq;
   double sgn2;
+  const int* gate;   // device, may be null: when *gate == 0 the product is skipped (see rfft_tube)
 };
 using ZGemmArgs = GemmArgs<double2>;
 using CGemmArgs = GemmArgs<float2>;
@@ -234,6 +237,15 @@ void ks_step(void* state, int m, int j, int method, const double* Pnorm, cudaStr
              cudaGraphConditionalHandle handle = 0, const double* stop = nullptr);
 // Solve for y over the first k columns; result in the state's y array.
 void ks_solve(void* state, int m, int k, int method, cudaStream_t st);
+// Inner step j after W = M(V_j), in one launch for short vectors (arnoldi_small_ok(N)): the MGS sweep
+// against V_0..V_j (writing column j of H), h_{j+1,j} = ||W||, the ks_step update (same handle and
+// stop semantics) and V_{j+1} = W / h_{j+1,j} (always formed; W itself is left as M(V_j)).  The basis
+// vectors are V + i ldv.  gate (device, may be null): the kernel returns at once when *gate == 0,
+// and sets *gate = 0 where ks_step would end a graph-captured cycle (stop must then be given).
+bool arnoldi_small_ok(long long N);
+template <typename T>
+void arnoldi_small(T* W, T* V, long long ldv, long long N, int j, int m, void* state, int method, cudaStream_t st,
+                   cudaGraphConditionalHandle handle = 0, const double* stop = nullptr, int* gate = nullptr);
 // Device addresses inside the state block.
 double* ks_H(void* state, int m);          // column-major (m+1) x m, H[i + (m+1)*j]
 double* ks_y(void* state, int m);

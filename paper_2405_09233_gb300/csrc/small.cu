@@ -53,13 +53,27 @@ __global__ void k_ks_init(double* st, int m, const double* beta_in) {
 // last step) and the kernel decides whether the cycle goes on: it sets that handle to 0 on breakdown,
 // a bad step, an estimate <= stop[0] (the tolerance times ||C||) or <= stop[1] (the inner tolerance
 // of mixed precision, or -1).
-__global__ void k_ks_step(double* st, int m, int j, int method, const double* Pnorm,
-                          cudaGraphConditionalHandle handle, const double* stop) {
+// Columns of the Givens state staged in shared memory (tGMRES, m <= kStageMax): thread 0 then
+// rotates without a chain of dependent global loads (~0.7 us each; ~8 us at j = 10 before).
+constexpr int kStageMax = 256;
+
+// Step j's update given h_{j+1,j} = hn; called by every thread of the block (one block).
+__device__ void ks_update(double* st, int m, int j, int method, double hn, cudaGraphConditionalHandle handle,
+                          const double* stop, int* gate = nullptr) {
+  __shared__ double s_col[kStageMax + 2], s_cs[kStageMax], s_sn[kStageMax];
   Layout L{m};
-  const double hn = sqrt(finalize_partials(Pnorm));
-  if (threadIdx.x != 0) return;
   double* H = st + L.H();
   const int ld = m + 1;
+  const bool staged = method == 0 && m <= kStageMax;
+  if (staged) {
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = H[i + ld * j];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+      s_cs[i] = st[L.cs() + i];
+      s_sn[i] = st[L.sn() + i];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
   H[(j + 1) + ld * j] = hn;
   const double beta = st[L.beta()];
   double flags = (hn <= kBreakdownRel * beta) ? 1.0 : 0.0;
@@ -69,13 +83,18 @@ __global__ void k_ks_step(double* st, int m, int j, int method, const double* Pn
     double* cs = st + L.cs();
     double* sn = st + L.sn();
     double* g = st + L.g();
-    for (int i = 0; i <= j + 1; ++i) R[i + ld * j] = H[i + ld * j];
+    double* col = staged ? s_col : R + ld * j;
+    const double* c_cs = staged ? s_cs : cs;
+    const double* c_sn = staged ? s_sn : sn;
+    if (!staged)
+      for (int i = 0; i <= j; ++i) col[i] = H[i + ld * j];
+    col[j + 1] = hn;
     for (int i = 0; i < j; ++i) {
-      const double a = R[i + ld * j], b = R[i + 1 + ld * j];
-      R[i + ld * j] = cs[i] * a + sn[i] * b;
-      R[i + 1 + ld * j] = -sn[i] * a + cs[i] * b;
+      const double a = col[i], b = col[i + 1];
+      col[i] = c_cs[i] * a + c_sn[i] * b;
+      col[i + 1] = -c_sn[i] * a + c_cs[i] * b;
     }
-    const double a = R[j + ld * j], b = R[j + 1 + ld * j];
+    const double a = col[j], b = col[j + 1];
     const double r = hypot(a, b);
     double c = 1.0, s = 0.0;
     if (r > 0.0) {
@@ -84,10 +103,13 @@ __global__ void k_ks_step(double* st, int m, int j, int method, const double* Pn
     }
     cs[j] = c;
     sn[j] = s;
-    R[j + ld * j] = r;
-    R[j + 1 + ld * j] = 0.0;
-    g[j + 1] = -s * g[j];
-    g[j] = c * g[j];
+    col[j] = r;
+    col[j + 1] = 0.0;
+    if (staged)
+      for (int i = 0; i <= j + 1; ++i) R[i + ld * j] = col[i];
+    const double gj = g[j];
+    g[j + 1] = -s * gj;
+    g[j] = c * gj;
     est = fabs(g[j + 1]);
   } else {
     // Gaussian elimination with partial pivoting on H_k (k = j+1), right-hand side beta e1.
@@ -140,20 +162,126 @@ __global__ void k_ks_step(double* st, int m, int j, int method, const double* Pn
   st[L.est() + 3] = flags;
   st[L.est() + 4] = j + 1;
   st[L.hist() + j] = est;
-  if (handle) {
+  if (handle || gate) {
     const bool go = flags == 0.0 && !(est <= stop[0]) && !(est <= stop[1]);
-    if (!go) cudaGraphSetConditional(handle, 0);
+    if (!go) {
+      if (handle) cudaGraphSetConditional(handle, 0);
+      if (gate) *gate = 0;
+    }
+  }
+}
+
+__global__ void k_ks_step(double* st, int m, int j, int method, const double* Pnorm,
+                          cudaGraphConditionalHandle handle, const double* stop) {
+  const double hn = sqrt(finalize_partials(Pnorm));
+  ks_update(st, m, j, method, hn, handle, stop);
+}
+
+// Everything of inner step j after W = M(V_j), for vectors short enough for one block of nt <= 512
+// threads (N <= nt R):
+// the modified Gram-Schmidt sweep h_ij = <V_i, W>, W -= h_ij V_i (i = 0..j, in order), the norm
+// h_{j+1,j} = ||W||, the Givens / Hessenberg update (ks_update) and V_{j+1} = W / h_{j+1,j}.  At
+// n = s = 24, p = 4 the multi-block form took ~85 us per step in j + 5 launches, most of it global
+// round trips of one short reduction after another; here W stays in registers, the next V_i is
+// loaded while the current inner product is reduced, and one launch does it all.  Same arithmetic
+// as the multi-block kernels (FP64 sums; an FP32 basis sums each thread's products in FP32 first),
+// in a different summation order.  The block is only as wide as N needs (nt = N / R rounded up to
+// whole warps): one SM issues 2 DFMA per clock, so every padded lane's dot and update cost as much
+// as a real one.
+template <typename T, int R>
+__global__ void __launch_bounds__(512, 1) k_arnoldi_small(T* __restrict__ W, T* __restrict__ V, long long ldv,
+                                                          int N, int j, int m, double* st, int method,
+                                                          cudaGraphConditionalHandle handle, const double* stop,
+                                                          int* gate) {
+  if (gate && *gate == 0) return;   // launched ahead of a cycle that has already ended
+  Layout L{m};
+  double* H = st + L.H();
+  const int ld = m + 1;
+  const int t = threadIdx.x, nt = blockDim.x;
+  T w[R], v[R], vn[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = t + nt * r;
+    w[r] = e < N ? W[e] : T(0);
+    v[r] = e < N ? V[e] : T(0);
+  }
+  auto dot = [&](const T (&x)[R]) {
+    if constexpr (sizeof(T) == 4) {
+      float f = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) f = fmaf(x[r], w[r], f);
+      return (double)f;
+    } else {
+      double acc = 0.0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc += x[r] * w[r];
+      return acc;
+    }
+  };
+  for (int i = 0; i <= j; ++i) {
+    const double part = dot(v);
+    if (i < j) {
+      const T* Vn = V + (long long)(i + 1) * ldv;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int e = t + nt * r;
+        vn[r] = e < N ? Vn[e] : T(0);
+      }
+    }
+    const double h = block_sum(part);
+    if (t == 0) H[i + ld * j] = h;
+    const T hT = (T)h;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      w[r] = w[r] - hT * v[r];
+      v[r] = vn[r];
+    }
+  }
+  const double hn = sqrt(block_sum(dot(w)));
+  ks_update(st, m, j, method, hn, handle, stop, gate);
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  T* Vj1 = V + (long long)(j + 1) * ldv;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = t + nt * r;
+    if (e < N) {
+      if constexpr (sizeof(T) == 4) Vj1[e] = w[r] * (float)inv;
+      else Vj1[e] = w[r] * inv;
+    }
   }
 }
 
 // tGMRES: back substitution R_k y = g_k.  tFOM: y is already the solution of the last step.
+// R_k and g_k are staged in shared memory first (k <= kSolveStage) so that one thread's substitution
+// does not wait on a global load per term (~29 us at k = 18 before).
+constexpr int kSolveStage = 64;
 __global__ void k_ks_solve(double* st, int m, int k, int method) {
-  if (threadIdx.x != 0 || method != 0) return;
+  if (method != 0) return;
+  __shared__ double sR[kSolveStage * kSolveStage], sg[kSolveStage], sy[kSolveStage];
   Layout L{m};
   const int ld = m + 1;
   const double* R = st + L.R();
   const double* g = st + L.g();
   double* y = st + L.y();
+  const bool staged = k <= kSolveStage;
+  if (staged) {
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int r = e % k, q = e / k;
+      sR[r + kSolveStage * q] = R[r + ld * q];
+    }
+    for (int r = threadIdx.x; r < k; r += blockDim.x) sg[r] = g[r];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  if (staged) {
+    for (int r = k - 1; r >= 0; --r) {
+      double v = sg[r];
+      for (int q = r + 1; q < k; ++q) v -= sR[r + kSolveStage * q] * sy[q];
+      sy[r] = v / sR[r + kSolveStage * r];
+    }
+    for (int r = 0; r < k; ++r) y[r] = sy[r];
+    return;
+  }
   for (int r = k - 1; r >= 0; --r) {
     double v = g[r];
     for (int q = r + 1; q < k; ++q) v -= R[r + ld * q] * y[q];
@@ -184,8 +312,28 @@ void ks_step(void* state, int m, int j, int method, const double* Pnorm, cudaStr
   TS_CUDA(cudaGetLastError());
 }
 
+bool arnoldi_small_ok(long long N) { return N >= 1 && N <= 512 * 16; }
+
+template <typename T>
+void arnoldi_small(T* W, T* V, long long ldv, long long N, int j, int m, void* state, int method, cudaStream_t st,
+                   cudaGraphConditionalHandle handle, const double* stop, int* gate) {
+  TS_REQUIRE(arnoldi_small_ok(N) && j >= 0 && j < m, "arnoldi_small: bad size");
+  double* s = static_cast<double*>(state);
+  const int n = (int)N;
+  auto threads = [&](int R) { return (int)((N + 32LL * R - 1) / (32LL * R) * 32); };   // <= 512
+  if (N <= 512 * 4) k_arnoldi_small<T, 4><<<1, threads(4), 0, st>>>(W, V, ldv, n, j, m, s, method, handle, stop, gate);
+  else if (N <= 512 * 8) k_arnoldi_small<T, 8><<<1, threads(8), 0, st>>>(W, V, ldv, n, j, m, s, method, handle, stop, gate);
+  else k_arnoldi_small<T, 16><<<1, threads(16), 0, st>>>(W, V, ldv, n, j, m, s, method, handle, stop, gate);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+template void arnoldi_small<double>(double*, double*, long long, long long, int, int, void*, int, cudaStream_t,
+                                    cudaGraphConditionalHandle, const double*, int*);
+template void arnoldi_small<float>(float*, float*, long long, long long, int, int, void*, int, cudaStream_t,
+                                   cudaGraphConditionalHandle, const double*, int*);
+
 void ks_solve(void* state, int m, int k, int method, cudaStream_t st) {
-  k_ks_solve<<<1, 32, 0, st>>>(static_cast<double*>(state), m, k, method);
+  k_ks_solve<<<1, 256, 0, st>>>(static_cast<double*>(state), m, k, method);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }

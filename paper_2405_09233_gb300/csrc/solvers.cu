@@ -6,12 +6,15 @@
 //             device gives the residual estimate; stop early when it reaches the tolerance;
 //             V_{j+1} = W / h_{j+1,j}.  Then y, X += V_k (*) y, and the true residual.
 // The host reads 4 doubles per inner step (estimate, 1/h, h, flags) to decide whether to stop --
-// except for small problems, which are bound by launch latency and by that look at every step:
-// from their second cycle on, a restart cycle runs as one CUDA graph in which step j is the body of a
-// conditional (IF)
-// node (step j + 1's node nested inside it) and the step's Givens / Hessenberg kernel switches the
-// remaining steps off on the device, so the host looks once per cycle.  Both forms run the same
-// kernels in the same order, so they give identical results.
+// except for small problems, which are bound by launch latency and by that look at every step.
+// Vectors of at most 8192 entries run everything after W = M(V_j) in one launch (arnoldi_small), and
+// on the FP64 DFMA engine (real basis, dense operator) a cycle's steps are launched ahead in chunks
+// behind a device gate that the step ending the cycle closes, so the host looks once per chunk.
+// Other problems of at most kGraphCycleMaxN unknowns run, from their second cycle on, each restart
+// cycle as one CUDA graph in which step j is the body of a conditional (IF) node (step j + 1's node
+// nested inside it) and the step's Givens / Hessenberg kernel switches the remaining steps off on the
+// device, so the host looks once per cycle.  All forms run the same kernels in the same order, so
+// they give identical results.
 //
 // Mixed precision: the Arnoldi cycle (basis, W, operator) runs in FP32 storage with a FP32 or
 // tensor-core operator, while R = C - M(X), the small problem, and X += ||R|| (V (*) y) stay in
@@ -179,15 +182,31 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
   // Hessenberg update (which, inside a graph, also decides whether the cycle goes on), and
   // V_{j+1} = W / h_{j+1,j} when `scale_next` (the graph always forms it; unused after the last step).
   double* stop_dev = sc + 8;   // [tol ||C||, inner threshold or -1] for the graph's stopping test
+  const bool small_steps = arnoldi_small_ok(Nb);   // the post-apply part of a step is one launch
+  // Small FP64 problems on the DFMA engine: a cycle's steps are launched ahead, kAheadChunk at a
+  // time, without waiting for each step's estimate; a step that ends the cycle closes a device gate
+  // and the kernels of the steps launched after it return at once.  (Each step of such a problem
+  // is a few short kernels; the host round trip per step had cost about as much as they do.)
+  const char* no_ahead = std::getenv("TSTAR_NO_LAUNCH_AHEAD");
+  const bool ahead = small_steps && sizeof(T) == 8 && !mixed && !spectral && !op->sp && !ozaki &&
+                     !ctx->timer.enabled && !(no_ahead && no_ahead[0] == '1');
+  constexpr int kAheadChunk = 8;
+  int* gate = ahead ? static_cast<int*>(ctx->ws.get("krylov_gate", sizeof(int))) : nullptr;
   auto inner_step = [&](int j, cudaGraphConditionalHandle handle, bool scale_next, cudaStream_t q) {
     if constexpr (sizeof(T) == 8) {
       if (spectral)   // W = M(V_j) slice by slice: the scaling commutes with the per-slice operator
         apply_f64_spectral(ctx, op, reinterpret_cast<const double2*>(basis_ptr(V, Nb, j)),
                            reinterpret_cast<double2*>(W), q);
+      else if (ahead)
+        apply_f64(ctx, op, basis_ptr(V, Nb, j), W, IRFFT_STORE, nullptr, nullptr, q, gate);
       else
         apply_basis(ctx, op, prec, basis_ptr(V, Nb, j), W, q);     // W = M(V_j)
     } else {
       apply_basis(ctx, op, prec, basis_ptr(V, Nb, j), W, q);
+    }
+    if (small_steps) {   // sweep, norm, Givens / Hessenberg update and V_{j+1} in one launch
+      arnoldi_small<T>(W, V, Nb, Nb, j, m, state, method, q, handle, stop_dev, ahead ? gate : nullptr);
+      return;
     }
     dot_partials<T>(basis_ptr(V, Nb, 0), W, Nb, Pp[0], q);
     for (int i = 0; i <= j; ++i) {                                  // MGS sweep, fused with the next dot
@@ -210,7 +229,8 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
     scale_dev<double, T>(R, basis_ptr(V, Nb, 0), N, sc + 3, q);
   };
   const char* no_graph = std::getenv("TSTAR_NO_GRAPH_CYCLE");
-  const bool graph_allowed = !ctx->timer.enabled && N <= kGraphCycleMaxN && !(no_graph && no_graph[0] == '1');
+  const bool graph_allowed =
+      !ahead && !ctx->timer.enabled && N <= kGraphCycleMaxN && !(no_graph && no_graph[0] == '1');
   std::unique_ptr<CycleGraph> cg;
   // Built when a second cycle starts: a one-cycle solve would not earn the graph back, and by then every
   // workspace buffer, operator copy and tuning choice a step needs exists (nothing may allocate or
@@ -293,6 +313,33 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
       info.iters += k;
       if (mixed) info.applies_low += k; else info.applies_fp64 += k;
       last_est = k > 0 ? hhist[k - 1] : last_est;
+    } else if (ahead) {
+      double* hstop = hs + 64;
+      hstop[0] = o.tol * normC;
+      hstop[1] = -1.0;
+      TS_CUDA(cudaMemcpyAsync(stop_dev, hstop, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+      TS_CUDA(cudaMemsetAsync(gate, 1, sizeof(int), st));    // non-zero: the cycle goes on
+      ks_init(state, m, sc + 2, st);
+      init_v1(st);
+      double* hest = hs + 96;
+      double* hhist = hs + 256;
+      int launched = 0;
+      while (launched < m) {
+        const int upto = std::min(m, launched + kAheadChunk);
+        for (int j = launched; j < upto; ++j) inner_step(j, 0, true, st);
+        launched = upto;
+        TS_CUDA(cudaMemcpyAsync(hest, ks_est(state, m), 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TS_CUDA(cudaStreamSynchronize(st));
+        k = (int)hest[4];
+        if (k < launched || (int)hest[3] != 0 || hest[0] <= o.tol * normC) break;   // the cycle has ended
+      }
+      TS_CUDA(cudaMemcpyAsync(hhist, ks_hist(state, m), m * sizeof(double), cudaMemcpyDeviceToHost, st));
+      TS_CUDA(cudaStreamSynchronize(st));
+      flags = hest[3];
+      for (int j = 0; j < k; ++j) push_hist(hhist[j]);
+      info.iters += k;
+      info.applies_fp64 += k;
+      last_est = k > 0 ? hhist[k - 1] : last_est;
     } else {
       ks_init(state, m, sc + 2, st);
       init_v1(st);
@@ -310,7 +357,7 @@ ts_status krylov_solve(ts_ctx* ctx, ts_op* op, const double* C, double* X, const
         const bool broke = ((int)flags & 1) != 0;
         const bool bad = ((int)flags & 6) != 0;
         if (bad || broke || est <= o.tol * normC || (mixed && est <= inner_tol * res)) break;
-        scale_dev<T, T>(W, basis_ptr(V, Nb, j + 1), Nb, ks_est(state, m) + 1, st);  // V_{j+1} = W / h
+        if (!small_steps) scale_dev<T, T>(W, basis_ptr(V, Nb, j + 1), Nb, ks_est(state, m) + 1, st);  // V_{j+1}
       }
     }
     ++info.cycles;
