@@ -814,7 +814,7 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
     int n_titems = 0, n_pitems = 0;
   };
   TcTables tct;
-  int tc_bn = kBatchTcBNs[0];
+  int tc_bn = tc_batch_sched(kBatchTcBNs[0], false);   // product schedule (column tile, persistent)
   if (tcin) {
     std::vector<size_t> poff(count);
     size_t ptot = 0;
@@ -884,33 +884,46 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
              std::to_string(plan.inst[i].K);
     if (!ctx->tune_loaded) tune_load(ctx);
     const auto tuned = ctx->tune.find(key);
-    std::vector<TcTables> cand_tables;
-    std::vector<int> cands;
+    // Candidates: every usable column tile, each with the one-CTA-per-item and the persistent
+    // schedule (tc_batch_sched); tables exist once per column tile.
+    std::vector<int> bns, cands;
+    std::vector<TcTables> bn_tables;
     int smax = 0;
     for (int i = 0; i < count; ++i) smax = std::max(smax, plan.inst[i].s);
-    for (int bn : kBatchTcBNs)
-      if ((bn == kBatchTcBNs[0] || bn / 2 < smax) && (tuned == ctx->tune.end() || tuned->second == bn)) {
-        cands.push_back(bn);
-        cand_tables.push_back(build_tables(bn));
+    auto add_cands = [&](bool only_cached) {
+      for (int bn : kBatchTcBNs) {
+        if (!(bn == kBatchTcBNs[0] || bn / 2 < smax)) continue;
+        bool any = false;
+        for (bool pers : {false, true}) {
+          const int c = tc_batch_sched(bn, pers);
+          if (only_cached && tuned->second != c) continue;
+          cands.push_back(c);
+          any = true;
+        }
+        if (any) {
+          bns.push_back(bn);
+          bn_tables.push_back(build_tables(bn));
+        }
       }
+    };
+    add_cands(tuned != ctx->tune.end());
     if (cands.empty()) {   // a cached choice this batch cannot use: tune again
       ctx->tune.erase(key);
-      for (int bn : kBatchTcBNs)
-        if (bn == kBatchTcBNs[0] || bn / 2 < smax) {
-          cands.push_back(bn);
-          cand_tables.push_back(build_tables(bn));
-        }
+      add_cands(false);
     }
+    auto tables_of = [&](int c) -> const TcTables& {
+      return bn_tables[std::find(bns.begin(), bns.end(), tc_batch_bn(c)) - bns.begin()];
+    };
     TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
     tc_bn = tune_pick(
         ctx, key, cands,
-        [&](int bn) {
-          const TcTables& t = cand_tables[std::find(cands.begin(), cands.end(), bn) - cands.begin()];
-          tc_batch_products(o.precision, bn, t.planes, t.pitems, t.n_pitems, t.maps, t.inst, d.act, t.titems,
+        [&](int c) {
+          const TcTables& t = tables_of(c);
+          tc_batch_products(o.precision, c, t.planes, t.pitems, t.n_pitems, t.maps, t.inst, d.act, t.titems,
                             t.n_titems, tc_err, st);
         },
         st);
-    tct = cand_tables[std::find(cands.begin(), cands.end(), tc_bn) - cands.begin()];
+    tct = tables_of(tc_bn);
     TS_CUDA(cudaMemsetAsync(tc_err, 0, sizeof(int) * 4, st));
   }
   // Emulated-FP64 slice products of every instance (X -> Y, spectral FP64), each gated on the device

@@ -24,6 +24,7 @@
 // Stages are recycled through full/empty mbarriers; tcgen05.commit arrives on "empty" when the
 // MMAs reading a stage have completed.  Every wait is bounded: on expiry the kernel records an
 // error code, skips the rest of its work, still frees its TMEM and returns.
+#include <algorithm>
 #include <cstdlib>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -249,6 +250,217 @@ __global__ void __launch_bounds__(192, 1)
   if (!active[it.x]) return;   // instance not in the current inner cycle (uniform over the CTA)
   const BTcInst& b = inst[it.x];
   tc_sylv_tile<BN, ESZ, PARTS>(maps[it.x], b.Y, b.n, b.s, b.nyq, it.y, it.z, it.w, err, 0, kWaitNs);
+}
+
+// Persistent batched form: gridDim.x CTAs (at most one per SM) walk the cost-sorted work list with
+// stride gridDim.x, skipping instances outside the current inner cycle.  Barriers are initialised
+// and tensor memory is allocated once per CTA; the TMA / MMA stage ring runs on from one item to the
+// next (one stage counter for the whole walk), and two accumulator sets in tensor memory let the
+// epilogue of item t drain while item t + 1 is multiplied (acc_full / acc_empty barriers per set).
+// Per item the MMAs and their order are those of k_b_tc, so both give bitwise the same products.
+// Every wait is bounded; after an expired wait each role stops where it is, the producer waits for
+// the stages it loaded, the MMA warp for the MMAs it issued, and tensor memory is freed.
+template <int BN, int ESZ, int PARTS>
+__global__ void __launch_bounds__(192, 1)
+    k_b_tc_persist(const TcMaps* __restrict__ maps, const BTcInst* __restrict__ inst, const int* __restrict__ active,
+                   const int4* __restrict__ items, int nitems, int* err) {
+  using Cfg = TcCfg<BN, ESZ>;
+  constexpr int kCols = 2 * Cfg::kTmemCols;   // two accumulator sets of (Re, Im)
+  static_assert(kCols <= 512, "tensor memory");
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStage);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * Cfg::kStages + 5);
+  const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + Cfg::kStages);
+  const uint32_t bar_accf = smem_u32(bars + 2 * Cfg::kStages);       // [2]: accumulator set ready
+  const uint32_t bar_acce = smem_u32(bars + 2 * Cfg::kStages + 2);   // [2]: accumulator set drained
+  const uint32_t bar_done = smem_u32(bars + 2 * Cfg::kStages + 4);   // every issued MMA completed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < Cfg::kStages; ++q) {
+      mbar_init(bar_full + 8 * q, 1);
+      mbar_init(bar_empty + 8 * q, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar_accf + 8 * b, 1);
+      mbar_init(bar_acce + 8 * b, 4);   // one arrival per epilogue warp
+    }
+    mbar_init(bar_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  auto iters_of = [&](const BTcInst& b) {
+    return PARTS * ((b.n + Cfg::kElemsK - 1) / Cfg::kElemsK + (b.s + Cfg::kElemsK - 1) / Cfg::kElemsK);
+  };
+
+  if (warp == 4) {
+    if (lane == 0) {
+      long long g = 0, issued = 0;   // stages walked / whose loads were issued
+      bool ok = true;
+      for (int q = blockIdx.x; q < nitems && ok; q += gridDim.x) {
+        const int4 it = items[q];
+        if (!active[it.x]) continue;
+        const BTcInst& b = inst[it.x];
+        const TcMaps& m = maps[it.x];
+        const int k = it.y, i0 = it.z, j0 = it.w;
+        const bool real = (k == 0) || (k == b.nyq);
+        const int it1 = (b.n + Cfg::kElemsK - 1) / Cfg::kElemsK, iters = iters_of(b);
+        for (int u = 0; u < iters; ++u, ++g) {
+          const int slot = (int)(g % Cfg::kStages);
+          const uint32_t phase = (uint32_t)(g / Cfg::kStages) & 1u;
+          if (!mbar_wait(bar_empty + 8 * slot, phase ^ 1u, err, 1)) {
+            ok = false;
+            break;
+          }
+          const uint32_t full = bar_full + 8 * slot;
+          mbar_expect_tx(full, real ? Cfg::kTileA + Cfg::kTileB : Cfg::kStage);
+          const uint32_t sA = base + slot * Cfg::kStage;
+          const uint32_t sAi = sA + Cfg::kTileA, sB = sA + 2 * Cfg::kTileA, sBi = sB + Cfg::kTileB;
+          const int blk = u / PARTS, part = u % PARTS;
+          const bool alo = part == 2, blo = part == 1;
+          if (blk < it1) {
+            const int l0 = blk * Cfg::kElemsK;
+            tma_load_3d(sA, alo ? &m.a_re_lo : &m.a_re, l0, i0, k, full);
+            tma_load_3d(sB, blo ? &m.xc_re_lo : &m.xc_re, l0, j0, k, full);
+            if (!real) {
+              tma_load_3d(sAi, alo ? &m.a_im_lo : &m.a_im, l0, i0, k, full);
+              tma_load_3d(sBi, blo ? &m.xc_im_lo : &m.xc_im, l0, j0, k, full);
+            }
+          } else {
+            const int l0 = (blk - it1) * Cfg::kElemsK;
+            tma_load_3d(sA, alo ? &m.xr_re_lo : &m.xr_re, l0, i0, k, full);
+            tma_load_3d(sB, blo ? &m.b_re_lo : &m.b_re, l0, j0, k, full);
+            if (!real) {
+              tma_load_3d(sAi, alo ? &m.xr_im_lo : &m.xr_im, l0, i0, k, full);
+              tma_load_3d(sBi, blo ? &m.b_im_lo : &m.b_im, l0, j0, k, full);
+            }
+          }
+          issued = g + 1;
+        }
+      }
+      for (long long u = issued > Cfg::kStages ? issued - Cfg::kStages : 0; u < issued; ++u)
+        mbar_wait(bar_full + 8 * (int)(u % Cfg::kStages), (uint32_t)(u / Cfg::kStages) & 1u, err, 4);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      constexpr int fmt = ESZ == 2 ? 1 : 2;
+      constexpr uint32_t idp = make_idesc(fmt, kTileM, BN, false);
+      constexpr uint32_t idn = make_idesc(fmt, kTileM, BN, true);
+      long long g = 0;
+      int t = 0;   // items multiplied by this CTA
+      bool ok = true;
+      for (int q = blockIdx.x; q < nitems && ok; q += gridDim.x) {
+        const int4 it = items[q];
+        if (!active[it.x]) continue;
+        const BTcInst& b = inst[it.x];
+        const bool real = (it.y == 0) || (it.y == b.nyq);
+        const int it1 = (b.n + Cfg::kElemsK - 1) / Cfg::kElemsK, iters = iters_of(b);
+        const int set = t & 1;
+        // the epilogue has drained this accumulator set's previous item (t - 2)
+        if (t >= 2 && !mbar_wait(bar_acce + 8 * set, (uint32_t)((t >> 1) + 1) & 1u, err, 6)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d_re = tmem + set * Cfg::kTmemCols, d_im = d_re + BN;
+        for (int u = 0; u < iters; ++u, ++g) {
+          const int slot = (int)(g % Cfg::kStages);
+          const uint32_t phase = (uint32_t)(g / Cfg::kStages) & 1u;
+          if (!mbar_wait(bar_full + 8 * slot, phase, err, 2)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sA = base + slot * Cfg::kStage;
+          const uint64_t dAr = smem_desc_sw128(sA), dAi = smem_desc_sw128(sA + Cfg::kTileA);
+          const uint64_t dBr = smem_desc_sw128(sA + 2 * Cfg::kTileA);
+          const uint64_t dBi = smem_desc_sw128(sA + 2 * Cfg::kTileA + Cfg::kTileB);
+#pragma unroll
+          for (int kk = 0; kk < Cfg::kSubK; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 2);
+            const uint32_t first = (u == 0 && kk == 0) ? 0u : 1u;
+            if (u / PARTS < it1) {
+              mma_issue(d_re, dAr + o, dBr + o, idp, first, ESZ == 4);
+              if (!real) {
+                mma_issue(d_re, dAi + o, dBi + o, idn, 1u, ESZ == 4);
+                mma_issue(d_im, dAi + o, dBr + o, idp, first, ESZ == 4);
+                mma_issue(d_im, dAr + o, dBi + o, idp, 1u, ESZ == 4);
+              }
+            } else {
+              mma_issue(d_re, dAr + o, dBr + o, idn, 1u, ESZ == 4);
+              if (!real) {
+                mma_issue(d_re, dAi + o, dBi + o, idp, 1u, ESZ == 4);
+                mma_issue(d_im, dAr + o, dBi + o, idn, 1u, ESZ == 4);
+                mma_issue(d_im, dAi + o, dBr + o, idn, 1u, ESZ == 4);
+              }
+            }
+          }
+          mma_commit(bar_empty + 8 * slot);
+        }
+        if (!ok) break;
+        mma_commit(bar_accf + 8 * set);
+        ++t;
+      }
+      // every MMA issued (also on an error path) completes before tensor memory is freed
+      mma_commit(bar_done);
+      mbar_wait(bar_done, 0u, err, 5);
+    }
+  } else {
+    // Epilogue: warp w reads TMEM lanes 32w..32w+31 (= output rows i0 + 32w + lane) of set t & 1.
+    int t = 0;
+    for (int q = blockIdx.x; q < nitems; q += gridDim.x) {
+      const int4 it = items[q];
+      if (!active[it.x]) continue;
+      const BTcInst& b = inst[it.x];
+      const int k = it.y, i0 = it.z, j0 = it.w;
+      const bool real = (k == 0) || (k == b.nyq);
+      const int set = t & 1;
+      if (!mbar_wait(bar_accf + 8 * set, (uint32_t)(t >> 1) & 1u, err, 3)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = i0 + warp * 32 + lane;
+      float2* Yk = b.Y + (long long)k * b.n * b.s;
+      const uint32_t lane_base = tmem + set * Cfg::kTmemCols + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float re[32], im[32];
+        tmem_ld32(lane_base + c0, re);
+        if (!real) {
+          tmem_ld32(lane_base + BN + c0, im);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) im[c] = 0.f;
+        }
+        if (row < b.n) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            const int j = j0 + c0 + c;
+            if (j < b.s) Yk[(long long)j * b.n + row] = make_float2(re[c], im[c]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_acce + 8 * set);
+      ++t;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 5) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  }
 }
 
 // Planar copies of the FP32 spectra of a batch: per (instance, slice, 32 x 32 tile) work item,
@@ -683,6 +895,17 @@ void batch_preload_bn() {
   cudaFuncAttributes fa;
   TS_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_b_tc<BN, ESZ, PARTS>));
   set_max_dynamic_smem((const void*)k_b_tc<BN, ESZ, PARTS>, Cfg::kSmem);
+  TS_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_b_tc_persist<BN, ESZ, PARTS>));
+  set_max_dynamic_smem((const void*)k_b_tc_persist<BN, ESZ, PARTS>, Cfg::kSmem);
+}
+
+int device_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  TS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return 152;
+  if (!cached[dev]) TS_CUDA(cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev));
+  return cached[dev];
 }
 
 template <typename OpT, int ESZ, int PARTS, bool SPLIT>
@@ -694,16 +917,26 @@ void batch_preload_t() {
 }
 
 template <typename OpT, int ESZ, int PARTS, bool SPLIT>
-void batch_products_t(int bn, const BTcPlanes* planes, const int4* pitems, int npitems, const TcMaps* maps,
+void batch_products_t(int sched, const BTcPlanes* planes, const int4* pitems, int npitems, const TcMaps* maps,
                       const BTcInst* inst, const int* active, const int4* items, int nitems, int* err,
                       cudaStream_t st) {
   k_b_planes<OpT, SPLIT><<<npitems, dim3(32, 8), 0, st>>>(planes, active, pitems);
   count_launch();
   TS_CUDA(cudaGetLastError());
-  if (bn == 128)
+  const int bn = tc_batch_bn(sched);
+  if (tc_batch_persistent(sched)) {
+    const int grid = std::min(nitems, device_sms());
+    if (bn == 128)
+      k_b_tc_persist<128, ESZ, PARTS><<<grid, 192, TcCfg<128, ESZ>::kSmem, st>>>(maps, inst, active, items, nitems,
+                                                                                err);
+    else
+      k_b_tc_persist<64, ESZ, PARTS><<<grid, 192, TcCfg<64, ESZ>::kSmem, st>>>(maps, inst, active, items, nitems,
+                                                                              err);
+  } else if (bn == 128) {
     k_b_tc<128, ESZ, PARTS><<<nitems, 192, TcCfg<128, ESZ>::kSmem, st>>>(maps, inst, active, items, err);
-  else
+  } else {
     k_b_tc<64, ESZ, PARTS><<<nitems, 192, TcCfg<64, ESZ>::kSmem, st>>>(maps, inst, active, items, err);
+  }
   count_launch();
   TS_CUDA(cudaGetLastError());
 }
@@ -766,16 +999,17 @@ void tc_batch_preload(int precision) {
   else batch_preload_t<float, 4, 3, true>();
 }
 
-void tc_batch_products(int precision, int bn, const BTcPlanes* planes, const int4* pitems, int npitems,
+void tc_batch_products(int precision, int sched, const BTcPlanes* planes, const int4* pitems, int npitems,
                        const TcMaps* maps, const BTcInst* inst, const int* active, const int4* items, int nitems,
                        int* err, cudaStream_t st) {
+  TS_REQUIRE(nitems > 0 && npitems > 0, "tc_batch_products: empty work list");
   if (precision == TS_MIXED_BF16)
-    batch_products_t<__nv_bfloat16, 2, 1, false>(bn, planes, pitems, npitems, maps, inst, active, items, nitems, err,
-                                                 st);
+    batch_products_t<__nv_bfloat16, 2, 1, false>(sched, planes, pitems, npitems, maps, inst, active, items, nitems,
+                                                 err, st);
   else if (precision == TS_MIXED_TF32)
-    batch_products_t<float, 4, 1, false>(bn, planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
+    batch_products_t<float, 4, 1, false>(sched, planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
   else
-    batch_products_t<float, 4, 3, true>(bn, planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
+    batch_products_t<float, 4, 3, true>(sched, planes, pitems, npitems, maps, inst, active, items, nitems, err, st);
 }
 
 double gemm_flops_tc(int n, int s, int K, int nyq) {

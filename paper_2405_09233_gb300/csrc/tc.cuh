@@ -62,15 +62,20 @@ struct BTcPlanes {
 };
 // Column tiles the batched kernel supports (chosen per batch by the autotuner).
 constexpr int kBatchTcBNs[2] = {64, 128};
+// A batched product schedule, as the autotuner stores it: the column tile bn, plus 1 for the
+// persistent kernel (one CTA per SM walking the work list) instead of one CTA per work item.
+inline int tc_batch_sched(int bn, bool persistent) { return bn + (persistent ? 1 : 0); }
+inline int tc_batch_bn(int sched) { return sched & ~1; }
+inline bool tc_batch_persistent(int sched) { return (sched & 1) != 0; }
 // Bytes of one instance's planar X copies (all planes) for `precision`.
 size_t tc_batch_plane_bytes(int n, int s, int K, int precision);
 // Fill `pl` (plane pointers carved from `base`) and `maps` (column tile bn) for one instance of a batch.
 void tc_batch_instance(ts_op* op, int precision, const float2* Xh, void* base, BTcPlanes* pl, TcMaps* maps, int bn);
 // Load the batched kernels and set their attributes (before any capture that records them).
 void tc_batch_preload(int precision);
-// Planar copies (planes work list) then the products (tiles work list, column tile bn) of the
+// Planar copies (planes work list) then the products (tiles work list, schedule sched) of the
 // active instances.
-void tc_batch_products(int precision, int bn, const BTcPlanes* planes, const int4* pitems, int npitems,
+void tc_batch_products(int precision, int sched, const BTcPlanes* planes, const int4* pitems, int npitems,
                        const TcMaps* maps, const BTcInst* inst, const int* active, const int4* items, int nitems,
                        int* err, cudaStream_t st);
 

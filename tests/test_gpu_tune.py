@@ -1,6 +1,7 @@
-"""The autotuner of the tcgen05 column tile: its choices are cached per context, persist through
+"""The autotuner of the tcgen05 column tile (and, for the batched solver, of the product schedule:
+one CTA per work item or a persistent CTA per SM): its choices are cached per context, persist through
 the TSTAR_TUNE_CACHE file, and do not change results (every output entry accumulates the same
-products in the same order whatever the tile width)."""
+products in the same order whatever the tile width or schedule)."""
 import numpy as np
 import pytest
 
@@ -112,6 +113,41 @@ def test_batched_tile_tuned(tmp_path, monkeypatch):
         st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, precision="mixed_bf16", engine="ozaki")
         assert st == 0 and all(x == 0 for x in sts)
         btc = [v for k, v in ctx.tune_entries().items() if k.startswith("btc:")]
-        assert len(btc) == 1 and btc[0] in (64, 128)
+        assert len(btc) == 1 and btc[0] in (64, 65, 128, 129)   # column tile, + 1 when persistent
         for op in ops:
             op.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed_bf16", "mixed_tf32x3"])
+def test_batched_schedules_agree_bitwise(tmp_path, monkeypatch, prec):
+    """Force each batched product schedule (column tile 64 or 128, one CTA per work item or the persistent
+    kernel walking the work list) through the cache file: the batched solves agree bit for bit."""
+    import torch
+    from paper_2405_09233_gb300 import Context
+    tag = _device_tag(tmp_path, monkeypatch)
+    shapes = [(96, 40, 4), (130, 150, 8), (64, 64, 2), (200, 90, 6)]   # ragged tiles, real and complex slices
+    key = f"btc:{PREC_CODE[prec]}:{len(shapes)}" + "".join(f":{n}x{s}x{p // 2 + 1}" for n, s, p in shapes)
+    probs = [inputs.dense_problem(n, s, p, seed=60 + i) for i, (n, s, p) in enumerate(shapes)]
+    Cs_h = [kr.sylv_apply(pr.A, pr.B, pr.Xstar) for pr in probs]
+    outs = {}
+    for sched in (64, 65, 128, 129):
+        cache = tmp_path / f"b_{sched}.txt"
+        cache.write_text(f"{tag} {key} {sched}\n")
+        monkeypatch.setenv("TSTAR_TUNE_CACHE", str(cache))
+        with Context(0) as ctx:
+            ops = [ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B)) for pr in probs]
+            Xs = [torch.zeros((p, s, n), dtype=torch.float64, device="cuda") for n, s, p in shapes]
+            st, infos, sts = ctx.batched_solve(ops, [to_dev(C) for C in Cs_h], Xs, restart=20, precision=prec)
+            assert st == 0 and all(x == 0 for x in sts)
+            assert ctx.tune_entries()[key] == sched          # the forced schedule ran; nothing was tuned
+            outs[sched] = ([from_dev(X) for X in Xs], [i.iters for i in infos])
+            for op in ops:
+                op.close()
+            ctx.workspace_check()
+        assert len(_lines(cache)) == 1
+    ref_X, ref_it = outs[64]
+    for sched in (65, 128, 129):
+        X, its = outs[sched]
+        assert its == ref_it, sched
+        for a, b in zip(ref_X, X):
+            assert np.array_equal(a, b), sched
