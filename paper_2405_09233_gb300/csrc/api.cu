@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <mutex>
+#include <iterator>
 #include <unordered_map>
 #include "internal.cuh"
 #include "apply.cuh"
@@ -55,14 +56,20 @@ namespace {
 struct OpPool {
   cudaMemPool_t pool = nullptr;
   cudaStream_t stream = nullptr;
-  // Released buffers wait here until kOpFreeDeferBytes have gathered (or an allocation fails, or a
-  // context is destroyed): then one device synchronisation covers them all, instead of one per
-  // buffer.  Until then they stay reserved, so nothing can reuse memory a kernel may still read.
-  std::unordered_map<void*, size_t> sizes;
+  // Released buffers wait in `pending` until kOpFreeDeferBytes have gathered, an allocation could
+  // reuse one of them, an allocation fails, or a context is destroyed: then one device
+  // synchronisation covers them all and they move to `cache`, idle blocks by size that later
+  // allocations of the same size take without any CUDA call.  Until that synchronisation nothing can
+  // reuse memory a kernel may still read.  Blocks beyond kOpCacheKeepBytes go back to the pool.
+  std::unordered_map<void*, size_t> sizes;   // every block handed out (live, pending or cached)
   std::vector<void*> pending;
   size_t pending_bytes = 0;
+  std::unordered_map<size_t, int> pending_count;              // pending blocks by size
+  std::unordered_map<size_t, std::vector<void*>> cache;       // idle blocks by size
+  size_t cache_bytes = 0;
 };
 constexpr size_t kOpFreeDeferBytes = 2ull << 30;
+constexpr size_t kOpCacheKeepBytes = 8ull << 30;
 std::mutex g_op_pool_mu;
 OpPool g_op_pool[64];
 
@@ -90,30 +97,71 @@ OpPool& op_pool_locked(int dev) {
   return q;
 }
 
-// Free every pending buffer of the pool after one device synchronisation (caller holds the lock).
+// Return cached blocks to the pool until at most `keep` bytes stay cached (the device is idle:
+// called right after a synchronisation, or for blocks no kernel has touched since one).
+void trim_cache_locked(OpPool& q, size_t keep) {
+  for (auto it = q.cache.begin(); it != q.cache.end() && q.cache_bytes > keep;) {
+    std::vector<void*>& v = it->second;
+    while (!v.empty() && q.cache_bytes > keep) {
+      cudaFreeAsync(v.back(), q.stream);
+      q.sizes.erase(v.back());
+      q.cache_bytes -= it->first;
+      v.pop_back();
+    }
+    it = v.empty() ? q.cache.erase(it) : std::next(it);
+  }
+}
+
+// Make every pending buffer idle with one device synchronisation and move it to the cache
+// (caller holds the lock).
 void flush_pending_locked(OpPool& q) {
   if (q.pending.empty()) return;
   cudaDeviceSynchronize();
   for (void* p : q.pending) {
-    cudaFreeAsync(p, q.stream);
-    q.sizes.erase(p);
+    const size_t b = q.sizes[p];
+    q.cache[b].push_back(p);
+    q.cache_bytes += b;
   }
   q.pending.clear();
+  q.pending_count.clear();
   q.pending_bytes = 0;
+  trim_cache_locked(q, kOpCacheKeepBytes);
 }
 
-// Allocate from the pool on `st` (or on the pool's own stream, synchronised, when st_given is false);
-// on failure, free what is pending and try once more.
+// An idle cached block of exactly `bytes`, or nullptr (caller holds the lock).
+void* take_cached_locked(OpPool& q, size_t bytes) {
+  auto it = q.cache.find(bytes);
+  if (it == q.cache.end() || it->second.empty()) return nullptr;
+  void* p = it->second.back();
+  it->second.pop_back();
+  q.cache_bytes -= bytes;
+  return p;
+}
+
+// Allocate from the cache, or from the pool on `st` (on the pool's own stream, synchronised, when
+// st_given is false).  A released block of the same size still pending is made idle first (one
+// device synchronisation) and reused; a failed pool allocation frees what is pending and cached
+// and tries once more.
 void* op_alloc_bytes(size_t bytes, bool st_given, cudaStream_t st) {
   const int dev = current_device_checked();
   std::lock_guard<std::mutex> lock(g_op_pool_mu);
   OpPool& q = op_pool_locked(dev);
-  if (!bytes) bytes = 16;
-  void* p = nullptr;
+  bytes = bytes ? (bytes + 255) / 256 * 256 : 256;
+  void* p = take_cached_locked(q, bytes);
+  if (!p) {
+    auto pc = q.pending_count.find(bytes);
+    if (pc != q.pending_count.end() && pc->second > 0) {
+      flush_pending_locked(q);
+      p = take_cached_locked(q, bytes);
+    }
+  }
+  if (p) return p;
   cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, q.pool, st_given ? st : q.stream);
-  if (e != cudaSuccess && !q.pending.empty()) {
+  if (e != cudaSuccess && (!q.pending.empty() || q.cache_bytes > 0)) {
     (void)cudaGetLastError();
     flush_pending_locked(q);
+    trim_cache_locked(q, 0);
+    cudaStreamSynchronize(q.stream);
     e = cudaMallocFromPoolAsync(&p, bytes, q.pool, st_given ? st : q.stream);
   }
   if (e == cudaSuccess && !st_given) e = cudaStreamSynchronize(q.stream);
@@ -137,8 +185,10 @@ void op_free(void* p) {
     std::lock_guard<std::mutex> lock(g_op_pool_mu);
     OpPool& q = op_pool_locked(dev);
     auto it = q.sizes.find(p);
+    if (it == q.sizes.end()) return;   // not a block of this pool
     q.pending.push_back(p);
-    q.pending_bytes += it != q.sizes.end() ? it->second : 0;
+    q.pending_bytes += it->second;
+    ++q.pending_count[it->second];
     if (q.pending_bytes >= kOpFreeDeferBytes) flush_pending_locked(q);
   } catch (const Error&) {
   }

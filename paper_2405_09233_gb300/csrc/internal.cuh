@@ -52,9 +52,10 @@ struct Workspace {
 // kOpPoolKeepBytes of freed memory reserved, so creating and destroying operators of recurring
 // shapes does not map and unmap device memory every time.  op_malloc returns memory usable on
 // every stream (like cudaMalloc) and throws TS_ERR_NOMEM on failure.  op_free defers the release:
-// buffers are kept (unusable by anyone) until 2 GiB of them have gathered, an allocation fails or
-// a context is destroyed, and are then returned together after one device synchronisation, so that
-// no pending kernel can still read them; nullptr is ignored.
+// buffers are kept (unusable by anyone) until 2 GiB of them have gathered, an allocation of the same
+// size asks for one, an allocation fails or a context is destroyed; then one device synchronisation
+// makes them all idle, so that no pending kernel can still read them, and they are kept (up to 8 GiB)
+// for allocations of exactly their size, which then need no CUDA call; nullptr is ignored.
 // ----------------------------------------------------------------------------------------------
 constexpr unsigned long long kOpPoolKeepBytes = 16ull << 30;
 void* op_malloc(size_t bytes);
