@@ -238,7 +238,7 @@ void ks_step(void* state, int m, int j, int method, const double* Pnorm, cudaStr
              cudaGraphConditionalHandle handle = 0, const double* stop = nullptr);
 // Solve for y over the first k columns; result in the state's y array.
 void ks_solve(void* state, int m, int k, int method, cudaStream_t st);
-// Inner step j after W = M(V_j), in one launch for short vectors (arnoldi_small_ok(N)): the MGS sweep
+// Inner step j after W = M(V_j), in one cluster launch for short vectors (arnoldi_small_ok(N)): the MGS sweep
 // against V_0..V_j (writing column j of H), h_{j+1,j} = ||W||, the ks_step update (same handle and
 // stop semantics) and V_{j+1} = W / h_{j+1,j} (always formed; W itself is left as M(V_j)).  The basis
 // vectors are V + i ldv.  gate (device, may be null): the kernel returns at once when *gate == 0,

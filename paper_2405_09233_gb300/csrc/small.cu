@@ -8,6 +8,7 @@
 // tFOM (§3.2): H_k y = beta e1 by Gaussian elimination with partial pivoting (a Hessenberg
 // matrix only needs a choice between rows c and c+1 at column c); the estimate is
 // h_{k+1,k} |y_k| (Proposition 3.3).
+#include <algorithm>
 #include "internal.cuh"
 #include "reduce.cuh"
 
@@ -177,33 +178,56 @@ __global__ void k_ks_step(double* st, int m, int j, int method, const double* Pn
   ks_update(st, m, j, method, hn, handle, stop);
 }
 
-// Everything of inner step j after W = M(V_j), for vectors short enough for one block of nt <= 512
-// threads (N <= nt R):
-// the modified Gram-Schmidt sweep h_ij = <V_i, W>, W -= h_ij V_i (i = 0..j, in order), the norm
-// h_{j+1,j} = ||W||, the Givens / Hessenberg update (ks_update) and V_{j+1} = W / h_{j+1,j}.  At
-// n = s = 24, p = 4 the multi-block form took ~85 us per step in j + 5 launches, most of it global
-// round trips of one short reduction after another; here W stays in registers, the next V_i is
-// loaded while the current inner product is reduced, and one launch does it all.  Same arithmetic
-// as the multi-block kernels (FP64 sums; an FP32 basis sums each thread's products in FP32 first),
-// in a different summation order.  The block is only as wide as N needs (nt = N / R rounded up to
-// whole warps): one SM issues 2 DFMA per clock, so every padded lane's dot and update cost as much
-// as a real one.
+// Everything of inner step j after W = M(V_j), for vectors of at most kArnMaxN entries, in one
+// launch of a thread-block cluster of CL <= kArnCL CTAs: the modified Gram-Schmidt sweep
+// h_ij = <V_i, W>, W -= h_ij V_i (i = 0..j, in order), the norm h_{j+1,j} = ||W||, the Givens /
+// Hessenberg update (ks_update, by CTA 0) and V_{j+1} = W / h_{j+1,j}.  CTA c owns a contiguous part
+// of the vectors, kept in registers (W) or loaded one pass ahead (the next V_i).  An inner product
+// is summed per warp (butterfly), every warp's partial is stored into every CTA's shared memory
+// (distributed shared memory), and after one cluster barrier each warp adds all partials in the same
+// fixed order, so every thread of every CTA holds the same value, bit for bit.  GB300's FP64 pipe
+// issues one warp's DFMA in 64 clocks per SM sub-partition, so one CTA spent ~2.3 us per MGS pass at
+// 2304 entries in FP64 issue alone; eight SMs cut that eightfold, and the pass is left with two short
+// reduction trees and the barrier.  Same arithmetic as the multi-block kernels (FP64 sums; an FP32
+// basis sums each thread's products in FP32 first), in a different summation order.  All CTAs pass
+// the same barriers (j is a kernel argument; the gate is read once, before the first barrier, and
+// written by CTA 0 only after the last), the first barrier precedes every remote store and no remote
+// store follows the last one.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+constexpr int kArnCL = 8, kArnMaxThreads = 512, kArnMaxN = kArnCL * kArnMaxThreads * 16;
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 template <typename T, int R>
-__global__ void __launch_bounds__(512, 1) k_arnoldi_small(T* __restrict__ W, T* __restrict__ V, long long ldv,
-                                                          int N, int j, int m, double* st, int method,
-                                                          cudaGraphConditionalHandle handle, const double* stop,
-                                                          int* gate) {
-  if (gate && *gate == 0) return;   // launched ahead of a cycle that has already ended
+__global__ void __launch_bounds__(kArnMaxThreads, 1)
+    k_arnoldi_cluster(T* __restrict__ W, T* __restrict__ V, long long ldv, int N, int j, int m, double* st,
+                      int method, cudaGraphConditionalHandle handle, const double* stop, int* gate) {
+  if (gate && *gate == 0) return;   // launched ahead of a cycle that has already ended (all CTAs alike)
+  __shared__ double slots[2][kArnCL * (kArnMaxThreads / 32)];
+  uint32_t rank, ncta;
+  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+  const int nt = blockDim.x, nw = nt / 32, t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  const int Nc = (N + (int)ncta - 1) / (int)ncta, e0 = (int)rank * Nc;
+  auto idx = [&](int r) {   // element of (thread, r), or -1
+    const int q = t + nt * r, e = e0 + q;
+    return (q < Nc && e < N) ? e : -1;
+  };
   Layout L{m};
   double* H = st + L.H();
   const int ld = m + 1;
-  const int t = threadIdx.x, nt = blockDim.x;
   T w[R], v[R], vn[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const int e = t + nt * r;
-    w[r] = e < N ? W[e] : T(0);
-    v[r] = e < N ? V[e] : T(0);
+    const int e = idx(r);
+    w[r] = e >= 0 ? W[e] : T(0);
+    v[r] = e >= 0 ? V[e] : T(0);
   }
   auto dot = [&](const T (&x)[R]) {
     if constexpr (sizeof(T) == 4) {
@@ -218,18 +242,39 @@ __global__ void __launch_bounds__(512, 1) k_arnoldi_small(T* __restrict__ W, T* 
       return acc;
     }
   };
+  int buf = 0;
+  auto cluster_sum = [&](double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) {
+      const uint32_t local = smem_addr(&slots[buf][(int)rank * nw + wp]);
+      for (uint32_t c = 0; c < ncta; ++c) {
+        uint32_t remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(c));
+        asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(remote), "d"(x) : "memory");
+      }
+    }
+    cluster_sync_all();
+    double y = 0.0;
+    for (int q = lane; q < (int)ncta * nw; q += 32) y += slots[buf][q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    buf ^= 1;
+    return y;
+  };
+  cluster_sync_all();   // every CTA of the cluster runs before any remote store
   for (int i = 0; i <= j; ++i) {
     const double part = dot(v);
     if (i < j) {
       const T* Vn = V + (long long)(i + 1) * ldv;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const int e = t + nt * r;
-        vn[r] = e < N ? Vn[e] : T(0);
+        const int e = idx(r);
+        vn[r] = e >= 0 ? Vn[e] : T(0);
       }
     }
-    const double h = block_sum(part);
-    if (t == 0) H[i + ld * j] = h;
+    const double h = cluster_sum(part);
+    if (rank == 0 && t == 0) H[i + ld * j] = h;
     const T hT = (T)h;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -237,14 +282,14 @@ __global__ void __launch_bounds__(512, 1) k_arnoldi_small(T* __restrict__ W, T* 
       v[r] = vn[r];
     }
   }
-  const double hn = sqrt(block_sum(dot(w)));
-  ks_update(st, m, j, method, hn, handle, stop, gate);
+  const double hn = sqrt(cluster_sum(dot(w)));
+  if (rank == 0) ks_update(st, m, j, method, hn, handle, stop, gate);
   const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   T* Vj1 = V + (long long)(j + 1) * ldv;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const int e = t + nt * r;
-    if (e < N) {
+    const int e = idx(r);
+    if (e >= 0) {
       if constexpr (sizeof(T) == 4) Vj1[e] = w[r] * (float)inv;
       else Vj1[e] = w[r] * inv;
     }
@@ -312,7 +357,25 @@ void ks_step(void* state, int m, int j, int method, const double* Pnorm, cudaStr
   TS_CUDA(cudaGetLastError());
 }
 
-bool arnoldi_small_ok(long long N) { return N >= 1 && N <= 512 * 16; }
+bool arnoldi_small_ok(long long N) { return N >= 1 && N <= kArnMaxN; }
+
+template <typename T, int R>
+void launch_arnoldi_cluster(int cl, int nt, T* W, T* V, long long ldv, int n, int j, int m, double* s, int method,
+                            cudaGraphConditionalHandle handle, const double* stop, int* gate, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl, 1, 1);
+  cfg.blockDim = dim3(nt, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TS_CUDA(cudaLaunchKernelEx(&cfg, k_arnoldi_cluster<T, R>, W, V, ldv, n, j, m, s, method, handle, stop, gate));
+}
 
 template <typename T>
 void arnoldi_small(T* W, T* V, long long ldv, long long N, int j, int m, void* state, int method, cudaStream_t st,
@@ -320,10 +383,18 @@ void arnoldi_small(T* W, T* V, long long ldv, long long N, int j, int m, void* s
   TS_REQUIRE(arnoldi_small_ok(N) && j >= 0 && j < m, "arnoldi_small: bad size");
   double* s = static_cast<double*>(state);
   const int n = (int)N;
-  auto threads = [&](int R) { return (int)((N + 32LL * R - 1) / (32LL * R) * 32); };   // <= 512
-  if (N <= 512 * 4) k_arnoldi_small<T, 4><<<1, threads(4), 0, st>>>(W, V, ldv, n, j, m, s, method, handle, stop, gate);
-  else if (N <= 512 * 8) k_arnoldi_small<T, 8><<<1, threads(8), 0, st>>>(W, V, ldv, n, j, m, s, method, handle, stop, gate);
-  else k_arnoldi_small<T, 16><<<1, threads(16), 0, st>>>(W, V, ldv, n, j, m, s, method, handle, stop, gate);
+  // CTAs: one per 64 entries up to kArnCL; threads: the CTA's share in R-element runs, whole warps
+  const int cl = (int)std::min<long long>(kArnCL, std::max<long long>(1, (N + 63) / 64));
+  const long long nc = (N + cl - 1) / cl;
+  auto threads = [&](int R) { return (int)((nc + 32LL * R - 1) / (32LL * R) * 32); };
+  if (nc <= kArnMaxThreads * 2LL)
+    launch_arnoldi_cluster<T, 2>(cl, threads(2), W, V, ldv, n, j, m, s, method, handle, stop, gate, st);
+  else if (nc <= kArnMaxThreads * 4LL)
+    launch_arnoldi_cluster<T, 4>(cl, threads(4), W, V, ldv, n, j, m, s, method, handle, stop, gate, st);
+  else if (nc <= kArnMaxThreads * 8LL)
+    launch_arnoldi_cluster<T, 8>(cl, threads(8), W, V, ldv, n, j, m, s, method, handle, stop, gate, st);
+  else
+    launch_arnoldi_cluster<T, 16>(cl, threads(16), W, V, ldv, n, j, m, s, method, handle, stop, gate, st);
   count_launch();
   TS_CUDA(cudaGetLastError());
 }

@@ -7,7 +7,8 @@
 //             V_{j+1} = W / h_{j+1,j}.  Then y, X += V_k (*) y, and the true residual.
 // The host reads 4 doubles per inner step (estimate, 1/h, h, flags) to decide whether to stop --
 // except for small problems, which are bound by launch latency and by that look at every step.
-// Vectors of at most 8192 entries run everything after W = M(V_j) in one launch (arnoldi_small), and
+// Vectors of at most 65536 entries run everything after W = M(V_j) in one launch (arnoldi_small, a
+// thread-block cluster), and
 // on the FP64 DFMA engine (real basis, dense operator) a cycle's steps are launched ahead in chunks
 // behind a device gate that the step ending the cycle closes, so the host looks once per chunk.
 // Other problems of at most kGraphCycleMaxN unknowns run, from their second cycle on, each restart

@@ -43,6 +43,8 @@ CASES = [  # (n, s, p, m, seed)
     (37, 5, 7, 8, 3),        # ragged, odd p
     (16, 9, 1, 10, 4),       # p = 1 (matrix Sylvester equation)
     (70, 66, 16, 12, 5),     # two 64-tiles in both dimensions
+    (40, 48, 16, 15, 6),     # 30720 unknowns: the one-launch step tail with 8 entries per thread
+    (60, 64, 16, 12, 7),     # 61440 unknowns: 16 entries per thread
 ]
 
 
@@ -96,20 +98,20 @@ def test_spectral_basis_rejected_where_unsupported(ctx):
 @pytest.mark.parametrize("case", [(24, 24, 4, 20, 0), (24, 24, 4, 5, 0), (37, 5, 7, 8, 3), (70, 66, 16, 4, 5)],
                          ids=lambda c: "n%d_s%d_p%d_m%d" % c[:4])
 def test_execution_forms_agree_bitwise(ctx, monkeypatch, method, case):
-    """A small problem's cycle launched ahead behind a device gate (<= 8192 unknowns) and a larger one's
+    """A small problem's cycle launched ahead behind a device gate (<= 65536 unknowns) and a larger one's
     cycle replayed as a conditional CUDA graph (from the second cycle on) run the same kernels in the same
     order as the per-step host loop: identical histories, cycle counts and X, bit for bit."""
     n, s, p, m, seed = case
     pr = inputs.dense_problem(n, s, p, seed=seed)
     _, X1, r1 = run(ctx, method, pr, m)
-    monkeypatch.setenv("TSTAR_NO_LAUNCH_AHEAD" if n * s * p <= 8192 else "TSTAR_NO_GRAPH_CYCLE", "1")
+    monkeypatch.setenv("TSTAR_NO_LAUNCH_AHEAD" if n * s * p <= 65536 else "TSTAR_NO_GRAPH_CYCLE", "1")
     _, X2, r2 = run(ctx, method, pr, m)
     assert r1.status == r2.status == 0
     assert r1.info.iters == r2.info.iters and r1.info.cycles == r2.info.cycles
     assert np.array_equal(np.asarray(r1.history), np.asarray(r2.history))
     assert np.array_equal(np.asarray(r1.true_history), np.asarray(r2.true_history))
     assert np.array_equal(X1, X2)
-    if n * s * p > 8192:
+    if n * s * p > 65536:
         assert r1.info.cycles >= 2     # the graph form was exercised
 
 
