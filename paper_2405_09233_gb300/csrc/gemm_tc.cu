@@ -609,39 +609,91 @@ __global__ void __launch_bounds__(256) k_rfft_planar(const float* __restrict__ X
   }
 }
 
-// Power-of-two p: register FFT version of k_rfft_planar.
-template <typename OpT, int P>
-__global__ void __launch_bounds__(256) k_rfft_planar_pow2(const float* __restrict__ X, OpT* __restrict__ re,
-                                                          OpT* __restrict__ im, int n, int s, int ldn,
-                                                          float* __restrict__ re_lo, float* __restrict__ im_lo) {
+// planes [k][j][ldn] (column-major X_k) -> planes [k][i][lds] (row-major X_k).
+// Power-of-two p: both planar layouts in one pass.  A CTA of 32 x 8 threads owns a tile of 32 rows
+// (i) x TJ columns (j) of tubes (TJ = 32, or 16 with the split-TF32 low parts); each thread runs
+// the register FFT of TJ / 8 tubes, writes the column-major planes [k][j][ldn] directly (coalesced
+// along i) and keeps the tile in shared memory, from which the row-major planes [k][i][lds] are
+// written coalesced along j.  Entries outside n x s are written as zeros in both layouts.  The
+// separate transpose re-read the column-major planes from memory (a third of the traffic of the
+// pair) and moved 64-byte rows.
+template <typename OpT, int P, bool SPLIT>
+__global__ void __launch_bounds__(256) k_rfft_planar_fused(const float* __restrict__ X, OpT* __restrict__ cre,
+                                                           OpT* __restrict__ cim, OpT* __restrict__ rre,
+                                                           OpT* __restrict__ rim, float* __restrict__ cre_lo,
+                                                           float* __restrict__ cim_lo, float* __restrict__ rre_lo,
+                                                           float* __restrict__ rim_lo, int n, int s, int ldn,
+                                                           int lds) {
+  constexpr int K = P / 2 + 1, TJ = SPLIT ? 16 : 32, NQ = TJ / 8;
+  extern __shared__ uint8_t pf_smem[];
+  OpT* tre = reinterpret_cast<OpT*>(pf_smem);             // [K][TJ][33]
+  OpT* tim = tre + K * TJ * 33;
+  float* tlr = reinterpret_cast<float*>(tim + K * TJ * 33);   // split: low parts, same shape
+  float* tli = tlr + (SPLIT ? K * TJ * 33 : 0);
   __shared__ float tc[P], tsn[P];
-  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+  for (int r = threadIdx.y * 32 + threadIdx.x; r < P; r += 256) {
     double sv, cv;
     sincospi(2.0 * r / P, &sv, &cv);
     tc[r] = (float)cv;
     tsn[r] = (float)sv;
   }
   __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TJ;
   const long long T = (long long)n * s;
-  const long long Tp = (long long)ldn * s;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < Tp; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % ldn);
-    const long long j = e / ldn;
-    const bool live = i < n;
-    rfft_reg<float, P>([&](int t) { return live ? X[t * T + j * n + i] : 0.f; },
+  const long long Tc = (long long)ldn * s, Tr = (long long)n * lds;
+  const int i = i0 + tx;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int jj = ty + 8 * q, j = j0 + jj;
+    const bool live = i < n && j < s;
+    rfft_reg<float, P>([&](int t) { return live ? X[t * T + (long long)j * n + i] : 0.f; },
                        [&](int kk, float a, float b) {
-                         re[kk * Tp + e] = to_op<OpT>(a);
-                         im[kk * Tp + e] = to_op<OpT>(b);
-                         if (re_lo) {
-                           re_lo[kk * Tp + e] = tf32_lo(a);
-                           im_lo[kk * Tp + e] = tf32_lo(b);
+                         const OpT ha = to_op<OpT>(a), hb = to_op<OpT>(b);
+                         tre[(kk * TJ + jj) * 33 + tx] = ha;
+                         tim[(kk * TJ + jj) * 33 + tx] = hb;
+                         float la = 0.f, lb = 0.f;
+                         if constexpr (SPLIT) {
+                           la = tf32_lo(a);
+                           lb = tf32_lo(b);
+                           tlr[(kk * TJ + jj) * 33 + tx] = la;
+                           tli[(kk * TJ + jj) * 33 + tx] = lb;
+                         }
+                         if (j < s && i < ldn) {
+                           const long long o = kk * Tc + (long long)j * ldn + i;
+                           cre[o] = ha;
+                           cim[o] = hb;
+                           if constexpr (SPLIT) {
+                             cre_lo[o] = la;
+                             cim_lo[o] = lb;
+                           }
                          }
                        },
                        tc, tsn);
   }
+  __syncthreads();
+  // row-major planes: rows i0 + r (r < 32), columns j0 + c (c < TJ), all K slices
+  for (int e = ty * 32 + tx; e < K * 32 * TJ; e += 256) {
+    const int c = e % TJ, r = (e / TJ) % 32, kk = e / (TJ * 32);
+    const int ir = i0 + r, jc = j0 + c;
+    if (ir < n && jc < lds) {
+      const long long o = kk * Tr + (long long)ir * lds + jc;
+      rre[o] = tre[(kk * TJ + c) * 33 + r];
+      rim[o] = tim[(kk * TJ + c) * 33 + r];
+      if constexpr (SPLIT) {
+        rre_lo[o] = tlr[(kk * TJ + c) * 33 + r];
+        rim_lo[o] = tli[(kk * TJ + c) * 33 + r];
+      }
+    }
+  }
 }
 
-// planes [k][j][ldn] (column-major X_k) -> planes [k][i][lds] (row-major X_k).
+template <typename OpT, int P, bool SPLIT>
+constexpr int planar_fused_smem() {
+  constexpr int K = P / 2 + 1, TJ = SPLIT ? 16 : 32;
+  return K * TJ * 33 * (2 * (int)sizeof(OpT) + (SPLIT ? 8 : 0));
+}
+
 template <typename OpT>
 __global__ void k_transpose_planes(const OpT* __restrict__ cre, const OpT* __restrict__ cim, OpT* __restrict__ rre,
                                    OpT* __restrict__ rim, int n, int s, int ldn, int lds) {
@@ -703,6 +755,27 @@ void prepare_operator(ts_op* op, TcOperands& t, cudaStream_t st) {
   TS_CUDA(cudaGetLastError());
 }
 
+template <typename OpT, int P, bool SPLIT>
+void planar_fused_p(const float* X, TcWork& w, int n, int s, int ldn, int lds, cudaStream_t st) {
+  constexpr int smem = planar_fused_smem<OpT, P, SPLIT>(), TJ = SPLIT ? 16 : 32;
+  set_max_dynamic_smem((const void*)k_rfft_planar_fused<OpT, P, SPLIT>, smem);
+  const dim3 grid((unsigned)((std::max(n, ldn) + 31) / 32), (unsigned)((std::max(s, lds) + TJ - 1) / TJ), 1);
+  k_rfft_planar_fused<OpT, P, SPLIT><<<grid, dim3(32, 8), smem, st>>>(
+      X, (OpT*)w.xc_re, (OpT*)w.xc_im, (OpT*)w.xr_re, (OpT*)w.xr_im, (float*)w.xc_re_lo, (float*)w.xc_im_lo,
+      (float*)w.xr_re_lo, (float*)w.xr_im_lo, n, s, ldn, lds);
+  count_launch();
+  TS_CUDA(cudaGetLastError());
+}
+
+template <typename OpT, bool SPLIT>
+void planar_fused(const float* X, TcWork& w, int n, int s, int p, int ldn, int lds, cudaStream_t st) {
+  if (p == 2) planar_fused_p<OpT, 2, SPLIT>(X, w, n, s, ldn, lds, st);
+  else if (p == 4) planar_fused_p<OpT, 4, SPLIT>(X, w, n, s, ldn, lds, st);
+  else if (p == 8) planar_fused_p<OpT, 8, SPLIT>(X, w, n, s, ldn, lds, st);
+  else if (p == 16) planar_fused_p<OpT, 16, SPLIT>(X, w, n, s, ldn, lds, st);
+  else planar_fused_p<OpT, 32, SPLIT>(X, w, n, s, ldn, lds, st);
+}
+
 template <typename OpT>
 void planar_dft(const float* X, TcWork& w, int n, int s, int p, int ldn, int lds, cudaStream_t st) {
   const long long Tp = (long long)ldn * s;
@@ -710,11 +783,12 @@ void planar_dft(const float* X, TcWork& w, int n, int s, int p, int ldn, int lds
   if (g > 152 * 16) g = 152 * 16;
   OpT* cre = (OpT*)w.xc_re; OpT* cim = (OpT*)w.xc_im;
   float* lre = (float*)w.xc_re_lo; float* lim = (float*)w.xc_im_lo;
-  if (p == 4) k_rfft_planar_pow2<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn, lre, lim);
-  else if (p == 8) k_rfft_planar_pow2<OpT, 8><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn, lre, lim);
-  else if (p == 16) k_rfft_planar_pow2<OpT, 16><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn, lre, lim);
-  else if (p == 32) k_rfft_planar_pow2<OpT, 32><<<g, 256, 0, st>>>(X, cre, cim, n, s, ldn, lre, lim);
-  else if (p <= 4) k_rfft_planar<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn, lre, lim);
+  if (p == 2 || p == 4 || p == 8 || p == 16 || p == 32) {   // both layouts in one pass
+    if (lre) planar_fused<OpT, true>(X, w, n, s, p, ldn, lds, st);
+    else planar_fused<OpT, false>(X, w, n, s, p, ldn, lds, st);
+    return;
+  }
+  if (p <= 4) k_rfft_planar<OpT, 4><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn, lre, lim);
   else if (p <= 8) k_rfft_planar<OpT, 8><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn, lre, lim);
   else if (p <= 16) k_rfft_planar<OpT, 16><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn, lre, lim);
   else if (p <= 32) k_rfft_planar<OpT, 32><<<g, 256, 0, st>>>(X, cre, cim, n, s, p, ldn, lre, lim);
