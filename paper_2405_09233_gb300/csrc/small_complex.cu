@@ -167,7 +167,13 @@ __global__ void k_schur_small(double2* __restrict__ Tall, double2* __restrict__ 
 }
 
 // LU with partial pivoting of M = H_k - t_jj I, lower bandwidth bw, one CTA per (j, k).
-// LU[(k*s + j)] is an N x N column-major factor; piv holds the row chosen at each step.
+// LU[(k*s + j)] is an N x N column-major factor; piv holds the row chosen at each step.  Per column
+// c: warp 0 finds the pivot among rows c..c+bw (shuffle argmax, first index on ties), swaps it into
+// column c, and forms the multipliers (kept in column c, and the first kLuMaxBw in shared memory);
+// then every thread takes columns q > c, applies the row interchange to its column and subtracts
+// the multipliers times M[c, q] down the band: two barriers per column.  (The first version reduced
+// the pivot candidates of all 256 threads serially and used five barriers per column.)
+constexpr int kLuMaxBw = 256;
 __global__ void __launch_bounds__(256) k_shifted_lu(const double2* __restrict__ H, long long sH,
                                                     const double2* __restrict__ T, double2* __restrict__ LU,
                                                     int* __restrict__ piv, int N, int bw, int s, int* err) {
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(256) k_shifted_lu(const double2* __restrict__ 
   }
   __shared__ int sp;
   __shared__ double sbest[256];
-  __shared__ int sidx[256];
+  __shared__ double2 sl[kLuMaxBw];
   __syncthreads();
   // max-norm of M: a pivot below N * 1e-14 * max|M| marks a (numerically) singular shift
   double mx = 0.0;
@@ -197,54 +203,60 @@ __global__ void __launch_bounds__(256) k_shifted_lu(const double2* __restrict__ 
   }
   __syncthreads();
   const double tiny = 1e-14 * N * sbest[0];
-  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = 0; c < N; ++c) {
-    const int rmax = (c + bw < N - 1) ? c + bw : N - 1;
-    // pivot search over rows c..rmax
-    double best = -1.0;
-    int bi = c;
-    for (int r = c + (int)threadIdx.x; r <= rmax; r += blockDim.x) {
-      const double v = cabs2(M[r + (long long)N * c]);
-      if (v > best) {
-        best = v;
-        bi = r;
-      }
-    }
-    sbest[threadIdx.x] = best;
-    sidx[threadIdx.x] = bi;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double b0 = -1.0;
-      int i0 = c;
-      for (int t = 0; t < (int)blockDim.x; ++t)
-        if (sbest[t] > b0 || (sbest[t] == b0 && sidx[t] < i0)) {
-          b0 = sbest[t];
-          i0 = sidx[t];
+    const int rmax = (c + bw < N - 1) ? c + bw : N - 1, nr = rmax - c;
+    double2* Mc = M + (long long)N * c;
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = c;
+      for (int r = c + lane; r <= rmax; r += 32) {
+        const double v = cabs2(Mc[r]);
+        if (v > best) {
+          best = v;
+          bi = r;
         }
-      sp = i0;
-      pv[c] = i0;
-      if (b0 <= tiny) atomicOr(err, 2);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      const int p = bi;
+      if (lane == 0) {
+        pv[c] = p;
+        sp = p;
+        if (best <= tiny) atomicOr(err, 2);
+        if (p != c) {
+          const double2 t0 = Mc[c];
+          Mc[c] = Mc[p];
+          Mc[p] = t0;
+        }
+      }
+      __syncwarp();
+      const double2 dinv = cdiv(make_double2(1.0, 0.0), Mc[c]);
+      for (int r = lane; r < nr; r += 32) {
+        const double2 l = cmul(Mc[c + 1 + r], dinv);
+        Mc[c + 1 + r] = l;
+        if (r < kLuMaxBw) sl[r] = l;
+      }
     }
     __syncthreads();
     const int p = sp;
-    if (p != c) {
-      for (int q = c + (int)threadIdx.x; q < N; q += blockDim.x) {
-        const double2 t0 = M[c + (long long)N * q];
-        M[c + (long long)N * q] = M[p + (long long)N * q];
-        M[p + (long long)N * q] = t0;
+    for (int q = c + 1 + (int)threadIdx.x; q < N; q += blockDim.x) {
+      double2* Mq = M + (long long)N * q;
+      if (p != c) {
+        const double2 t0 = Mq[c];
+        Mq[c] = Mq[p];
+        Mq[p] = t0;
       }
-    }
-    __syncthreads();
-    const double2 dinv = cdiv(make_double2(1.0, 0.0), M[c + (long long)N * c]);
-    const int nr = rmax - c;
-    for (int r = c + 1 + (int)threadIdx.x; r <= rmax; r += blockDim.x)
-      M[r + (long long)N * c] = cmul(M[r + (long long)N * c], dinv);
-    __syncthreads();
-    const long long work = (long long)nr * (N - c - 1);
-    for (long long w = threadIdx.x; w < work; w += blockDim.x) {
-      const int r = c + 1 + (int)(w % nr);
-      const int q = c + 1 + (int)(w / nr);
-      M[r + (long long)N * q] = csub(M[r + (long long)N * q], cmul(M[r + (long long)N * c], M[c + (long long)N * q]));
+      const double2 u = Mq[c];
+      for (int r = 0; r < nr; ++r)
+        Mq[c + 1 + r] = csub(Mq[c + 1 + r], cmul(r < kLuMaxBw ? sl[r] : Mc[c + 1 + r], u));
     }
     __syncthreads();
   }
