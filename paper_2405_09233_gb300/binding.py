@@ -222,14 +222,17 @@ class Context:
         return Operator(self, h, n, s, p)
 
     def t_bartels_stewart(self, A, B, C, X=None):
-        """Small dense STE A*X - X*B = C by t-Bartels-Stewart; (p, n, n), (p, s, s), (p, s, n) tensors."""
+        """Small dense STE A*X - X*B = C by t-Bartels-Stewart; (p, n, n), (p, s, s), (p, s, n) tensors.
+        Raises TstarError when the library reports TS_SINGULAR (no solution was formed)."""
         import torch
         p, n, _ = A.shape
         s = B.shape[1]
         if X is None:
             X = torch.empty_like(C)
-        self._check(lib().ts_t_bartels_stewart(self._h, _ptr(A), n, _ptr(B), s, p, _ptr(C), _ptr(X),
-                                               _stream(A, B, C, X)), "ts_t_bartels_stewart")
+        st = self._check(lib().ts_t_bartels_stewart(self._h, _ptr(A), n, _ptr(B), s, p, _ptr(C), _ptr(X),
+                                                    _stream(A, B, C, X)), "ts_t_bartels_stewart")
+        if st != 0:   # TS_SINGULAR: X holds no solution
+            raise TstarError(st, f"ts_t_bartels_stewart: {lib().ts_last_error(self._h).decode()}")
         return X
 
     def sylv_apply(self, op: "Operator", X, Y=None):

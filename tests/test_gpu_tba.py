@@ -41,9 +41,12 @@ def scipy_slices(prob):
     return [sp.csr_matrix((sl.val, sl.col, sl.rowptr), shape=(prob.n, prob.n)) for sl in prob.slices]
 
 
-@pytest.mark.parametrize("dims", [(6, 3, 1), (8, 5, 2), (12, 4, 3), (20, 6, 4), (33, 7, 5), (16, 16, 8), (50, 2, 7)],
+@pytest.mark.parametrize("dims", [(6, 3, 1), (8, 5, 2), (12, 4, 3), (20, 6, 4), (33, 7, 5), (16, 16, 8), (50, 2, 7),
+                                  (8, 64, 2), (64, 64, 4), (128, 96, 4)],
                          ids=lambda d: "n%d_s%d_p%d" % d)
 def test_t_bartels_stewart_matches_oracle(ctx, dims):
+    """Up to mid sizes: (8, 64, 2) is a slice whose complex Schur iteration once stalled on its last 2 x 2
+    window (fused multiply-add rounding kept the subdiagonal just above the deflation test)."""
     n, s, p = dims
     pr = inputs.dense_problem(n, s, p, seed=80 + n)
     C = kr.sylv_apply(pr.A, pr.B, pr.Xstar)
