@@ -70,7 +70,7 @@ def test_t_bartels_stewart_singular_reported(ctx):
 
 
 @pytest.mark.parametrize("case", [(40, 4, 4, 4, 1), (30, 5, 5, 4, 2), (60, 3, 2, 6, 3), (64, 8, 8, 3, 4),
-                                  (24, 24, 4, 3, 0)], ids=lambda c: "n%d_s%d_p%d_m%d" % c[:4])
+                                  (24, 24, 4, 3, 0), (256, 64, 4, 3, 6)], ids=lambda c: "n%d_s%d_p%d_m%d" % c[:4])
 def test_tbas_dense_matches_oracle(ctx, case):
     import torch
     n, s, p, m, seed = case
@@ -90,7 +90,7 @@ def test_tbas_dense_matches_oracle(ctx, case):
     op.close()
 
 
-@pytest.mark.parametrize("shape", [(6, 3, 3), (12, 4, 4), (10, 8, 8)], ids=lambda d: "grid%d_s%d_p%d" % d)
+@pytest.mark.parametrize("shape", [(6, 3, 3), (12, 4, 4), (10, 8, 8), (20, 64, 4)], ids=lambda d: "grid%d_s%d_p%d" % d)
 def test_sparse_operator_apply_and_tbas(ctx, shape):
     import torch
     grid, s, p = shape
