@@ -85,7 +85,9 @@ ts_status ts_tstar(ts_ctx* ctx, const double* A, int n1, int n2, const double* B
  * caller and freed with ts_op_destroy before ts_destroy(ctx).  With A and B in
  * device memory the preparation is asynchronous on `stream`: the operator may
  * be used on that stream at once, on another stream once `stream` has been
- * synchronised (host inputs are staged and the call returns after the work). */
+ * synchronised.  Host inputs are staged through the context's buffers; the call
+ * returns once they have been copied (the caller may then reuse its arrays),
+ * and the operator follows the same stream rule. */
 ts_status ts_op_create_dense(ts_ctx* ctx, const double* A, int n, const double* B, int s, int p,
                              unsigned flags, ts_op** op, ts_stream stream);
 /* Prepare M(X) = A*X - X*B with a sparse A given by its p frontal slices in CSR form (host

@@ -351,14 +351,23 @@ void StagedOut::finish() {
 // Forward DFT of the operator tensors once (§8 setup: A_k, B_k for k <= p/2).
 static void op_prepare(ts_op* op, const double* A, const double* B, cudaStream_t st) {
   const int n = op->n, s = op->s, p = op->p, K = op->K;
+  ts_ctx* ctx = op->ctx;
   op_alloc_on(op->Ah, sizeof(double2) * (size_t)K * n * n, st);
   op_alloc_on(op->Bh, sizeof(double2) * (size_t)K * s * s, st);
-  StagedIn a(op->ctx, "stage_A", A, (size_t)n * n * p, st);
-  StagedIn b(op->ctx, "stage_B", B, (size_t)s * s * p, st);
+  // Host inputs go through the context's staging buffers: a copy into them waits (on the device)
+  // for the DFTs of the previous creation that read them, and the call returns once its own copies
+  // are done, so the caller may reuse its arrays while the DFTs run on.
+  const bool host_in = !is_device_ptr(A) || !is_device_ptr(B);
+  if (host_in) TS_CUDA(cudaStreamWaitEvent(st, ctx->ev_stage_free, 0));
+  StagedIn a(ctx, "stage_A", A, (size_t)n * n * p, st);
+  StagedIn b(ctx, "stage_B", B, (size_t)s * s * p, st);
+  if (host_in) TS_CUDA(cudaEventRecord(ctx->ev_stage_copied, st));
   rfft_tube<double, double2>(a.dev, op->Ah, (long long)n * n, p, st);
   rfft_tube<double, double2>(b.dev, op->Bh, (long long)s * s, p, st);
-  // host inputs went through the context's staging buffers, which the next call may reuse
-  if (a.staged || b.staged) TS_CUDA(cudaStreamSynchronize(st));
+  if (host_in) {
+    TS_CUDA(cudaEventRecord(ctx->ev_stage_free, st));
+    TS_CUDA(cudaEventSynchronize(ctx->ev_stage_copied));
+  }
 }
 
 void apply_f64(ts_ctx* ctx, const ts_op* op, const double* X, double* Y, int mode, const double* C,
@@ -475,6 +484,8 @@ ts_status ts_create(ts_ctx** out, int device) {
     TS_CUDA(cudaMallocHost(&ctx->host_scalars, 1024 * sizeof(double)));
     TS_CUDA(cudaEventCreate(&ctx->ev0));
     TS_CUDA(cudaEventCreate(&ctx->ev1));
+    TS_CUDA(cudaEventCreateWithFlags(&ctx->ev_stage_copied, cudaEventDisableTiming));
+    TS_CUDA(cudaEventCreateWithFlags(&ctx->ev_stage_free, cudaEventDisableTiming));
     *out = ctx;
     return TS_OK;
   } catch (const ts::Error& e) {
@@ -500,6 +511,8 @@ void ts_destroy(ts_ctx* ctx) {
   if (ctx->host_scalars) cudaFreeHost(ctx->host_scalars);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->ev_stage_copied) cudaEventDestroy(ctx->ev_stage_copied);
+  if (ctx->ev_stage_free) cudaEventDestroy(ctx->ev_stage_free);
   delete ctx;
 }
 
@@ -666,8 +679,10 @@ ts_status ts_op_create_csr(ts_ctx* ctx, int n, int p, const int* rowptr, const i
     op->p = p;
     op->K = num_slices(p);
     op_alloc(op->Bh, sizeof(double2) * (size_t)op->K * s * s);
+    TS_CUDA(cudaStreamWaitEvent(st, ctx->ev_stage_free, 0));   // staging buffer free (see op_prepare)
     StagedIn b(ctx, "stage_B", B, (size_t)s * s * p, st);
     rfft_tube<double, double2>(b.dev, op->Bh, (long long)s * s, p, st);
+    TS_CUDA(cudaEventRecord(ctx->ev_stage_free, st));
     op_prepare_csr(op, rowptr, col, val, st);
     *out = op;
     return TS_OK;

@@ -130,6 +130,9 @@ struct ts_ctx {
   ts::Workspace ws;
   double* host_scalars = nullptr;  // pinned, 1024 doubles, for small host<->device transfers
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // Operator creation from host arrays: copies done (the caller's arrays are free again), and the
+  // DFTs that read the staging buffers done (the next creation may overwrite them).
+  cudaEvent_t ev_stage_copied = nullptr, ev_stage_free = nullptr;
   cudaStream_t bstream = nullptr;  // private stream of the batched solver (graph capture)
   std::vector<cudaStream_t> side;  // side streams of the batched solver's parallel branches
   std::map<std::string, int> tune; // launch shapes chosen by the autotuner (tune.cuh), by problem key
