@@ -30,14 +30,8 @@ namespace ts {
 void ensure_f32_operator(ts_op* op, cudaStream_t st);  // lowprec.cu
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
 __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a*b + c
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
-}
-__device__ __forceinline__ double2 cfmac(double2 a, double2 b, double2 c) {  // conj(a)*b + c
-  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
 }
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {  // a*b + c, FP32
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
@@ -54,7 +48,6 @@ __device__ __forceinline__ double slice_weight(int k, int p) {
 }
 
 constexpr int kMaxS = 64;           // block width supported by the row kernels
-constexpr int kLanesT = kMaxS / 32;
 
 // C2: double2 (FP64), or float2 for the FP32 inner cycle of mixed-precision TBAS (MODE 0 only).
 template <typename C2>
