@@ -1,6 +1,4 @@
 """Shared helpers for the GPU parity tests (layout conversion, tolerances, the library context)."""
-import numpy as np
-
 from paper_2405_09233_gb300 import inputs
 
 U64 = 2.0 ** -53  # unit roundoff of FP64

@@ -7,7 +7,6 @@ records the error, frees its tensor memory and returns, and the mixed-precision 
 TS_ERR_TIMEOUT.  No copy or MMA is left in flight, nothing faults, and the same context must then
 solve normally (which also shows the tensor memory was released: every later kernel allocates it).
 """
-import numpy as np
 import pytest
 
 from oracle import krylov as kr, tproduct as tp

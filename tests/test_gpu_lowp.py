@@ -99,7 +99,6 @@ def test_mixed_full_size_n4096_s256_p32(ctx, prec):
 
 def test_lowp_rejects_host_memory(ctx):
     import torch
-    from paper_2405_09233_gb300 import TstarError
     from paper_2405_09233_gb300 import binding
     pr = inputs.dense_problem(8, 4, 2, seed=1)
     op = ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B))
