@@ -937,10 +937,12 @@ def run_batched(a, rank, world, local, dev):
     cpu = cpu_baseline_batched(b.specs) if rank == 0 and world == 1 and not a.no_cpu_baseline else None
     # the autotuner's choice for the batched tensor-core products: column tile, and whether the
     # persistent kernel (one CTA per SM walking the work list) won over one CTA per work item
-    tc_schedule = None
+    tc_schedule, simt_tiles = None, {}
     for key_, v in ctx.tune_entries().items():
         if key_.startswith("btc:"):
             tc_schedule = {"column_tile": v & ~1, "persistent": bool(v & 1)}
+        elif key_.startswith("bsimt:"):     # CUDA-core products' column width, per element size
+            simt_tiles["fp64" if key_.startswith("bsimt:8:") else "fp32"] = v
     if rank == 0:
         line = {"metric": METRIC, "value": b.unknowns * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -950,7 +952,7 @@ def run_batched(a, rank, world, local, dev):
                            "tol": 1e-10, "precision": prec, "fp64_engine": a.engine, "method": "batched tGMRES",
                            "max_relres_true": relres, "max_relres_fp64_dfma": cert, "max_err_vs_xstar": err,
                            "l2": "inputs larger than L2 (5 GB basis)", "sms": sms,
-                           "tensor_core_schedule": tc_schedule},
+                           "tensor_core_schedule": tc_schedule, "cuda_core_tile_columns": simt_tiles or None},
                 "e2e": {"value": b.unknowns * world / statistics.median(t_e2e), "unit": UNIT,
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": len(t_e2e),
                         "statistic": "median"},

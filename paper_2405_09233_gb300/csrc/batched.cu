@@ -345,9 +345,12 @@ __global__ void __launch_bounds__(kTubes) k_b_irfft(BDev d, const Cplx* __restri
 }
 
 // --- per-slice products over the work list ---------------------------------------------------------
-// TINY: every instance has n, s <= kTinyL and the items are 8 x 4 tiles for kTinyThreads (gemm_tiny_tile);
-// otherwise 64 x 64 tiles for kGemmNT threads.
-template <typename Real, int MASK, int TINY>
+// TILE 0: every instance has n, s <= kTinyL and the items are 8 x 4 tiles for kTinyThreads
+// (gemm_tiny_tile); otherwise 64 x TILE tiles (TILE = 64, 32 or 16 columns; 4 x TILE/16 outputs per
+// thread) for kGemmNT threads.  Every TILE > 0 sums each output entry's products in the same order
+// (phase 1's reduction index, then phase 2's), so the column width, which the autotuner picks,
+// changes which CTA forms an entry and how much padding it computes, never the entry's value.
+template <typename Real, int MASK, int TILE>
 __global__ void __launch_bounds__(kGemmNT, 1) k_b_gemm(BDev d, const int4* __restrict__ items,
                                                        const typename CplxOf<Real>::T* __restrict__ Xh,
                                                        typename CplxOf<Real>::T* __restrict__ Yh) {
@@ -373,8 +376,33 @@ __global__ void __launch_bounds__(kGemmNT, 1) k_b_gemm(BDev d, const int4* __res
   a.B2 = Bh; a.sB2 = (long long)in.s * in.s; a.ldb2 = in.s; a.L2 = in.s;
   a.Y = Yh + in.offS; a.sY = T; a.ldy = in.n;
   a.M = in.n; a.N = in.s; a.K = in.K; a.nyq = in.nyq; a.sgn2 = -1.0;
-  if constexpr (TINY) gemm_tiny_tile<Real>(a, it.y, it.z, it.w);
-  else gemm_tile<Real>(a, it.y, it.z, it.w);
+  if constexpr (TILE == 0) gemm_tiny_tile<Real>(a, it.y, it.z, it.w);
+  else gemm_tile<Real, kGemmBM, TILE, 4, TILE / 16>(a, it.y, it.z, it.w);
+}
+
+// Column widths the autotuner chooses from for the CUDA-core work-list products, and one work list.
+constexpr int kBatchSimtBNs[] = {64, 32, 16};
+struct SimtList {
+  int bn;              // 0: the 8 x 4 tiles of an all-tiny batch
+  const int4* items;   // device work list
+  int count;
+};
+
+// One launch of the work-list products (no launch counting: the callers count, once per launch or
+// per graph replay).
+template <typename Real, int MASK>
+void launch_b_gemm(const SimtList& l, const BDev& d, const void* X, void* Y, cudaStream_t st) {
+  using Cplx = typename CplxOf<Real>::T;
+  const Cplx* x = static_cast<const Cplx*>(X);
+  Cplx* y = static_cast<Cplx*>(Y);
+  switch (l.bn) {
+    case 0: k_b_gemm<Real, MASK, 0><<<l.count, kTinyThreads, 0, st>>>(d, l.items, x, y); break;
+    case 64: k_b_gemm<Real, MASK, 64><<<l.count, kGemmNT, 0, st>>>(d, l.items, x, y); break;
+    case 32: k_b_gemm<Real, MASK, 32><<<l.count, kGemmNT, 0, st>>>(d, l.items, x, y); break;
+    case 16: k_b_gemm<Real, MASK, 16><<<l.count, kGemmNT, 0, st>>>(d, l.items, x, y); break;
+    default: TS_REQUIRE(false, "batched products: unknown tile width");
+  }
+  TS_CUDA(cudaGetLastError());
 }
 
 // --- small per-instance kernels ---------------------------------------------------------------------
@@ -496,11 +524,12 @@ void preload_cycle_kernels() {
   cudaFuncAttributes fa;
   const void* fns[] = {
       (const void*)k_b_ks_init, (const void*)k_b_scale_R<T>, (const void*)k_b_rfft<T, Real2, 0, 0>,
-      (const void*)k_b_gemm<T, 0, 0>, (const void*)k_b_gemm<T, 0, 1>, (const void*)k_b_irfft<T, Real2, 0>,
+      (const void*)k_b_gemm<T, 0, 0>, (const void*)k_b_gemm<T, 0, 64>, (const void*)k_b_gemm<T, 0, 32>,
+      (const void*)k_b_gemm<T, 0, 16>, (const void*)k_b_irfft<T, Real2, 0>,
       (const void*)k_b_dot<T>,
       (const void*)k_b_mgs<T>, (const void*)k_b_givens, (const void*)k_b_scale_W<T>, (const void*)k_b_solve_y,
       (const void*)k_b_axpy<T>, (const void*)k_b_rfft<double, double2, 1, 1>, (const void*)k_b_gemm<double, 1, 0>,
-      (const void*)k_b_gemm<double, 1, 1>,
+      (const void*)k_b_gemm<double, 1, 64>, (const void*)k_b_gemm<double, 1, 32>, (const void*)k_b_gemm<double, 1, 16>,
       (const void*)k_b_irfft<double, double2, 1>, (const void*)k_b_finalize_norm, (const void*)k_b_any_active};
   for (const void* f : fns) TS_CUDA(cudaFuncGetAttributes(&fa, f));
 }
@@ -509,8 +538,7 @@ struct BatchPlan {
   std::vector<BInst> inst;
   std::vector<int> nb_inst, tb_inst;
   std::vector<long long> nb_off, tb_off;
-  std::vector<int4> items;
-  bool tiny = false;   // items are 8 x 4 tiles (gemm_tiny_tile) instead of 64 x 64
+  bool tiny = false;   // CUDA-core products on 8 x 4 tiles (gemm_tiny_tile) instead of 64 x BN
   long long totN = 0, totS = 0;
 };
 
@@ -658,45 +686,83 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
     }
     b.tb1 = (int)plan.tb_inst.size();
   }
-  // CUDA-core slice products: warp-sized 8 x 4 tiles when every instance is tiny (a 64 x 64 tile
-  // of a 24 x 24 product issues 10x the FP64 work it needs), else 64 x 64 tiles.
-  plan.tiny = true;
-  for (const BInst& b : plan.inst) plan.tiny = plan.tiny && b.n <= kTinyL && b.s <= kTinyL;
-  const int tbm = plan.tiny ? kTinyBM : kGemmBM, tbn = plan.tiny ? kTinyBN : kGemmBN;
-  for (int i = 0; i < count; ++i) {
-    const BInst& b = plan.inst[i];
-    for (int k = 0; k < b.K; ++k)
-      for (int i0 = 0; i0 < b.n; i0 += tbm)
-        for (int j0 = 0; j0 < b.s; j0 += tbn) plan.items.push_back(make_int4(i, k, i0, j0));
-  }
   plan.totN = (plan.totN + 3) / 4 * 4;   // every basis vector V + j totN starts 16-byte aligned
-  // Largest tiles first (reduction length n + s; real slices are a quarter of the work).
-  std::stable_sort(plan.items.begin(), plan.items.end(), [&](const int4& a, const int4& b) {
-    auto cost = [&](const int4& q) {
-      const BInst& x = plan.inst[q.x];
-      const double w = (q.y == 0 || q.y == x.nyq) ? 1.0 : 4.0;
-      return w * (x.n + x.s);
-    };
-    return cost(a) > cost(b);
-  });
-  TS_REQUIRE(plan.items.size() < (size_t)INT32_MAX && plan.nb_inst.size() < (size_t)INT32_MAX, "batch too large");
+  TS_REQUIRE(plan.nb_inst.size() < (size_t)INT32_MAX, "batch too large");
   const size_t tsz = mixed ? sizeof(float) : sizeof(double);
   auto get = [&](const char* name, size_t bytes) { return ctx->ws.get(name, bytes); };
   char* base = (char*)get("b_tables", sizeof(BInst) * count + 16 * (plan.nb_inst.size() + plan.tb_inst.size()) +
-                                          sizeof(int4) * plan.items.size() + 1024);
+                                          1024);
   BInst* d_inst = (BInst*)base;
   int* d_nb_inst = (int*)(d_inst + count);
   long long* d_nb_off = (long long*)(((uintptr_t)(d_nb_inst + plan.nb_inst.size()) + 15) & ~(uintptr_t)15);
   int* d_tb_inst = (int*)(d_nb_off + plan.nb_off.size());
   long long* d_tb_off = (long long*)(((uintptr_t)(d_tb_inst + plan.tb_inst.size()) + 15) & ~(uintptr_t)15);
-  int4* d_items = (int4*)(((uintptr_t)(d_tb_off + plan.tb_off.size()) + 15) & ~(uintptr_t)15);
   // the tables are copied from pageable memory: synchronous, before anything is captured
   TS_CUDA(cudaMemcpy(d_inst, plan.inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
   TS_CUDA(cudaMemcpy(d_nb_inst, plan.nb_inst.data(), sizeof(int) * plan.nb_inst.size(), cudaMemcpyHostToDevice));
   TS_CUDA(cudaMemcpy(d_nb_off, plan.nb_off.data(), sizeof(long long) * plan.nb_off.size(), cudaMemcpyHostToDevice));
   TS_CUDA(cudaMemcpy(d_tb_inst, plan.tb_inst.data(), sizeof(int) * plan.tb_inst.size(), cudaMemcpyHostToDevice));
   TS_CUDA(cudaMemcpy(d_tb_off, plan.tb_off.data(), sizeof(long long) * plan.tb_off.size(), cudaMemcpyHostToDevice));
-  TS_CUDA(cudaMemcpy(d_items, plan.items.data(), sizeof(int4) * plan.items.size(), cudaMemcpyHostToDevice));
+  // CUDA-core slice products (FP64: the residuals on the DFMA engine and the whole cycle of a TS_FP64
+  // batch on it; FP32: the inner products of TS_MIXED_FP32) run over a work list of (instance, slice,
+  // row, column) tiles: warp-sized 8 x 4 tiles when every instance is tiny (a 64 x 64 tile of a
+  // 24 x 24 product issues 10x the FP64 work it needs), else 64 x BN tiles, BN in kBatchSimtBNs picked
+  // per element size and batch shape by the autotuner.  The FP64 pipe (2 DFMA per clock per SM) is
+  // far slower than shared memory, so a narrow tile that pads s less can win for FP64 while FP32
+  // wants the reuse of wide tiles.  A cached choice needs only its own list.
+  const bool simt64 = !ozaki, simt32 = mixed && !tcin;
+  plan.tiny = true;
+  for (const BInst& b : plan.inst) plan.tiny = plan.tiny && b.n <= kTinyL && b.s <= kTinyL;
+  std::string simt_shape = ":" + std::to_string(count);
+  for (const BInst& b : plan.inst)
+    simt_shape += ":" + std::to_string(b.n) + "x" + std::to_string(b.s) + "x" + std::to_string(b.K);
+  auto simt_key = [&](int esz) { return "bsimt:" + std::to_string(esz) + simt_shape; };
+  if (!ctx->tune_loaded) tune_load(ctx);
+  auto simt_cands = [&](int esz) {
+    if (plan.tiny) return std::vector<int>{0};
+    const auto t = ctx->tune.find(simt_key(esz));
+    for (int bn : kBatchSimtBNs)
+      if (t != ctx->tune.end() && t->second == bn) return std::vector<int>{bn};
+    return std::vector<int>(std::begin(kBatchSimtBNs), std::end(kBatchSimtBNs));
+  };
+  std::vector<SimtList> simt;
+  {
+    std::vector<int> need;
+    for (int esz : {8, 4}) {
+      if (!(esz == 8 ? simt64 : simt32)) continue;
+      for (int bn : simt_cands(esz))
+        if (std::find(need.begin(), need.end(), bn) == need.end()) need.push_back(bn);
+    }
+    for (int bn : need) {
+      const int tbm = bn == 0 ? kTinyBM : kGemmBM, tbn = bn == 0 ? kTinyBN : bn;
+      std::vector<int4> items;
+      for (int i = 0; i < count; ++i) {
+        const BInst& b = plan.inst[i];
+        for (int k = 0; k < b.K; ++k)
+          for (int i0 = 0; i0 < b.n; i0 += tbm)
+            for (int j0 = 0; j0 < b.s; j0 += tbn) items.push_back(make_int4(i, k, i0, j0));
+      }
+      // Largest tiles first (reduction length n + s; real slices are a quarter of the work).
+      std::stable_sort(items.begin(), items.end(), [&](const int4& a, const int4& b) {
+        auto cost = [&](const int4& q) {
+          const BInst& x = plan.inst[q.x];
+          const double w = (q.y == 0 || q.y == x.nyq) ? 1.0 : 4.0;
+          return w * (x.n + x.s);
+        };
+        return cost(a) > cost(b);
+      });
+      TS_REQUIRE(items.size() < (size_t)INT32_MAX, "batch too large");
+      int4* dev = (int4*)get(("b_items_" + std::to_string(bn)).c_str(), sizeof(int4) * items.size());
+      TS_CUDA(cudaMemcpy(dev, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+      simt.push_back(SimtList{bn, dev, (int)items.size()});
+    }
+  }
+  auto simt_list = [&](int bn) -> const SimtList& {
+    size_t q = 0;
+    while (q + 1 < simt.size() && simt[q].bn != bn) ++q;
+    TS_REQUIRE(!simt.empty() && simt[q].bn == bn, "batched products: no work list for the chosen tile");
+    return simt[q];
+  };
 
   void* V = get("b_V", tsz * (size_t)(m + 1) * plan.totN);
   void* W = get("b_W", tsz * (size_t)plan.totN);
@@ -802,7 +868,24 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
   std::vector<int> hflags(2 * count, 1);
   TS_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * 2 * count, cudaMemcpyHostToDevice, st));
   TS_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * 16 * count, st));
-  const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size(), nit = (int)plan.items.size();
+  const int nbs = (int)plan.nb_inst.size(), ntb = (int)plan.tb_inst.size();
+  // Column widths of the CUDA-core products, tuned on one product pass of the whole batch with every
+  // instance active (flags set above) from zeroed inputs; before anything is captured.
+  auto simt_pick = [&](int esz) -> int {
+    if (plan.tiny) return 0;
+    const std::vector<int> cands = simt_cands(esz);
+    if (cands.size() > 1)
+      TS_CUDA(cudaMemsetAsync(esz == 8 ? (void*)Xh64 : Xh, 0, (size_t)2 * esz * plan.totS, st));
+    return tune_pick(
+        ctx, simt_key(esz), cands,
+        [&](int bn) {
+          if (esz == 8) launch_b_gemm<double, 0>(simt_list(bn), d, Xh64, Yh64, st);
+          else launch_b_gemm<float, 0>(simt_list(bn), d, Xh, Yh, st);
+          count_launch();
+        },
+        st);
+  };
+  const int simt_bn64 = simt64 ? simt_pick(8) : 0, simt_bn32 = simt32 ? simt_pick(4) : 0;
   // Tensor-core inner products: every instance's planar X copies, tensor maps and work lists,
   // made before anything is captured.
   struct TcTables {
@@ -952,23 +1035,15 @@ ts_status batched_entry(ts_ctx* ctx, int count, const ts_instance* insts, const 
                         tct.titems, tct.n_titems, tc_err, s2);
       return 2;
     }
-    if (mixed) {
-      if (plan.tiny) k_b_gemm<float, 0, 1><<<nit, kTinyThreads, 0, s2>>>(d, d_items, (float2*)Xh, (float2*)Yh);
-      else k_b_gemm<float, 0, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, (float2*)Xh, (float2*)Yh);
-    } else {
-      if (plan.tiny) k_b_gemm<double, 0, 1><<<nit, kTinyThreads, 0, s2>>>(d, d_items, (double2*)Xh, (double2*)Yh);
-      else k_b_gemm<double, 0, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, (double2*)Xh, (double2*)Yh);
-    }
-    TS_CUDA(cudaGetLastError());
+    if (mixed) launch_b_gemm<float, 0>(simt_list(simt_bn32), d, Xh, Yh, s2);
+    else launch_b_gemm<double, 0>(simt_list(simt_bn64), d, Xh, Yh, s2);
     return 1;
   };
   // FP64 slice products of a true residual: the (instance, slice, tile) work list on CUDA cores, or
   // one emulated-FP64 product per instance (each gated by the instance's cycle flag).
   auto residual_products = [&](cudaStream_t s2) -> int {
     if (!ozaki) {
-      if (plan.tiny) k_b_gemm<double, 1, 1><<<nit, kTinyThreads, 0, s2>>>(d, d_items, Xh64, Yh64);
-      else k_b_gemm<double, 1, 0><<<nit, kGemmNT, 0, s2>>>(d, d_items, Xh64, Yh64);
-      TS_CUDA(cudaGetLastError());
+      launch_b_gemm<double, 1>(simt_list(simt_bn64), d, Xh64, Yh64, s2);
       return 1;
     }
     return oz_all(s2, Xh64, Yh64, d.cyc);

@@ -130,9 +130,10 @@ def test_batched_schedules_agree_bitwise(tmp_path, monkeypatch, prec):
     probs = [inputs.dense_problem(n, s, p, seed=60 + i) for i, (n, s, p) in enumerate(shapes)]
     Cs_h = [kr.sylv_apply(pr.A, pr.B, pr.Xstar) for pr in probs]
     outs = {}
+    simt = f"bsimt:8:{len(shapes)}" + "".join(f":{n}x{s}x{p // 2 + 1}" for n, s, p in shapes)
     for sched in (64, 65, 128, 129):
         cache = tmp_path / f"b_{sched}.txt"
-        cache.write_text(f"{tag} {key} {sched}\n")
+        cache.write_text(f"{tag} {key} {sched}\n{tag} {simt} 64\n")   # and the FP64 residual products' tile
         monkeypatch.setenv("TSTAR_TUNE_CACHE", str(cache))
         with Context(0) as ctx:
             ops = [ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B)) for pr in probs]
@@ -144,10 +145,74 @@ def test_batched_schedules_agree_bitwise(tmp_path, monkeypatch, prec):
             for op in ops:
                 op.close()
             ctx.workspace_check()
-        assert len(_lines(cache)) == 1
+        assert len(_lines(cache)) == 2
     ref_X, ref_it = outs[64]
     for sched in (65, 128, 129):
         X, its = outs[sched]
         assert its == ref_it, sched
         for a, b in zip(ref_X, X):
             assert np.array_equal(a, b), sched
+
+
+def _batched_solve_forced(tmp_path, monkeypatch, tag, shapes, prec, forced, name):
+    """One batched solve (FP64 engine: DFMA) with the cache file holding exactly `forced` (key -> value)."""
+    import torch
+    from paper_2405_09233_gb300 import Context
+    probs = [inputs.dense_problem(n, s, p, seed=80 + i) for i, (n, s, p) in enumerate(shapes)]
+    cache = tmp_path / name
+    cache.write_text("".join(f"{tag} {k} {v}\n" for k, v in forced.items()))
+    monkeypatch.setenv("TSTAR_TUNE_CACHE", str(cache))
+    with Context(0) as ctx:
+        ops = [ctx.op_create_dense(to_dev(pr.A), to_dev(pr.B)) for pr in probs]
+        Cs = [to_dev(kr.sylv_apply(pr.A, pr.B, pr.Xstar)) for pr in probs]
+        Xs = [torch.zeros((p, s, n), dtype=torch.float64, device="cuda") for n, s, p in shapes]
+        st, infos, sts = ctx.batched_solve(ops, Cs, Xs, restart=20, precision=prec)
+        assert st == 0 and all(x == 0 for x in sts)
+        ent = ctx.tune_entries()
+        out = ([from_dev(X) for X in Xs], [i.iters for i in infos], ent)
+        for op in ops:
+            op.close()
+        ctx.workspace_check()
+    return out, _lines(cache)
+
+
+SIMT_SHAPES = [(96, 40, 4), (130, 150, 8), (70, 17, 2), (200, 90, 6)]   # s ragged for 16-, 32- and 64-wide tiles
+
+
+def _simt_key(esz, shapes):
+    return f"bsimt:{esz}:{len(shapes)}" + "".join(f":{n}x{s}x{p // 2 + 1}" for n, s, p in shapes)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp32"])
+def test_batched_cuda_core_tiles_agree_bitwise(tmp_path, monkeypatch, prec):
+    """Force each column width of the CUDA-core work-list products (64, 32, 16 columns; FP64 for the DFMA
+    residuals and a whole FP64 cycle, FP32 for the inner products of mixed FP32) through the cache file:
+    every output entry sums the same products in the same order, so the batched solves agree bit for bit."""
+    tag = _device_tag(tmp_path, monkeypatch)
+    esz = 8 if prec == "fp64" else 4
+    key = _simt_key(esz, SIMT_SHAPES)
+    outs = {}
+    for bn in (64, 32, 16):
+        forced = {key: bn}
+        if esz == 4:
+            forced[_simt_key(8, SIMT_SHAPES)] = 64              # the FP64 residual products: fixed
+        (X, its, ent), lines = _batched_solve_forced(tmp_path, monkeypatch, tag, SIMT_SHAPES, prec, forced,
+                                                     f"simt_{prec}_{bn}.txt")
+        assert ent[key] == bn                                  # the forced width ran; nothing was tuned
+        assert len(lines) == len(forced)
+        outs[bn] = (X, its)
+    ref_X, ref_it = outs[64]
+    for bn in (32, 16):
+        X, its = outs[bn]
+        assert its == ref_it, bn
+        for a, b in zip(ref_X, X):
+            assert np.array_equal(a, b), bn
+
+
+def test_batched_cuda_core_tile_tuned(tmp_path, monkeypatch):
+    """Unforced, the FP64 batched solve tunes the CUDA-core column width once and persists it."""
+    tag = _device_tag(tmp_path, monkeypatch)
+    key = _simt_key(8, SIMT_SHAPES)
+    (X, its, ent), lines = _batched_solve_forced(tmp_path, monkeypatch, tag, SIMT_SHAPES, "fp64", {}, "simt_tuned.txt")
+    assert ent[key] in (64, 32, 16)
+    assert [ln.split()[1:] for ln in lines] == [[key, str(ent[key])]]
