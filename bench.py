@@ -155,7 +155,8 @@ def ozaki_roofline(flops_per_launch, pair_flops_per_launch, avg_ms, sustained, s
                        flops_per_launch / (avg_ms * 1e-3) / 1e12, share)}
 
 
-def fp64_gemm_roofline(executed_per_launch, conventional_per_launch, avg_ms, share, sms, mhz, dgemm_tflops=None):
+def fp64_gemm_roofline(executed_per_launch, conventional_per_launch, avg_ms, share, sms, mhz, dgemm_tflops=None,
+                       probe_tflops=None):
     """The FP64 CUDA-core slice GEMM.  It implements the three-multiplication (Gauss) complex product,
     whose FLOP count is 6 per complex multiply-add (3 DFMA) and 2 per real one: achieved = that count
     / launch time, against the FP64 peak derived from the device's SM count and maximum clock."""
@@ -167,8 +168,23 @@ def fp64_gemm_roofline(executed_per_launch, conventional_per_launch, avg_ms, sha
             f"{sms} SMs x {mhz:.0f} MHz. Kernel share of the step: {share:.3f}")
     if dgemm_tflops:
         note += f". cuBLAS DGEMM (8192^3, torch) in this run: {dgemm_tflops:.3f} TFLOP/s"
+    note += probe_note(probe_tflops)
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_gemm_slices<double> (FP64 DFMA, 3-multiply complex)", "note": note}
+            "traffic": None, "kernel": "k_gemm_slices<double> (FP64 DFMA, 3-multiply complex)", "note": note,
+            "peak_probe": probe_tflops}
+
+
+def probe_note(probe_tflops):
+    return (f". Measured FP64 FMA loop (ts_probe_fp64_peak, 8 independent chains per thread) in this run: "
+            f"{probe_tflops:.3f} TFLOP/s" if probe_tflops else "")
+
+
+def measure_fp64_probe(ctx):
+    """The FP64 roof measured on the device by the library's FMA loop (a cross-check of the derived one)."""
+    try:
+        return ctx.probe_fp64_peak()
+    except Exception:   # report the run without it rather than fail the bench
+        return None
 
 
 def lowp_gemm_roofline(precision, flops_per_launch, avg_ms, sustained, share, sms, mhz):
@@ -193,7 +209,8 @@ def lowp_gemm_roofline(precision, flops_per_launch, avg_ms, sustained, share, sm
                      + f"; 8 FLOP per complex multiply-add. Kernel share of the step: {share:.3f}")}
 
 
-def stats_rooflines(st, n, s, p, total_ms, sustained, precision, sms, mhz, workload, dgemm=None, exec_ratio=None):
+def stats_rooflines(st, n, s, p, total_ms, sustained, precision, sms, mhz, workload, dgemm=None, exec_ratio=None,
+                    probe=None):
     """Roofline objects of every slice-product class the library timed; the first is the dominant one.
     exec_ratio (batched workloads): executed / conventional FLOPs of the FP64 products over the batch."""
     out = []
@@ -204,7 +221,8 @@ def stats_rooflines(st, n, s, p, total_ms, sustained, precision, sms, mhz, workl
             executed = conv * exec_ratio
         else:
             conv, executed = slice_flops(n, s, p, 8), slice_flops(n, s, p, 6)
-        r = fp64_gemm_roofline(executed, conv, st.gemm_ms / st.gemm_launches, st.gemm_ms / total_ms, sms, mhz, dgemm)
+        r = fp64_gemm_roofline(executed, conv, st.gemm_ms / st.gemm_launches, st.gemm_ms / total_ms, sms, mhz, dgemm,
+                               probe)
         if not batched:
             r["traffic"] = traffic_for("k_gemm_slices<double>", workload)
         out.append((st.gemm_ms, r))
@@ -751,7 +769,9 @@ def main():
     sms = device_sms(dev)
     mhz = clk.get("sm_max_mhz") or peaks()["sm_max_mhz"]
     dgemm = measure_dgemm_tflops(dev) if rank == 0 and st.gemm_launches else None
-    rooflines = stats_rooflines(st, n, s, p, kernel_ms, True, a.precision, sms, mhz, a.workload, dgemm)
+    probe = measure_fp64_probe(ctx) if rank == 0 and st.gemm_launches else None
+    rooflines = stats_rooflines(st, n, s, p, kernel_ms, True, a.precision, sms, mhz, a.workload, dgemm,
+                                probe=probe)
     if small:
         for r in rooflines:
             r["note"] += ("; latency-bound workload: a roofline fraction says little here (the kernel split is "
@@ -1030,6 +1050,7 @@ def run_tbas(a, rank, world, local, dev):
     sms = device_sms(dev)
     mhz = clk.get("sm_max_mhz") or peaks()["sm_max_mhz"]
     peak64 = fp64_peak_tflops(sms, mhz)
+    probe = measure_fp64_probe(ctx) if rank == 0 else None
     rooflines = []
     if stt.tba_launches:
         blk_ms = stt.tba_ms / stt.tba_launches
@@ -1040,7 +1061,8 @@ def run_tbas(a, rank, world, local, dev):
             "kernel": "k_gram / k_rows_mm (TBAS tubal Gram and block update, FP64 complex, n x s blocks)",
             "note": ("FLOPs of the 3-multiply complex form the kernels implement (6 n s^2 per slice product); peak "
                      "derived: 2 DFMA/clk/SM x %d SMs x %.0f MHz. Share of the step: %.3f (timed with events around "
-                     "each product)" % (sms, mhz, stt.tba_ms / (ms * a.steps)))}))
+                     "each product)" % (sms, mhz, stt.tba_ms / (ms * a.steps))) + probe_note(probe),
+            "peak_probe": probe}))
     if stt.spmm_launches:
         sp_ms = stt.spmm_ms / stt.spmm_launches
         sp_tf = stt.spmm_flops / stt.spmm_launches / (sp_ms * 1e-3) / 1e12
@@ -1053,7 +1075,8 @@ def run_tbas(a, rank, world, local, dev):
             "note": ("FLOPs executed: 8 per stored complex value and block column; peak derived: 2 DFMA/clk/SM x %d "
                      "SMs x %.0f MHz. Algorithmic bytes (values, pattern, V once, W once) / time = %.0f GB/s = %.3f of "
                      "measured HBM. Share of the step: %.3f" % (sms, mhz, sp_gbs, sp_gbs / peaks()["hbm_gbs"],
-                                                                stt.spmm_ms / (ms * a.steps)))}))
+                                                                stt.spmm_ms / (ms * a.steps))) + probe_note(probe),
+            "peak_probe": probe}))
     rooflines.sort(key=lambda t: -t[0])
     rooflines = [r for _, r in rooflines]
     # end to end: B, C and X in host memory (the CSR arrays are host arrays by contract)

@@ -270,8 +270,9 @@ ts_status ts_t_bartels_stewart(ts_ctx* ctx, const double* A, int n, const double
 ts_status ts_workspace_check(ts_ctx* ctx);
 
 /* Launch shapes chosen by the autotuner (no counterpart in the paper: the column-tile width of the
- * tcgen05 slice products, timed over its candidates on the first call of each shape and precision,
- * then cached in the context; with the environment variable TSTAR_TUNE_CACHE naming a file, also
+ * tcgen05 slice products, and in batched solves the tensor-core product schedule and the column
+ * width of the CUDA-core work-list tiles, timed over their candidates on the first call of each shape
+ * and precision, then cached in the context; with the environment variable TSTAR_TUNE_CACHE naming a file, also
  * read from and appended to that file, per device).  Writes the context's entries as
  * "<key> <value>\n" lines, NUL-terminated, into `buf` (host memory of `cap` bytes; nothing is
  * written if buf is NULL or cap is 0) and stores the bytes needed, terminator included, in
@@ -320,6 +321,14 @@ ts_status ts_stats_enable(ts_ctx* ctx, int enable);
 ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out);
 /* Zero the statistics and the process-wide launch counter. */
 ts_status ts_stats_reset(ts_ctx* ctx);
+
+/* The FP64 roof of ctx's device, measured (no counterpart in the paper: the denominator of the
+ * rooflines reported for FP64 kernels on CUDA cores).  Launches on `stream` a kernel in which every
+ * thread runs 8 independent fused multiply-add chains on registers (4 CTAs of 256 threads per SM;
+ * one short untimed launch, then one timed with CUDA events, ~30 ms on a GB300) and stores
+ * 2 x (multiply-adds) / seconds / 1e12 in *tflops (host memory).  Uses ~1.2 MB of the context's
+ * workspace.  TS_ERR_ARG if ctx or tflops is NULL.  Synchronous. */
+ts_status ts_probe_fp64_peak(ts_ctx* ctx, double* tflops, ts_stream stream);
 
 #ifdef __cplusplus
 }

@@ -94,6 +94,7 @@ _SIGNATURES = {
     "ts_stats_enable": (_i, [_vp, _i]),
     "ts_stats_get": (_i, [_vp, ctypes.POINTER(Stats)]),
     "ts_stats_reset": (_i, [_vp]),
+    "ts_probe_fp64_peak": (_i, [_vp, ctypes.POINTER(_d), _vp]),
 }
 
 
@@ -162,6 +163,15 @@ class Context:
     def workspace_check(self):
         """Raise TstarError if any workspace buffer was written past its end."""
         self._check(lib().ts_workspace_check(self._h), "ts_workspace_check")
+
+    def probe_fp64_peak(self) -> float:
+        """Measured FP64 fused multiply-add rate of the device in TFLOP/s (ts_probe_fp64_peak), on the
+        current stream."""
+        import torch
+        out = ctypes.c_double(0.0)
+        st = ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        self._check(lib().ts_probe_fp64_peak(self._h, ctypes.byref(out), st), "ts_probe_fp64_peak")
+        return out.value
 
     def tune_entries(self) -> dict:
         """The autotuner's choices in this context, {key: value} (ts_tune_entries)."""

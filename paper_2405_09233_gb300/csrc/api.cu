@@ -819,6 +819,15 @@ ts_status ts_stats_get(ts_ctx* ctx, ts_stats* out) {
   TS_API_END(ctx)
 }
 
+ts_status ts_probe_fp64_peak(ts_ctx* ctx, double* tflops, ts_stream stream) {
+  if (!ctx || !tflops) return TS_ERR_ARG;
+  TS_API_BEGIN
+  TS_CUDA(cudaSetDevice(ctx->device));
+  *tflops = fp64_fma_peak_tflops(ctx, reinterpret_cast<cudaStream_t>(stream));
+  return TS_OK;
+  TS_API_END(ctx)
+}
+
 ts_status ts_stats_reset(ts_ctx* ctx) {
   if (!ctx) return TS_ERR_ARG;
   TS_API_BEGIN

@@ -207,6 +207,8 @@ struct GemmArgs {
 using ZGemmArgs = GemmArgs<double2>;
 using CGemmArgs = GemmArgs<float2>;
 void zgemm_slices_f64(const ZGemmArgs& a, cudaStream_t st);
+// Measured FP64 fused multiply-add rate of ctx's device in TFLOP/s (peak.cu); synchronises st.
+double fp64_fma_peak_tflops(ts_ctx* ctx, cudaStream_t st);
 void cgemm_slices_f32(const CGemmArgs& a, cudaStream_t st);
 
 // ---------------- vector kernels (vec.cu) ----------------
