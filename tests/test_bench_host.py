@@ -96,3 +96,27 @@ def test_reference_arm_times_the_oracle_and_honours_steps():
     assert line["cpu_baseline"]["kind"] == "oracle" and "complete oracle tGMRES(20)" in line["cpu_baseline"]["sample"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["oracle_complete_solve_s"] > 0
+
+
+def test_fp64_roofline_carries_the_measured_probe():
+    """The derived FP64 roof stays the denominator; the measured FMA loop is reported beside it."""
+    r = bench.fp64_gemm_roofline(98.8e9, 128.8e9, 84.1, 0.97, 152, 2070.0, 1.10, 1.2554)
+    assert r["peak"] == pytest.approx(4.0 * 152 * 2070e6 / 1e12)
+    assert r["frac"] == pytest.approx(98.8e9 / 84.1e-3 / 1e12 / r["peak"])
+    assert r["peak_probe"] == 1.2554 and "1.255 TFLOP/s" in r["note"]
+    r0 = bench.fp64_gemm_roofline(98.8e9, 128.8e9, 84.1, 0.97, 152, 2070.0)
+    assert r0["peak_probe"] is None and "FMA loop" not in r0["note"]
+
+
+def test_fp64_probe_failure_does_not_fail_the_bench():
+    class NoGpu:
+        def probe_fp64_peak(self):
+            raise RuntimeError("no device")
+
+    class Fixed:
+        def probe_fp64_peak(self):
+            return 1.25
+
+    assert bench.measure_fp64_probe(NoGpu()) is None
+    assert bench.measure_fp64_probe(Fixed()) == 1.25
+    assert bench.probe_note(None) == ""
