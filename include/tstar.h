@@ -217,6 +217,8 @@ typedef struct {
  * the cycle's inner tolerance is opts->inner_tol (0: 1e-6 for FP32 and split TF32, 1e-3 TF32,
  * 1e-2 BF16).  opts->fp64_engine picks the engine of every FP64 product (the residuals, and the
  * whole cycle of a TS_FP64 batch): TS_ENGINE_DFMA or TS_ENGINE_OZAKI (opts->ozaki_digits).
+ * The first call for a batch shape times the candidate launch shapes of its slice products (the
+ * autotuner; see ts_tune_entries) before the cycle is captured; later calls reuse the choice.
  * opts->restart <= 128; dense operators with p <= 64.  infos / statuses (count entries each, may
  * be NULL) receive each instance's result; the call returns TS_OK when every instance reached its
  * tolerance, TS_NOT_CONVERGED (or TS_ERR_NONFINITE) otherwise.  Synchronous. */
